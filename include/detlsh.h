@@ -1,0 +1,180 @@
+/*
+ * detlsh.h -- C-ABI of the GB300 (sm_103a) DET-LSH hot path.
+ *
+ * DET-LSH (arXiv 2603.24920) answers c^2-k-ANN queries in Euclidean space:
+ *   build : K*L Gaussian projections (Eq. 1), dynamic equal-frequency encoding
+ *           of each projected coordinate into N_r regions (Sec. III-A, Alg. 1),
+ *           and one DE-Tree per projected space (Sec. III-B, Alg. 2);
+ *   query : range queries over the L DE-Trees with node lower bounds
+ *           (Alg. 3, Sec. IV-C) and the optimised leaf handling of Sec. VI-B2,
+ *           inside the c^2-k-ANN loop of Alg. 5 started at the "magic" r_min
+ *           of Sec. V-B1, then exact-distance verification and top-k.
+ * Every step runs in CUDA kernels on one GPU; there is no CPU fallback.
+ *
+ * Conventions
+ *   - Pointers named "data", "queries", "ids", "dists" may be host or device
+ *     memory (the library asks the CUDA driver which); the library copies as
+ *     needed.  Accessors named detlsh_get_* write host memory.
+ *   - The caller owns every input and output buffer; the library owns the
+ *     index (device memory) until detlsh_free.
+ *   - Every function returns a detlsh_status.  On error no output is written
+ *     and an existing index stays valid.
+ *   - An index is immutable after build; detlsh_query may be called from
+ *     several host threads on distinct streams.
+ *   - "stream" arguments are cudaStream_t values (NULL = legacy default).
+ */
+#ifndef DETLSH_H
+#define DETLSH_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    DETLSH_OK = 0,
+    DETLSH_ERR_INVALID_ARG = -1,     /* a size or parameter is out of range     */
+    DETLSH_ERR_NONFINITE_INPUT = -2, /* NaN/Inf in data or queries, or a
+                                        projection overflows FP32              */
+    DETLSH_ERR_OOM = -3,             /* device or host allocation failed       */
+    DETLSH_ERR_CUDA = -4,            /* a CUDA runtime call failed             */
+    DETLSH_ERR_CAPACITY = -5,        /* an internal work list overflowed       */
+    DETLSH_ERR_NO_DEVICE = -6        /* no usable CUDA device                  */
+} detlsh_status;
+
+/* Node boxes used by the range query's lower bound (Sec. IV-C). */
+enum { DETLSH_BOX_PREFIX = 0, /* regions of the node's iSAX prefix (paper)   */
+       DETLSH_BOX_TIGHT = 1 /* min/max code of the node's points           */ };
+
+/* Precision of the exact-distance verification step (Alg. 5, top-k). */
+enum { DETLSH_PREC_FP32 = 0,        /* FP32 distances over every candidate  */
+       DETLSH_PREC_BF16_REFINE = 1  /* BF16 scores, FP32 re-rank of the top
+                                       rerank_mult * k                       */ };
+
+typedef struct detlsh_index detlsh_index;
+
+typedef struct {
+    int32_t L;              /* projected spaces = DE-Trees, 1..16 (default 4)      */
+    int32_t K;              /* dimensions per projected space, 1..16 (default 16)  */
+    int32_t N_r;            /* regions per dimension, power of two in [2,256]
+                               (default 256, Sec. III-A)                           */
+    int32_t max_size;       /* leaf capacity of Alg. 2, >= 1 (default 64)          */
+    uint64_t seed;          /* projection and sample seed                          */
+    double sample_frac;     /* breakpoint sample n_s / n, in (0,1] (default 0.1)  */
+    int32_t box_mode;       /* DETLSH_BOX_PREFIX (default) or DETLSH_BOX_TIGHT     */
+    int32_t keep_bf16;      /* 1: also keep a BF16 copy of the data (default 1)    */
+    int32_t keep_projections; /* 1: keep the n x L*K projections (default 0)      */
+} detlsh_build_params;
+
+typedef struct {
+    double beta;            /* false-positive budget: stop at beta*n + k
+                               candidates (Alg. 5; default 0.1, Sec. VI-A)         */
+    double c;               /* approximation ratio, 1.1 <= c <= 16 (default 1.5)   */
+    int32_t precision;      /* DETLSH_PREC_FP32 (default) / DETLSH_PREC_BF16_REFINE */
+    int32_t rerank_mult;    /* BF16 path: FP32 re-rank of the top rerank_mult*k
+                               (default 4)                                         */
+} detlsh_query_params;
+
+/* Fill *p with the defaults listed above (Sec. V-B1, Sec. VI-A). */
+int detlsh_default_build_params(detlsh_build_params *p);
+int detlsh_default_query_params(detlsh_query_params *p);
+
+/*
+ * Build the index over n points of dimension d (row-major FP32, n*d values).
+ * Encoding phase (Sec. III-A, Alg. 1) and indexing phase (Sec. III-B, Alg. 2):
+ *   A      : K*L projection vectors, entries N(0,1) (Eq. 1), drawn from seed;
+ *   P      : every h_t(o) = a_t . o, the exact dot product rounded once to FP32;
+ *   B      : per projected dimension, interior breakpoints = equal-frequency
+ *            order statistics of a ~sample_frac sample, ends = min/max of all
+ *            n points;
+ *   codes  : region index of every projected coordinate (8-bit symbol);
+ *   trees  : per projected space, 2^K first-layer nodes split on the most even
+ *            dimension while a node holds more than max_size points.
+ * Requirements: 1 <= n < 2^31, 1 <= d <= 65536, L*K <= 256.  The data is
+ * copied; the caller's buffer may be freed afterwards.
+ * Errors: INVALID_ARG, NONFINITE_INPUT, OOM, CUDA, NO_DEVICE.
+ */
+int detlsh_build(const float *data, int64_t n, int32_t d, int32_t L, int32_t K,
+                 int32_t N_r, uint64_t seed, detlsh_index **out);
+int detlsh_build_ex(const float *data, int64_t n, int32_t d, const detlsh_build_params *p,
+                    void *stream, detlsh_index **out);
+
+/*
+ * c^2-k-ANN queries (Alg. 5).  queries: m x d row-major FP32.  For each query:
+ * r_min is the smallest radius of the grid r_j = c^j (j = -127..127) whose
+ * union over the L range queries holds at least beta*n + k points (magic
+ * r_min, Sec. V-B1); Alg. 5 then runs at r_min: trees in order, the leaves of
+ * each range query (lower bound <= eps*r, whole leaves, Sec. VI-B2) entering
+ * S in ascending lower-bound order (ties: leaf order) until |S| >= beta*n + k;
+ * eps^2 = chi^2_{alpha1}(K) with alpha1 = exp(-1/L) (Eq. 2, Lemma 3).
+ * Output: ids (int64, m x k) and Euclidean dists (FP32, m x k), ascending,
+ * ties by smaller id.  detlsh_query uses beta = 0.1 and FP32 verification.
+ * Requirements: m >= 0, 1 <= k <= min(n, 1024).
+ * Errors: INVALID_ARG, NONFINITE_INPUT, OOM, CUDA, CAPACITY.
+ */
+int detlsh_query(const detlsh_index *ix, const float *queries, int64_t m, int32_t k, double c,
+                 int64_t *ids, float *dists);
+/* As detlsh_query, with per-query k (nullable: k_max for all) and parameters;
+ * rows are k_max wide, padded with id -1 and dist +inf past the query's k. */
+int detlsh_query_ex(const detlsh_index *ix, const float *queries, int64_t m,
+                    const int32_t *k_per_query, int32_t k_max, const detlsh_query_params *qp,
+                    void *stream, int64_t *ids, float *dists);
+
+/* Release the index and its device memory.  NULL is accepted. */
+int detlsh_free(detlsh_index *ix);
+
+/* Human-readable text of a status code (static storage). */
+const char *detlsh_status_string(int status);
+
+/* ---------------------------------------------------------------------------
+ * Introspection and parity accessors (host outputs).
+ * ------------------------------------------------------------------------- */
+typedef struct {
+    int64_t n;
+    int32_t d, L, K, N_r, max_size, box_mode, has_bf16;
+    int64_t sample_size;        /* points used for the breakpoints           */
+    int64_t num_leaves[16];     /* leaves of each DE-Tree                     */
+    int64_t max_leaf_size;
+    double eps2;                /* eps^2 of Eq. 2                             */
+    int64_t device_bytes;       /* device memory held by the index           */
+    int64_t projection_fallbacks; /* projections computed by the exact
+                                     big-integer path during the build       */
+} detlsh_info;
+
+int detlsh_get_info(const detlsh_index *ix, detlsh_info *info);
+/* Projection vectors A, (L*K) x d, row t = tree*K + dim (Eq. 1). */
+int detlsh_get_projection_matrix(const detlsh_index *ix, float *A);
+/* Sampled point ids, ascending (sample_size values). */
+int detlsh_get_sample(const detlsh_index *ix, int64_t *ids);
+/* Breakpoints, (L*K) x (N_r+1) (Sec. III-A). */
+int detlsh_get_breakpoints(const detlsh_index *ix, float *B);
+/* Codes, n x (L*K) bytes, point-major (Alg. 1). */
+int detlsh_get_codes(const detlsh_index *ix, uint8_t *codes);
+/* Projections, n x (L*K); only if built with keep_projections. */
+int detlsh_get_projections(const detlsh_index *ix, float *P);
+/* DE-Tree t (Alg. 2): leaves in canonical order (first-layer key ascending,
+ * child 0 before child 1), perm = point ids leaf by leaf (ascending within a
+ * leaf), leaf_begin (num_leaves+1), box lo/hi and prefix lengths
+ * (num_leaves x K bytes each), leaf_of (n). */
+int detlsh_get_tree(const detlsh_index *ix, int32_t t, int64_t *perm, int64_t *leaf_begin,
+                    uint8_t *box_lo, uint8_t *box_hi, uint8_t *nbits, int64_t *leaf_of);
+/* Squared-radius grid T(j) = fp32(eps^2 c^(2j)), j = -127..127, T(127) = inf. */
+int detlsh_get_level_table(const detlsh_index *ix, double c, float *T);
+/* Exact FP32 projections of m rows with the index's A (m x L*K, host or
+ * device in/out), the same kernels the build uses. */
+int detlsh_project(const detlsh_index *ix, const float *rows, int64_t m, float *out,
+                   void *stream);
+/* Candidate sets of Alg. 5 for m queries: S (host, m x cap, arrival order
+ * unspecified), S_size, j* (radius grid index of r_min) and i* (tree at which
+ * |S| reached beta*n + k; -1 when beta*n + k > n and S is every point).
+ * Fails with CAPACITY if a set exceeds cap. */
+int detlsh_query_candidates(const detlsh_index *ix, const float *queries, int64_t m, int32_t k,
+                            const detlsh_query_params *qp, int64_t cap, int64_t *S,
+                            int64_t *S_size, int32_t *jstar, int32_t *istar);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DETLSH_H */

@@ -1,0 +1,756 @@
+// api.cu -- C-ABI of the DET-LSH hot path (include/detlsh.h): argument
+// checks, device memory of the index, and the order of the kernels.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "kernels.h"
+
+// ---------------------------------------------------------------------------
+static thread_local char g_last_cuda[256];
+
+void dl_set_last_cuda_error(cudaError_t e, const char *what, const char *file, int line) {
+  snprintf(g_last_cuda, sizeof g_last_cuda, "%s: %s (%s:%d)", cudaGetErrorString(e), what, file,
+           line);
+}
+
+struct detlsh_index {
+  int device = 0;
+  int64_t n = 0;
+  int d = 0, L = 0, K = 0, LK = 0, N_r = 0, bbits = 0, M = 0, box_mode = 0;
+  uint64_t seed = 0;
+  double frac = 0.1, eps2 = 0.0;
+  int64_t m_sample = 0;
+  int64_t nleaves[16] = {0}, leaf_off[17] = {0};
+  int64_t max_leaf = 0, max_leaves = 0;
+  int64_t device_bytes = 0;
+  int64_t fb_total = 0;
+  // device arrays
+  float *X = nullptr;
+  __nv_bfloat16 *Xh = nullptr;
+  float *A = nullptr, *B = nullptr, *P = nullptr;
+  uint8_t *codes = nullptr;
+  uint32_t *sample = nullptr;
+  uint32_t *perm = nullptr, *leaf_begin = nullptr, *leaf_of = nullptr;
+  uint8_t *leaf_lo = nullptr, *leaf_hi = nullptr, *leaf_nb = nullptr;
+  std::vector<void *> owned;
+  // per-index query buffers, reused across calls (guarded by qmu)
+  std::mutex qmu;
+  struct QBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+  };
+  QBuf qQ, qQh, qQp, qk, qids, qdists, qT, qscratch, qstat, qS, qfb;
+};
+
+namespace {
+
+using namespace dl;
+
+template <class T>
+int dalloc(detlsh_index *ix, T **p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  void *q = nullptr;
+  DL_CUDA(cudaMalloc(&q, sizeof(T) * count));
+  *p = static_cast<T *>(q);
+  if (ix) {
+    ix->owned.push_back(q);
+    ix->device_bytes += (int64_t)(sizeof(T) * count);
+  }
+  return DETLSH_OK;
+}
+
+struct TempPool {
+  std::vector<void *> ptrs;
+  template <class T>
+  int get(T **p, size_t count) {
+    *p = nullptr;
+    if (count == 0) count = 1;
+    void *q = nullptr;
+    DL_CUDA(cudaMalloc(&q, sizeof(T) * count));
+    ptrs.push_back(q);
+    *p = static_cast<T *>(q);
+    return DETLSH_OK;
+  }
+  ~TempPool() {
+    for (void *q : ptrs) cudaFree(q);
+  }
+};
+
+int grow(detlsh_index::QBuf &b, size_t bytes) {
+  if (b.bytes >= bytes && b.p) return DETLSH_OK;
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.bytes = 0;
+  DL_CUDA(cudaMalloc(&b.p, bytes ? bytes : 1));
+  b.bytes = bytes;
+  return DETLSH_OK;
+}
+
+bool is_device_ptr(const void *p) {
+  if (!p) return false;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+int copy_in(void *dst, const void *src, size_t bytes, cudaStream_t st) {
+  if (bytes == 0) return DETLSH_OK;
+  DL_CUDA(cudaMemcpyAsync(dst, src, bytes,
+                          is_device_ptr(src) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+  return DETLSH_OK;
+}
+
+int copy_out(void *dst, const void *src, size_t bytes, cudaStream_t st) {
+  if (bytes == 0) return DETLSH_OK;
+  DL_CUDA(cudaMemcpyAsync(dst, src, bytes,
+                          is_device_ptr(dst) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+  return DETLSH_OK;
+}
+
+// Eq. 1: entries of the K*L projection vectors are N(0,1).  Pair (2u, 2u+1)
+// of row t comes from Philox4x32-10 block (u, t, stream 2, 0) keyed by the
+// seed, through Box-Muller in FP64, rounded to FP32.
+void projection_matrix(int LK, int d, uint64_t seed, float *A) {
+  const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+  for (int t = 0; t < LK; ++t) {
+    for (int u = 0; 2 * u < d; ++u) {
+      const U4 r = philox4x32_10(U4{(uint32_t)u, (uint32_t)t, STREAM_PROJ, 0u}, k0, k1);
+      const double u1 = ((double)r.x + 1.0) * 0x1p-32;
+      const double u2 = (double)r.y * 0x1p-32;
+      const double rad = std::sqrt(-2.0 * std::log(u1));
+      const double th = 6.283185307179586 * u2;
+      const float z0 = (float)(rad * std::cos(th)) + 0.0f;
+      const float z1 = (float)(rad * std::sin(th)) + 0.0f;
+      A[(int64_t)t * d + 2 * u] = z0;
+      if (2 * u + 1 < d) A[(int64_t)t * d + 2 * u + 1] = z1;
+    }
+  }
+}
+
+// Pr[chi^2(K) > x] (Lemma 2), closed forms for even and odd K.
+double chi2_tail(double x, int K) {
+  if (x <= 0.0) return 1.0;
+  const double h = 0.5 * x;
+  if ((K & 1) == 0) {
+    double term = 1.0, sum = 1.0;
+    for (int i = 1; i < K / 2; ++i) {
+      term *= h / i;
+      sum += term;
+    }
+    return std::exp(-h) * sum;
+  }
+  double term = 1.0, sum = 0.0;
+  for (int i = 1; i <= (K - 1) / 2; ++i) {
+    if (i > 1) term *= x / (2 * i - 1);
+    sum += term;
+  }
+  return std::erfc(std::sqrt(h)) + std::exp(-h) * std::sqrt(2.0 * x / 3.141592653589793) * sum;
+}
+
+// Eq. 2 with L = -1/ln(alpha1): eps^2 is the upper alpha1 quantile of chi^2(K).
+double eps2_of(int K, int L) {
+  const double a1 = std::exp(-1.0 / L);
+  double lo = 0.0, hi = 1.0;
+  while (chi2_tail(hi, K) > a1) hi *= 2.0;
+  for (int it = 0; it < 200; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (mid <= lo || mid >= hi) break;
+    if (chi2_tail(mid, K) > a1) lo = mid; else hi = mid;
+  }
+  return 0.5 * (lo + hi);
+}
+
+// Squared-radius grid of the magic r_min (Sec. V-B1): r_j = c^j.
+void level_table(double eps2, double c, float *T) {
+  for (int i = 0; i < NLEV; ++i) T[i] = (float)(eps2 * std::pow(c, 2.0 * (double)(i + JMIN)));
+  T[NLEV - 1] = INFINITY;
+}
+
+__global__ void k_fill_minmax(uint32_t *mm, int LK) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < LK) { mm[2 * t] = 0xffffffffu; mm[2 * t + 1] = 0u; }
+}
+
+__global__ void k_iota(uint32_t *p, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = (uint32_t)i;
+}
+
+__global__ void k_f32_to_bf16(const float *s, __nv_bfloat16 *d, int64_t count) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+       i += (int64_t)gridDim.x * blockDim.x)
+    d[i] = __float2bfloat16_rn(s[i]);
+}
+
+int check_err(int *err_dev, cudaStream_t st) {
+  int h = 0;
+  DL_CUDA(cudaMemcpyAsync(&h, err_dev, sizeof(int), cudaMemcpyDeviceToHost, st));
+  DL_CUDA(cudaStreamSynchronize(st));
+  return h;
+}
+
+int validate_build(int64_t n, int32_t d, const detlsh_build_params *p) {
+  if (!p) return DETLSH_ERR_INVALID_ARG;
+  if (n < 1 || n >= (int64_t)0x7fffffff) return DETLSH_ERR_INVALID_ARG;
+  if (d < 1 || d > 65536) return DETLSH_ERR_INVALID_ARG;
+  if (p->L < 1 || p->L > 16 || p->K < 1 || p->K > 16 || p->L * p->K > 256)
+    return DETLSH_ERR_INVALID_ARG;
+  if (p->N_r < 2 || p->N_r > 256 || (p->N_r & (p->N_r - 1))) return DETLSH_ERR_INVALID_ARG;
+  if (p->max_size < 1) return DETLSH_ERR_INVALID_ARG;
+  if (!(p->sample_frac > 0.0 && p->sample_frac <= 1.0)) return DETLSH_ERR_INVALID_ARG;
+  if (p->box_mode != DETLSH_BOX_PREFIX && p->box_mode != DETLSH_BOX_TIGHT)
+    return DETLSH_ERR_INVALID_ARG;
+  return DETLSH_OK;
+}
+
+int build_impl(detlsh_index *ix, const float *data, cudaStream_t st, const detlsh_build_params *p) {
+  const int64_t n = ix->n;
+  const int d = ix->d, L = ix->L, K = ix->K, LK = ix->LK, N_r = ix->N_r;
+  TempPool tp;
+  // data copy (the index keeps its own FP32 rows for verification)
+  DL_TRY(dalloc(ix, &ix->X, (size_t)n * d));
+  DL_TRY(copy_in(ix->X, data, sizeof(float) * (size_t)n * d, st));
+  // projection vectors (Eq. 1)
+  std::vector<float> Ah((size_t)LK * d);
+  projection_matrix(LK, d, ix->seed, Ah.data());
+  DL_TRY(dalloc(ix, &ix->A, (size_t)LK * d));
+  DL_CUDA(cudaMemcpyAsync(ix->A, Ah.data(), sizeof(float) * Ah.size(), cudaMemcpyHostToDevice, st));
+  // status words and the exact-path list
+  int *err = nullptr;
+  uint32_t *fb_count = nullptr;
+  unsigned long long *fb_total = nullptr;
+  uint2 *fb_list = nullptr;
+  const uint32_t fb_cap = (uint32_t)std::min<int64_t>(std::max<int64_t>(n * LK / 256, 65536), 1 << 24);
+  DL_TRY(tp.get(&err, 1));
+  DL_TRY(tp.get(&fb_count, 1));
+  DL_TRY(tp.get(&fb_total, 1));
+  DL_TRY(tp.get(&fb_list, fb_cap));
+  DL_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
+  DL_CUDA(cudaMemsetAsync(fb_total, 0, sizeof(unsigned long long), st));
+  ProjArgs pa;
+  pa.fb_list = fb_list; pa.fb_count = fb_count; pa.fb_cap = fb_cap;
+  pa.fb_total = fb_total; pa.err = err;
+
+  // ---- sample (Sec. III-A) ----
+  DL_TRY(dalloc(ix, &ix->sample, (size_t)n));
+  uint32_t *blk = nullptr;
+  DL_TRY(tp.get(&blk, sample_blocks(n) + 4));
+  int64_t m = 0;
+  DL_TRY(sample_ids(n, ix->seed, ix->frac, ix->sample, blk, &m, st));
+  if (m < 2 * (int64_t)N_r) {
+    k_iota<<<(unsigned)std::min<int64_t>(ceil_div(n, 256), 4096), 256, 0, st>>>(ix->sample, n);
+    DL_CUDA(cudaGetLastError());
+    m = n;
+  }
+  ix->m_sample = m;
+
+  // ---- breakpoints: sample projections, sorted per column ----
+  float *Ps = nullptr;
+  DL_TRY(tp.get(&Ps, (size_t)LK * m));
+  ProjArgs ps = pa;
+  ps.P = Ps;
+  ps.ldP = m;
+  DL_TRY(project_rows(ix->X, d, ix->sample, m, d, ix->A, LK, 1, ps, st));
+  int e = check_err(err, st);
+  if (e) return e;
+  DL_TRY(float_to_keys(Ps, (int64_t)LK * m, st));
+  SortTemp srt;
+  const size_t cnt_cap = std::max<size_t>((size_t)LK * 256 * sort_tiles(m), 256 * sort_tiles(n));
+  DL_TRY(tp.get(&srt.counts, cnt_cap));
+  srt.count_cap = cnt_cap;
+  DL_TRY(tp.get(&srt.keys_alt, std::max<size_t>((size_t)LK * m, (size_t)n)));
+  DL_TRY(tp.get(&srt.vals_alt, (size_t)n));
+  DL_TRY(tp.get(&srt.digit_base, (size_t)LK * 256));
+  DL_TRY(segmented_sort(reinterpret_cast<uint32_t *>(Ps), nullptr, LK, m, 32, srt, st));
+  DL_TRY(dalloc(ix, &ix->B, (size_t)LK * (N_r + 1)));
+  DL_TRY(extract_breakpoints(reinterpret_cast<uint32_t *>(Ps), LK, m, N_r, ix->B, st));
+
+  // ---- all projections, encoded (Alg. 1), and column min/max ----
+  DL_TRY(dalloc(ix, &ix->codes, (size_t)L * n * CODE_STRIDE));
+  DL_CUDA(cudaMemsetAsync(ix->codes, 0, (size_t)L * n * CODE_STRIDE, st));
+  uint32_t *minmax = nullptr;
+  DL_TRY(tp.get(&minmax, (size_t)2 * LK));
+  k_fill_minmax<<<(unsigned)ceil_div(LK, 128), 128, 0, st>>>(minmax, LK);
+  ProjArgs pe = pa;
+  pe.codes = ix->codes; pe.n = n; pe.B = ix->B; pe.N_r = N_r; pe.K = K; pe.minmax = minmax;
+  DL_TRY(project_rows(ix->X, d, nullptr, n, d, ix->A, LK, 2, pe, st));
+  e = check_err(err, st);
+  if (e) return e;
+  DL_TRY(finish_breakpoint_ends(minmax, LK, N_r, ix->B, st));
+  if (p->keep_projections) {
+    DL_TRY(dalloc(ix, &ix->P, (size_t)n * LK));
+    ProjArgs pp = pa;
+    pp.P = ix->P;
+    pp.ldP = LK;
+    DL_TRY(project_rows(ix->X, d, nullptr, n, d, ix->A, LK, 0, pp, st));
+  }
+  if (p->keep_bf16) {
+    DL_TRY(dalloc(ix, &ix->Xh, (size_t)n * d));
+    DL_TRY(dl::f32_to_bf16(ix->X, ix->Xh, n * (int64_t)d, st));
+  }
+  unsigned long long fbt = 0;
+  DL_CUDA(cudaMemcpyAsync(&fbt, fb_total, sizeof fbt, cudaMemcpyDeviceToHost, st));
+
+  // ---- DE-Trees (Alg. 2) ----
+  TreeTemp tt;
+  DL_TRY(tp.get(&tt.keys, (size_t)n));
+  DL_TRY(tp.get(&tt.vals, (size_t)n));
+  DL_TRY(tp.get(&tt.codesA, (size_t)n));
+  DL_TRY(tp.get(&tt.codesB, (size_t)n));
+  DL_TRY(tp.get(&tt.idsB, (size_t)n));
+  DL_TRY(tp.get(&tt.node_begin, (size_t)n + 1));
+  DL_TRY(tp.get(&tt.node_count, (size_t)n));
+  DL_TRY(tp.get(&tt.block_counts, sample_blocks(n) + 4));
+  DL_TRY(tp.get(&tt.tmp_begin, (size_t)n));
+  DL_TRY(tp.get(&tt.tmp_box, (size_t)n * 48));
+  DL_TRY(tp.get(&tt.leaf_base, (size_t)n));
+  DL_TRY(tp.get(&tt.scalars, 8));
+  tt.sort = srt;
+  DL_TRY(dalloc(ix, &ix->perm, (size_t)L * n));
+  DL_TRY(dalloc(ix, &ix->leaf_of, (size_t)L * n));
+  std::vector<uint32_t *> t_begin(L);
+  std::vector<uint8_t *> t_box(L);
+  uint32_t *lb_tmp = nullptr;
+  uint8_t *lo_tmp = nullptr, *hi_tmp = nullptr, *nb_tmp = nullptr;
+  DL_TRY(tp.get(&lb_tmp, (size_t)n + 1));
+  DL_TRY(tp.get(&lo_tmp, (size_t)n * 16));
+  DL_TRY(tp.get(&hi_tmp, (size_t)n * 16));
+  DL_TRY(tp.get(&nb_tmp, (size_t)n * 16));
+  for (int t = 0; t < L; ++t) {
+    TreeBuildArgs a;
+    a.n = n; a.K = K; a.bbits = ix->bbits; a.M = ix->M; a.box_mode = ix->box_mode;
+    a.codes_t = ix->codes + (size_t)t * n * CODE_STRIDE;
+    a.perm = ix->perm + (size_t)t * n;
+    a.leaf_begin = lb_tmp; a.leaf_lo = lo_tmp; a.leaf_hi = hi_tmp; a.leaf_nb = nb_tmp;
+    a.leaf_of = ix->leaf_of; a.L = L; a.t = t;
+    int64_t nl = 0, ml = 0;
+    DL_TRY(build_tree(a, tt, &nl, &ml, st));
+    ix->nleaves[t] = nl;
+    ix->max_leaf = std::max(ix->max_leaf, ml);
+    ix->max_leaves = std::max(ix->max_leaves, nl);
+    DL_TRY(tp.get(&t_begin[t], (size_t)nl + 1));
+    DL_TRY(tp.get(&t_box[t], (size_t)nl * 48));
+    DL_CUDA(cudaMemcpyAsync(t_begin[t], lb_tmp, sizeof(uint32_t) * (nl + 1), cudaMemcpyDeviceToDevice, st));
+    DL_CUDA(cudaMemcpyAsync(t_box[t], lo_tmp, (size_t)nl * 16, cudaMemcpyDeviceToDevice, st));
+    DL_CUDA(cudaMemcpyAsync(t_box[t] + nl * 16, hi_tmp, (size_t)nl * 16, cudaMemcpyDeviceToDevice, st));
+    DL_CUDA(cudaMemcpyAsync(t_box[t] + nl * 32, nb_tmp, (size_t)nl * 16, cudaMemcpyDeviceToDevice, st));
+  }
+  int64_t tl = 0;
+  for (int t = 0; t < L; ++t) { ix->leaf_off[t] = tl; tl += ix->nleaves[t]; }
+  ix->leaf_off[L] = tl;
+  DL_TRY(dalloc(ix, &ix->leaf_begin, (size_t)tl + L));
+  DL_TRY(dalloc(ix, &ix->leaf_lo, (size_t)tl * 16));
+  DL_TRY(dalloc(ix, &ix->leaf_hi, (size_t)tl * 16));
+  DL_TRY(dalloc(ix, &ix->leaf_nb, (size_t)tl * 16));
+  for (int t = 0; t < L; ++t) {
+    const int64_t nl = ix->nleaves[t], o = ix->leaf_off[t];
+    DL_CUDA(cudaMemcpyAsync(ix->leaf_begin + o + t, t_begin[t], sizeof(uint32_t) * (nl + 1),
+                            cudaMemcpyDeviceToDevice, st));
+    DL_CUDA(cudaMemcpyAsync(ix->leaf_lo + o * 16, t_box[t], (size_t)nl * 16, cudaMemcpyDeviceToDevice, st));
+    DL_CUDA(cudaMemcpyAsync(ix->leaf_hi + o * 16, t_box[t] + nl * 16, (size_t)nl * 16,
+                            cudaMemcpyDeviceToDevice, st));
+    DL_CUDA(cudaMemcpyAsync(ix->leaf_nb + o * 16, t_box[t] + nl * 32, (size_t)nl * 16,
+                            cudaMemcpyDeviceToDevice, st));
+  }
+  DL_CUDA(cudaStreamSynchronize(st));
+  ix->fb_total = (int64_t)fbt;
+  ix->eps2 = eps2_of(K, L);
+  return DETLSH_OK;
+}
+
+void free_index(detlsh_index *ix) {
+  if (!ix) return;
+  for (void *q : ix->owned) cudaFree(q);
+  for (auto *b : {&ix->qQ, &ix->qQh, &ix->qQp, &ix->qk, &ix->qids, &ix->qdists, &ix->qT,
+                  &ix->qscratch, &ix->qstat, &ix->qS, &ix->qfb})
+    if (b->p) cudaFree(b->p);
+  delete ix;
+}
+
+QueryIndexView view_of(const detlsh_index *ix) {
+  QueryIndexView v;
+  v.n = ix->n; v.d = ix->d; v.L = ix->L; v.K = ix->K; v.LK = ix->LK; v.N_r = ix->N_r;
+  v.X = ix->X; v.Xh = ix->Xh; v.B = ix->B; v.perm = ix->perm; v.leaf_begin = ix->leaf_begin;
+  v.leaf_lo = ix->leaf_lo; v.leaf_hi = ix->leaf_hi; v.leaf_of = ix->leaf_of;
+  for (int t = 0; t <= 16; ++t) v.leaf_off[t] = t <= ix->L ? ix->leaf_off[t] : ix->leaf_off[ix->L];
+  v.max_leaves = ix->max_leaves;
+  v.max_leaf_size = ix->max_leaf;
+  return v;
+}
+
+int validate_query(const detlsh_index *ix, int64_t m, int32_t k_max, const detlsh_query_params *qp) {
+  if (!ix || !qp || m < 0) return DETLSH_ERR_INVALID_ARG;
+  if (k_max < 1 || k_max > 1024 || k_max > ix->n) return DETLSH_ERR_INVALID_ARG;
+  if (!(qp->c >= 1.1 && qp->c <= 16.0)) return DETLSH_ERR_INVALID_ARG;
+  if (!(qp->beta >= 0.0 && std::isfinite(qp->beta))) return DETLSH_ERR_INVALID_ARG;
+  if (qp->precision != DETLSH_PREC_FP32 && qp->precision != DETLSH_PREC_BF16_REFINE)
+    return DETLSH_ERR_INVALID_ARG;
+  if (qp->precision == DETLSH_PREC_BF16_REFINE &&
+      (!ix->Xh || (ix->d % 8) != 0 || qp->rerank_mult < 1))
+    return DETLSH_ERR_INVALID_ARG;
+  return DETLSH_OK;
+}
+
+// Shared body of detlsh_query_ex and detlsh_query_candidates (qmu held).
+int query_impl(detlsh_index *ix, const float *queries, int64_t m, const int32_t *kq,
+               int32_t k_max, const detlsh_query_params *qp, cudaStream_t st, int64_t *ids,
+               float *dists, int64_t S_cap, int64_t *S, int64_t *S_size, int32_t *jstar,
+               int32_t *istar) {
+  const int d = ix->d, LK = ix->LK;
+  std::vector<int32_t> kh;
+  if (kq) {
+    kh.resize((size_t)m);
+    if (is_device_ptr(kq)) DL_CUDA(cudaMemcpy(kh.data(), kq, sizeof(int32_t) * m, cudaMemcpyDeviceToHost));
+    else memcpy(kh.data(), kq, sizeof(int32_t) * m);
+    for (int32_t v : kh)
+      if (v < 1 || v > k_max) return DETLSH_ERR_INVALID_ARG;
+  }
+  DL_TRY(grow(ix->qQ, sizeof(float) * (size_t)m * d));
+  DL_TRY(grow(ix->qQp, sizeof(float) * (size_t)m * LK));
+  DL_TRY(grow(ix->qids, sizeof(int64_t) * (size_t)m * k_max));
+  DL_TRY(grow(ix->qdists, sizeof(float) * (size_t)m * k_max));
+  DL_TRY(grow(ix->qT, sizeof(float) * 256));
+  DL_TRY(grow(ix->qstat, 256));
+  float *Q = static_cast<float *>(ix->qQ.p);
+  float *Qp = static_cast<float *>(ix->qQp.p);
+  int *err = static_cast<int *>(ix->qstat.p);
+  uint32_t *fb_count = reinterpret_cast<uint32_t *>(static_cast<char *>(ix->qstat.p) + 16);
+  uint32_t *counter = reinterpret_cast<uint32_t *>(static_cast<char *>(ix->qstat.p) + 32);
+  DL_CUDA(cudaMemsetAsync(ix->qstat.p, 0, 256, st));
+  DL_TRY(copy_in(Q, queries, sizeof(float) * (size_t)m * d, st));
+  // exact query projections q'_i = H_i(q) (Alg. 5)
+  const uint32_t fb_cap = (uint32_t)std::max<int64_t>(1024, m * LK / 64);
+  DL_TRY(grow(ix->qfb, sizeof(uint2) * fb_cap));
+  ProjArgs pa;
+  pa.P = Qp; pa.ldP = LK; pa.fb_count = fb_count; pa.fb_cap = fb_cap; pa.err = err;
+  pa.fb_list = static_cast<uint2 *>(ix->qfb.p);
+  DL_TRY(project_rows(Q, d, nullptr, m, d, ix->A, LK, 0, pa, st));
+  const __nv_bfloat16 *Qh = nullptr;
+  if (qp->precision == DETLSH_PREC_BF16_REFINE) {
+    DL_TRY(grow(ix->qQh, sizeof(__nv_bfloat16) * (size_t)m * d));
+    DL_TRY(dl::f32_to_bf16(Q, static_cast<__nv_bfloat16 *>(ix->qQh.p), m * (int64_t)d, st));
+    Qh = static_cast<const __nv_bfloat16 *>(ix->qQh.p);
+  }
+  float Th[256];
+  level_table(ix->eps2, qp->c, Th);
+  Th[255] = INFINITY;
+  DL_CUDA(cudaMemcpyAsync(ix->qT.p, Th, sizeof Th, cudaMemcpyHostToDevice, st));
+  int32_t *kd = nullptr;
+  if (kq) {
+    DL_TRY(grow(ix->qk, sizeof(int32_t) * (size_t)m));
+    kd = static_cast<int32_t *>(ix->qk.p);
+    DL_CUDA(cudaMemcpyAsync(kd, kh.data(), sizeof(int32_t) * m, cudaMemcpyHostToDevice, st));
+  }
+  const double tb = std::ceil(qp->beta * (double)ix->n);
+  const int64_t tau_base = tb > (double)ix->n ? ix->n + 1 : (int64_t)tb;
+  int64_t cap = (tau_base + k_max > ix->n) ? ix->n
+                                            : std::min<int64_t>(ix->n, tau_base + k_max + ix->max_leaf);
+  QueryIndexView v = view_of(ix);
+  QueryArgs qa{};
+  qa.Q = Q; qa.Qh = Qh; qa.Qp = Qp; qa.m = m; qa.kq = kd; qa.k_max = k_max;
+  qa.tau_base = tau_base; qa.T = static_cast<const float *>(ix->qT.p);
+  qa.precision = qp->precision; qa.rerank_mult = qp->rerank_mult;
+  qa.ids = static_cast<int64_t *>(ix->qids.p);
+  qa.dists = static_cast<float *>(ix->qdists.p);
+  if (S) {
+    DL_TRY(grow(ix->qS, sizeof(int64_t) * (size_t)m * S_cap + 3 * 8 * (size_t)m));
+    qa.S_out = static_cast<int64_t *>(ix->qS.p);
+    qa.S_cap = S_cap;
+    qa.S_size = qa.S_out + (size_t)m * S_cap;
+    qa.jstar = reinterpret_cast<int32_t *>(qa.S_size + m);
+    qa.istar = qa.jstar + m;
+  }
+  qa.cand_cap = cap;
+  query_slot_offsets(v, cap, qa.off);
+  qa.slot_bytes = qa.off[7];
+  int slots = query_slots(v);
+  slots = (int)std::min<int64_t>(slots, std::max<int64_t>(m, 1));
+  // keep the scratch within a quarter of the free device memory
+  size_t freeb = 0, totb = 0;
+  DL_CUDA(cudaMemGetInfo(&freeb, &totb));
+  while (slots > 1 && (size_t)slots * qa.slot_bytes > freeb / 4 + ix->qscratch.bytes) slots /= 2;
+  DL_TRY(grow(ix->qscratch, (size_t)slots * qa.slot_bytes));
+  qa.scratch = static_cast<uint8_t *>(ix->qscratch.p);
+  qa.nslots = slots;
+  qa.work_counter = counter;
+  qa.err = err;
+  int e = check_err(err, st);  // projection status (non-finite queries)
+  if (e) return e;
+  DL_TRY(run_queries(v, qa, st));
+  e = check_err(err, st);
+  if (e) return e;
+  if (ids) DL_TRY(copy_out(ids, qa.ids, sizeof(int64_t) * (size_t)m * k_max, st));
+  if (dists) DL_TRY(copy_out(dists, qa.dists, sizeof(float) * (size_t)m * k_max, st));
+  if (S) {
+    DL_CUDA(cudaMemcpyAsync(S, qa.S_out, sizeof(int64_t) * (size_t)m * S_cap, cudaMemcpyDeviceToHost, st));
+    DL_CUDA(cudaMemcpyAsync(S_size, qa.S_size, sizeof(int64_t) * (size_t)m, cudaMemcpyDeviceToHost, st));
+    DL_CUDA(cudaMemcpyAsync(jstar, qa.jstar, sizeof(int32_t) * (size_t)m, cudaMemcpyDeviceToHost, st));
+    DL_CUDA(cudaMemcpyAsync(istar, qa.istar, sizeof(int32_t) * (size_t)m, cudaMemcpyDeviceToHost, st));
+  }
+  DL_CUDA(cudaStreamSynchronize(st));
+  return DETLSH_OK;
+}
+
+}  // namespace
+
+namespace dl {
+int f32_to_bf16(const float *src, __nv_bfloat16 *dst, int64_t count, cudaStream_t st) {
+  if (count <= 0) return DETLSH_OK;
+  k_f32_to_bf16<<<(unsigned)std::min<int64_t>(ceil_div(count, 256), 8192), 256, 0, st>>>(src, dst, count);
+  DL_CUDA(cudaGetLastError());
+  return DETLSH_OK;
+}
+}  // namespace dl
+
+// ===========================================================================
+// C-ABI
+// ===========================================================================
+extern "C" {
+
+int detlsh_default_build_params(detlsh_build_params *p) {
+  if (!p) return DETLSH_ERR_INVALID_ARG;
+  p->L = 4;
+  p->K = 16;
+  p->N_r = 256;
+  p->max_size = 64;
+  p->seed = 0;
+  p->sample_frac = 0.1;
+  p->box_mode = DETLSH_BOX_PREFIX;
+  p->keep_bf16 = 1;
+  p->keep_projections = 0;
+  return DETLSH_OK;
+}
+
+int detlsh_default_query_params(detlsh_query_params *p) {
+  if (!p) return DETLSH_ERR_INVALID_ARG;
+  p->beta = 0.1;
+  p->c = 1.5;
+  p->precision = DETLSH_PREC_FP32;
+  p->rerank_mult = 4;
+  return DETLSH_OK;
+}
+
+const char *detlsh_status_string(int s) {
+  switch (s) {
+    case DETLSH_OK: return "ok";
+    case DETLSH_ERR_INVALID_ARG: return "invalid argument";
+    case DETLSH_ERR_NONFINITE_INPUT: return "non-finite input or projection overflow";
+    case DETLSH_ERR_OOM: return "out of memory";
+    case DETLSH_ERR_CUDA: return g_last_cuda[0] ? g_last_cuda : "CUDA error";
+    case DETLSH_ERR_CAPACITY: return "internal work list capacity exceeded";
+    case DETLSH_ERR_NO_DEVICE: return "no CUDA device";
+  }
+  return "unknown status";
+}
+
+int detlsh_build_ex(const float *data, int64_t n, int32_t d, const detlsh_build_params *p,
+                    void *stream, detlsh_index **out) {
+  if (!out || !data) return DETLSH_ERR_INVALID_ARG;
+  *out = nullptr;
+  const int v = validate_build(n, d, p);
+  if (v) return v;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+    cudaGetLastError();
+    return DETLSH_ERR_NO_DEVICE;
+  }
+  detlsh_index *ix = new (std::nothrow) detlsh_index();
+  if (!ix) return DETLSH_ERR_OOM;
+  cudaGetDevice(&ix->device);
+  ix->n = n; ix->d = d; ix->L = p->L; ix->K = p->K; ix->LK = p->L * p->K; ix->N_r = p->N_r;
+  ix->M = p->max_size; ix->box_mode = p->box_mode; ix->seed = p->seed; ix->frac = p->sample_frac;
+  while ((1 << ix->bbits) < ix->N_r) ++ix->bbits;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int s = build_impl(ix, data, st, p);
+  if (s != DETLSH_OK) {
+    cudaStreamSynchronize(st);
+    free_index(ix);
+    return s;
+  }
+  *out = ix;
+  return DETLSH_OK;
+}
+
+int detlsh_build(const float *data, int64_t n, int32_t d, int32_t L, int32_t K, int32_t N_r,
+                 uint64_t seed, detlsh_index **out) {
+  detlsh_build_params p;
+  detlsh_default_build_params(&p);
+  p.L = L; p.K = K; p.N_r = N_r; p.seed = seed;
+  return detlsh_build_ex(data, n, d, &p, nullptr, out);
+}
+
+int detlsh_free(detlsh_index *ix) {
+  free_index(ix);
+  return DETLSH_OK;
+}
+
+int detlsh_query_ex(const detlsh_index *cix, const float *queries, int64_t m,
+                    const int32_t *k_per_query, int32_t k_max, const detlsh_query_params *qp,
+                    void *stream, int64_t *ids, float *dists) {
+  detlsh_query_params def;
+  detlsh_default_query_params(&def);
+  if (!qp) qp = &def;
+  const int v = validate_query(cix, m, k_max, qp);
+  if (v) return v;
+  if (m == 0) return DETLSH_OK;
+  if (!queries || !ids || !dists) return DETLSH_ERR_INVALID_ARG;
+  detlsh_index *ix = const_cast<detlsh_index *>(cix);
+  std::lock_guard<std::mutex> g(ix->qmu);
+  return query_impl(ix, queries, m, k_per_query, k_max, qp, static_cast<cudaStream_t>(stream), ids,
+                    dists, 0, nullptr, nullptr, nullptr, nullptr);
+}
+
+int detlsh_query(const detlsh_index *ix, const float *queries, int64_t m, int32_t k, double c,
+                 int64_t *ids, float *dists) {
+  detlsh_query_params qp;
+  detlsh_default_query_params(&qp);
+  qp.c = c;
+  return detlsh_query_ex(ix, queries, m, nullptr, k, &qp, nullptr, ids, dists);
+}
+
+int detlsh_query_candidates(const detlsh_index *cix, const float *queries, int64_t m, int32_t k,
+                            const detlsh_query_params *qp, int64_t cap, int64_t *S,
+                            int64_t *S_size, int32_t *jstar, int32_t *istar) {
+  detlsh_query_params def;
+  detlsh_default_query_params(&def);
+  if (!qp) qp = &def;
+  const int v = validate_query(cix, m, k, qp);
+  if (v) return v;
+  if (m == 0) return DETLSH_OK;
+  if (!queries || !S || !S_size || !jstar || !istar || cap < 1) return DETLSH_ERR_INVALID_ARG;
+  detlsh_index *ix = const_cast<detlsh_index *>(cix);
+  std::lock_guard<std::mutex> g(ix->qmu);
+  return query_impl(ix, queries, m, nullptr, k, qp, nullptr, nullptr, nullptr, cap, S, S_size,
+                    jstar, istar);
+}
+
+int detlsh_get_info(const detlsh_index *ix, detlsh_info *info) {
+  if (!ix || !info) return DETLSH_ERR_INVALID_ARG;
+  memset(info, 0, sizeof *info);
+  info->n = ix->n; info->d = ix->d; info->L = ix->L; info->K = ix->K; info->N_r = ix->N_r;
+  info->max_size = ix->M; info->box_mode = ix->box_mode; info->has_bf16 = ix->Xh != nullptr;
+  info->sample_size = ix->m_sample;
+  for (int t = 0; t < ix->L; ++t) info->num_leaves[t] = ix->nleaves[t];
+  info->max_leaf_size = ix->max_leaf;
+  info->eps2 = ix->eps2;
+  info->device_bytes = ix->device_bytes;
+  info->projection_fallbacks = ix->fb_total;
+  return DETLSH_OK;
+}
+
+int detlsh_get_projection_matrix(const detlsh_index *ix, float *A) {
+  if (!ix || !A) return DETLSH_ERR_INVALID_ARG;
+  DL_CUDA(cudaMemcpy(A, ix->A, sizeof(float) * (size_t)ix->LK * ix->d, cudaMemcpyDeviceToHost));
+  return DETLSH_OK;
+}
+
+int detlsh_get_sample(const detlsh_index *ix, int64_t *ids) {
+  if (!ix || !ids) return DETLSH_ERR_INVALID_ARG;
+  std::vector<uint32_t> h((size_t)ix->m_sample);
+  DL_CUDA(cudaMemcpy(h.data(), ix->sample, sizeof(uint32_t) * h.size(), cudaMemcpyDeviceToHost));
+  for (size_t i = 0; i < h.size(); ++i) ids[i] = h[i];
+  return DETLSH_OK;
+}
+
+int detlsh_get_breakpoints(const detlsh_index *ix, float *B) {
+  if (!ix || !B) return DETLSH_ERR_INVALID_ARG;
+  DL_CUDA(cudaMemcpy(B, ix->B, sizeof(float) * (size_t)ix->LK * (ix->N_r + 1), cudaMemcpyDeviceToHost));
+  return DETLSH_OK;
+}
+
+int detlsh_get_codes(const detlsh_index *ix, uint8_t *codes) {
+  if (!ix || !codes) return DETLSH_ERR_INVALID_ARG;
+  std::vector<uint8_t> h((size_t)ix->L * ix->n * CODE_STRIDE);
+  DL_CUDA(cudaMemcpy(h.data(), ix->codes, h.size(), cudaMemcpyDeviceToHost));
+  for (int64_t p = 0; p < ix->n; ++p)
+    for (int t = 0; t < ix->L; ++t)
+      for (int j = 0; j < ix->K; ++j)
+        codes[p * ix->LK + t * ix->K + j] = h[((size_t)t * ix->n + p) * CODE_STRIDE + j];
+  return DETLSH_OK;
+}
+
+int detlsh_get_projections(const detlsh_index *ix, float *P) {
+  if (!ix || !P || !ix->P) return DETLSH_ERR_INVALID_ARG;
+  DL_CUDA(cudaMemcpy(P, ix->P, sizeof(float) * (size_t)ix->n * ix->LK, cudaMemcpyDeviceToHost));
+  return DETLSH_OK;
+}
+
+int detlsh_get_tree(const detlsh_index *ix, int32_t t, int64_t *perm, int64_t *leaf_begin,
+                    uint8_t *box_lo, uint8_t *box_hi, uint8_t *nbits, int64_t *leaf_of) {
+  if (!ix || t < 0 || t >= ix->L) return DETLSH_ERR_INVALID_ARG;
+  const int64_t n = ix->n, nl = ix->nleaves[t], o = ix->leaf_off[t];
+  const int K = ix->K;
+  if (perm) {
+    std::vector<uint32_t> h((size_t)n);
+    DL_CUDA(cudaMemcpy(h.data(), ix->perm + (size_t)t * n, 4 * h.size(), cudaMemcpyDeviceToHost));
+    for (int64_t i = 0; i < n; ++i) perm[i] = h[i];
+  }
+  if (leaf_begin) {
+    std::vector<uint32_t> h((size_t)nl + 1);
+    DL_CUDA(cudaMemcpy(h.data(), ix->leaf_begin + o + t, 4 * h.size(), cudaMemcpyDeviceToHost));
+    for (int64_t i = 0; i <= nl; ++i) leaf_begin[i] = h[i];
+  }
+  const uint8_t *src[3] = {ix->leaf_lo, ix->leaf_hi, ix->leaf_nb};
+  uint8_t *dst[3] = {box_lo, box_hi, nbits};
+  for (int a = 0; a < 3; ++a) {
+    if (!dst[a]) continue;
+    std::vector<uint8_t> h((size_t)nl * 16);
+    DL_CUDA(cudaMemcpy(h.data(), src[a] + o * 16, h.size(), cudaMemcpyDeviceToHost));
+    for (int64_t l = 0; l < nl; ++l)
+      for (int j = 0; j < K; ++j) dst[a][l * K + j] = h[(size_t)l * 16 + j];
+  }
+  if (leaf_of) {
+    std::vector<uint32_t> h((size_t)n * ix->L);
+    DL_CUDA(cudaMemcpy(h.data(), ix->leaf_of, 4 * h.size(), cudaMemcpyDeviceToHost));
+    for (int64_t i = 0; i < n; ++i) leaf_of[i] = h[(size_t)i * ix->L + t];
+  }
+  return DETLSH_OK;
+}
+
+int detlsh_get_level_table(const detlsh_index *ix, double c, float *T) {
+  if (!ix || !T || !(c > 1.0)) return DETLSH_ERR_INVALID_ARG;
+  level_table(ix->eps2, c, T);
+  return DETLSH_OK;
+}
+
+int detlsh_project(const detlsh_index *cix, const float *rows, int64_t m, float *out, void *stream) {
+  if (!cix || m < 0) return DETLSH_ERR_INVALID_ARG;
+  if (m == 0) return DETLSH_OK;
+  if (!rows || !out) return DETLSH_ERR_INVALID_ARG;
+  detlsh_index *ix = const_cast<detlsh_index *>(cix);
+  std::lock_guard<std::mutex> g(ix->qmu);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  DL_TRY(grow(ix->qQ, sizeof(float) * (size_t)m * ix->d));
+  DL_TRY(grow(ix->qQp, sizeof(float) * (size_t)m * ix->LK));
+  DL_TRY(grow(ix->qstat, 256));
+  DL_CUDA(cudaMemsetAsync(ix->qstat.p, 0, 256, st));
+  float *Q = static_cast<float *>(ix->qQ.p);
+  DL_TRY(copy_in(Q, rows, sizeof(float) * (size_t)m * ix->d, st));
+  ProjArgs pa;
+  pa.P = static_cast<float *>(ix->qQp.p);
+  pa.ldP = ix->LK;
+  pa.err = static_cast<int *>(ix->qstat.p);
+  pa.fb_count = reinterpret_cast<uint32_t *>(static_cast<char *>(ix->qstat.p) + 16);
+  pa.fb_cap = (uint32_t)std::max<int64_t>(1024, m * ix->LK / 64);
+  DL_TRY(grow(ix->qfb, sizeof(uint2) * pa.fb_cap));
+  pa.fb_list = static_cast<uint2 *>(ix->qfb.p);
+  DL_TRY(project_rows(Q, ix->d, nullptr, m, ix->d, ix->A, ix->LK, 0, pa, st));
+  const int e = check_err(pa.err, st);
+  if (e) return e;
+  DL_TRY(copy_out(out, ix->qQp.p, sizeof(float) * (size_t)m * ix->LK, st));
+  DL_CUDA(cudaStreamSynchronize(st));
+  return DETLSH_OK;
+}
+
+}  // extern "C"

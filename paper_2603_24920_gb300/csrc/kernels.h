@@ -1,0 +1,134 @@
+// kernels.h -- host-side launchers of the DET-LSH kernels (internal).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace dl {
+
+// ---- exact projection (project.cu) ----------------------------------------
+struct ProjArgs {
+  // modes 0 (row-major P[row][col]) and 1 (column-major P[col][row])
+  float *P = nullptr;
+  int64_t ldP = 0;
+  // mode 2: encode into codes[tree][n][16] and track per-column min/max
+  uint8_t *codes = nullptr;
+  int64_t n = 0;
+  const float *B = nullptr;  // [LK][N_r+1]
+  int N_r = 0, K = 0;
+  uint32_t *minmax = nullptr;  // [LK][2] order-preserving keys
+  // outputs the compensated path cannot certify
+  uint2 *fb_list = nullptr;
+  uint32_t *fb_count = nullptr;
+  uint32_t fb_cap = 0;
+  unsigned long long *fb_total = nullptr;  // running count (device)
+  int *err = nullptr;                      // device status word
+};
+
+// rows == nullptr: rows 0..nrows-1 of X; else the listed row ids.
+int project_rows(const float *X, int64_t ldx, const uint32_t *rows, int64_t nrows, int d,
+                 const float *A, int LK, int mode, ProjArgs o, cudaStream_t st);
+
+// ---- sorting and compaction (sort.cu) --------------------------------------
+struct SortTemp {
+  uint32_t *keys_alt = nullptr, *vals_alt = nullptr;
+  uint32_t *counts = nullptr;  // [segs][256][tiles]
+  uint32_t *digit_base = nullptr;
+  size_t count_cap = 0;
+};
+size_t sort_tiles(int64_t len);
+// Stable LSD radix sort of nseg equal-length segments (keys, optional values)
+// on key bits [0, nbits).  Result ends in keys/vals.
+int segmented_sort(uint32_t *keys, uint32_t *vals, int nseg, int64_t len, int nbits,
+                   SortTemp &tmp, cudaStream_t st);
+
+// Ids of the sampled points in ascending order (Philox stream 3); returns m.
+int sample_ids(int64_t n, uint64_t seed, double frac, uint32_t *ids, uint32_t *block_counts,
+               int64_t *m_out, cudaStream_t st);
+size_t sample_blocks(int64_t n);
+
+// Float sample columns -> order keys in place; breakpoint extraction.
+int float_to_keys(float *v, int64_t count, cudaStream_t st);
+int extract_breakpoints(const uint32_t *sorted_keys, int LK, int64_t m, int N_r, float *B,
+                        cudaStream_t st);
+int finish_breakpoint_ends(const uint32_t *minmax, int LK, int N_r, float *B, cudaStream_t st);
+
+// ---- DE-Tree layout (tree.cu) ----------------------------------------------
+struct TreeBuildArgs {
+  int64_t n;
+  int K, bbits, M, box_mode;
+  const uint8_t *codes_t;  // codes of this tree, [n][16]
+  // outputs
+  uint32_t *perm;          // [n] point ids leaf by leaf
+  uint32_t *leaf_begin;    // [nleaves+1]
+  uint8_t *leaf_lo, *leaf_hi, *leaf_nb;  // [nleaves][16]
+  uint32_t *leaf_of;       // [n][L] (column t)
+  int L, t;
+};
+struct TreeTemp {
+  uint32_t *keys = nullptr, *vals = nullptr;
+  uint4 *codesA = nullptr, *codesB = nullptr;
+  uint32_t *idsB = nullptr;
+  uint32_t *node_begin = nullptr, *node_count = nullptr, *block_counts = nullptr;
+  uint32_t *tmp_begin = nullptr;
+  uint8_t *tmp_box = nullptr;  // [n][48]: lo, hi, nb
+  uint32_t *leaf_base = nullptr;
+  uint32_t *scalars = nullptr;
+  SortTemp sort;
+};
+// Builds one tree; returns the number of leaves through *nleaves.  The leaf
+// arrays must hold n entries (n+1 for leaf_begin).
+int build_tree(const TreeBuildArgs &a, TreeTemp &tmp, int64_t *nleaves, int64_t *max_leaf,
+               cudaStream_t st);
+
+// ---- queries (query.cu) ----------------------------------------------------
+struct QueryIndexView {
+  int64_t n;
+  int d, L, K, LK, N_r;
+  const float *X;
+  const __nv_bfloat16 *Xh;
+  const float *B;            // [LK][N_r+1]
+  const uint32_t *perm;      // [L][n]
+  const uint32_t *leaf_begin;  // concatenated, tree t at leaf_off[t] + t
+  const uint8_t *leaf_lo, *leaf_hi;  // [total_leaves][16]
+  const uint32_t *leaf_of;   // [n][L]
+  int64_t leaf_off[17];      // leaf index offset of each tree (prefix)
+  int64_t max_leaves;        // max leaves of one tree
+  int64_t max_leaf_size;
+};
+struct QueryArgs {
+  const float *Q;            // [m][d]
+  const __nv_bfloat16 *Qh;   // [m][d] (bf16 path)
+  const float *Qp;           // [m][LK] exact projections
+  int64_t m;
+  const int32_t *kq;         // per-query k (nullable)
+  int k_max;
+  int64_t tau_base;          // ceil(beta * n)
+  const float *T;            // [255] radius grid
+  int precision, rerank_mult;
+  int64_t *ids;              // [m][k_max]
+  float *dists;              // [m][k_max]
+  // optional candidate export
+  int64_t *S_out;            // [m][S_cap] (device)
+  int64_t S_cap;
+  int64_t *S_size;
+  int32_t *jstar, *istar;
+  // scratch: one slot per CTA, offsets from query_slot_offsets
+  uint8_t *scratch;
+  int64_t slot_bytes;
+  int64_t off[8];
+  int64_t cand_cap;
+  int nslots;
+  uint32_t *work_counter;
+  int *err;
+};
+size_t query_slot_bytes(const QueryIndexView &ix, int64_t cand_cap, int rerank_cap);
+void query_slot_offsets(const QueryIndexView &ix, int64_t cand_cap, int64_t off[8]);
+int query_slots(const QueryIndexView &ix);
+int run_queries(const QueryIndexView &ix, const QueryArgs &qa, cudaStream_t st);
+
+// ---- misc (api.cu) ----------------------------------------------------------
+int f32_to_bf16(const float *src, __nv_bfloat16 *dst, int64_t count, cudaStream_t st);
+
+}  // namespace dl

@@ -1,0 +1,359 @@
+// project.cu -- exact FP32 projection h_t(o) = a_t . o (Eq. 1) and the
+// fused region encoding of Alg. 1, for sm_103a.
+//
+// Definition: the projection is the exact real dot product of the FP32
+// operands, rounded once to the nearest FP32 (ties to even).  That value does
+// not depend on summation order, so breakpoints, codes and trees built on it
+// are reproducible bit for bit.
+//
+// Fast path (CUDA cores): the compensated dot product of Ogita, Rump and
+// Oishi ("Accurate sum and dot product", SIAM J. Sci. Comput. 26(6), 2005):
+// each product is split exactly with an FMA (TwoProduct), the running sum
+// with Knuth's TwoSum, and the exact error terms are summed separately.  The
+// kernel also accumulates a rigorous bound E on what that separate sum lost;
+// the result y = fl(p + s) is the correctly rounded value whenever
+// |TwoSum error of (p + s)| + E stays below half the FP32 spacing at y.
+// Uncertified outputs (about 1e-5 of them) go to a list that an exact
+// big-integer kernel recomputes.
+#include "common.cuh"
+#include "kernels.h"
+
+#include <algorithm>
+
+namespace dl {
+
+constexpr int PJ_ROWS = 64;
+constexpr int PJ_COLS = 64;
+constexpr int PJ_KC = 32;
+constexpr int PJ_THREADS = 256;
+
+// u * (1 + 2^-6) rounded up, u = 2^-24: covers the rounding of the error
+// accumulator for d <= 65536.
+__device__ __forceinline__ float err_factor() { return 6.0536e-08f; }
+
+__device__ __forceinline__ void dot2_step(float &p, float &s, float &e, float x, float a) {
+  const float h = __fmul_rn(x, a);
+  const float r = __fmaf_rn(x, a, -h);              // x*a = h + r exactly
+  const float t = __fadd_rn(p, h);
+  const float z = __fsub_rn(t, p);
+  const float q = __fadd_rn(__fsub_rn(p, __fsub_rn(t, z)), __fsub_rn(h, z));  // p+h = t+q
+  p = t;
+  const float w = __fadd_rn(q, r);
+  s = __fadd_rn(s, w);
+  e = __fadd_rn(e, __fadd_rn(fabsf(w), fabsf(s)));   // rounding of w and s
+}
+
+// Returns true when y is certified to be the correctly rounded value.
+__device__ __forceinline__ bool dot2_finish(float p, float s, float e, int d, float &y) {
+  y = __fadd_rn(p, s);
+  const float bv = __fsub_rn(y, p);
+  const float zz = __fadd_rn(__fsub_rn(p, __fsub_rn(y, bv)), __fsub_rn(s, bv));
+  // E >= u*(sum |w_i| + |s_i|) + underflow allowance d * 2^-148.
+  const float tiny = __fmul_rn((float)d, __uint_as_float(2u));
+  const float E = __fmaf_ru(e, err_factor(), tiny);
+  const uint32_t yb = __float_as_uint(y);
+  const uint32_t ex = (yb >> 23) & 0xffu;
+  if (ex == 0xffu || ex < 32u) return false;        // non-finite or tiny: exact path
+  float hb = __uint_as_float((ex - 24u) << 23);     // half the spacing above |y|
+  if ((yb & 0x7fffffu) == 0u) hb = __fmul_rn(hb, 0.5f);  // power of two: spacing below halves
+  const float lhs = __fadd_ru(fabsf(zz), E);
+  return lhs < hb;
+}
+
+// Exact dot product rounded once to FP32, with a 640-bit fixed-point
+// accumulator (value = sum dig[i] * 2^(32 i - 298)).  Used for the rare
+// outputs the compensated path cannot certify.  Sets *bad on a non-finite
+// operand or an FP32 overflow of the result.
+__device__ float exact_dot_rn(const float *__restrict__ a, const float *__restrict__ x, int d,
+                              bool *bad) {
+  long long dig[20];
+#pragma unroll
+  for (int i = 0; i < 20; ++i) dig[i] = 0;
+  for (int i = 0; i < d; ++i) {
+    const uint32_t ab = __float_as_uint(a[i]), xb = __float_as_uint(x[i]);
+    const uint32_t ae = (ab >> 23) & 0xffu, xe = (xb >> 23) & 0xffu;
+    if (ae == 0xffu || xe == 0xffu) { *bad = true; return 0.0f; }
+    const uint64_t am = (ab & 0x7fffffu) | (ae ? 0x800000u : 0u);
+    const uint64_t xm = (xb & 0x7fffffu) | (xe ? 0x800000u : 0u);
+    if (am == 0 || xm == 0) continue;
+    const int pos = (int)(ae ? ae : 1u) + (int)(xe ? xe : 1u) - 2;  // bit offset of the product
+    const uint64_t prod = am * xm;                                    // < 2^48
+    const int c = pos >> 5, b = pos & 31;
+    const uint64_t lo = prod << b;
+    const uint64_t hi = b ? (prod >> (64 - b)) : 0ull;
+    const long long p0 = (long long)(lo & 0xffffffffull);
+    const long long p1 = (long long)(lo >> 32);
+    const long long p2 = (long long)hi;
+    if ((ab ^ xb) >> 31) { dig[c] -= p0; dig[c + 1] -= p1; dig[c + 2] -= p2; }
+    else                 { dig[c] += p0; dig[c + 1] += p1; dig[c + 2] += p2; }
+  }
+  // carry-propagate into 32-bit digits, top digit signed
+  for (int i = 0; i < 19; ++i) {
+    const long long carry = dig[i] >> 32;
+    dig[i] -= carry * 4294967296ll;
+    dig[i + 1] += carry;
+  }
+  const bool neg = dig[19] < 0;
+  if (neg) {
+    for (int i = 0; i < 20; ++i) dig[i] = -dig[i];
+    for (int i = 0; i < 19; ++i) {
+      const long long carry = dig[i] >> 32;
+      dig[i] -= carry * 4294967296ll;
+      dig[i + 1] += carry;
+    }
+  }
+  int top = -1;
+  for (int i = 19; i >= 0; --i) {
+    if (dig[i]) { top = 32 * i + 63 - __clzll(dig[i]); break; }  // digits are < 2^32
+  }
+  if (top < 0) return 0.0f;
+  auto bit = [&](int q) -> uint32_t {
+    return q < 0 ? 0u : (uint32_t)((dig[q >> 5] >> (q & 31)) & 1);
+  };
+  int lsb = top - 23;
+  if (lsb < 149) lsb = 149;  // 2^-149 = FP32 subnormal spacing
+  uint32_t mant = 0;
+  for (int q = top; q >= lsb; --q) mant = (mant << 1) | bit(q);
+  const uint32_t rb = bit(lsb - 1);
+  uint32_t sticky = 0;
+  for (int q = lsb - 2; q >= 0 && !sticky; --q) sticky = bit(q);
+  if (rb && (sticky || (mant & 1u))) ++mant;
+  if (mant == (1u << 24)) { mant >>= 1; ++lsb; }
+  if (mant == 0) return 0.0f;
+  const int e2 = lsb - 298;  // value = mant * 2^e2
+  if (e2 + 24 > 128) { *bad = true; return 0.0f; }
+  const float v = scalbnf((float)mant, e2);
+  return neg ? -v : v;
+}
+
+// ---------------------------------------------------------------------------
+// Epilogues.
+// ---------------------------------------------------------------------------
+// Interior breakpoints of a tile's columns are staged with a row stride of
+// 257 floats so that the 16 columns a warp searches fall in distinct banks.
+constexpr int BSTRIDE = 257;
+
+__device__ __forceinline__ uint32_t region_of(const float *__restrict__ Bint, int nint, float y) {
+  // number of interior breakpoints strictly below y (Alg. 1, lowest region on ties)
+  int lo = 0, hi = nint;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (Bint[mid] < y) lo = mid + 1; else hi = mid;
+  }
+  return (uint32_t)lo;
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(PJ_THREADS)
+k_project(const float *__restrict__ X, int64_t ldx, const uint32_t *__restrict__ rows,
+          int64_t nrows, int d, const float *__restrict__ A, int LK, int W, ProjArgs o) {
+  // W = columns per tile, a multiple of K so that a tile never splits a tree
+  __shared__ float Xs[PJ_ROWS][PJ_KC + 1];
+  __shared__ float As[PJ_COLS][PJ_KC + 1];
+  extern __shared__ float dyn[];  // MODE 2: EncodeSmem + code staging
+
+  const int tid = threadIdx.x;
+  const int tx = tid & 15, ty = tid >> 4;
+  const int64_t row0 = (int64_t)blockIdx.x * PJ_ROWS;
+  const int col0 = blockIdx.y * W;
+  const int LKt = min(LK, col0 + W);  // end of this tile's columns
+
+  float p[4][4], s[4][4], e[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) p[i][j] = s[i][j] = e[i][j] = 0.0f;
+
+  for (int kc = 0; kc < d; kc += PJ_KC) {
+    const int kmax = min(PJ_KC, d - kc);
+    __syncthreads();
+    for (int idx = tid; idx < PJ_ROWS * PJ_KC; idx += PJ_THREADS) {
+      const int r = idx / PJ_KC, c = idx % PJ_KC;
+      const int64_t rr = row0 + r;
+      float v = 0.0f;
+      if (rr < nrows && c < kmax) {
+        const int64_t src = rows ? (int64_t)rows[rr] : rr;
+        v = X[src * ldx + kc + c];
+      }
+      Xs[r][c] = v;
+      const int oc = col0 + r;
+      As[r][c] = (oc < LKt && c < kmax) ? A[(int64_t)oc * d + kc + c] : 0.0f;
+    }
+    __syncthreads();
+#pragma unroll 2
+    for (int kk = 0; kk < kmax; ++kk) {
+      float xv[4], av[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) xv[i] = Xs[ty + 16 * i][kk];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) av[j] = As[tx + 16 * j][kk];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) dot2_step(p[i][j], s[i][j], e[i][j], xv[i], av[j]);
+    }
+  }
+
+  if constexpr (MODE == 2) {
+    // stage interior breakpoints of this tile's columns
+    float *Bs = dyn;                                                        // [64][BSTRIDE]
+    uint8_t *cst = reinterpret_cast<uint8_t *>(dyn + PJ_COLS * BSTRIDE);  // [64 rows][64 cols]
+    const int nint = o.N_r - 1;
+    __syncthreads();
+    for (int idx = tid; idx < PJ_COLS * 256; idx += PJ_THREADS) {
+      const int c = idx >> 8, z = idx & 255;
+      const int oc = col0 + c;
+      Bs[c * BSTRIDE + z] = (oc < LKt && z < nint) ? o.B[(int64_t)oc * (o.N_r + 1) + 1 + z] : 0.0f;
+    }
+    __syncthreads();
+    float cmin[4], cmax[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) { cmin[j] = __int_as_float(0x7f800000); cmax[j] = -cmin[j]; }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int r = ty + 16 * i;
+      const int64_t rr = row0 + r;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int c = tx + 16 * j;
+        const int oc = col0 + c;
+        float y;
+        const bool ok = dot2_finish(p[i][j], s[i][j], e[i][j], d, y);
+        uint8_t code = 0;
+        if (rr < nrows && oc < LKt) {
+          if (ok) {
+            code = (uint8_t)region_of(Bs + c * BSTRIDE, nint, y);
+            cmin[j] = fminf(cmin[j], y);
+            cmax[j] = fmaxf(cmax[j], y);
+          } else {
+            const uint32_t slot = atomicAdd(o.fb_count, 1u);
+            if (slot < o.fb_cap) o.fb_list[slot] = make_uint2((uint32_t)rr, (uint32_t)oc);
+          }
+        }
+        cst[r * PJ_COLS + c] = code;
+      }
+    }
+    // per-column min/max: reduce over the 16 row groups through shared memory
+    __syncthreads();
+    float *red = reinterpret_cast<float *>(cst + PJ_ROWS * PJ_COLS);  // [16][64][2]
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      red[(ty * PJ_COLS + tx + 16 * j) * 2 + 0] = cmin[j];
+      red[(ty * PJ_COLS + tx + 16 * j) * 2 + 1] = cmax[j];
+    }
+    __syncthreads();
+    if (tid < PJ_COLS && col0 + tid < LKt) {
+      float mn = red[tid * 2], mx = red[tid * 2 + 1];
+      for (int g = 1; g < 16; ++g) {
+        mn = fminf(mn, red[(g * PJ_COLS + tid) * 2]);
+        mx = fmaxf(mx, red[(g * PJ_COLS + tid) * 2 + 1]);
+      }
+      if (mn <= mx) {
+        atomicMin(&o.minmax[(col0 + tid) * 2 + 0], fkey(mn + 0.0f));
+        atomicMax(&o.minmax[(col0 + tid) * 2 + 1], fkey(mx + 0.0f));
+      }
+    }
+    // codes: 16 bytes per (tree, point); this tile covers trees col0/K ...
+    const int K = o.K;
+    const int ntree = (LKt - col0) / K;
+    const int t0 = col0 / K;
+    for (int idx = tid; idx < PJ_ROWS * ntree; idx += PJ_THREADS) {
+      const int r = idx / ntree, tt = idx % ntree;
+      const int64_t rr = row0 + r;
+      if (rr >= nrows) continue;
+      uint32_t w[4] = {0u, 0u, 0u, 0u};
+      for (int j = 0; j < K; ++j)
+        w[j >> 2] |= (uint32_t)cst[r * PJ_COLS + tt * K + j] << (8 * (j & 3));
+      uint4 *dst = reinterpret_cast<uint4 *>(o.codes + ((int64_t)(t0 + tt) * o.n + rr) * CODE_STRIDE);
+      *dst = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+    return;
+  }
+
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int64_t rr = row0 + ty + 16 * i;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int oc = col0 + tx + 16 * j;
+      float y;
+      const bool ok = dot2_finish(p[i][j], s[i][j], e[i][j], d, y);
+      if (rr < nrows && oc < LKt) {
+        if (!ok) {
+          const uint32_t slot = atomicAdd(o.fb_count, 1u);
+          if (slot < o.fb_cap) o.fb_list[slot] = make_uint2((uint32_t)rr, (uint32_t)oc);
+          y = 0.0f;
+        }
+        if (MODE == 0) o.P[rr * o.ldP + oc] = y + 0.0f;
+        else o.P[(int64_t)oc * o.ldP + rr] = y + 0.0f;
+      }
+    }
+  }
+}
+
+// Exact recomputation of the listed outputs.  The count is read on the
+// device, so no host synchronisation is needed; if the list overflowed, every
+// output is recomputed exactly (slow, but still exact).
+template <int MODE>
+__global__ void k_project_exact(const float *__restrict__ X, int64_t ldx,
+                                const uint32_t *__restrict__ rows, int64_t nrows, int d,
+                                const float *__restrict__ A, int LK, ProjArgs o) {
+  const uint32_t cnt = *o.fb_count;
+  if (cnt == 0) return;
+  const bool all = cnt > o.fb_cap;
+  if (blockIdx.x == 0 && threadIdx.x == 0 && o.fb_total)
+    atomicAdd(o.fb_total, (unsigned long long)(all ? nrows * (int64_t)LK : (int64_t)cnt));
+  const int64_t total = all ? nrows * (int64_t)LK : (int64_t)cnt;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int64_t rr;
+    int oc;
+    if (all) { rr = i / LK; oc = (int)(i % LK); }
+    else { const uint2 f = o.fb_list[i]; rr = f.x; oc = (int)f.y; }
+    const int64_t src = rows ? (int64_t)rows[rr] : rr;
+    bool bad = false;
+    float y = exact_dot_rn(A + (int64_t)oc * d, X + src * ldx, d, &bad);
+    if (bad) { atomicExch(o.err, (int)DETLSH_ERR_NONFINITE_INPUT); continue; }
+    y = y + 0.0f;  // exact zero is +0
+    if (MODE == 0) { o.P[rr * o.ldP + oc] = y; continue; }
+    if (MODE == 1) { o.P[(int64_t)oc * o.ldP + rr] = y; continue; }
+    const float *Bint = o.B + (int64_t)oc * (o.N_r + 1) + 1;
+    const uint32_t code = region_of(Bint, o.N_r - 1, y);
+    const int t = oc / o.K, j = oc % o.K;
+    o.codes[((int64_t)t * o.n + rr) * CODE_STRIDE + j] = (uint8_t)code;
+    atomicMin(&o.minmax[oc * 2 + 0], fkey(y));
+    atomicMax(&o.minmax[oc * 2 + 1], fkey(y));
+  }
+}
+
+template <int MODE>
+static int project_impl(const float *X, int64_t ldx, const uint32_t *rows, int64_t nrows, int d,
+                        const float *A, int LK, ProjArgs o, cudaStream_t st) {
+  if (nrows <= 0) return DETLSH_OK;
+  DL_CUDA(cudaMemsetAsync(o.fb_count, 0, sizeof(uint32_t), st));
+  const int W = (MODE == 2) ? (PJ_COLS / o.K) * o.K : PJ_COLS;
+  dim3 grid((unsigned)ceil_div(nrows, PJ_ROWS), (unsigned)ceil_div(LK, W));
+  size_t dyn = 0;
+  if (MODE == 2) {
+    dyn = sizeof(float) * PJ_COLS * BSTRIDE + PJ_ROWS * PJ_COLS + sizeof(float) * 16 * PJ_COLS * 2;
+    DL_CUDA(cudaFuncSetAttribute(k_project<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)dyn));
+  }
+  k_project<MODE><<<grid, PJ_THREADS, dyn, st>>>(X, ldx, rows, nrows, d, A, LK, W, o);
+  DL_CUDA(cudaGetLastError());
+  k_project_exact<MODE><<<256, 128, 0, st>>>(X, ldx, rows, nrows, d, A, LK, o);
+  DL_CUDA(cudaGetLastError());
+  return DETLSH_OK;
+}
+
+int project_rows(const float *X, int64_t ldx, const uint32_t *rows, int64_t nrows, int d,
+                 const float *A, int LK, int mode, ProjArgs o, cudaStream_t st) {
+  switch (mode) {
+    case 0: return project_impl<0>(X, ldx, rows, nrows, d, A, LK, o, st);
+    case 1: return project_impl<1>(X, ldx, rows, nrows, d, A, LK, o, st);
+    case 2: return project_impl<2>(X, ldx, rows, nrows, d, A, LK, o, st);
+  }
+  return DETLSH_ERR_INVALID_ARG;
+}
+
+}  // namespace dl

@@ -1,0 +1,696 @@
+// query.cu -- batched c^2-k-ANN queries over the DE-Trees (Alg. 3-5) for
+// sm_103a.  One persistent launch: each CTA takes queries from a global work
+// counter and runs the whole query in its own scratch slot.
+//
+// Per query (q' = exact projections, computed beforehand by the projection
+// kernel):
+//  1. Range-query bounds (Alg. 3, Sec. IV-C): for every leaf of every tree,
+//     LB^2 = sum_j gap_j^2 with gap_j the distance from q'_j to the leaf's
+//     breakpoint interval [B(lo_j), B(hi_j + 1)], in FP32, dimensions in
+//     order, from a per-tree lookup table g[j][z] = B_j[z] - q'_j held in
+//     shared memory.  The leaf's level is the smallest radius index j with
+//     LB^2 <= T(j) = fp32(eps^2 c^(2j)): the first radius of the grid whose
+//     range query takes the whole leaf (optimisation (1) of Sec. VI-B2).
+//  2. Magic r_min (Sec. V-B1): N(j) = |union over trees of points in leaves
+//     of level <= j|; r_min = c^{j*}, j* = min{j : N(j) >= beta*n + k}.
+//     Union counts use an owner rule instead of per-query bitmaps: a point is
+//     counted once, by the first tree attaining its smallest level.
+//  3. Alg. 5 at r_min: trees in order; a point is new in tree t if no earlier
+//     tree holds it within level j*; i* = first tree where the running count
+//     reaches beta*n + k; inside tree i* the leaves enter in ascending
+//     (LB^2, leaf index) order -- the priority queue of Sec. VI-B2 -- until the
+//     count is reached (a weighted radix select on LB^2).
+//  4. Verification: exact distances of every candidate (FP32, or BF16 scores
+//     with an FP32 re-rank of the best rerank_mult*k) and top-k by
+//     (distance, id) via radix select.
+#include "common.cuh"
+#include "compact.cuh"
+#include "kernels.h"
+
+#include <algorithm>
+
+namespace dl {
+
+constexpr int QT = 256;
+constexpr int QW = QT / 32;
+constexpr int KMAX = 1024;
+constexpr int RR_MAX = 4096;  // re-rank pool of the BF16 path
+
+struct Slot {
+  float *lb2;       // [total_leaves]
+  uint8_t *lev;     // [total_leaves]
+  uint32_t *cval;   // [max_leaves]
+  uint32_t *cand;   // [cap]
+  uint32_t *key;    // [cap] order keys of distances
+  uint32_t *rid;    // [RR_MAX] re-rank ids
+  uint32_t *rkey;   // [RR_MAX]
+};
+
+__host__ __device__ inline int64_t align_up(int64_t v, int64_t a) { return (v + a - 1) / a * a; }
+
+struct SlotLayout {
+  int64_t lb2, lev, cval, cand, key, rid, rkey, total;
+};
+
+static SlotLayout slot_layout(const QueryIndexView &ix, int64_t cap) {
+  const int64_t tl = ix.leaf_off[ix.L];
+  SlotLayout s;
+  int64_t o = 0;
+  s.lb2 = o; o = align_up(o + 4 * tl, 256);
+  s.lev = o; o = align_up(o + tl, 256);
+  s.cval = o; o = align_up(o + 4 * ix.max_leaves, 256);
+  s.cand = o; o = align_up(o + 4 * cap, 256);
+  s.key = o; o = align_up(o + 4 * cap, 256);
+  s.rid = o; o = align_up(o + 4 * RR_MAX, 256);
+  s.rkey = o; o = align_up(o + 4 * RR_MAX, 256);
+  s.total = o;
+  return s;
+}
+
+size_t query_slot_bytes(const QueryIndexView &ix, int64_t cand_cap, int) {
+  return (size_t)slot_layout(ix, cand_cap).total;
+}
+
+void query_slot_offsets(const QueryIndexView &ix, int64_t cand_cap, int64_t off[8]) {
+  const SlotLayout l = slot_layout(ix, cand_cap);
+  off[0] = l.lb2; off[1] = l.lev; off[2] = l.cval; off[3] = l.cand;
+  off[4] = l.key; off[5] = l.rid; off[6] = l.rkey; off[7] = l.total;
+}
+
+struct QShared {
+  float T[256];
+  uint32_t H[256];
+  uint32_t rh[256];
+  uint32_t wt[32];
+  uint32_t topk_key[KMAX];
+  uint32_t topk_id[KMAX];
+  // scalars
+  int64_t qi;
+  int jhi, jstar, istar;
+  uint32_t need, ncand, sel_v, sel_below, cut_leaf, nres;
+  int allpts;
+};
+
+__device__ __forceinline__ uint32_t byte_of(const uint4 &c, int j) {
+  const uint32_t w = j < 4 ? c.x : j < 8 ? c.y : j < 12 ? c.z : c.w;
+  return (w >> (8 * (j & 3))) & 255u;
+}
+
+// Smallest radix level with x <= T[level] (T[254] = +inf).
+__device__ __forceinline__ uint32_t level_of(const float *T, float x) {
+  int lo = 0, hi = NLEV - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (x <= T[mid]) hi = mid; else lo = mid + 1;
+  }
+  return (uint32_t)lo;
+}
+
+// Block-wide weighted radix select over 32-bit keys: finds the smallest key
+// v with W(key <= v) >= need, where item i has (key_i, weight_i) from get(i)
+// (weight 0 = absent).  Returns v in sm.sel_v and W(key < v) in sm.sel_below.
+template <class Get>
+__device__ void block_select(int64_t N, Get get, uint32_t need, QShared &sm) {
+  uint32_t prefix = 0, below = 0;
+  for (int shift = 24; shift >= 0; shift -= 8) {
+    sm.rh[threadIdx.x] = 0;
+    __syncthreads();
+    const uint32_t hmask = (shift == 24) ? 0u : (0xffffffffu << (shift + 8));
+    for (int64_t i = threadIdx.x; i < N; i += QT) {
+      uint32_t k, w;
+      get(i, k, w);
+      if (w && (k & hmask) == (prefix & hmask)) atomicAdd(&sm.rh[(k >> shift) & 255u], w);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      uint32_t acc = below;
+      int dg = 255;
+      for (int g = 0; g < 256; ++g) {
+        if (acc + sm.rh[g] >= need) { dg = g; break; }
+        acc += sm.rh[g];
+      }
+      sm.sel_v = prefix | ((uint32_t)dg << shift);
+      sm.sel_below = acc;
+    }
+    __syncthreads();
+    prefix = sm.sel_v;
+    below = sm.sel_below;
+    __syncthreads();
+  }
+}
+
+struct QCtx {
+  const QueryIndexView &ix;
+  const QueryArgs &qa;
+  QShared &sm;
+  float *lut;       // [16][N_r+1]
+  uint32_t *hist;   // [L][256] leaf-size histograms by level
+  int32_t *D;       // [L][256] new-point difference arrays
+  Slot s;
+  int64_t qi;
+};
+
+__device__ __forceinline__ uint32_t leaf_begin_of(const QueryIndexView &ix, int t, int64_t l) {
+  return ix.leaf_begin[ix.leaf_off[t] + t + l];
+}
+
+// Smallest level of point p over trees t' < tlim (255 if none).
+__device__ __forceinline__ uint32_t min_level_before(const QueryIndexView &ix, const Slot &s,
+                                                     uint32_t p, int tlim) {
+  uint32_t f = 255u;
+  const uint32_t *lo = ix.leaf_of + (int64_t)p * ix.L;
+  for (int u = 0; u < tlim; ++u) f = min(f, (uint32_t)s.lev[ix.leaf_off[u] + lo[u]]);
+  return f;
+}
+
+// ---- step 1: leaf lower bounds and levels --------------------------------
+__device__ void leaf_bounds(QCtx &c) {
+  const QueryIndexView &ix = c.ix;
+  const int K = ix.K, NR1 = ix.N_r + 1;
+  const float *qp = c.qa.Qp + c.qi * ix.LK;
+  for (int t = 0; t < ix.L; ++t) {
+    for (int idx = threadIdx.x; idx < K * NR1; idx += QT) {
+      const int j = idx / NR1, z = idx % NR1;
+      c.lut[j * NR1 + z] = __fsub_rn(ix.B[(int64_t)(t * K + j) * NR1 + z], qp[t * K + j]);
+    }
+    __syncthreads();
+    const int64_t nl = ix.leaf_off[t + 1] - ix.leaf_off[t];
+    const uint4 *lo4 = reinterpret_cast<const uint4 *>(ix.leaf_lo) + ix.leaf_off[t];
+    const uint4 *hi4 = reinterpret_cast<const uint4 *>(ix.leaf_hi) + ix.leaf_off[t];
+    for (int64_t l = threadIdx.x; l < nl; l += QT) {
+      const uint4 lo = lo4[l], hi = hi4[l];
+      float acc = 0.0f;
+      for (int j = 0; j < K; ++j) {
+        const float a = c.lut[j * NR1 + byte_of(lo, j)];
+        const float b = -c.lut[j * NR1 + byte_of(hi, j) + 1];
+        const float gap = fmaxf(fmaxf(a, b), 0.0f);
+        acc = __fadd_rn(acc, __fmul_rn(gap, gap));
+      }
+      const uint32_t lv = level_of(c.sm.T, acc);
+      c.s.lb2[ix.leaf_off[t] + l] = acc;
+      c.s.lev[ix.leaf_off[t] + l] = (uint8_t)lv;
+      const uint32_t sz = leaf_begin_of(ix, t, l + 1) - leaf_begin_of(ix, t, l);
+      atomicAdd(&c.hist[t * 256 + lv], sz);
+    }
+    __syncthreads();
+  }
+}
+
+// ---- step 2: owner-rule union counts and per-tree new-point counts -------
+__device__ void union_counts(QCtx &c) {
+  const QueryIndexView &ix = c.ix;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t jhi = (uint32_t)c.sm.jhi;
+  for (int t = 0; t < ix.L; ++t) {
+    const int64_t nl = ix.leaf_off[t + 1] - ix.leaf_off[t];
+    const uint8_t *levt = c.s.lev + ix.leaf_off[t];
+    const uint32_t *permt = ix.perm + (int64_t)t * ix.n;
+    for (int64_t chunk = (int64_t)warp * 32; chunk < nl; chunk += QT) {
+      const int64_t l = chunk + lane;
+      const uint32_t mylv = l < nl ? levt[l] : 255u;
+      unsigned mask = __ballot_sync(FULL, l < nl && mylv <= jhi);
+      while (mask) {
+        const int src = __ffs(mask) - 1;
+        mask &= mask - 1;
+        const int64_t lq = chunk + src;
+        const uint32_t lvt = __shfl_sync(FULL, mylv, src);
+        const uint32_t b = leaf_begin_of(ix, t, lq), e = leaf_begin_of(ix, t, lq + 1);
+        for (uint32_t i = b + lane; i < e; i += 32) {
+          const uint32_t p = permt[i];
+          const uint32_t *lo = ix.leaf_of + (int64_t)p * ix.L;
+          uint32_t m = 255u, f = 255u;
+          int owner = -1;
+          for (int u = 0; u < ix.L; ++u) {
+            const uint32_t lv = (u == t) ? lvt : (uint32_t)c.s.lev[ix.leaf_off[u] + lo[u]];
+            if (lv < m) { m = lv; owner = u; }
+            if (u < t) f = min(f, lv);
+          }
+          if (owner == t) atomicAdd(&c.sm.H[m], 1u);
+          if (f > lvt) {  // new in tree t for levels in [lvt, f)
+            atomicAdd(&c.D[t * 256 + lvt], 1);
+            if (f <= jhi) atomicAdd(&c.D[t * 256 + f], -1);
+          }
+        }
+      }
+    }
+  }
+  __syncthreads();
+}
+
+// ---- step 3: candidate cut inside tree i* and candidate list -------------
+__device__ void cut_and_collect(QCtx &c) {
+  const QueryIndexView &ix = c.ix;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t js = (uint32_t)c.sm.jstar;
+  const int is = c.sm.istar;
+  const int64_t nli = ix.leaf_off[is + 1] - ix.leaf_off[is];
+  const uint8_t *levi = c.s.lev + ix.leaf_off[is];
+  const float *lbi = c.s.lb2 + ix.leaf_off[is];
+  const uint32_t *permi = ix.perm + (int64_t)is * ix.n;
+  // new points of every qualifying leaf of tree i*
+  for (int64_t chunk = (int64_t)warp * 32; chunk < nli; chunk += QT) {
+    const int64_t l = chunk + lane;
+    const bool q = l < nli && levi[l] <= js;
+    if (l < nli) c.s.cval[l] = 0;
+    unsigned mask = __ballot_sync(FULL, q);
+    while (mask) {
+      const int src = __ffs(mask) - 1;
+      mask &= mask - 1;
+      const int64_t lq = chunk + src;
+      const uint32_t b = leaf_begin_of(ix, is, lq), e = leaf_begin_of(ix, is, lq + 1);
+      uint32_t cnt = 0;
+      if (is == 0) {
+        cnt = e - b;
+      } else {
+        for (uint32_t base = b; base < e; base += 32) {
+          const uint32_t i = base + lane;
+          bool nw = false;
+          if (i < e) nw = min_level_before(ix, c.s, permi[i], is) > js;
+          cnt += __popc(__ballot_sync(FULL, nw));
+        }
+      }
+      if (lane == 0) c.s.cval[lq] = cnt;
+    }
+  }
+  __syncthreads();
+  // smallest LB^2 value v whose leaves (lev <= j*) reach the count still needed
+  const uint32_t need = c.sm.need;
+  auto get = [&](int64_t l, uint32_t &k, uint32_t &w) {
+    w = (levi[l] <= js) ? c.s.cval[l] : 0u;
+    k = __float_as_uint(lbi[l]);
+  };
+  block_select(nli, get, need, c.sm);
+  const uint32_t v = c.sm.sel_v;
+  const uint32_t need2 = need - c.sm.sel_below;
+  // among leaves with LB^2 == v, leaf order decides: first prefix reaching need2
+  if (threadIdx.x == 0) c.sm.cut_leaf = 0xffffffffu;
+  __syncthreads();
+  uint32_t run = 0;
+  for (int64_t base = 0; base < nli; base += QT) {
+    const int64_t l = base + threadIdx.x;
+    uint32_t w = 0;
+    if (l < nli && levi[l] <= js && __float_as_uint(lbi[l]) == v) w = c.s.cval[l];
+    uint32_t tot;
+    const uint32_t ex = block_exclusive_scan(w, c.sm.wt, &tot);
+    if (w && run + ex < need2 && run + ex + w >= need2) c.sm.cut_leaf = (uint32_t)l;
+    run += tot;
+    __syncthreads();
+    if (c.sm.cut_leaf != 0xffffffffu) break;
+  }
+  __syncthreads();
+  const uint32_t cut = c.sm.cut_leaf;
+  // collect S: trees before i* whole (new points only), tree i* up to the cut
+  if (threadIdx.x == 0) c.sm.ncand = 0;
+  __syncthreads();
+  for (int t = 0; t <= is; ++t) {
+    const int64_t nl = ix.leaf_off[t + 1] - ix.leaf_off[t];
+    const uint8_t *levt = c.s.lev + ix.leaf_off[t];
+    const float *lbt = c.s.lb2 + ix.leaf_off[t];
+    const uint32_t *permt = ix.perm + (int64_t)t * ix.n;
+    for (int64_t chunk = (int64_t)warp * 32; chunk < nl; chunk += QT) {
+      const int64_t l = chunk + lane;
+      bool q = l < nl && levt[l] <= js;
+      if (q && t == is) {
+        const uint32_t kb = __float_as_uint(lbt[l]);
+        q = kb < v || (kb == v && (uint32_t)l <= cut);
+      }
+      unsigned mask = __ballot_sync(FULL, q);
+      while (mask) {
+        const int src = __ffs(mask) - 1;
+        mask &= mask - 1;
+        const int64_t lq = chunk + src;
+        const uint32_t b = leaf_begin_of(ix, t, lq), e = leaf_begin_of(ix, t, lq + 1);
+        for (uint32_t base = b; base < e; base += 32) {
+          const uint32_t i = base + lane;
+          bool take = false;
+          uint32_t p = 0;
+          if (i < e) {
+            p = permt[i];
+            take = (t == 0) || min_level_before(ix, c.s, p, t) > js;
+          }
+          const unsigned tm = __ballot_sync(FULL, take);
+          uint32_t pos0 = 0;
+          if (lane == 0 && tm) pos0 = atomicAdd(&c.sm.ncand, (uint32_t)__popc(tm));
+          pos0 = __shfl_sync(FULL, pos0, 0);
+          const uint32_t pos = pos0 + __popc(tm & ((1u << lane) - 1u));
+          if (take && pos < (uint32_t)c.qa.cand_cap) c.s.cand[pos] = p;
+        }
+      }
+    }
+  }
+  __syncthreads();
+}
+
+// ---- step 4: distances ----------------------------------------------------
+// FP32: one warp per candidate, lanes over float4 chunks (d % 4 == 0) or
+// scalars; butterfly reduction.  Four candidates per warp in flight.
+__device__ void distances_fp32(QCtx &c, int64_t nc, bool allpts) {
+  const QueryIndexView &ix = c.ix;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int d = ix.d;
+  const float *q = c.qa.Q + c.qi * d;
+  const bool vec = (d & 3) == 0;
+  for (int64_t i0 = (int64_t)warp * 4; i0 < nc; i0 += QW * 4) {
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    uint32_t pid[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int64_t i = i0 + u;
+      pid[u] = i < nc ? (allpts ? (uint32_t)i : c.s.cand[i]) : 0u;
+    }
+    if (vec) {
+      const int d4 = d >> 2;
+      for (int ch = lane; ch < d4; ch += 32) {
+        const float4 qv = reinterpret_cast<const float4 *>(q)[ch];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          if (i0 + u >= nc) continue;
+          const float4 xv = reinterpret_cast<const float4 *>(ix.X + (int64_t)pid[u] * d)[ch];
+          float t0 = __fsub_rn(qv.x, xv.x), t1 = __fsub_rn(qv.y, xv.y);
+          float t2 = __fsub_rn(qv.z, xv.z), t3 = __fsub_rn(qv.w, xv.w);
+          acc[u] = __fmaf_rn(t0, t0, acc[u]);
+          acc[u] = __fmaf_rn(t1, t1, acc[u]);
+          acc[u] = __fmaf_rn(t2, t2, acc[u]);
+          acc[u] = __fmaf_rn(t3, t3, acc[u]);
+        }
+      }
+    } else {
+      for (int ch = lane; ch < d; ch += 32) {
+        const float qv = q[ch];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          if (i0 + u >= nc) continue;
+          const float t0 = __fsub_rn(qv, ix.X[(int64_t)pid[u] * d + ch]);
+          acc[u] = __fmaf_rn(t0, t0, acc[u]);
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) acc[u] = __fadd_rn(acc[u], __shfl_xor_sync(FULL, acc[u], o));
+      if (lane == 0 && i0 + u < nc) c.s.key[i0 + u] = __float_as_uint(acc[u]);
+    }
+  }
+  __syncthreads();
+}
+
+// BF16 scores: rows of 8-element uint4 chunks; a group of G lanes per
+// candidate (G = 8, 16 or 32 by d), 32/G candidates per warp at once.
+__device__ void distances_bf16(QCtx &c, int64_t nc, bool allpts) {
+  const QueryIndexView &ix = c.ix;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int d = ix.d;
+  const int d8 = d >> 3;  // d % 8 == 0 required for this path
+  const int G = d8 <= 8 ? 8 : (d8 <= 16 ? 16 : 32);
+  const int per = 32 / G;
+  const int g = lane / G, gl = lane % G;
+  const uint4 *q8 = reinterpret_cast<const uint4 *>(c.qa.Qh + c.qi * d);
+  for (int64_t i0 = (int64_t)warp * per; i0 < nc; i0 += QW * per) {
+    const int64_t i = i0 + g;
+    float acc = 0.f;
+    if (i < nc) {
+      const uint32_t p = allpts ? (uint32_t)i : c.s.cand[i];
+      const uint4 *x8 = reinterpret_cast<const uint4 *>(ix.Xh + (int64_t)p * d);
+      for (int ch = gl; ch < d8; ch += G) {
+        const uint4 qv = q8[ch], xv = x8[ch];
+        const __nv_bfloat162 *qa = reinterpret_cast<const __nv_bfloat162 *>(&qv);
+        const __nv_bfloat162 *xa = reinterpret_cast<const __nv_bfloat162 *>(&xv);
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+          const float2 qf = __bfloat1622float2(qa[h]), xf = __bfloat1622float2(xa[h]);
+          const float t0 = qf.x - xf.x, t1 = qf.y - xf.y;
+          acc = __fmaf_rn(t0, t0, acc);
+          acc = __fmaf_rn(t1, t1, acc);
+        }
+      }
+    }
+    for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
+    if (gl == 0 && i < nc) c.s.key[i] = __float_as_uint(acc);
+  }
+  __syncthreads();
+}
+
+// ---- step 5: top-k by (key, id) -------------------------------------------
+// Selects the kk smallest (key, id) pairs among n items from get(i) and
+// leaves them sorted in sm.topk_key / sm.topk_id[0..kk).
+template <class Get>
+__device__ void topk_select(int64_t n, int kk, Get get, QShared &sm) {
+  auto gk = [&](int64_t i, uint32_t &k, uint32_t &w) { uint32_t id; get(i, k, id); w = 1u; };
+  block_select(n, gk, (uint32_t)kk, sm);
+  const uint32_t vk = sm.sel_v;
+  const uint32_t below = sm.sel_below;
+  // ties at vk: the (kk - below) smallest ids
+  auto gi = [&](int64_t i, uint32_t &k, uint32_t &w) {
+    uint32_t key, id;
+    get(i, key, id);
+    k = id;
+    w = key == vk ? 1u : 0u;
+  };
+  block_select(n, gi, (uint32_t)kk - below, sm);
+  const uint32_t idcut = sm.sel_v;
+  if (threadIdx.x == 0) sm.nres = 0;
+  __syncthreads();
+  for (int64_t i = threadIdx.x; i < n; i += QT) {
+    uint32_t key, id;
+    get(i, key, id);
+    if (key < vk || (key == vk && id <= idcut)) {
+      const uint32_t pos = atomicAdd(&sm.nres, 1u);
+      if (pos < KMAX) { sm.topk_key[pos] = key; sm.topk_id[pos] = id; }
+    }
+  }
+  __syncthreads();
+  // bitonic sort of the kk results by (key, id), padded to a power of two
+  int np = 1;
+  while (np < kk) np <<= 1;
+  for (int i = kk + threadIdx.x; i < np; i += QT) {
+    sm.topk_key[i] = 0xffffffffu;
+    sm.topk_id[i] = 0xffffffffu;
+  }
+  __syncthreads();
+  for (int size = 2; size <= np; size <<= 1) {
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      for (int i = threadIdx.x; i < np; i += QT) {
+        const int j = i ^ stride;
+        if (j > i) {
+          const bool up = (i & size) == 0;
+          const uint64_t a = ((uint64_t)sm.topk_key[i] << 32) | sm.topk_id[i];
+          const uint64_t b = ((uint64_t)sm.topk_key[j] << 32) | sm.topk_id[j];
+          if ((a > b) == up) {
+            sm.topk_key[i] = (uint32_t)(b >> 32); sm.topk_id[i] = (uint32_t)b;
+            sm.topk_key[j] = (uint32_t)(a >> 32); sm.topk_id[j] = (uint32_t)a;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+__global__ void __launch_bounds__(QT) k_query(QueryIndexView ix, QueryArgs qa) {
+  extern __shared__ __align__(16) uint8_t dsm[];
+  QShared &sm = *reinterpret_cast<QShared *>(dsm);
+  float *lut = reinterpret_cast<float *>(dsm + align_up(sizeof(QShared), 16));
+  uint32_t *hist = reinterpret_cast<uint32_t *>(lut + 16 * (ix.N_r + 1));
+  int32_t *D = reinterpret_cast<int32_t *>(hist + 256 * ix.L);
+
+  uint8_t *base = qa.scratch + (int64_t)blockIdx.x * qa.slot_bytes;
+  Slot s;
+  s.lb2 = reinterpret_cast<float *>(base + qa.off[0]);
+  s.lev = base + qa.off[1];
+  s.cval = reinterpret_cast<uint32_t *>(base + qa.off[2]);
+  s.cand = reinterpret_cast<uint32_t *>(base + qa.off[3]);
+  s.key = reinterpret_cast<uint32_t *>(base + qa.off[4]);
+  s.rid = reinterpret_cast<uint32_t *>(base + qa.off[5]);
+  s.rkey = reinterpret_cast<uint32_t *>(base + qa.off[6]);
+  for (int i = threadIdx.x; i < 256; i += QT) sm.T[i] = i < NLEV ? qa.T[i] : __int_as_float(0x7f800000);
+  __syncthreads();
+
+  while (true) {
+    if (threadIdx.x == 0) sm.qi = atomicAdd(qa.work_counter, 1u);
+    __syncthreads();
+    const int64_t qi = sm.qi;
+    if (qi >= qa.m) break;
+    QCtx c{ix, qa, sm, lut, hist, D, s, qi};
+    const int k = qa.kq ? qa.kq[qi] : qa.k_max;
+    const int64_t tau = qa.tau_base + k;
+    const bool allpts = tau > ix.n;
+    int64_t nc;
+    if (allpts) {
+      // beta*n + k > n: the budget is never met; Alg. 5 stops through its
+      // second condition with S = every point.
+      nc = ix.n;
+      if (threadIdx.x == 0) { sm.jstar = NLEV - 1; sm.istar = -1; }
+    } else {
+      for (int i = threadIdx.x; i < 256 * ix.L; i += QT) { hist[i] = 0; D[i] = 0; }
+      sm.H[threadIdx.x] = 0;
+      __syncthreads();
+      leaf_bounds(c);
+      if (threadIdx.x == 0) {
+        // smallest level where some single tree reaches tau: j* <= jhi
+        uint32_t cum[16];
+        for (int t = 0; t < ix.L; ++t) cum[t] = 0;
+        int jhi = NLEV - 1;
+        for (int j = 0; j < NLEV && jhi == NLEV - 1; ++j) {
+          for (int t = 0; t < ix.L; ++t) {
+            cum[t] += hist[t * 256 + j];
+            if (cum[t] >= (uint64_t)tau) { jhi = j; break; }
+          }
+        }
+        sm.jhi = jhi;
+      }
+      __syncthreads();
+      union_counts(c);
+      if (threadIdx.x == 0) {
+        uint64_t N = 0;
+        int js = sm.jhi;
+        for (int j = 0; j <= sm.jhi; ++j) {
+          N += sm.H[j];
+          if (N >= (uint64_t)tau) { js = j; break; }
+        }
+        int64_t cum = 0, basev = 0;
+        int is = ix.L - 1;
+        for (int t = 0; t < ix.L; ++t) {
+          int64_t nt = 0;
+          for (int j = 0; j <= js; ++j) nt += D[t * 256 + j];
+          if (cum + nt >= tau) { is = t; basev = cum; break; }
+          cum += nt;
+        }
+        sm.jstar = js;
+        sm.istar = is;
+        sm.need = (uint32_t)(tau - basev);
+      }
+      __syncthreads();
+      cut_and_collect(c);
+      nc = sm.ncand;
+      if (nc > qa.cand_cap) {
+        // cannot happen for |S| < beta*n + k + largest leaf; report and skip
+        if (threadIdx.x == 0) atomicExch(qa.err, (int)DETLSH_ERR_CAPACITY);
+        nc = qa.cand_cap;
+      }
+    }
+    if (qa.S_out) {
+      for (int64_t i = threadIdx.x; i < nc && i < qa.S_cap; i += QT)
+        qa.S_out[qi * qa.S_cap + i] = allpts ? i : (int64_t)s.cand[i];
+      if (threadIdx.x == 0) {
+        qa.S_size[qi] = nc;
+        qa.jstar[qi] = sm.jstar + JMIN;
+        qa.istar[qi] = sm.istar;
+        if (nc > qa.S_cap) atomicExch(qa.err, (int)DETLSH_ERR_CAPACITY);
+      }
+    }
+    // verification and top-k
+    if (qa.precision == DETLSH_PREC_BF16_REFINE) {
+      distances_bf16(c, nc, allpts);
+      int R = qa.rerank_mult * k;
+      if (R > RR_MAX) R = RR_MAX;
+      if (R > nc) R = (int)nc;
+      if (R < k) R = k;
+      auto get_s = [&](int64_t i, uint32_t &key, uint32_t &id) {
+        key = s.key[i];
+        id = allpts ? (uint32_t)i : s.cand[i];
+      };
+      // pick the R best BF16 scores (unsorted is enough): threshold select
+      auto gk = [&](int64_t i, uint32_t &kk2, uint32_t &w) { uint32_t id; get_s(i, kk2, id); w = 1u; };
+      block_select(nc, gk, (uint32_t)R, sm);
+      const uint32_t vk = sm.sel_v, below = sm.sel_below;
+      auto gi = [&](int64_t i, uint32_t &kk2, uint32_t &w) {
+        uint32_t key, id;
+        get_s(i, key, id);
+        kk2 = id;
+        w = key == vk ? 1u : 0u;
+      };
+      block_select(nc, gi, (uint32_t)R - below, sm);
+      const uint32_t idcut = sm.sel_v;
+      if (threadIdx.x == 0) sm.nres = 0;
+      __syncthreads();
+      for (int64_t i = threadIdx.x; i < nc; i += QT) {
+        uint32_t key, id;
+        get_s(i, key, id);
+        if (key < vk || (key == vk && id <= idcut)) {
+          const uint32_t pos = atomicAdd(&sm.nres, 1u);
+          if (pos < RR_MAX) s.rid[pos] = id;
+        }
+      }
+      __syncthreads();
+      // exact FP32 distances of the re-rank pool
+      {
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        const int d = ix.d;
+        const float *q = qa.Q + qi * d;
+        for (int r = warp; r < R; r += QW) {
+          const uint32_t p = s.rid[r];
+          float acc = 0.f;
+          if ((d & 3) == 0) {
+            for (int ch = lane; ch < (d >> 2); ch += 32) {
+              const float4 qv = reinterpret_cast<const float4 *>(q)[ch];
+              const float4 xv = reinterpret_cast<const float4 *>(ix.X + (int64_t)p * d)[ch];
+              float t0 = __fsub_rn(qv.x, xv.x), t1 = __fsub_rn(qv.y, xv.y);
+              float t2 = __fsub_rn(qv.z, xv.z), t3 = __fsub_rn(qv.w, xv.w);
+              acc = __fmaf_rn(t0, t0, acc);
+              acc = __fmaf_rn(t1, t1, acc);
+              acc = __fmaf_rn(t2, t2, acc);
+              acc = __fmaf_rn(t3, t3, acc);
+            }
+          } else {
+            for (int ch = lane; ch < d; ch += 32) {
+              const float t0 = __fsub_rn(q[ch], ix.X[(int64_t)p * d + ch]);
+              acc = __fmaf_rn(t0, t0, acc);
+            }
+          }
+          for (int o = 16; o > 0; o >>= 1) acc = __fadd_rn(acc, __shfl_xor_sync(FULL, acc, o));
+          if (lane == 0) s.rkey[r] = __float_as_uint(acc);
+        }
+        __syncthreads();
+      }
+      auto get_r = [&](int64_t i, uint32_t &key, uint32_t &id) { key = s.rkey[i]; id = s.rid[i]; };
+      topk_select(R, k, get_r, sm);
+    } else {
+      distances_fp32(c, nc, allpts);
+      auto get_s = [&](int64_t i, uint32_t &key, uint32_t &id) {
+        key = s.key[i];
+        id = allpts ? (uint32_t)i : s.cand[i];
+      };
+      topk_select(nc, k, get_s, sm);
+    }
+    for (int r = threadIdx.x; r < qa.k_max; r += QT) {
+      if (r < k) {
+        qa.ids[qi * qa.k_max + r] = (int64_t)sm.topk_id[r];
+        qa.dists[qi * qa.k_max + r] = __fsqrt_rn(__uint_as_float(sm.topk_key[r]));
+      } else {
+        qa.ids[qi * qa.k_max + r] = -1;
+        qa.dists[qi * qa.k_max + r] = __int_as_float(0x7f800000);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+static size_t query_smem(const QueryIndexView &ix) {
+  return (size_t)align_up(sizeof(QShared), 16) + sizeof(float) * 16 * (ix.N_r + 1) +
+         sizeof(uint32_t) * 256 * ix.L * 2;
+}
+
+int query_slots(const QueryIndexView &ix) {
+  int dev = 0, sms = 0, per = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const size_t smem = query_smem(ix);
+  cudaFuncSetAttribute(k_query, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_query, QT, smem);
+  if (per < 1) per = 1;
+  return sms * per;
+}
+
+int run_queries(const QueryIndexView &ix, const QueryArgs &qa, cudaStream_t st) {
+  if (qa.m <= 0) return DETLSH_OK;
+  const size_t smem = query_smem(ix);
+  DL_CUDA(cudaFuncSetAttribute(k_query, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  DL_CUDA(cudaMemsetAsync(qa.work_counter, 0, sizeof(uint32_t), st));
+  const int grid = (int)std::min<int64_t>(qa.nslots, qa.m);
+  k_query<<<grid, QT, smem, st>>>(ix, qa);
+  DL_CUDA(cudaGetLastError());
+  return DETLSH_OK;
+}
+
+}  // namespace dl
