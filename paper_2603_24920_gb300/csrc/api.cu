@@ -38,6 +38,9 @@ struct detlsh_index {
   uint32_t *sample = nullptr;
   uint32_t *perm = nullptr, *leaf_begin = nullptr, *leaf_of = nullptr;
   uint8_t *leaf_lo = nullptr, *leaf_hi = nullptr, *leaf_nb = nullptr;
+  uint8_t *blk_lo = nullptr, *blk_hi = nullptr;  // hulls of LEAF_BLOCK-leaf runs
+  int64_t blk_off[17] = {0};
+  uint32_t epoch_next = 1;  // query scratch tags leaf levels with per-query epochs
   std::vector<void *> owned;
   // per-index query buffers, reused across calls (guarded by qmu)
   std::mutex qmu;
@@ -83,13 +86,15 @@ struct TempPool {
   }
 };
 
-int grow(detlsh_index::QBuf &b, size_t bytes) {
+int grow(detlsh_index::QBuf &b, size_t bytes, bool *fresh = nullptr) {
+  if (fresh) *fresh = false;
   if (b.bytes >= bytes && b.p) return DETLSH_OK;
   if (b.p) cudaFree(b.p);
   b.p = nullptr;
   b.bytes = 0;
   DL_CUDA(cudaMalloc(&b.p, bytes ? bytes : 1));
   b.bytes = bytes;
+  if (fresh) *fresh = true;
   return DETLSH_OK;
 }
 
@@ -363,6 +368,17 @@ int build_impl(detlsh_index *ix, const float *data, cudaStream_t st, const detls
     DL_CUDA(cudaMemcpyAsync(ix->leaf_nb + o * 16, t_box[t] + nl * 32, (size_t)nl * 16,
                             cudaMemcpyDeviceToDevice, st));
   }
+  // hulls of runs of LEAF_BLOCK leaves, the coarse level of the range query
+  int64_t tb = 0;
+  for (int t = 0; t < L; ++t) { ix->blk_off[t] = tb; tb += ceil_div(ix->nleaves[t], LEAF_BLOCK); }
+  ix->blk_off[L] = tb;
+  for (int t = L + 1; t <= 16; ++t) ix->blk_off[t] = tb;
+  DL_TRY(dalloc(ix, &ix->blk_lo, (size_t)tb * 16));
+  DL_TRY(dalloc(ix, &ix->blk_hi, (size_t)tb * 16));
+  for (int t = 0; t < L; ++t)
+    DL_TRY(block_hulls(ix->leaf_lo + ix->leaf_off[t] * 16, ix->leaf_hi + ix->leaf_off[t] * 16,
+                       ix->nleaves[t], ix->blk_lo + ix->blk_off[t] * 16,
+                       ix->blk_hi + ix->blk_off[t] * 16, st));
   DL_CUDA(cudaStreamSynchronize(st));
   ix->fb_total = (int64_t)fbt;
   ix->eps2 = eps2_of(K, L);
@@ -383,6 +399,8 @@ QueryIndexView view_of(const detlsh_index *ix) {
   v.n = ix->n; v.d = ix->d; v.L = ix->L; v.K = ix->K; v.LK = ix->LK; v.N_r = ix->N_r;
   v.X = ix->X; v.Xh = ix->Xh; v.B = ix->B; v.perm = ix->perm; v.leaf_begin = ix->leaf_begin;
   v.leaf_lo = ix->leaf_lo; v.leaf_hi = ix->leaf_hi; v.leaf_of = ix->leaf_of;
+  v.blk_lo = ix->blk_lo; v.blk_hi = ix->blk_hi;
+  for (int t = 0; t <= 16; ++t) v.blk_off[t] = ix->blk_off[t];
   for (int t = 0; t <= 16; ++t) v.leaf_off[t] = t <= ix->L ? ix->leaf_off[t] : ix->leaf_off[ix->L];
   v.max_leaves = ix->max_leaves;
   v.max_leaf_size = ix->max_leaf;
@@ -473,14 +491,23 @@ int query_impl(detlsh_index *ix, const float *queries, int64_t m, const int32_t 
   }
   qa.cand_cap = cap;
   query_slot_offsets(v, cap, qa.off);
-  qa.slot_bytes = qa.off[7];
+  qa.slot_bytes = qa.off[11];  // total bytes of one slot
   int slots = query_slots(v);
   slots = (int)std::min<int64_t>(slots, std::max<int64_t>(m, 1));
   // keep the scratch within a quarter of the free device memory
   size_t freeb = 0, totb = 0;
   DL_CUDA(cudaMemGetInfo(&freeb, &totb));
   while (slots > 1 && (size_t)slots * qa.slot_bytes > freeb / 4 + ix->qscratch.bytes) slots /= 2;
-  DL_TRY(grow(ix->qscratch, (size_t)slots * qa.slot_bytes));
+  bool fresh = false;
+  DL_TRY(grow(ix->qscratch, (size_t)slots * qa.slot_bytes, &fresh));
+  // Leaf levels in the scratch carry a per-query epoch (base + query index);
+  // start from zeroed scratch whenever it is new or the epochs would wrap.
+  if (fresh || (uint64_t)ix->epoch_next + (uint64_t)m + 1 >= (1ull << 24)) {
+    DL_CUDA(cudaMemsetAsync(ix->qscratch.p, 0, ix->qscratch.bytes, st));
+    ix->epoch_next = 1;
+  }
+  qa.epoch_base = ix->epoch_next;
+  ix->epoch_next += (uint32_t)m;
   qa.scratch = static_cast<uint8_t *>(ix->qscratch.p);
   qa.nslots = slots;
   qa.work_counter = counter;

@@ -22,6 +22,9 @@ constexpr int JMIN = -127;
 // Codes are stored 16 bytes per (tree, point): K <= 16.
 constexpr int CODE_STRIDE = 16;
 
+// Leaves are grouped in runs of this many (canonical order) under a hull box.
+constexpr int LEAF_BLOCK = 32;
+
 struct U4 {
   uint32_t x, y, z, w;
 };

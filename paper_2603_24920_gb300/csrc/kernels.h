@@ -81,6 +81,9 @@ struct TreeTemp {
 // arrays must hold n entries (n+1 for leaf_begin).
 int build_tree(const TreeBuildArgs &a, TreeTemp &tmp, int64_t *nleaves, int64_t *max_leaf,
                cudaStream_t st);
+// Hull boxes of runs of LEAF_BLOCK leaves: [ceil(nleaves/LEAF_BLOCK)][16] each.
+int block_hulls(const uint8_t *lo, const uint8_t *hi, int64_t nleaves, uint8_t *hlo, uint8_t *hhi,
+                cudaStream_t st);
 
 // ---- queries (query.cu) ----------------------------------------------------
 struct QueryIndexView {
@@ -93,7 +96,9 @@ struct QueryIndexView {
   const uint32_t *leaf_begin;  // concatenated, tree t at leaf_off[t] + t
   const uint8_t *leaf_lo, *leaf_hi;  // [total_leaves][16]
   const uint32_t *leaf_of;   // [n][L]
+  const uint8_t *blk_lo, *blk_hi;  // [total_blocks][16] hulls of LEAF_BLOCK leaves
   int64_t leaf_off[17];      // leaf index offset of each tree (prefix)
+  int64_t blk_off[17];       // block index offset of each tree (prefix)
   int64_t max_leaves;        // max leaves of one tree
   int64_t max_leaf_size;
 };
@@ -117,14 +122,15 @@ struct QueryArgs {
   // scratch: one slot per CTA, offsets from query_slot_offsets
   uint8_t *scratch;
   int64_t slot_bytes;
-  int64_t off[8];
+  int64_t off[12];
   int64_t cand_cap;
+  uint32_t epoch_base;       // leaf levels are tagged (epoch << 8 | level), epoch = base + qi
   int nslots;
   uint32_t *work_counter;
   int *err;
 };
 size_t query_slot_bytes(const QueryIndexView &ix, int64_t cand_cap, int rerank_cap);
-void query_slot_offsets(const QueryIndexView &ix, int64_t cand_cap, int64_t off[8]);
+void query_slot_offsets(const QueryIndexView &ix, int64_t cand_cap, int64_t off[12]);
 int query_slots(const QueryIndexView &ix);
 int run_queries(const QueryIndexView &ix, const QueryArgs &qa, cudaStream_t st);
 

@@ -37,9 +37,13 @@ constexpr int KMAX = 1024;
 constexpr int RR_MAX = 4096;  // re-rank pool of the BF16 path
 
 struct Slot {
-  float *lb2;       // [total_leaves]
-  uint8_t *lev;     // [total_leaves]
-  uint32_t *cval;   // [max_leaves]
+  uint32_t *lev;    // [total_leaves] (epoch << 8) | level of expanded leaves
+  uint8_t *blev;    // [total_blocks] block levels (255 = beyond the bound)
+  uint32_t *border; // [total_blocks] block ids ordered by level
+  uint32_t *lleaf;  // [total_leaves] per-tree lists of expanded leaves (at leaf_off[t])
+  float *llb2;      // [total_leaves]
+  uint8_t *llev;    // [total_leaves]
+  uint32_t *cval;   // [max_leaves] new points per list entry of tree i*
   uint32_t *cand;   // [cap]
   uint32_t *key;    // [cap] order keys of distances
   uint32_t *rid;    // [RR_MAX] re-rank ids
@@ -48,47 +52,39 @@ struct Slot {
 
 __host__ __device__ inline int64_t align_up(int64_t v, int64_t a) { return (v + a - 1) / a * a; }
 
-struct SlotLayout {
-  int64_t lb2, lev, cval, cand, key, rid, rkey, total;
-};
-
-static SlotLayout slot_layout(const QueryIndexView &ix, int64_t cap) {
-  const int64_t tl = ix.leaf_off[ix.L];
-  SlotLayout s;
+static void slot_layout(const QueryIndexView &ix, int64_t cap, int64_t off[12]) {
+  const int64_t tl = ix.leaf_off[ix.L], tb = ix.blk_off[ix.L];
+  const int64_t sz[11] = {4 * tl, tb, 4 * tb, 4 * tl, 4 * tl, tl, 4 * ix.max_leaves,
+                          4 * cap, 4 * cap, 4 * RR_MAX, 4 * RR_MAX};
   int64_t o = 0;
-  s.lb2 = o; o = align_up(o + 4 * tl, 256);
-  s.lev = o; o = align_up(o + tl, 256);
-  s.cval = o; o = align_up(o + 4 * ix.max_leaves, 256);
-  s.cand = o; o = align_up(o + 4 * cap, 256);
-  s.key = o; o = align_up(o + 4 * cap, 256);
-  s.rid = o; o = align_up(o + 4 * RR_MAX, 256);
-  s.rkey = o; o = align_up(o + 4 * RR_MAX, 256);
-  s.total = o;
-  return s;
+  for (int i = 0; i < 11; ++i) { off[i] = o; o = align_up(o + sz[i], 256); }
+  off[11] = o;
 }
 
 size_t query_slot_bytes(const QueryIndexView &ix, int64_t cand_cap, int) {
-  return (size_t)slot_layout(ix, cand_cap).total;
+  int64_t off[12];
+  slot_layout(ix, cand_cap, off);
+  return (size_t)off[11];
 }
 
-void query_slot_offsets(const QueryIndexView &ix, int64_t cand_cap, int64_t off[8]) {
-  const SlotLayout l = slot_layout(ix, cand_cap);
-  off[0] = l.lb2; off[1] = l.lev; off[2] = l.cval; off[3] = l.cand;
-  off[4] = l.key; off[5] = l.rid; off[6] = l.rkey; off[7] = l.total;
+void query_slot_offsets(const QueryIndexView &ix, int64_t cand_cap, int64_t off[12]) {
+  slot_layout(ix, cand_cap, off);
 }
 
 struct QShared {
   float T[256];
   uint32_t H[256];
   uint32_t rh[256];
+  uint32_t bstart[256];
   uint32_t wt[32];
   uint32_t topk_key[KMAX];
   uint32_t topk_id[KMAX];
+  uint32_t nlist[16];
   // scalars
   int64_t qi;
-  int jhi, jstar, istar;
-  uint32_t need, ncand, sel_v, sel_below, cut_leaf, nres;
-  int allpts;
+  int jhi, jstar, istar, jcur, stop;
+  uint32_t need, ncand, sel_v, sel_below, nres, epoch;
+  uint64_t cum;
 };
 
 __device__ __forceinline__ uint32_t byte_of(const uint4 &c, int j) {
@@ -96,7 +92,7 @@ __device__ __forceinline__ uint32_t byte_of(const uint4 &c, int j) {
   return (w >> (8 * (j & 3))) & 255u;
 }
 
-// Smallest radix level with x <= T[level] (T[254] = +inf).
+// Smallest radius level with x <= T[level] (T[254] = +inf).
 __device__ __forceinline__ uint32_t level_of(const float *T, float x) {
   int lo = 0, hi = NLEV - 1;
   while (lo < hi) {
@@ -144,53 +140,142 @@ struct QCtx {
   const QueryArgs &qa;
   QShared &sm;
   float *lut;       // [16][N_r+1]
-  uint32_t *hist;   // [L][256] leaf-size histograms by level
+  uint32_t *hist;   // [L][256] point counts of expanded leaves by level
   int32_t *D;       // [L][256] new-point difference arrays
   Slot s;
   int64_t qi;
+  int64_t tau;
 };
 
 __device__ __forceinline__ uint32_t leaf_begin_of(const QueryIndexView &ix, int t, int64_t l) {
   return ix.leaf_begin[ix.leaf_off[t] + t + l];
 }
 
+// Level of leaf l of tree t for this query; leaves never expanded are
+// beyond the final bound and read as 255.
+__device__ __forceinline__ uint32_t leaf_level(const QueryIndexView &ix, const Slot &s, uint32_t ep,
+                                               int t, uint32_t l) {
+  const uint32_t v = s.lev[ix.leaf_off[t] + l];
+  return (v >> 8) == ep ? (v & 255u) : 255u;
+}
+
 // Smallest level of point p over trees t' < tlim (255 if none).
 __device__ __forceinline__ uint32_t min_level_before(const QueryIndexView &ix, const Slot &s,
-                                                     uint32_t p, int tlim) {
+                                                     uint32_t ep, uint32_t p, int tlim) {
   uint32_t f = 255u;
   const uint32_t *lo = ix.leaf_of + (int64_t)p * ix.L;
-  for (int u = 0; u < tlim; ++u) f = min(f, (uint32_t)s.lev[ix.leaf_off[u] + lo[u]]);
+  for (int u = 0; u < tlim; ++u) f = min(f, leaf_level(ix, s, ep, u, lo[u]));
   return f;
 }
 
-// ---- step 1: leaf lower bounds and levels --------------------------------
-__device__ void leaf_bounds(QCtx &c) {
+// Squared lower bound of a box (Sec. IV-C) from the per-tree table
+// lut[j][z] = B_j[z] - q'_j: per dimension gap = max(0, B(lo) - q, q - B(hi+1)),
+// summed in FP32 over dimensions in order.
+__device__ __forceinline__ float box_lb2(const float *lut, int NR1, int K, const uint4 &lo,
+                                         const uint4 &hi) {
+  float acc = 0.0f;
+  for (int j = 0; j < K; ++j) {
+    const float a = lut[j * NR1 + byte_of(lo, j)];
+    const float b = -lut[j * NR1 + byte_of(hi, j) + 1];
+    const float gap = fmaxf(fmaxf(a, b), 0.0f);
+    acc = __fadd_rn(acc, __fmul_rn(gap, gap));
+  }
+  return acc;
+}
+
+// ---- step 1: range-query levels, expanding leaf blocks in level order ----
+// For tree t: hull levels of every block; blocks at level <= the current
+// bound J are bucketed by level and expanded in ascending order.  A leaf's
+// level is never below its block's, so after expanding the blocks of level
+// <= j the per-level point counts of tree t are complete up to j.  Expansion
+// stops at the first j where tree t alone holds beta*n + k points (that j
+// bounds j* from above) or at J; J shrinks to it.  Every leaf of level <= the
+// final J therefore ends up expanded and listed.
+__device__ void expand_levels(QCtx &c) {
   const QueryIndexView &ix = c.ix;
+  QShared &sm = c.sm;
   const int K = ix.K, NR1 = ix.N_r + 1;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const float *qp = c.qa.Qp + c.qi * ix.LK;
+  const uint32_t ep = sm.epoch;
+  if (threadIdx.x == 0) sm.jhi = NLEV - 1;
+  __syncthreads();
   for (int t = 0; t < ix.L; ++t) {
     for (int idx = threadIdx.x; idx < K * NR1; idx += QT) {
       const int j = idx / NR1, z = idx % NR1;
       c.lut[j * NR1 + z] = __fsub_rn(ix.B[(int64_t)(t * K + j) * NR1 + z], qp[t * K + j]);
     }
+    sm.rh[threadIdx.x] = 0;
+    if (threadIdx.x == 0) { sm.nlist[t] = 0; sm.cum = 0; sm.stop = 0; sm.jcur = NLEV; }
     __syncthreads();
+    const uint32_t J0 = (uint32_t)sm.jhi;
+    const int64_t nb = ix.blk_off[t + 1] - ix.blk_off[t];
     const int64_t nl = ix.leaf_off[t + 1] - ix.leaf_off[t];
-    const uint4 *lo4 = reinterpret_cast<const uint4 *>(ix.leaf_lo) + ix.leaf_off[t];
-    const uint4 *hi4 = reinterpret_cast<const uint4 *>(ix.leaf_hi) + ix.leaf_off[t];
-    for (int64_t l = threadIdx.x; l < nl; l += QT) {
-      const uint4 lo = lo4[l], hi = hi4[l];
-      float acc = 0.0f;
-      for (int j = 0; j < K; ++j) {
-        const float a = c.lut[j * NR1 + byte_of(lo, j)];
-        const float b = -c.lut[j * NR1 + byte_of(hi, j) + 1];
-        const float gap = fmaxf(fmaxf(a, b), 0.0f);
-        acc = __fadd_rn(acc, __fmul_rn(gap, gap));
+    const uint4 *hlo = reinterpret_cast<const uint4 *>(ix.blk_lo) + ix.blk_off[t];
+    const uint4 *hhi = reinterpret_cast<const uint4 *>(ix.blk_hi) + ix.blk_off[t];
+    uint8_t *blev = c.s.blev + ix.blk_off[t];
+    for (int64_t b = threadIdx.x; b < nb; b += QT) {
+      const uint32_t lv = level_of(sm.T, box_lb2(c.lut, NR1, K, hlo[b], hhi[b]));
+      blev[b] = lv <= J0 ? (uint8_t)lv : (uint8_t)255;
+      if (lv <= J0) {
+        atomicAdd(&sm.rh[lv], 1u);
+        atomicMin(&sm.jcur, (int)lv);
       }
-      const uint32_t lv = level_of(c.sm.T, acc);
-      c.s.lb2[ix.leaf_off[t] + l] = acc;
-      c.s.lev[ix.leaf_off[t] + l] = (uint8_t)lv;
-      const uint32_t sz = leaf_begin_of(ix, t, l + 1) - leaf_begin_of(ix, t, l);
-      atomicAdd(&c.hist[t * 256 + lv], sz);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      uint32_t acc = 0;
+      for (int j = 0; j < 256; ++j) { sm.bstart[j] = acc; acc += sm.rh[j]; }
+    }
+    __syncthreads();
+    // bucket the blocks by level (ids in border[bstart[lv] ...])
+    for (int64_t b = threadIdx.x; b < nb; b += QT) {
+      const uint32_t lv = blev[b];
+      if (lv <= J0) {
+        const uint32_t pos = atomicAdd(&sm.bstart[lv], 1u);
+        c.s.border[ix.blk_off[t] + pos] = (uint32_t)b;
+      }
+    }
+    __syncthreads();
+    // bstart[j] now holds the end of bucket j; its start is end - count
+    uint32_t *hist_t = c.hist + t * 256;
+    const uint4 *llo = reinterpret_cast<const uint4 *>(ix.leaf_lo) + ix.leaf_off[t];
+    const uint4 *lhi = reinterpret_cast<const uint4 *>(ix.leaf_hi) + ix.leaf_off[t];
+    for (int j = sm.jcur; j <= (int)J0; ++j) {
+      const uint32_t e = sm.bstart[j], s0 = e - sm.rh[j];
+      const uint32_t Jnow = (uint32_t)sm.jhi;
+      for (uint32_t i = s0 + warp; i < e; i += QW) {
+        const uint32_t b = c.s.border[ix.blk_off[t] + i];
+        const int64_t l = (int64_t)b * LEAF_BLOCK + lane;
+        const bool valid = l < nl;
+        uint32_t lv = 255u;
+        float lb = 0.0f;
+        if (valid) {
+          lb = box_lb2(c.lut, NR1, K, llo[l], lhi[l]);
+          lv = level_of(sm.T, lb);
+          c.s.lev[ix.leaf_off[t] + l] = (ep << 8) | lv;
+          atomicAdd(&hist_t[lv], leaf_begin_of(ix, t, l + 1) - leaf_begin_of(ix, t, l));
+        }
+        const bool keep = valid && lv <= Jnow;
+        const unsigned km = __ballot_sync(FULL, keep);
+        uint32_t p0 = 0;
+        if (lane == 0 && km) p0 = atomicAdd(&sm.nlist[t], (uint32_t)__popc(km));
+        p0 = __shfl_sync(FULL, p0, 0);
+        if (keep) {
+          const uint32_t pos = (uint32_t)ix.leaf_off[t] + p0 + __popc(km & ((1u << lane) - 1u));
+          c.s.lleaf[pos] = (uint32_t)l;
+          c.s.llb2[pos] = lb;
+          c.s.llev[pos] = (uint8_t)lv;
+        }
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        sm.cum += hist_t[j];
+        if (sm.cum >= (uint64_t)c.tau) { sm.jhi = min(sm.jhi, j); sm.stop = 1; }
+        if (j >= sm.jhi) sm.stop = 1;
+      }
+      __syncthreads();
+      if (sm.stop) break;
     }
     __syncthreads();
   }
@@ -200,19 +285,20 @@ __device__ void leaf_bounds(QCtx &c) {
 __device__ void union_counts(QCtx &c) {
   const QueryIndexView &ix = c.ix;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const uint32_t jhi = (uint32_t)c.sm.jhi;
+  const uint32_t jhi = (uint32_t)c.sm.jhi, ep = c.sm.epoch;
   for (int t = 0; t < ix.L; ++t) {
-    const int64_t nl = ix.leaf_off[t + 1] - ix.leaf_off[t];
-    const uint8_t *levt = c.s.lev + ix.leaf_off[t];
+    const int64_t nlist = c.sm.nlist[t];
     const uint32_t *permt = ix.perm + (int64_t)t * ix.n;
-    for (int64_t chunk = (int64_t)warp * 32; chunk < nl; chunk += QT) {
-      const int64_t l = chunk + lane;
-      const uint32_t mylv = l < nl ? levt[l] : 255u;
-      unsigned mask = __ballot_sync(FULL, l < nl && mylv <= jhi);
+    const int64_t lo0 = ix.leaf_off[t];
+    for (int64_t chunk = (int64_t)warp * 32; chunk < nlist; chunk += QT) {
+      const int64_t e_ = chunk + lane;
+      const uint32_t mylv = e_ < nlist ? c.s.llev[lo0 + e_] : 255u;
+      const uint32_t myleaf = e_ < nlist ? c.s.lleaf[lo0 + e_] : 0u;
+      unsigned mask = __ballot_sync(FULL, e_ < nlist && mylv <= jhi);
       while (mask) {
         const int src = __ffs(mask) - 1;
         mask &= mask - 1;
-        const int64_t lq = chunk + src;
+        const uint32_t lq = __shfl_sync(FULL, myleaf, src);
         const uint32_t lvt = __shfl_sync(FULL, mylv, src);
         const uint32_t b = leaf_begin_of(ix, t, lq), e = leaf_begin_of(ix, t, lq + 1);
         for (uint32_t i = b + lane; i < e; i += 32) {
@@ -221,7 +307,7 @@ __device__ void union_counts(QCtx &c) {
           uint32_t m = 255u, f = 255u;
           int owner = -1;
           for (int u = 0; u < ix.L; ++u) {
-            const uint32_t lv = (u == t) ? lvt : (uint32_t)c.s.lev[ix.leaf_off[u] + lo[u]];
+            const uint32_t lv = (u == t) ? lvt : leaf_level(ix, c.s, ep, u, lo[u]);
             if (lv < m) { m = lv; owner = u; }
             if (u < t) f = min(f, lv);
           }
@@ -241,22 +327,22 @@ __device__ void union_counts(QCtx &c) {
 __device__ void cut_and_collect(QCtx &c) {
   const QueryIndexView &ix = c.ix;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const uint32_t js = (uint32_t)c.sm.jstar;
+  const uint32_t js = (uint32_t)c.sm.jstar, ep = c.sm.epoch;
   const int is = c.sm.istar;
-  const int64_t nli = ix.leaf_off[is + 1] - ix.leaf_off[is];
-  const uint8_t *levi = c.s.lev + ix.leaf_off[is];
-  const float *lbi = c.s.lb2 + ix.leaf_off[is];
+  const int64_t li0 = ix.leaf_off[is];
+  const int64_t nli = c.sm.nlist[is];
   const uint32_t *permi = ix.perm + (int64_t)is * ix.n;
-  // new points of every qualifying leaf of tree i*
+  // new points of every qualifying listed leaf of tree i*
   for (int64_t chunk = (int64_t)warp * 32; chunk < nli; chunk += QT) {
-    const int64_t l = chunk + lane;
-    const bool q = l < nli && levi[l] <= js;
-    if (l < nli) c.s.cval[l] = 0;
+    const int64_t e_ = chunk + lane;
+    const bool q = e_ < nli && c.s.llev[li0 + e_] <= js;
+    const uint32_t myleaf = e_ < nli ? c.s.lleaf[li0 + e_] : 0u;
+    if (e_ < nli) c.s.cval[e_] = 0;
     unsigned mask = __ballot_sync(FULL, q);
     while (mask) {
       const int src = __ffs(mask) - 1;
       mask &= mask - 1;
-      const int64_t lq = chunk + src;
+      const uint32_t lq = __shfl_sync(FULL, myleaf, src);
       const uint32_t b = leaf_begin_of(ix, is, lq), e = leaf_begin_of(ix, is, lq + 1);
       uint32_t cnt = 0;
       if (is == 0) {
@@ -265,60 +351,51 @@ __device__ void cut_and_collect(QCtx &c) {
         for (uint32_t base = b; base < e; base += 32) {
           const uint32_t i = base + lane;
           bool nw = false;
-          if (i < e) nw = min_level_before(ix, c.s, permi[i], is) > js;
+          if (i < e) nw = min_level_before(ix, c.s, ep, permi[i], is) > js;
           cnt += __popc(__ballot_sync(FULL, nw));
         }
       }
-      if (lane == 0) c.s.cval[lq] = cnt;
+      if (lane == 0) c.s.cval[chunk + src] = cnt;
     }
   }
   __syncthreads();
-  // smallest LB^2 value v whose leaves (lev <= j*) reach the count still needed
+  // priority order (LB^2, leaf index): smallest LB^2 value v reaching the
+  // count still needed, then the smallest leaf index among LB^2 == v
   const uint32_t need = c.sm.need;
-  auto get = [&](int64_t l, uint32_t &k, uint32_t &w) {
-    w = (levi[l] <= js) ? c.s.cval[l] : 0u;
-    k = __float_as_uint(lbi[l]);
+  auto get_lb = [&](int64_t i, uint32_t &k, uint32_t &w) {
+    w = (c.s.llev[li0 + i] <= js) ? c.s.cval[i] : 0u;
+    k = __float_as_uint(c.s.llb2[li0 + i]);
   };
-  block_select(nli, get, need, c.sm);
+  block_select(nli, get_lb, need, c.sm);
   const uint32_t v = c.sm.sel_v;
   const uint32_t need2 = need - c.sm.sel_below;
-  // among leaves with LB^2 == v, leaf order decides: first prefix reaching need2
-  if (threadIdx.x == 0) c.sm.cut_leaf = 0xffffffffu;
-  __syncthreads();
-  uint32_t run = 0;
-  for (int64_t base = 0; base < nli; base += QT) {
-    const int64_t l = base + threadIdx.x;
-    uint32_t w = 0;
-    if (l < nli && levi[l] <= js && __float_as_uint(lbi[l]) == v) w = c.s.cval[l];
-    uint32_t tot;
-    const uint32_t ex = block_exclusive_scan(w, c.sm.wt, &tot);
-    if (w && run + ex < need2 && run + ex + w >= need2) c.sm.cut_leaf = (uint32_t)l;
-    run += tot;
-    __syncthreads();
-    if (c.sm.cut_leaf != 0xffffffffu) break;
-  }
-  __syncthreads();
-  const uint32_t cut = c.sm.cut_leaf;
+  auto get_id = [&](int64_t i, uint32_t &k, uint32_t &w) {
+    const bool q = c.s.llev[li0 + i] <= js && __float_as_uint(c.s.llb2[li0 + i]) == v;
+    w = q ? c.s.cval[i] : 0u;
+    k = c.s.lleaf[li0 + i];
+  };
+  block_select(nli, get_id, need2, c.sm);
+  const uint32_t cut = c.sm.sel_v;
   // collect S: trees before i* whole (new points only), tree i* up to the cut
   if (threadIdx.x == 0) c.sm.ncand = 0;
   __syncthreads();
   for (int t = 0; t <= is; ++t) {
-    const int64_t nl = ix.leaf_off[t + 1] - ix.leaf_off[t];
-    const uint8_t *levt = c.s.lev + ix.leaf_off[t];
-    const float *lbt = c.s.lb2 + ix.leaf_off[t];
+    const int64_t nlist = c.sm.nlist[t];
+    const int64_t lo0 = ix.leaf_off[t];
     const uint32_t *permt = ix.perm + (int64_t)t * ix.n;
-    for (int64_t chunk = (int64_t)warp * 32; chunk < nl; chunk += QT) {
-      const int64_t l = chunk + lane;
-      bool q = l < nl && levt[l] <= js;
+    for (int64_t chunk = (int64_t)warp * 32; chunk < nlist; chunk += QT) {
+      const int64_t e_ = chunk + lane;
+      bool q = e_ < nlist && c.s.llev[lo0 + e_] <= js;
+      const uint32_t myleaf = e_ < nlist ? c.s.lleaf[lo0 + e_] : 0u;
       if (q && t == is) {
-        const uint32_t kb = __float_as_uint(lbt[l]);
-        q = kb < v || (kb == v && (uint32_t)l <= cut);
+        const uint32_t kb = __float_as_uint(c.s.llb2[lo0 + e_]);
+        q = kb < v || (kb == v && myleaf <= cut);
       }
       unsigned mask = __ballot_sync(FULL, q);
       while (mask) {
         const int src = __ffs(mask) - 1;
         mask &= mask - 1;
-        const int64_t lq = chunk + src;
+        const uint32_t lq = __shfl_sync(FULL, myleaf, src);
         const uint32_t b = leaf_begin_of(ix, t, lq), e = leaf_begin_of(ix, t, lq + 1);
         for (uint32_t base = b; base < e; base += 32) {
           const uint32_t i = base + lane;
@@ -326,7 +403,7 @@ __device__ void cut_and_collect(QCtx &c) {
           uint32_t p = 0;
           if (i < e) {
             p = permt[i];
-            take = (t == 0) || min_level_before(ix, c.s, p, t) > js;
+            take = (t == 0) || min_level_before(ix, c.s, ep, p, t) > js;
           }
           const unsigned tm = __ballot_sync(FULL, take);
           uint32_t pos0 = 0;
@@ -496,13 +573,17 @@ __global__ void __launch_bounds__(QT) k_query(QueryIndexView ix, QueryArgs qa) {
 
   uint8_t *base = qa.scratch + (int64_t)blockIdx.x * qa.slot_bytes;
   Slot s;
-  s.lb2 = reinterpret_cast<float *>(base + qa.off[0]);
-  s.lev = base + qa.off[1];
-  s.cval = reinterpret_cast<uint32_t *>(base + qa.off[2]);
-  s.cand = reinterpret_cast<uint32_t *>(base + qa.off[3]);
-  s.key = reinterpret_cast<uint32_t *>(base + qa.off[4]);
-  s.rid = reinterpret_cast<uint32_t *>(base + qa.off[5]);
-  s.rkey = reinterpret_cast<uint32_t *>(base + qa.off[6]);
+  s.lev = reinterpret_cast<uint32_t *>(base + qa.off[0]);
+  s.blev = base + qa.off[1];
+  s.border = reinterpret_cast<uint32_t *>(base + qa.off[2]);
+  s.lleaf = reinterpret_cast<uint32_t *>(base + qa.off[3]);
+  s.llb2 = reinterpret_cast<float *>(base + qa.off[4]);
+  s.llev = base + qa.off[5];
+  s.cval = reinterpret_cast<uint32_t *>(base + qa.off[6]);
+  s.cand = reinterpret_cast<uint32_t *>(base + qa.off[7]);
+  s.key = reinterpret_cast<uint32_t *>(base + qa.off[8]);
+  s.rid = reinterpret_cast<uint32_t *>(base + qa.off[9]);
+  s.rkey = reinterpret_cast<uint32_t *>(base + qa.off[10]);
   for (int i = threadIdx.x; i < 256; i += QT) sm.T[i] = i < NLEV ? qa.T[i] : __int_as_float(0x7f800000);
   __syncthreads();
 
@@ -511,9 +592,9 @@ __global__ void __launch_bounds__(QT) k_query(QueryIndexView ix, QueryArgs qa) {
     __syncthreads();
     const int64_t qi = sm.qi;
     if (qi >= qa.m) break;
-    QCtx c{ix, qa, sm, lut, hist, D, s, qi};
     const int k = qa.kq ? qa.kq[qi] : qa.k_max;
     const int64_t tau = qa.tau_base + k;
+    QCtx c{ix, qa, sm, lut, hist, D, s, qi, tau};
     const bool allpts = tau > ix.n;
     int64_t nc;
     if (allpts) {
@@ -524,22 +605,9 @@ __global__ void __launch_bounds__(QT) k_query(QueryIndexView ix, QueryArgs qa) {
     } else {
       for (int i = threadIdx.x; i < 256 * ix.L; i += QT) { hist[i] = 0; D[i] = 0; }
       sm.H[threadIdx.x] = 0;
+      if (threadIdx.x == 0) sm.epoch = qa.epoch_base + (uint32_t)qi;
       __syncthreads();
-      leaf_bounds(c);
-      if (threadIdx.x == 0) {
-        // smallest level where some single tree reaches tau: j* <= jhi
-        uint32_t cum[16];
-        for (int t = 0; t < ix.L; ++t) cum[t] = 0;
-        int jhi = NLEV - 1;
-        for (int j = 0; j < NLEV && jhi == NLEV - 1; ++j) {
-          for (int t = 0; t < ix.L; ++t) {
-            cum[t] += hist[t * 256 + j];
-            if (cum[t] >= (uint64_t)tau) { jhi = j; break; }
-          }
-        }
-        sm.jhi = jhi;
-      }
-      __syncthreads();
+      expand_levels(c);
       union_counts(c);
       if (threadIdx.x == 0) {
         uint64_t N = 0;

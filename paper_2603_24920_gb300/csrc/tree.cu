@@ -322,6 +322,42 @@ __global__ void k_leaf_write(LeafWriteArgs a, int64_t F) {
 
 __global__ void k_set_u32(uint32_t *p, uint32_t v) { *p = v; }
 
+// Hull boxes of consecutive runs of LEAF_BLOCK leaves (in canonical order):
+// per dimension the smallest lo and largest hi of the run.  A hull contains
+// every leaf box of its run, so its lower bound bounds theirs from below.
+__global__ void k_block_hulls(const uint8_t *__restrict__ lo, const uint8_t *__restrict__ hi,
+                              int64_t nleaves, int64_t nblocks, uint8_t *hlo, uint8_t *hhi) {
+  const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nblocks) return;
+  uint32_t mn[16], mx[16];
+  for (int j = 0; j < 16; ++j) { mn[j] = 255u; mx[j] = 0u; }
+  const int64_t l1 = nleaves < (b + 1) * LEAF_BLOCK ? nleaves : (b + 1) * LEAF_BLOCK;
+  for (int64_t l = b * LEAF_BLOCK; l < l1; ++l) {
+    const uint4 a = reinterpret_cast<const uint4 *>(lo)[l];
+    const uint4 c = reinterpret_cast<const uint4 *>(hi)[l];
+    for (int j = 0; j < 16; ++j) {
+      mn[j] = min(mn[j], code_byte(a, j));
+      mx[j] = max(mx[j], code_byte(c, j));
+    }
+  }
+  uint32_t w0[4] = {0, 0, 0, 0}, w1[4] = {0, 0, 0, 0};
+  for (int j = 0; j < 16; ++j) {
+    w0[j >> 2] |= mn[j] << (8 * (j & 3));
+    w1[j >> 2] |= mx[j] << (8 * (j & 3));
+  }
+  reinterpret_cast<uint4 *>(hlo)[b] = make_uint4(w0[0], w0[1], w0[2], w0[3]);
+  reinterpret_cast<uint4 *>(hhi)[b] = make_uint4(w1[0], w1[1], w1[2], w1[3]);
+}
+
+int block_hulls(const uint8_t *lo, const uint8_t *hi, int64_t nleaves, uint8_t *hlo, uint8_t *hhi,
+                cudaStream_t st) {
+  const int64_t nb = ceil_div(nleaves, LEAF_BLOCK);
+  if (nb == 0) return DETLSH_OK;
+  k_block_hulls<<<(unsigned)ceil_div(nb, 128), 128, 0, st>>>(lo, hi, nleaves, nb, hlo, hhi);
+  DL_CUDA(cudaGetLastError());
+  return DETLSH_OK;
+}
+
 int build_tree(const TreeBuildArgs &A, TreeTemp &T, int64_t *nleaves, int64_t *max_leaf,
                cudaStream_t st) {
   const int64_t n = A.n;
