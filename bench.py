@@ -1,0 +1,389 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 DET-LSH hot path (build + batched c^2-k-ANN queries).
+
+Workload: the n = 1,000,000 x d = 128 SIFT-like clustered configuration
+(integer values 0-255 stored as fp32, 1,000 centres, sigma 20), 10,000 queries,
+k = 50, L = 4, K = 16, N_r = 256, c = 1.5, max_size = 64, at the operating
+point beta = 0.002 (recall@10 >= 0.9, checked every run against exact FP64
+brute force on 200 queries).  Inputs are seeded and synthetic.
+
+One step = the whole hot path on one batch: build the index from the
+device-resident data (projection, breakpoints, encoding, DE-Trees), then answer
+the 10,000 queries with the BF16+refine path and with the plain FP32 path.
+value = queries/s of the BF16+refine path (device-resident inputs).
+
+Usage: python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+Under torchrun each rank runs its own replica on its own queries (weak
+scaling, no collective on the data path).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+
+CONFIG = "c2"
+BETA = 0.002
+C_RATIO = 1.5
+RECALL_QUERIES = 200
+METRIC = "build Mpts/s; queries/s at recall@10>=0.9, BF16+refine vs plain FP32 path"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--beta", type=float, default=BETA)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)),
+            int(os.environ.get("WORLD_SIZE", 1)))
+
+
+def reduce_max(vals, world):
+    """Element-wise max over ranks of a list of floats (timing only)."""
+    if world == 1:
+        return list(vals)
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor(vals, dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.cpu().tolist()
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def queries_for_rank(cfg, rank):
+    """Rank 0 answers the configuration's queries; rank r > 0 its own batch."""
+    c = workloads.CONFIGS[cfg]
+    stream = 1 if rank == 0 else 100 + rank
+    return workloads.generate(c["kind"], c["m"], c["d"], c["seed"], stream)
+
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region (clocks and throttle reasons)."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu):
+        self.gpu = gpu
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            time.sleep(0.25)
+            self.proc.terminate()
+            self.proc.wait()
+
+    def summary(self):
+        rows = []
+        if self.path and os.path.exists(self.path):
+            for line in open(self.path):
+                p = [x.strip() for x in line.split(",")]
+                if len(p) >= 9:
+                    rows.append(p)
+            os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        return json.load(open(p)), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def recall_at(ids, gt, k):
+    return float(np.mean([len(set(ids[i, :k].tolist()) & set(gt[i, :k].tolist())) / k
+                          for i in range(gt.shape[0])]))
+
+
+def overall_ratio(d, gd, k):
+    r = []
+    for i in range(gd.shape[0]):
+        for j in range(k):
+            r.append(1.0 if gd[i, j] == 0 and d[i, j] == 0 else d[i, j] / max(gd[i, j], 1e-30))
+    return float(np.mean(r))
+
+
+def exact_knn_fp64(torch, Xd, Q, k):
+    """Ground truth for recall: exact FP64 brute force (plain PyTorch)."""
+    Qd = torch.from_numpy(Q).to(Xd.device, torch.float64)
+    ids, ds = [], []
+    for i in range(0, Qd.shape[0], 25):
+        dd = torch.cdist(Qd[i:i + 25], Xd, compute_mode="donot_use_mm_for_euclid_dist")
+        v, ix = torch.topk(dd, k, largest=False)
+        ids.append(ix.cpu())
+        ds.append(v.cpu())
+    return torch.cat(ids).numpy(), torch.cat(ds).numpy()
+
+
+def cpu_baseline(X, Q, k, beta, nq=64):
+    """The oracle as it stands, on the host cores: full-data build + nq queries."""
+    import oracle
+    t0 = time.perf_counter()
+    ix = oracle.Index(X, L=4, K=16, N_r=256, seed=0, frac=0.1, M=64)
+    tb = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    ix.query_batch(Q[:nq], k, beta=beta, c=C_RATIO)
+    tq = time.perf_counter() - t0
+    cores = os.cpu_count()
+    return {"value": nq / tq, "unit": "queries/s", "cores": cores, "kind": "oracle",
+            "build_mpts_s": X.shape[0] / tb / 1e6,
+            "sample": "oracle index built on all %d points (%.1f s), then %d of the %d queries "
+                      "(OpenMP over queries, %d threads, %.1f s)"
+                      % (X.shape[0], tb, nq, Q.shape[0], cores, tq)}
+
+
+def run_reference(args):
+    """Reference arm: the CPU oracle, timed on the host cores."""
+    rank, _, world = dist_env()
+    if rank != 0:
+        return
+    cfg = workloads.CONFIGS[CONFIG]
+    X = workloads.generate(cfg["kind"], cfg["n"], cfg["d"], cfg["seed"], 0)
+    Q = queries_for_rank(CONFIG, 0)
+    k = cfg["k"]
+    import oracle
+    t0 = time.perf_counter()
+    ix = oracle.Index(X, L=4, K=16, N_r=256, seed=0, frac=0.1, M=64)
+    tb = time.perf_counter() - t0
+    per_step = 32
+    times = []
+    for s in range(args.warmup + args.steps):
+        lo = (s * per_step) % Q.shape[0]
+        t0 = time.perf_counter()
+        ix.query_batch(Q[lo:lo + per_step], k, beta=args.beta, c=C_RATIO)
+        if s >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    value = per_step * len(times) / sum(times)
+    cores = os.cpu_count()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "queries/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": config_dict(args.beta),
+        "build_mpts_s": cfg["n"] / tb / 1e6,
+        "cpu_baseline": {"value": value, "unit": "queries/s", "cores": cores, "kind": "oracle",
+                         "sample": "oracle built on all %d points; each step answers %d "
+                                   "queries (OpenMP, %d threads)" % (cfg["n"], per_step, cores)},
+        "e2e": {"value": value, "unit": "queries/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def config_dict(beta):
+    c = workloads.CONFIGS[CONFIG]
+    return {"workload": "SIFT-like clustered n=1e6 d=128 (ints 0-255 as fp32), 10k queries, k=50",
+            "n": c["n"], "d": c["d"], "queries": c["m"], "k": c["k"], "L": 4, "K": 16,
+            "N_r": 256, "max_size": 64, "beta": beta, "c": C_RATIO,
+            "l2": "inputs larger than L2 (fp32 data 512 MB, bf16 copy 256 MB)"}
+
+
+def run_gb300(args):
+    import torch
+    rank, local, world = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_2603_24920_gb300 import detlsh as D
+    D.lib()
+
+    cfg = workloads.CONFIGS[CONFIG]
+    X = workloads.generate(cfg["kind"], cfg["n"], cfg["d"], cfg["seed"], 0)
+    Q = queries_for_rank(CONFIG, rank)
+    n, d, m, k = X.shape[0], X.shape[1], Q.shape[0], cfg["k"]
+    Xd = torch.from_numpy(X).cuda()
+    Qd = torch.from_numpy(Q).cuda()
+    st = torch.cuda.current_stream()
+    kw = dict(L=4, K=16, N_r=256, seed=0, max_size=64, stream=st)
+
+    def step():
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        e[0].record(st)
+        h = D.detlsh_build(Xd, **kw)
+        e[1].record(st)
+        tb = D.detlsh_get_timings(h)
+        ib, db = D.detlsh_query_ex(h, Qd, k, beta=args.beta, c=C_RATIO,
+                                   precision=D.PREC_BF16_REFINE, stream=st)
+        e[2].record(st)
+        tq_b = D.detlsh_get_timings(h)
+        i32, d32 = D.detlsh_query_ex(h, Qd, k, beta=args.beta, c=C_RATIO,
+                                     precision=D.PREC_FP32, stream=st)
+        e[3].record(st)
+        tq_f = D.detlsh_get_timings(h)
+        torch.cuda.synchronize()
+        info = D.detlsh_get_info(h)
+        D.detlsh_free(h)
+        ms = [e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2]), e[2].elapsed_time(e[3])]
+        return ms, tb, tq_b, tq_f, info, (ib, db, i32, d32)
+
+    # quality at the operating point (untimed): exact FP64 ground truth
+    _, _, _, _, info, (ib, db, i32, d32) = step()
+    gt_ids, gt_d = exact_knn_fp64(torch, Xd.double(), Q[:RECALL_QUERIES], k)
+    ib, db = ib[:RECALL_QUERIES].cpu().numpy(), db[:RECALL_QUERIES].cpu().numpy()
+    i32, d32 = i32[:RECALL_QUERIES].cpu().numpy(), d32[:RECALL_QUERIES].cpu().numpy()
+    quality = {"recall_at_10_bf16": recall_at(ib, gt_ids, 10),
+               "recall_at_10_fp32": recall_at(i32, gt_ids, 10),
+               "recall_at_k_bf16": recall_at(ib, gt_ids, k),
+               "recall_at_k_fp32": recall_at(i32, gt_ids, k),
+               "overall_ratio_bf16": overall_ratio(db, gt_d, k),
+               "overall_ratio_fp32": overall_ratio(d32, gt_d, k),
+               "recall_queries": RECALL_QUERIES}
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    barrier(world)
+    torch.cuda.synchronize()
+    recs = []
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            recs.append(step())
+        torch.cuda.synchronize()
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks = clk.summary()
+
+    t_build = [r[0][0] for r in recs]
+    t_qb = [r[0][1] for r in recs]
+    t_qf = [r[0][2] for r in recs]
+    mean = lambda v: sum(v) / len(v)  # noqa: E731
+    tmax = reduce_max([mean(t_build), mean(t_qb), mean(t_qf),
+                       mean([a + b + c for a, b, c in zip(t_build, t_qb, t_qf)])], world)
+    value = world * m / (tmax[1] / 1e3)
+    plain_qps = world * m / (tmax[2] / 1e3)
+    build_mpts = world * n / (tmax[0] / 1e3) / 1e6
+    launches = sum(r[1].build_launches + r[2].query_launches + r[3].query_launches for r in recs)
+
+    # dominant kernel: the persistent query kernel (BF16+refine call)
+    tb, tqb = recs[-1][1], recs[-1][2]
+    kern_ms = mean([r[2].query_kernel_ms for r in recs])
+    R = min(4 * k, 4096)
+    alg_bytes = (32.0 * (tqb.query_blocks + tqb.query_leaves)
+                 + tqb.query_points_visited * (4.0 + 4.0 * 4)
+                 + tqb.query_candidates * (2.0 * d + 4.0)
+                 + tqb.query_count * (R * 4.0 * d + 2.0 * d))
+    peaks, src = measured_peaks()
+    achieved = alg_bytes / (kern_ms / 1e3) / 1e9
+    shares = {"query_kernel_ms": kern_ms,
+              "query_kernel_fp32_ms": mean([r[3].query_kernel_ms for r in recs]),
+              "build_ms": mean([r[1].build_ms for r in recs]),
+              "build_stages_ms": {"sample": tb.sample_ms, "breakpoints": tb.breakpoints_ms,
+                                  "encode": tb.encode_ms, "trees": tb.trees_ms}}
+
+    # end to end through the C-ABI with pinned host buffers
+    Xh = torch.from_numpy(X).pin_memory()
+    Qh = torch.from_numpy(Q).pin_memory()
+    ids_h = torch.empty((m, k), dtype=torch.int64).pin_memory()
+    d_h = torch.empty((m, k), dtype=torch.float32).pin_memory()
+    e2e_q, e2e_b = [], []
+    for s in range(args.warmup + args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        h = D.detlsh_build(Xh, L=4, K=16, N_r=256, seed=0, max_size=64)
+        t1 = time.perf_counter()
+        D.detlsh_query_ex(h, Qh, k, beta=args.beta, c=C_RATIO, precision=D.PREC_BF16_REFINE,
+                          ids=ids_h, dists=d_h)
+        t2 = time.perf_counter()
+        D.detlsh_free(h)
+        if s >= args.warmup:
+            e2e_b.append(t1 - t0)
+            e2e_q.append(t2 - t1)
+    e2e_max = reduce_max([mean(e2e_q), mean(e2e_b)], world)
+
+    if rank != 0:
+        return
+    cpu = None
+    if not args.no_cpu_baseline:
+        cpu = cpu_baseline(X, Q, k, args.beta)
+    line = {
+        "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": tmax[3],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
+        "data": "synthetic", "config": config_dict(args.beta),
+        "build_mpts_s": build_mpts, "plain_fp32_qps": plain_qps,
+        "bf16_over_fp32": value / plain_qps,
+        "quality": quality,
+        "timings_ms": shares,
+        "gpu_launches": int(launches),
+        "roofline": {"kernel": "k_query (BF16+refine)", "bound": "hbm", "achieved": achieved,
+                     "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
+                     "peak_source": src, "traffic": None,
+                     "algorithmic_bytes_per_launch": alg_bytes,
+                     "launch_ms": kern_ms},
+        "e2e": {"value": m * world / e2e_max[0], "unit": "queries/s",
+                "h2d_bytes_per_step": int(m * d * 4), "d2h_bytes_per_step": int(m * k * 12),
+                "build_mpts_s": n * world / e2e_max[1] / 1e6,
+                "build_h2d_bytes": int(n * d * 4)},
+        "clocks": clocks,
+        "cpu_baseline": cpu,
+        "index": {"leaves_per_tree": list(info.num_leaves)[:4], "max_leaf": info.max_leaf_size,
+                  "device_bytes": info.device_bytes,
+                  "projection_fallbacks": info.projection_fallbacks},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gb300(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -161,6 +161,28 @@ int detlsh_get_tree(const detlsh_index *ix, int32_t t, int64_t *perm, int64_t *l
                     uint8_t *box_lo, uint8_t *box_hi, uint8_t *nbits, int64_t *leaf_of);
 /* Squared-radius grid T(j) = fp32(eps^2 c^(2j)), j = -127..127, T(127) = inf. */
 int detlsh_get_level_table(const detlsh_index *ix, double c, float *T);
+/* Device times (CUDA events on the caller's stream) of the last build and of
+ * the last query call on this index, the number of kernels each launched,
+ * and the work the last query call did. */
+typedef struct {
+    float build_ms;            /* whole build                                   */
+    float sample_ms;           /* Bernoulli sample + sample projections         */
+    float breakpoints_ms;      /* radix sort of the sample columns + extraction */
+    float encode_ms;           /* projections of all n points + region codes    */
+    float trees_ms;            /* L DE-Tree layouts + leaf-run hulls            */
+    float query_ms;            /* whole last query call (device part)           */
+    float query_project_ms;    /* query projections                             */
+    float query_kernel_ms;     /* the persistent query kernel                   */
+    int64_t build_launches;    /* kernels launched by the build                 */
+    int64_t query_launches;    /* kernels launched by the last query call       */
+    int64_t query_count;       /* queries in the last call                      */
+    int64_t query_candidates;  /* sum of |S| over those queries                 */
+    int64_t query_leaves;      /* leaves whose bound was computed (expanded)    */
+    int64_t query_blocks;      /* leaf-run hulls whose bound was computed       */
+    int64_t query_points_visited; /* leaf points visited by the union counts   */
+} detlsh_timings;
+int detlsh_get_timings(const detlsh_index *ix, detlsh_timings *t);
+
 /* Exact FP32 projections of m rows with the index's A (m x L*K, host or
  * device in/out), the same kernels the build uses. */
 int detlsh_project(const detlsh_index *ix, const float *rows, int64_t m, float *out,

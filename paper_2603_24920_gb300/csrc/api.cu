@@ -12,7 +12,12 @@
 #include "kernels.h"
 
 // ---------------------------------------------------------------------------
+#include <atomic>
+
 static thread_local char g_last_cuda[256];
+static std::atomic<long long> g_launches{0};
+
+void dl_count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 void dl_set_last_cuda_error(cudaError_t e, const char *what, const char *file, int line) {
   snprintf(g_last_cuda, sizeof g_last_cuda, "%s: %s (%s:%d)", cudaGetErrorString(e), what, file,
@@ -41,6 +46,8 @@ struct detlsh_index {
   uint8_t *blk_lo = nullptr, *blk_hi = nullptr;  // hulls of LEAF_BLOCK-leaf runs
   int64_t blk_off[17] = {0};
   uint32_t epoch_next = 1;  // query scratch tags leaf levels with per-query epochs
+  cudaEvent_t ev[8] = {nullptr};
+  detlsh_timings timings{};
   std::vector<void *> owned;
   // per-index query buffers, reused across calls (guarded by qmu)
   std::mutex qmu;
@@ -198,6 +205,21 @@ __global__ void k_f32_to_bf16(const float *s, __nv_bfloat16 *d, int64_t count) {
     d[i] = __float2bfloat16_rn(s[i]);
 }
 
+int ensure_events(detlsh_index *ix) {
+  for (auto &e : ix->ev)
+    if (!e) DL_CUDA(cudaEventCreate(&e));
+  return DETLSH_OK;
+}
+
+float ev_ms(cudaEvent_t a, cudaEvent_t b) {
+  float ms = 0.0f;
+  if (cudaEventElapsedTime(&ms, a, b) != cudaSuccess) {
+    cudaGetLastError();
+    return -1.0f;
+  }
+  return ms;
+}
+
 int check_err(int *err_dev, cudaStream_t st) {
   int h = 0;
   DL_CUDA(cudaMemcpyAsync(&h, err_dev, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -223,6 +245,9 @@ int build_impl(detlsh_index *ix, const float *data, cudaStream_t st, const detls
   const int64_t n = ix->n;
   const int d = ix->d, L = ix->L, K = ix->K, LK = ix->LK, N_r = ix->N_r;
   TempPool tp;
+  DL_TRY(ensure_events(ix));
+  const long long launches0 = g_launches.load();
+  DL_CUDA(cudaEventRecord(ix->ev[0], st));
   // data copy (the index keeps its own FP32 rows for verification)
   DL_TRY(dalloc(ix, &ix->X, (size_t)n * d));
   DL_TRY(copy_in(ix->X, data, sizeof(float) * (size_t)n * d, st));
@@ -255,6 +280,7 @@ int build_impl(detlsh_index *ix, const float *data, cudaStream_t st, const detls
   DL_TRY(sample_ids(n, ix->seed, ix->frac, ix->sample, blk, &m, st));
   if (m < 2 * (int64_t)N_r) {
     k_iota<<<(unsigned)std::min<int64_t>(ceil_div(n, 256), 4096), 256, 0, st>>>(ix->sample, n);
+    dl_count_launch();
     DL_CUDA(cudaGetLastError());
     m = n;
   }
@@ -269,6 +295,7 @@ int build_impl(detlsh_index *ix, const float *data, cudaStream_t st, const detls
   DL_TRY(project_rows(ix->X, d, ix->sample, m, d, ix->A, LK, 1, ps, st));
   int e = check_err(err, st);
   if (e) return e;
+  DL_CUDA(cudaEventRecord(ix->ev[1], st));
   DL_TRY(float_to_keys(Ps, (int64_t)LK * m, st));
   SortTemp srt;
   const size_t cnt_cap = std::max<size_t>((size_t)LK * 256 * sort_tiles(m), 256 * sort_tiles(n));
@@ -281,18 +308,21 @@ int build_impl(detlsh_index *ix, const float *data, cudaStream_t st, const detls
   DL_TRY(dalloc(ix, &ix->B, (size_t)LK * (N_r + 1)));
   DL_TRY(extract_breakpoints(reinterpret_cast<uint32_t *>(Ps), LK, m, N_r, ix->B, st));
 
+  DL_CUDA(cudaEventRecord(ix->ev[2], st));
   // ---- all projections, encoded (Alg. 1), and column min/max ----
   DL_TRY(dalloc(ix, &ix->codes, (size_t)L * n * CODE_STRIDE));
   DL_CUDA(cudaMemsetAsync(ix->codes, 0, (size_t)L * n * CODE_STRIDE, st));
   uint32_t *minmax = nullptr;
   DL_TRY(tp.get(&minmax, (size_t)2 * LK));
   k_fill_minmax<<<(unsigned)ceil_div(LK, 128), 128, 0, st>>>(minmax, LK);
+  dl_count_launch();
   ProjArgs pe = pa;
   pe.codes = ix->codes; pe.n = n; pe.B = ix->B; pe.N_r = N_r; pe.K = K; pe.minmax = minmax;
   DL_TRY(project_rows(ix->X, d, nullptr, n, d, ix->A, LK, 2, pe, st));
   e = check_err(err, st);
   if (e) return e;
   DL_TRY(finish_breakpoint_ends(minmax, LK, N_r, ix->B, st));
+  DL_CUDA(cudaEventRecord(ix->ev[3], st));
   if (p->keep_projections) {
     DL_TRY(dalloc(ix, &ix->P, (size_t)n * LK));
     ProjArgs pp = pa;
@@ -379,15 +409,24 @@ int build_impl(detlsh_index *ix, const float *data, cudaStream_t st, const detls
     DL_TRY(block_hulls(ix->leaf_lo + ix->leaf_off[t] * 16, ix->leaf_hi + ix->leaf_off[t] * 16,
                        ix->nleaves[t], ix->blk_lo + ix->blk_off[t] * 16,
                        ix->blk_hi + ix->blk_off[t] * 16, st));
+  DL_CUDA(cudaEventRecord(ix->ev[4], st));
   DL_CUDA(cudaStreamSynchronize(st));
   ix->fb_total = (int64_t)fbt;
   ix->eps2 = eps2_of(K, L);
+  ix->timings.build_ms = ev_ms(ix->ev[0], ix->ev[4]);
+  ix->timings.sample_ms = ev_ms(ix->ev[0], ix->ev[1]);
+  ix->timings.breakpoints_ms = ev_ms(ix->ev[1], ix->ev[2]);
+  ix->timings.encode_ms = ev_ms(ix->ev[2], ix->ev[3]);
+  ix->timings.trees_ms = ev_ms(ix->ev[3], ix->ev[4]);
+  ix->timings.build_launches = g_launches.load() - launches0;
   return DETLSH_OK;
 }
 
 void free_index(detlsh_index *ix) {
   if (!ix) return;
   for (void *q : ix->owned) cudaFree(q);
+  for (auto &e : ix->ev)
+    if (e) cudaEventDestroy(e);
   for (auto *b : {&ix->qQ, &ix->qQh, &ix->qQp, &ix->qk, &ix->qids, &ix->qdists, &ix->qT,
                   &ix->qscratch, &ix->qstat, &ix->qS, &ix->qfb})
     if (b->p) cudaFree(b->p);
@@ -426,6 +465,8 @@ int query_impl(detlsh_index *ix, const float *queries, int64_t m, const int32_t 
                float *dists, int64_t S_cap, int64_t *S, int64_t *S_size, int32_t *jstar,
                int32_t *istar) {
   const int d = ix->d, LK = ix->LK;
+  DL_TRY(ensure_events(ix));
+  const long long launches0 = g_launches.load();
   std::vector<int32_t> kh;
   if (kq) {
     kh.resize((size_t)m);
@@ -446,6 +487,8 @@ int query_impl(detlsh_index *ix, const float *queries, int64_t m, const int32_t 
   uint32_t *fb_count = reinterpret_cast<uint32_t *>(static_cast<char *>(ix->qstat.p) + 16);
   uint32_t *counter = reinterpret_cast<uint32_t *>(static_cast<char *>(ix->qstat.p) + 32);
   DL_CUDA(cudaMemsetAsync(ix->qstat.p, 0, 256, st));
+  unsigned long long *stats = reinterpret_cast<unsigned long long *>(static_cast<char *>(ix->qstat.p) + 64);
+  DL_CUDA(cudaEventRecord(ix->ev[5], st));
   DL_TRY(copy_in(Q, queries, sizeof(float) * (size_t)m * d, st));
   // exact query projections q'_i = H_i(q) (Alg. 5)
   const uint32_t fb_cap = (uint32_t)std::max<int64_t>(1024, m * LK / 64);
@@ -512,11 +555,25 @@ int query_impl(detlsh_index *ix, const float *queries, int64_t m, const int32_t 
   qa.nslots = slots;
   qa.work_counter = counter;
   qa.err = err;
+  qa.stats = stats;
   int e = check_err(err, st);  // projection status (non-finite queries)
   if (e) return e;
+  DL_CUDA(cudaEventRecord(ix->ev[6], st));
   DL_TRY(run_queries(v, qa, st));
+  DL_CUDA(cudaEventRecord(ix->ev[7], st));
   e = check_err(err, st);
   if (e) return e;
+  unsigned long long hs[4];
+  DL_CUDA(cudaMemcpy(hs, stats, sizeof hs, cudaMemcpyDeviceToHost));
+  ix->timings.query_project_ms = ev_ms(ix->ev[5], ix->ev[6]);
+  ix->timings.query_kernel_ms = ev_ms(ix->ev[6], ix->ev[7]);
+  ix->timings.query_ms = ev_ms(ix->ev[5], ix->ev[7]);
+  ix->timings.query_launches = g_launches.load() - launches0;
+  ix->timings.query_count = m;
+  ix->timings.query_candidates = (int64_t)hs[0];
+  ix->timings.query_leaves = (int64_t)hs[1];
+  ix->timings.query_blocks = (int64_t)hs[2];
+  ix->timings.query_points_visited = (int64_t)hs[3];
   if (ids) DL_TRY(copy_out(ids, qa.ids, sizeof(int64_t) * (size_t)m * k_max, st));
   if (dists) DL_TRY(copy_out(dists, qa.dists, sizeof(float) * (size_t)m * k_max, st));
   if (S) {
@@ -535,6 +592,7 @@ namespace dl {
 int f32_to_bf16(const float *src, __nv_bfloat16 *dst, int64_t count, cudaStream_t st) {
   if (count <= 0) return DETLSH_OK;
   k_f32_to_bf16<<<(unsigned)std::min<int64_t>(ceil_div(count, 256), 8192), 256, 0, st>>>(src, dst, count);
+  dl_count_launch();
   DL_CUDA(cudaGetLastError());
   return DETLSH_OK;
 }
@@ -742,6 +800,12 @@ int detlsh_get_tree(const detlsh_index *ix, int32_t t, int64_t *perm, int64_t *l
     DL_CUDA(cudaMemcpy(h.data(), ix->leaf_of, 4 * h.size(), cudaMemcpyDeviceToHost));
     for (int64_t i = 0; i < n; ++i) leaf_of[i] = h[(size_t)i * ix->L + t];
   }
+  return DETLSH_OK;
+}
+
+int detlsh_get_timings(const detlsh_index *ix, detlsh_timings *t) {
+  if (!ix || !t) return DETLSH_ERR_INVALID_ARG;
+  *t = ix->timings;
   return DETLSH_OK;
 }
 

@@ -79,3 +79,6 @@ __host__ __device__ inline int64_t ceil_div(int64_t a, int64_t b) { return (a + 
   } while (0)
 
 void dl_set_last_cuda_error(cudaError_t e, const char *what, const char *file, int line);
+
+// Counts kernel launches made by the library (reported by detlsh_get_timings).
+void dl_count_launch();

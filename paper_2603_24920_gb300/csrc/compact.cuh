@@ -79,8 +79,11 @@ int compact(int64_t n, Flag f, uint32_t *block_counts, uint32_t *out, uint32_t *
     return DETLSH_OK;
   }
   k_compact_count<<<(unsigned)nb, CP_THREADS, 0, st>>>(n, f, block_counts);
+  dl_count_launch();
   k_scan_counts<<<1, 1024, 0, st>>>(block_counts, nb, count);
+  dl_count_launch();
   k_compact_write<<<(unsigned)nb, CP_THREADS, 0, st>>>(n, f, block_counts, out);
+  dl_count_launch();
   DL_CUDA(cudaGetLastError());
   return DETLSH_OK;
 }

@@ -128,6 +128,7 @@ struct QueryArgs {
   int nslots;
   uint32_t *work_counter;
   int *err;
+  unsigned long long *stats;  // [4]: candidates, leaves expanded, hull blocks, points visited
 };
 size_t query_slot_bytes(const QueryIndexView &ix, int64_t cand_cap, int rerank_cap);
 void query_slot_offsets(const QueryIndexView &ix, int64_t cand_cap, int64_t off[12]);

@@ -340,8 +340,10 @@ static int project_impl(const float *X, int64_t ldx, const uint32_t *rows, int64
                                  (int)dyn));
   }
   k_project<MODE><<<grid, PJ_THREADS, dyn, st>>>(X, ldx, rows, nrows, d, A, LK, W, o);
+  dl_count_launch();
   DL_CUDA(cudaGetLastError());
   k_project_exact<MODE><<<256, 128, 0, st>>>(X, ldx, rows, nrows, d, A, LK, o);
+  dl_count_launch();
   DL_CUDA(cudaGetLastError());
   return DETLSH_OK;
 }

@@ -85,6 +85,7 @@ struct QShared {
   int jhi, jstar, istar, jcur, stop;
   uint32_t need, ncand, sel_v, sel_below, nres, epoch;
   uint64_t cum;
+  unsigned long long n_blocks, n_leaves, n_visit;  // work counters of this CTA
 };
 
 __device__ __forceinline__ uint32_t byte_of(const uint4 &c, int j) {
@@ -214,6 +215,7 @@ __device__ void expand_levels(QCtx &c) {
     const uint4 *hlo = reinterpret_cast<const uint4 *>(ix.blk_lo) + ix.blk_off[t];
     const uint4 *hhi = reinterpret_cast<const uint4 *>(ix.blk_hi) + ix.blk_off[t];
     uint8_t *blev = c.s.blev + ix.blk_off[t];
+    if (threadIdx.x == 0) sm.n_blocks += (unsigned long long)nb;
     for (int64_t b = threadIdx.x; b < nb; b += QT) {
       const uint32_t lv = level_of(sm.T, box_lb2(c.lut, NR1, K, hlo[b], hhi[b]));
       blev[b] = lv <= J0 ? (uint8_t)lv : (uint8_t)255;
@@ -258,6 +260,8 @@ __device__ void expand_levels(QCtx &c) {
         }
         const bool keep = valid && lv <= Jnow;
         const unsigned km = __ballot_sync(FULL, keep);
+        const unsigned vm = __ballot_sync(FULL, valid);
+        if (lane == 0) atomicAdd(&sm.n_leaves, (unsigned long long)__popc(vm));
         uint32_t p0 = 0;
         if (lane == 0 && km) p0 = atomicAdd(&sm.nlist[t], (uint32_t)__popc(km));
         p0 = __shfl_sync(FULL, p0, 0);
@@ -301,6 +305,7 @@ __device__ void union_counts(QCtx &c) {
         const uint32_t lq = __shfl_sync(FULL, myleaf, src);
         const uint32_t lvt = __shfl_sync(FULL, mylv, src);
         const uint32_t b = leaf_begin_of(ix, t, lq), e = leaf_begin_of(ix, t, lq + 1);
+        if (lane == 0) atomicAdd(&c.sm.n_visit, (unsigned long long)(e - b));
         for (uint32_t i = b + lane; i < e; i += 32) {
           const uint32_t p = permt[i];
           const uint32_t *lo = ix.leaf_of + (int64_t)p * ix.L;
@@ -585,6 +590,7 @@ __global__ void __launch_bounds__(QT) k_query(QueryIndexView ix, QueryArgs qa) {
   s.rid = reinterpret_cast<uint32_t *>(base + qa.off[9]);
   s.rkey = reinterpret_cast<uint32_t *>(base + qa.off[10]);
   for (int i = threadIdx.x; i < 256; i += QT) sm.T[i] = i < NLEV ? qa.T[i] : __int_as_float(0x7f800000);
+  if (threadIdx.x == 0) { sm.n_blocks = 0; sm.n_leaves = 0; sm.n_visit = 0; }
   __syncthreads();
 
   while (true) {
@@ -721,6 +727,7 @@ __global__ void __launch_bounds__(QT) k_query(QueryIndexView ix, QueryArgs qa) {
       };
       topk_select(nc, k, get_s, sm);
     }
+    if (threadIdx.x == 0 && qa.stats) atomicAdd(&qa.stats[0], (unsigned long long)nc);
     for (int r = threadIdx.x; r < qa.k_max; r += QT) {
       if (r < k) {
         qa.ids[qi * qa.k_max + r] = (int64_t)sm.topk_id[r];
@@ -731,6 +738,11 @@ __global__ void __launch_bounds__(QT) k_query(QueryIndexView ix, QueryArgs qa) {
       }
     }
     __syncthreads();
+  }
+  if (threadIdx.x == 0 && qa.stats) {
+    atomicAdd(&qa.stats[1], sm.n_leaves);
+    atomicAdd(&qa.stats[2], sm.n_blocks);
+    atomicAdd(&qa.stats[3], sm.n_visit);
   }
 }
 
@@ -757,6 +769,7 @@ int run_queries(const QueryIndexView &ix, const QueryArgs &qa, cudaStream_t st) 
   DL_CUDA(cudaMemsetAsync(qa.work_counter, 0, sizeof(uint32_t), st));
   const int grid = (int)std::min<int64_t>(qa.nslots, qa.m);
   k_query<<<grid, QT, smem, st>>>(ix, qa);
+  dl_count_launch();
   DL_CUDA(cudaGetLastError());
   return DETLSH_OK;
 }

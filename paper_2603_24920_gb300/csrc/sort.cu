@@ -119,10 +119,14 @@ int segmented_sort(uint32_t *keys, uint32_t *vals, int nseg, int64_t len, int nb
   for (int shift = 0; shift < nbits; shift += 8, ++passes) {
     dim3 g((unsigned)tiles, (unsigned)nseg);
     k_radix_hist<<<g, SORT_THREADS, 0, st>>>(kin, len, shift, tmp.counts, tiles);
+    dl_count_launch();
     k_radix_scan_digit<<<dim3(256, nseg), SORT_THREADS, 0, st>>>(tmp.counts, tiles, tmp.digit_base);
+    dl_count_launch();
     k_radix_scan_totals<<<nseg, 256, 0, st>>>(tmp.digit_base);
+    dl_count_launch();
     k_radix_scatter<<<g, SORT_THREADS, 0, st>>>(kin, vin, kout, vout, len, shift, tmp.counts,
                                                 tmp.digit_base, tiles);
+    dl_count_launch();
     DL_CUDA(cudaGetLastError());
     std::swap(kin, kout);
     std::swap(vin, vout);
@@ -198,6 +202,7 @@ int float_to_keys(float *v, int64_t count, cudaStream_t st) {
   if (count <= 0) return DETLSH_OK;
   const int64_t blocks = std::min<int64_t>(ceil_div(count, 256), 65535);
   k_float_to_keys<<<(unsigned)blocks, 256, 0, st>>>(v, count);
+  dl_count_launch();
   DL_CUDA(cudaGetLastError());
   return DETLSH_OK;
 }
@@ -219,6 +224,7 @@ __global__ void k_extract_breakpoints(const uint32_t *__restrict__ sorted, int L
 int extract_breakpoints(const uint32_t *sorted_keys, int LK, int64_t m, int N_r, float *B,
                         cudaStream_t st) {
   k_extract_breakpoints<<<LK, 256, 0, st>>>(sorted_keys, LK, m, N_r, B);
+  dl_count_launch();
   DL_CUDA(cudaGetLastError());
   return DETLSH_OK;
 }
@@ -233,6 +239,7 @@ __global__ void k_finish_ends(const uint32_t *minmax, int LK, int N_r, float *B)
 
 int finish_breakpoint_ends(const uint32_t *minmax, int LK, int N_r, float *B, cudaStream_t st) {
   k_finish_ends<<<(unsigned)ceil_div(LK, 128), 128, 0, st>>>(minmax, LK, N_r, B);
+  dl_count_launch();
   DL_CUDA(cudaGetLastError());
   return DETLSH_OK;
 }

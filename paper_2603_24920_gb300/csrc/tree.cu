@@ -354,6 +354,7 @@ int block_hulls(const uint8_t *lo, const uint8_t *hi, int64_t nleaves, uint8_t *
   const int64_t nb = ceil_div(nleaves, LEAF_BLOCK);
   if (nb == 0) return DETLSH_OK;
   k_block_hulls<<<(unsigned)ceil_div(nb, 128), 128, 0, st>>>(lo, hi, nleaves, nb, hlo, hhi);
+  dl_count_launch();
   DL_CUDA(cudaGetLastError());
   return DETLSH_OK;
 }
@@ -364,10 +365,12 @@ int build_tree(const TreeBuildArgs &A, TreeTemp &T, int64_t *nleaves, int64_t *m
   const int gs = (int)std::min<int64_t>(ceil_div(n, 256), 4096);
   DL_CUDA(cudaMemsetAsync(T.scalars, 0, 4 * sizeof(uint32_t), st));
   k_first_keys<<<gs, 256, 0, st>>>(A.codes_t, n, A.K, A.bbits, T.keys, T.vals);
+  dl_count_launch();
   DL_CUDA(cudaGetLastError());
   DL_TRY(segmented_sort(T.keys, T.vals, 1, n, A.K, T.sort, st));
   k_gather_codes<<<gs, 256, 0, st>>>(reinterpret_cast<const uint4 *>(A.codes_t), T.vals, n,
                                      T.codesA);
+  dl_count_launch();
   DL_CUDA(cudaGetLastError());
   // first-layer nodes = runs of equal keys
   uint32_t *F_dev = T.scalars;
@@ -376,6 +379,7 @@ int build_tree(const TreeBuildArgs &A, TreeTemp &T, int64_t *nleaves, int64_t *m
   DL_CUDA(cudaMemcpyAsync(&F, F_dev, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
   DL_CUDA(cudaStreamSynchronize(st));
   k_set_u32<<<1, 1, 0, st>>>(T.node_begin + F, (uint32_t)n);
+  dl_count_launch();
   SubtreeArgs sa;
   sa.n = n; sa.K = A.K; sa.bbits = A.bbits; sa.M = A.M; sa.box_mode = A.box_mode;
   sa.node_begin = T.node_begin;
@@ -387,11 +391,13 @@ int build_tree(const TreeBuildArgs &A, TreeTemp &T, int64_t *nleaves, int64_t *m
   sa.tmp_box = T.tmp_box;
   sa.err = reinterpret_cast<int *>(T.scalars + 2);
   k_subtree<<<F, TB_THREADS, 0, st>>>(sa);
+  dl_count_launch();
   DL_CUDA(cudaGetLastError());
   // leaf numbering
   DL_CUDA(cudaMemcpyAsync(T.leaf_base, T.node_count, sizeof(uint32_t) * F,
                           cudaMemcpyDeviceToDevice, st));
   k_scan_counts<<<1, 1024, 0, st>>>(T.leaf_base, F, T.scalars + 1);
+  dl_count_launch();
   DL_CUDA(cudaMemsetAsync(T.scalars + 3, 0, sizeof(uint32_t), st));
   LeafWriteArgs lw;
   lw.n = n; lw.L = A.L; lw.t = A.t;
@@ -400,12 +406,14 @@ int build_tree(const TreeBuildArgs &A, TreeTemp &T, int64_t *nleaves, int64_t *m
   lw.leaf_begin = A.leaf_begin; lw.leaf_lo = A.leaf_lo; lw.leaf_hi = A.leaf_hi;
   lw.leaf_nb = A.leaf_nb; lw.leaf_of = A.leaf_of; lw.max_leaf = T.scalars + 3;
   k_leaf_write<<<(unsigned)ceil_div((int64_t)F * 32, 256), 256, 0, st>>>(lw, F);
+  dl_count_launch();
   DL_CUDA(cudaGetLastError());
   uint32_t hs[4];
   DL_CUDA(cudaMemcpyAsync(hs, T.scalars, sizeof(hs), cudaMemcpyDeviceToHost, st));
   DL_CUDA(cudaStreamSynchronize(st));
   if (hs[2] != 0) return (int)hs[2];
   k_set_u32<<<1, 1, 0, st>>>(A.leaf_begin + hs[1], (uint32_t)n);
+  dl_count_launch();
   DL_CUDA(cudaGetLastError());
   *nleaves = hs[1];
   *max_leaf = hs[3];

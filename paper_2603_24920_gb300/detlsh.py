@@ -45,6 +45,20 @@ class Info(C.Structure):
                 ("projection_fallbacks", C.c_int64)]
 
 
+class Timings(C.Structure):
+    _fields_ = [("build_ms", C.c_float), ("sample_ms", C.c_float),
+                ("breakpoints_ms", C.c_float), ("encode_ms", C.c_float),
+                ("trees_ms", C.c_float), ("query_ms", C.c_float),
+                ("query_project_ms", C.c_float), ("query_kernel_ms", C.c_float),
+                ("build_launches", C.c_int64), ("query_launches", C.c_int64),
+                ("query_count", C.c_int64), ("query_candidates", C.c_int64),
+                ("query_leaves", C.c_int64), ("query_blocks", C.c_int64),
+                ("query_points_visited", C.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 _lib = None
 
 # (name, restype, argtypes) of every entry point declared in include/detlsh.h
@@ -66,6 +80,7 @@ SIGNATURES = [
     ("detlsh_get_projections", C.c_int, [_P, _P]),
     ("detlsh_get_tree", C.c_int, [_P, _I32, _P, _P, _P, _P, _P, _P]),
     ("detlsh_get_level_table", C.c_int, [_P, _F64, _P]),
+    ("detlsh_get_timings", C.c_int, [_P, C.POINTER(Timings)]),
     ("detlsh_project", C.c_int, [_P, _P, _I64, _P, _P]),
     ("detlsh_query_candidates", C.c_int, [_P, _P, _I64, _I32, C.POINTER(QueryParams), _I64,
                                           _P, _P, _P, _P]),
@@ -233,6 +248,12 @@ def detlsh_get_tree(h, t):
                                  _ptr(out["hi"]), _ptr(out["nb"]), _ptr(out["leaf_of"])),
            "detlsh_get_tree")
     return out
+
+
+def detlsh_get_timings(h):
+    t = Timings()
+    _check(lib().detlsh_get_timings(h, C.byref(t)), "detlsh_get_timings")
+    return t
 
 
 def detlsh_get_level_table(h, c):
