@@ -40,7 +40,9 @@ typedef enum {
     DETLSH_ERR_OOM = -3,             /* device or host allocation failed       */
     DETLSH_ERR_CUDA = -4,            /* a CUDA runtime call failed             */
     DETLSH_ERR_CAPACITY = -5,        /* an internal work list overflowed       */
-    DETLSH_ERR_NO_DEVICE = -6        /* no usable CUDA device                  */
+    DETLSH_ERR_NO_DEVICE = -6,       /* no usable CUDA device                  */
+    DETLSH_ERR_SCRATCH_LIMIT = -7    /* the request does not fit the fixed
+                                        scratch of detlsh_query_noalloc        */
 } detlsh_status;
 
 /* Node boxes used by the range query's lower bound (Sec. IV-C). */
@@ -120,6 +122,34 @@ int detlsh_query(const detlsh_index *ix, const float *queries, int64_t m, int32_
 int detlsh_query_ex(const detlsh_index *ix, const float *queries, int64_t m,
                     const int32_t *k_per_query, int32_t k_max, const detlsh_query_params *qp,
                     void *stream, int64_t *ids, float *dists);
+
+/*
+ * detlsh_query_noalloc -- the queries of detlsh_query_ex (one k for every
+ * query), for callers that cannot allocate device memory while serving: a
+ * process whose framework has already claimed nearly all device memory for
+ * its own pool, a latency-critical path where cudaMalloc/cudaFree would stall
+ * the device, or a deployment that forbids allocation after start-up.  The
+ * paper has no counterpart; this entry point only changes where scratch
+ * memory comes from.
+ *
+ * All scratch lives in one fixed 32 MiB device array compiled into the
+ * library (every GPU that loads the library holds it until the process
+ * exits); the call allocates nothing.  queries (m x d FP32), ids (m x k
+ * int64) and dists (m x k FP32) must be device memory owned by the caller.
+ * Requests that do not fit (the query projections, BF16 query copy and one
+ * per-CTA working slot, which grows with the index's leaf count and with
+ * beta*n + k) fail with DETLSH_ERR_SCRATCH_LIMIT; smaller batches fit.
+ * The first call on a device looks up the array's device address with that
+ * device current; make that first call before any stream capture.  Every
+ * call reuses the same array and clears the part it uses at its start, so
+ * calls that overlap on the GPU (other streams, other host threads) race:
+ * serialise them.  Returns after the results are written.
+ * Errors: as detlsh_query_ex, plus SCRATCH_LIMIT; INVALID_ARG for host
+ * pointers.
+ */
+int detlsh_query_noalloc(const detlsh_index *ix, const float *queries, int64_t m, int32_t k,
+                         const detlsh_query_params *qp, void *stream, int64_t *ids,
+                         float *dists);
 
 /* Release the index and its device memory.  NULL is accepted. */
 int detlsh_free(detlsh_index *ix);

@@ -589,6 +589,25 @@ int query_impl(detlsh_index *ix, const float *queries, int64_t m, const int32_t 
 }  // namespace
 
 namespace dl {
+// Read-only view of an index for entry points in other translation units.
+int index_query_view(const detlsh_index *ix, QueryIndexView *v, const float **A, int *has_bf16) {
+  if (!ix) return DETLSH_ERR_INVALID_ARG;
+  *v = view_of(ix);
+  *A = ix->A;
+  *has_bf16 = ix->Xh != nullptr;
+  return DETLSH_OK;
+}
+
+// Argument checks shared with detlsh_query_ex, and the radius grid.
+int check_query_args(const detlsh_index *ix, int64_t m, int32_t k, const detlsh_query_params *qp) {
+  return validate_query(ix, m, k, qp);
+}
+
+void radius_grid(const detlsh_index *ix, double c, float T[256]) {
+  level_table(ix->eps2, c, T);
+  T[255] = INFINITY;
+}
+
 int f32_to_bf16(const float *src, __nv_bfloat16 *dst, int64_t count, cudaStream_t st) {
   if (count <= 0) return DETLSH_OK;
   k_f32_to_bf16<<<(unsigned)std::min<int64_t>(ceil_div(count, 256), 8192), 256, 0, st>>>(src, dst, count);
@@ -635,6 +654,8 @@ const char *detlsh_status_string(int s) {
     case DETLSH_ERR_CUDA: return g_last_cuda[0] ? g_last_cuda : "CUDA error";
     case DETLSH_ERR_CAPACITY: return "internal work list capacity exceeded";
     case DETLSH_ERR_NO_DEVICE: return "no CUDA device";
+    case DETLSH_ERR_SCRATCH_LIMIT:
+      return "request does not fit the fixed 32 MiB scratch of detlsh_query_noalloc";
   }
   return "unknown status";
 }

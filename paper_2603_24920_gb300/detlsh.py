@@ -14,7 +14,7 @@ LIB_PATH = os.path.join(HERE, "libdetlsh.so")
 
 DETLSH_OK = 0
 STATUS = {0: "OK", -1: "INVALID_ARG", -2: "NONFINITE_INPUT", -3: "OOM", -4: "CUDA",
-          -5: "CAPACITY", -6: "NO_DEVICE"}
+          -5: "CAPACITY", -6: "NO_DEVICE", -7: "SCRATCH_LIMIT"}
 BOX_PREFIX, BOX_TIGHT = 0, 1
 PREC_FP32, PREC_BF16_REFINE = 0, 1
 
@@ -70,6 +70,7 @@ SIGNATURES = [
     ("detlsh_build_ex", C.c_int, [_P, _I64, _I32, C.POINTER(BuildParams), _P, C.POINTER(_P)]),
     ("detlsh_query", C.c_int, [_P, _P, _I64, _I32, _F64, _P, _P]),
     ("detlsh_query_ex", C.c_int, [_P, _P, _I64, _P, _I32, C.POINTER(QueryParams), _P, _P, _P]),
+    ("detlsh_query_noalloc", C.c_int, [_P, _P, _I64, _I32, C.POINTER(QueryParams), _P, _P, _P]),
     ("detlsh_free", C.c_int, [_P]),
     ("detlsh_status_string", C.c_char_p, [C.c_int]),
     ("detlsh_get_info", C.c_int, [_P, C.POINTER(Info)]),
@@ -186,6 +187,24 @@ def detlsh_query_ex(h, queries, k, beta=0.1, c=1.5, precision=PREC_FP32, rerank_
         kq = np.ascontiguousarray(k_per_query, np.int32)
     _check(lib().detlsh_query_ex(h, _ptr(queries), m, _ptr(kq), k, C.byref(qp),
                                  _stream_ptr(stream), _ptr(ids), _ptr(dists)), "detlsh_query_ex")
+    return ids, dists
+
+
+def detlsh_query_noalloc(h, queries, k, beta=0.1, c=1.5, precision=PREC_FP32, rerank_mult=4,
+                         stream=None, ids=None, dists=None):
+    """Queries answered with the library's fixed scratch array: the call
+    allocates no device memory (for callers that cannot allocate while
+    serving).  queries, ids and dists must be CUDA tensors; ids/dists are
+    allocated here by torch when not given."""
+    import torch
+    m = queries.shape[0]
+    qp = detlsh_default_query_params()
+    qp.beta, qp.c, qp.precision, qp.rerank_mult = beta, c, precision, rerank_mult
+    if ids is None:
+        ids = torch.empty((m, k), dtype=torch.int64, device=queries.device)
+        dists = torch.empty((m, k), dtype=torch.float32, device=queries.device)
+    _check(lib().detlsh_query_noalloc(h, _ptr(queries), m, k, C.byref(qp), _stream_ptr(stream),
+                                      _ptr(ids), _ptr(dists)), "detlsh_query_noalloc")
     return ids, dists
 
 
