@@ -521,6 +521,8 @@ int query_impl(detlsh_index *ix, const float *queries, int64_t m, const int32_t 
   QueryArgs qa{};
   qa.Q = Q; qa.Qh = Qh; qa.Qp = Qp; qa.m = m; qa.kq = kd; qa.k_max = k_max;
   qa.tau_base = tau_base; qa.T = static_cast<const float *>(ix->qT.p);
+  qa.lg_eps2 = (float)std::log2(ix->eps2);
+  qa.inv_2lg_c = (float)(1.0 / (2.0 * std::log2(qp->c)));
   qa.precision = qp->precision; qa.rerank_mult = qp->rerank_mult;
   qa.ids = static_cast<int64_t *>(ix->qids.p);
   qa.dists = static_cast<float *>(ix->qdists.p);

@@ -111,6 +111,7 @@ struct QueryArgs {
   int k_max;
   int64_t tau_base;          // ceil(beta * n)
   const float *T;            // [255] radius grid
+  float lg_eps2, inv_2lg_c;  // log2(eps^2), 1/(2 log2 c): level estimate before the exact fix-up
   int precision, rerank_mult;
   int64_t *ids;              // [m][k_max]
   float *dists;              // [m][k_max]

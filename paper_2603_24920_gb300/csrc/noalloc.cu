@@ -128,6 +128,8 @@ extern "C" int detlsh_query_noalloc(const detlsh_index *ix, const float *queries
   }
   qa.Q = queries; qa.Qh = Qh; qa.Qp = pa.P; qa.m = m; qa.kq = nullptr; qa.k_max = k;
   qa.tau_base = tau_base; qa.T = reinterpret_cast<const float *>(base + o_T);
+  qa.lg_eps2 = (float)std::log2((double)Th[127]);  // T(0) = eps^2 seeds the level estimate
+  qa.inv_2lg_c = (float)(1.0 / (2.0 * std::log2(qp->c)));
   qa.precision = qp->precision; qa.rerank_mult = qp->rerank_mult;
   qa.ids = ids; qa.dists = dists;
   qa.cand_cap = cap;

@@ -86,6 +86,13 @@ struct QShared {
   uint32_t need, ncand, sel_v, sel_below, nres, epoch;
   uint64_t cum;
   unsigned long long n_blocks, n_leaves, n_visit;  // work counters of this CTA
+  int use_hash;
+  uint32_t hash_bits, hash_count;
+  int sel_g;
+  uint64_t sel_bf;
+  int64_t newt[16];
+  uint32_t cpos;
+  int jchk;
 };
 
 __device__ __forceinline__ uint32_t byte_of(const uint4 &c, int j) {
@@ -93,21 +100,81 @@ __device__ __forceinline__ uint32_t byte_of(const uint4 &c, int j) {
   return (w >> (8 * (j & 3))) & 255u;
 }
 
-// Smallest radius level with x <= T[level] (T[254] = +inf).
-__device__ __forceinline__ uint32_t level_of(const float *T, float x) {
-  int lo = 0, hi = NLEV - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi) >> 1;
-    if (x <= T[mid]) hi = mid; else lo = mid + 1;
+// Smallest radius level with x <= T[level] (T is nondecreasing, T[254] = +inf).
+// A log2 estimate of the level is corrected against T itself, so the result
+// is exactly the table's answer whatever the estimate's rounding.
+__device__ __forceinline__ uint32_t level_of(const float *T, float x, float lg_eps2,
+                                             float inv_2lg_c) {
+  if (!(x > 0.0f)) return 0u;
+  int i = NLEV - 1;
+  if (x <= 3.0e38f) {
+    i = (int)ceilf((__log2f(x) - lg_eps2) * inv_2lg_c) - JMIN;
+    i = max(0, min(NLEV - 1, i));
   }
-  return (uint32_t)lo;
+  while (i > 0 && x <= T[i - 1]) --i;
+  while (x > T[i]) ++i;
+  return (uint32_t)i;
+}
+
+// Adds w to bins[v] once per distinct v among the active lanes of a warp
+// (shared-memory atomics on a few hot bins would otherwise serialise).
+__device__ __forceinline__ void warp_bin_add(uint32_t *bins, bool active, uint32_t v, uint32_t w) {
+  unsigned act = __ballot_sync(FULL, active);
+  const int lane = threadIdx.x & 31;
+  while (act) {
+    const int src = __ffs(act) - 1;
+    const uint32_t key = __shfl_sync(FULL, v, src);
+    const bool mine = active && v == key;
+    const unsigned grp = __ballot_sync(FULL, mine);
+    const uint32_t sum = __reduce_add_sync(FULL, mine ? w : 0u);
+    if (lane == src) atomicAdd(&bins[key], sum);
+    act &= ~grp;
+  }
+}
+
+// Warp 0 finds, over 256 bins, the first bin g with
+// below + sum(bins[0..g]) >= need, and writes g and the sum of the bins
+// before it (plus below) to shared memory.  Every thread of the block calls
+// it; only warp 0 works.  With no crossing it reports bin 255.
+__device__ __forceinline__ void warp_first_crossing(const uint32_t *bins, uint64_t below,
+                                                    uint64_t need, int *g_out, uint64_t *before) {
+  if (threadIdx.x >= 32) return;
+  const int lane = threadIdx.x;
+  uint32_t v[8];
+  uint64_t sum = 0;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) { v[i] = bins[lane * 8 + i]; sum += v[i]; }
+  uint64_t incl = sum;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint64_t y = __shfl_up_sync(FULL, incl, o);
+    if (lane >= o) incl += y;
+  }
+  const uint64_t excl = incl - sum;
+  const bool mine = below + excl < need && below + incl >= need;
+  const unsigned b = __ballot_sync(FULL, mine);
+  const int src = b ? __ffs(b) - 1 : 31;
+  if (lane == src) {
+    uint64_t acc = below + excl;
+    int g = lane * 8 + 7;
+    if (mine) {
+      for (int i = 0; i < 8; ++i) {
+        if (acc + v[i] >= need) { g = lane * 8 + i; break; }
+        acc += v[i];
+      }
+    } else {
+      acc = below + incl - v[7];
+    }
+    *g_out = g;
+    *before = acc;
+  }
 }
 
 // Block-wide weighted radix select over 32-bit keys: finds the smallest key
 // v with W(key <= v) >= need, where item i has (key_i, weight_i) from get(i)
 // (weight 0 = absent).  Returns v in sm.sel_v and W(key < v) in sm.sel_below.
 template <class Get>
-__device__ void block_select(int64_t N, Get get, uint32_t need, QShared &sm) {
+__device__ __forceinline__ void block_select(int64_t N, Get get, uint32_t need, QShared &sm) {
   uint32_t prefix = 0, below = 0;
   for (int shift = 24; shift >= 0; shift -= 8) {
     sm.rh[threadIdx.x] = 0;
@@ -119,21 +186,14 @@ __device__ void block_select(int64_t N, Get get, uint32_t need, QShared &sm) {
       if (w && (k & hmask) == (prefix & hmask)) atomicAdd(&sm.rh[(k >> shift) & 255u], w);
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-      uint32_t acc = below;
-      int dg = 255;
-      for (int g = 0; g < 256; ++g) {
-        if (acc + sm.rh[g] >= need) { dg = g; break; }
-        acc += sm.rh[g];
-      }
-      sm.sel_v = prefix | ((uint32_t)dg << shift);
-      sm.sel_below = acc;
-    }
+    warp_first_crossing(sm.rh, below, need, &sm.sel_g, &sm.sel_bf);
     __syncthreads();
-    prefix = sm.sel_v;
-    below = sm.sel_below;
+    prefix |= (uint32_t)sm.sel_g << shift;
+    below = (uint32_t)sm.sel_bf;
     __syncthreads();
   }
+  if (threadIdx.x == 0) { sm.sel_v = prefix; sm.sel_below = below; }
+  __syncthreads();
 }
 
 struct QCtx {
@@ -152,20 +212,37 @@ __device__ __forceinline__ uint32_t leaf_begin_of(const QueryIndexView &ix, int 
   return ix.leaf_begin[ix.leaf_off[t] + t + l];
 }
 
-// Level of leaf l of tree t for this query; leaves never expanded are
-// beyond the final bound and read as 255.
-__device__ __forceinline__ uint32_t leaf_level(const QueryIndexView &ix, const Slot &s, uint32_t ep,
-                                               int t, uint32_t l) {
-  const uint32_t v = s.lev[ix.leaf_off[t] + l];
-  return (v >> 8) == ep ? (v & 255u) : 255u;
+// Level of leaf l of tree u for this query.  After the expansion, the levels
+// of every listed leaf at or below the final bound sit in a shared-memory
+// hash table (when they fit); otherwise they are read from the slot's
+// epoch-tagged array.  Leaves absent from both are beyond the bound: 255.
+__device__ __forceinline__ uint32_t leaf_level_h(const QueryIndexView &ix, const Slot &s,
+                                                 const QShared &sm, const float *lut, int u,
+                                                 uint32_t l) {
+  if (sm.use_hash) {
+    const uint32_t key = (uint32_t)(ix.leaf_off[u] + l) + 1u;
+    const uint32_t *keys = reinterpret_cast<const uint32_t *>(lut);
+    const uint8_t *levs = reinterpret_cast<const uint8_t *>(keys + (1u << sm.hash_bits));
+    const uint32_t mask = (1u << sm.hash_bits) - 1u;
+    uint32_t h = (key * 0x9E3779B1u) >> (32 - sm.hash_bits);
+    while (true) {  // load factor <= 1/2: an empty slot always ends the probe
+      const uint32_t k = keys[h];
+      if (k == key) return levs[h];
+      if (k == 0u) return 255u;
+      h = (h + 1u) & mask;
+    }
+  }
+  const uint32_t v = s.lev[ix.leaf_off[u] + l];
+  return (v >> 8) == sm.epoch ? (v & 255u) : 255u;
 }
 
 // Smallest level of point p over trees t' < tlim (255 if none).
 __device__ __forceinline__ uint32_t min_level_before(const QueryIndexView &ix, const Slot &s,
-                                                     uint32_t ep, uint32_t p, int tlim) {
+                                                     const QShared &sm, const float *lut,
+                                                     uint32_t p, int tlim) {
   uint32_t f = 255u;
   const uint32_t *lo = ix.leaf_of + (int64_t)p * ix.L;
-  for (int u = 0; u < tlim; ++u) f = min(f, leaf_level(ix, s, ep, u, lo[u]));
+  for (int u = 0; u < tlim; ++u) f = min(f, leaf_level_h(ix, s, sm, lut, u, lo[u]));
   return f;
 }
 
@@ -192,7 +269,7 @@ __device__ __forceinline__ float box_lb2(const float *lut, int NR1, int K, const
 // stops at the first j where tree t alone holds beta*n + k points (that j
 // bounds j* from above) or at J; J shrinks to it.  Every leaf of level <= the
 // final J therefore ends up expanded and listed.
-__device__ void expand_levels(QCtx &c) {
+__device__ __forceinline__ void expand_levels(QCtx &c) {
   const QueryIndexView &ix = c.ix;
   QShared &sm = c.sm;
   const int K = ix.K, NR1 = ix.N_r + 1;
@@ -216,18 +293,30 @@ __device__ void expand_levels(QCtx &c) {
     const uint4 *hhi = reinterpret_cast<const uint4 *>(ix.blk_hi) + ix.blk_off[t];
     uint8_t *blev = c.s.blev + ix.blk_off[t];
     if (threadIdx.x == 0) sm.n_blocks += (unsigned long long)nb;
-    for (int64_t b = threadIdx.x; b < nb; b += QT) {
-      const uint32_t lv = level_of(sm.T, box_lb2(c.lut, NR1, K, hlo[b], hhi[b]));
-      blev[b] = lv <= J0 ? (uint8_t)lv : (uint8_t)255;
-      if (lv <= J0) {
-        atomicAdd(&sm.rh[lv], 1u);
-        atomicMin(&sm.jcur, (int)lv);
+    for (int64_t b0 = 0; b0 < nb; b0 += QT) {  // uniform trip count for warp_bin_add
+      const int64_t b = b0 + threadIdx.x;
+      uint32_t lv = 255u;
+      if (b < nb) {
+        lv = level_of(sm.T, box_lb2(c.lut, NR1, K, hlo[b], hhi[b]), c.qa.lg_eps2, c.qa.inv_2lg_c);
+        blev[b] = lv <= J0 ? (uint8_t)lv : (uint8_t)255;
+        if (lv <= J0) atomicMin(&sm.jcur, (int)lv);
       }
+      warp_bin_add(sm.rh, b < nb && lv <= J0, lv, 1u);
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-      uint32_t acc = 0;
-      for (int j = 0; j < 256; ++j) { sm.bstart[j] = acc; acc += sm.rh[j]; }
+    if (threadIdx.x < 32) {  // exclusive prefix of the per-level block counts
+      uint32_t v[8], sum = 0;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) { v[i] = sm.rh[lane * 8 + i]; sum += v[i]; }
+      uint32_t incl = sum;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(FULL, incl, o);
+        if (lane >= o) incl += y;
+      }
+      uint32_t acc = incl - sum;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) { sm.bstart[lane * 8 + i] = acc; acc += v[i]; }
     }
     __syncthreads();
     // bucket the blocks by level (ids in border[bstart[lv] ...])
@@ -243,21 +332,29 @@ __device__ void expand_levels(QCtx &c) {
     uint32_t *hist_t = c.hist + t * 256;
     const uint4 *llo = reinterpret_cast<const uint4 *>(ix.leaf_lo) + ix.leaf_off[t];
     const uint4 *lhi = reinterpret_cast<const uint4 *>(ix.leaf_hi) + ix.leaf_off[t];
-    for (int j = sm.jcur; j <= (int)J0; ++j) {
-      const uint32_t e = sm.bstart[j], s0 = e - sm.rh[j];
+    // Expand the level-sorted blocks in chunks.  After a chunk, every block
+    // below the level of the next unexpanded block is done, so this tree's
+    // point counts are complete for those levels: check them for beta*n + k.
+    if (threadIdx.x == 0) { sm.cpos = 0; sm.jchk = sm.jcur; }
+    __syncthreads();
+    const uint32_t nsel = sm.bstart[255];
+    while (true) {
       const uint32_t Jnow = (uint32_t)sm.jhi;
-      for (uint32_t i = s0 + warp; i < e; i += QW) {
+      const uint32_t p0c = sm.cpos, p1c = min(nsel, p0c + (uint32_t)(2 * QW));
+      for (uint32_t i = p0c + warp; i < p1c; i += QW) {
         const uint32_t b = c.s.border[ix.blk_off[t] + i];
         const int64_t l = (int64_t)b * LEAF_BLOCK + lane;
         const bool valid = l < nl;
         uint32_t lv = 255u;
         float lb = 0.0f;
+        uint32_t sz = 0;
         if (valid) {
           lb = box_lb2(c.lut, NR1, K, llo[l], lhi[l]);
-          lv = level_of(sm.T, lb);
+          lv = level_of(sm.T, lb, c.qa.lg_eps2, c.qa.inv_2lg_c);
           c.s.lev[ix.leaf_off[t] + l] = (ep << 8) | lv;
-          atomicAdd(&hist_t[lv], leaf_begin_of(ix, t, l + 1) - leaf_begin_of(ix, t, l));
+          sz = leaf_begin_of(ix, t, l + 1) - leaf_begin_of(ix, t, l);
         }
+        warp_bin_add(hist_t, valid, lv, sz);
         const bool keep = valid && lv <= Jnow;
         const unsigned km = __ballot_sync(FULL, keep);
         const unsigned vm = __ballot_sync(FULL, valid);
@@ -274,9 +371,15 @@ __device__ void expand_levels(QCtx &c) {
       }
       __syncthreads();
       if (threadIdx.x == 0) {
-        sm.cum += hist_t[j];
-        if (sm.cum >= (uint64_t)c.tau) { sm.jhi = min(sm.jhi, j); sm.stop = 1; }
-        if (j >= sm.jhi) sm.stop = 1;
+        const int jnext = p1c < nsel ? (int)blev[c.s.border[ix.blk_off[t] + p1c]] : NLEV;
+        int j = sm.jchk;
+        for (; j < jnext && j <= sm.jhi; ++j) {
+          sm.cum += hist_t[j];
+          if (sm.cum >= (uint64_t)c.tau) { sm.jhi = j; sm.stop = 1; break; }
+        }
+        sm.jchk = j;  // first level not yet added
+        if (jnext > sm.jhi || p1c >= nsel) sm.stop = 1;
+        sm.cpos = p1c;
       }
       __syncthreads();
       if (sm.stop) break;
@@ -285,8 +388,54 @@ __device__ void expand_levels(QCtx &c) {
   }
 }
 
+// ---- step 1b: shared-memory table of the levels at or below the bound ----
+// Reuses the lookup table's space (no longer needed): keys (global leaf
+// index + 1, 0 = empty) then one level byte per slot, linear probing.
+__device__ __forceinline__ void build_level_hash(QCtx &c) {
+  const QueryIndexView &ix = c.ix;
+  QShared &sm = c.sm;
+  const uint32_t jhi = (uint32_t)sm.jhi;
+  const uint32_t bytes = 16u * (uint32_t)(ix.N_r + 1) * 4u;
+  uint32_t bits = 0;
+  while ((1u << (bits + 1)) * 5u <= bytes && bits + 1 <= 12) ++bits;
+  if (threadIdx.x == 0) { sm.hash_count = 0; sm.hash_bits = bits; }
+  __syncthreads();
+  uint32_t cnt = 0;
+  for (int t = 0; t < ix.L; ++t)
+    for (int64_t e = threadIdx.x; e < sm.nlist[t]; e += QT)
+      cnt += c.s.llev[ix.leaf_off[t] + e] <= jhi;
+  atomicAdd(&sm.hash_count, cnt);
+  __syncthreads();
+  const uint32_t slots = 1u << bits;
+  const bool use = bits >= 4 && sm.hash_count * 2u <= slots;
+  if (!use) {
+    if (threadIdx.x == 0) sm.use_hash = 0;
+    __syncthreads();
+    return;
+  }
+  uint32_t *keys = reinterpret_cast<uint32_t *>(c.lut);
+  uint8_t *levs = reinterpret_cast<uint8_t *>(keys + slots);
+  for (uint32_t i = threadIdx.x; i < slots; i += QT) keys[i] = 0u;
+  __syncthreads();
+  for (int t = 0; t < ix.L; ++t) {
+    for (int64_t e = threadIdx.x; e < sm.nlist[t]; e += QT) {
+      const uint32_t lv = c.s.llev[ix.leaf_off[t] + e];
+      if (lv > jhi) continue;
+      const uint32_t key = (uint32_t)(ix.leaf_off[t] + c.s.lleaf[ix.leaf_off[t] + e]) + 1u;
+      uint32_t h = (key * 0x9E3779B1u) >> (32 - bits);
+      while (true) {
+        const uint32_t old = atomicCAS(&keys[h], 0u, key);
+        if (old == 0u || old == key) { levs[h] = (uint8_t)lv; break; }
+        h = (h + 1u) & (slots - 1u);
+      }
+    }
+  }
+  if (threadIdx.x == 0) sm.use_hash = 1;
+  __syncthreads();
+}
+
 // ---- step 2: owner-rule union counts and per-tree new-point counts -------
-__device__ void union_counts(QCtx &c) {
+__device__ __forceinline__ void union_counts(QCtx &c) {
   const QueryIndexView &ix = c.ix;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t jhi = (uint32_t)c.sm.jhi, ep = c.sm.epoch;
@@ -306,21 +455,26 @@ __device__ void union_counts(QCtx &c) {
         const uint32_t lvt = __shfl_sync(FULL, mylv, src);
         const uint32_t b = leaf_begin_of(ix, t, lq), e = leaf_begin_of(ix, t, lq + 1);
         if (lane == 0) atomicAdd(&c.sm.n_visit, (unsigned long long)(e - b));
-        for (uint32_t i = b + lane; i < e; i += 32) {
-          const uint32_t p = permt[i];
-          const uint32_t *lo = ix.leaf_of + (int64_t)p * ix.L;
+        for (uint32_t base = b; base < e; base += 32) {
+          const uint32_t i = base + lane;
+          const bool valid = i < e;
           uint32_t m = 255u, f = 255u;
           int owner = -1;
-          for (int u = 0; u < ix.L; ++u) {
-            const uint32_t lv = (u == t) ? lvt : leaf_level(ix, c.s, ep, u, lo[u]);
-            if (lv < m) { m = lv; owner = u; }
-            if (u < t) f = min(f, lv);
+          if (valid) {
+            const uint32_t p = permt[i];
+            const uint32_t *lo = ix.leaf_of + (int64_t)p * ix.L;
+            for (int u = 0; u < ix.L; ++u) {
+              const uint32_t lv = (u == t) ? lvt : leaf_level_h(ix, c.s, c.sm, c.lut, u, lo[u]);
+              if (lv < m) { m = lv; owner = u; }
+              if (u < t) f = min(f, lv);
+            }
           }
-          if (owner == t) atomicAdd(&c.sm.H[m], 1u);
-          if (f > lvt) {  // new in tree t for levels in [lvt, f)
-            atomicAdd(&c.D[t * 256 + lvt], 1);
-            if (f <= jhi) atomicAdd(&c.D[t * 256 + f], -1);
-          }
+          warp_bin_add(c.sm.H, valid && owner == t, m, 1u);
+          // new in tree t for levels in [lvt, f)
+          const unsigned nw = __ballot_sync(FULL, valid && f > lvt);
+          if (lane == 0 && nw) atomicAdd(&c.D[t * 256 + lvt], (int)__popc(nw));
+          warp_bin_add(reinterpret_cast<uint32_t *>(c.D + t * 256), valid && f > lvt && f <= jhi,
+                       f, 0xffffffffu);  // adds -1 per point (two's complement)
         }
       }
     }
@@ -329,7 +483,7 @@ __device__ void union_counts(QCtx &c) {
 }
 
 // ---- step 3: candidate cut inside tree i* and candidate list -------------
-__device__ void cut_and_collect(QCtx &c) {
+__device__ __forceinline__ void cut_and_collect(QCtx &c) {
   const QueryIndexView &ix = c.ix;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t js = (uint32_t)c.sm.jstar, ep = c.sm.epoch;
@@ -356,7 +510,7 @@ __device__ void cut_and_collect(QCtx &c) {
         for (uint32_t base = b; base < e; base += 32) {
           const uint32_t i = base + lane;
           bool nw = false;
-          if (i < e) nw = min_level_before(ix, c.s, ep, permi[i], is) > js;
+          if (i < e) nw = min_level_before(ix, c.s, c.sm, c.lut, permi[i], is) > js;
           cnt += __popc(__ballot_sync(FULL, nw));
         }
       }
@@ -408,7 +562,7 @@ __device__ void cut_and_collect(QCtx &c) {
           uint32_t p = 0;
           if (i < e) {
             p = permt[i];
-            take = (t == 0) || min_level_before(ix, c.s, ep, p, t) > js;
+            take = (t == 0) || min_level_before(ix, c.s, c.sm, c.lut, p, t) > js;
           }
           const unsigned tm = __ballot_sync(FULL, take);
           uint32_t pos0 = 0;
@@ -426,7 +580,7 @@ __device__ void cut_and_collect(QCtx &c) {
 // ---- step 4: distances ----------------------------------------------------
 // FP32: one warp per candidate, lanes over float4 chunks (d % 4 == 0) or
 // scalars; butterfly reduction.  Four candidates per warp in flight.
-__device__ void distances_fp32(QCtx &c, int64_t nc, bool allpts) {
+__device__ __forceinline__ void distances_fp32(QCtx &c, int64_t nc, bool allpts) {
   const QueryIndexView &ix = c.ix;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int d = ix.d;
@@ -479,7 +633,7 @@ __device__ void distances_fp32(QCtx &c, int64_t nc, bool allpts) {
 
 // BF16 scores: rows of 8-element uint4 chunks; a group of G lanes per
 // candidate (G = 8, 16 or 32 by d), 32/G candidates per warp at once.
-__device__ void distances_bf16(QCtx &c, int64_t nc, bool allpts) {
+__device__ __forceinline__ void distances_bf16(QCtx &c, int64_t nc, bool allpts) {
   const QueryIndexView &ix = c.ix;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int d = ix.d;
@@ -517,7 +671,7 @@ __device__ void distances_bf16(QCtx &c, int64_t nc, bool allpts) {
 // Selects the kk smallest (key, id) pairs among n items from get(i) and
 // leaves them sorted in sm.topk_key / sm.topk_id[0..kk).
 template <class Get>
-__device__ void topk_select(int64_t n, int kk, Get get, QShared &sm) {
+__device__ __forceinline__ void topk_select(int64_t n, int kk, Get get, QShared &sm) {
   auto gk = [&](int64_t i, uint32_t &k, uint32_t &w) { uint32_t id; get(i, k, id); w = 1u; };
   block_select(n, gk, (uint32_t)kk, sm);
   const uint32_t vk = sm.sel_v;
@@ -569,7 +723,7 @@ __device__ void topk_select(int64_t n, int kk, Get get, QShared &sm) {
   }
 }
 
-__global__ void __launch_bounds__(QT) k_query(QueryIndexView ix, QueryArgs qa) {
+__global__ void __launch_bounds__(QT, 5) k_query(QueryIndexView ix, QueryArgs qa) {
   extern __shared__ __align__(16) uint8_t dsm[];
   QShared &sm = *reinterpret_cast<QShared *>(dsm);
   float *lut = reinterpret_cast<float *>(dsm + align_up(sizeof(QShared), 16));
@@ -614,21 +768,29 @@ __global__ void __launch_bounds__(QT) k_query(QueryIndexView ix, QueryArgs qa) {
       if (threadIdx.x == 0) sm.epoch = qa.epoch_base + (uint32_t)qi;
       __syncthreads();
       expand_levels(c);
+      build_level_hash(c);
       union_counts(c);
-      if (threadIdx.x == 0) {
-        uint64_t N = 0;
-        int js = sm.jhi;
-        for (int j = 0; j <= sm.jhi; ++j) {
-          N += sm.H[j];
-          if (N >= (uint64_t)tau) { js = j; break; }
+      // j* = first level whose union count reaches tau (<= jhi by construction)
+      warp_first_crossing(sm.H, 0, (uint64_t)tau, &sm.sel_g, &sm.sel_bf);
+      __syncthreads();
+      const int js = min(sm.sel_g, sm.jhi);
+      {  // points new in each tree at level j*: one warp per tree
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        for (int t = warp; t < ix.L; t += QW) {
+          int64_t v = 0;
+          for (int j = lane; j <= js; j += 32) v += D[t * 256 + j];
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+          if (lane == 0) sm.newt[t] = v;
         }
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) {
         int64_t cum = 0, basev = 0;
         int is = ix.L - 1;
         for (int t = 0; t < ix.L; ++t) {
-          int64_t nt = 0;
-          for (int j = 0; j <= js; ++j) nt += D[t * 256 + j];
-          if (cum + nt >= tau) { is = t; basev = cum; break; }
-          cum += nt;
+          if (cum + sm.newt[t] >= tau) { is = t; basev = cum; break; }
+          cum += sm.newt[t];
         }
         sm.jstar = js;
         sm.istar = is;
