@@ -62,44 +62,77 @@ namespace {
 
 using namespace dl;
 
+// Device memory comes from a library-owned stream-ordered pool per device
+// that keeps freed blocks for reuse: repeated builds and growing query
+// buffers then allocate without synchronising the device.
+constexpr int kPoolDevices = 64;
+std::mutex g_pool_mu;
+cudaMemPool_t g_pool[kPoolDevices] = {};
+
+int pool_get(cudaMemPool_t *out) {
+  int dev = 0;
+  DL_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kPoolDevices) return DETLSH_ERR_NO_DEVICE;
+  std::lock_guard<std::mutex> g(g_pool_mu);
+  if (!g_pool[dev]) {
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pool;
+    DL_CUDA(cudaMemPoolCreate(&pool, &props));
+    uint64_t keep = UINT64_MAX;
+    DL_CUDA(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep));
+    g_pool[dev] = pool;
+  }
+  *out = g_pool[dev];
+  return DETLSH_OK;
+}
+
+int pool_alloc(void **p, size_t bytes, cudaStream_t st) {
+  cudaMemPool_t pool;
+  DL_TRY(pool_get(&pool));
+  DL_CUDA(cudaMallocFromPoolAsync(p, bytes ? bytes : 1, pool, st));
+  return DETLSH_OK;
+}
+
 template <class T>
-int dalloc(detlsh_index *ix, T **p, size_t count) {
+int dalloc(detlsh_index *ix, T **p, size_t count, cudaStream_t st) {
   *p = nullptr;
   if (count == 0) count = 1;
   void *q = nullptr;
-  DL_CUDA(cudaMalloc(&q, sizeof(T) * count));
+  DL_TRY(pool_alloc(&q, sizeof(T) * count, st));
   *p = static_cast<T *>(q);
-  if (ix) {
-    ix->owned.push_back(q);
-    ix->device_bytes += (int64_t)(sizeof(T) * count);
-  }
+  ix->owned.push_back(q);
+  ix->device_bytes += (int64_t)(sizeof(T) * count);
   return DETLSH_OK;
 }
 
 struct TempPool {
+  cudaStream_t st;
   std::vector<void *> ptrs;
+  explicit TempPool(cudaStream_t s) : st(s) {}
   template <class T>
   int get(T **p, size_t count) {
     *p = nullptr;
-    if (count == 0) count = 1;
     void *q = nullptr;
-    DL_CUDA(cudaMalloc(&q, sizeof(T) * count));
+    DL_TRY(pool_alloc(&q, sizeof(T) * (count ? count : 1), st));
     ptrs.push_back(q);
     *p = static_cast<T *>(q);
     return DETLSH_OK;
   }
   ~TempPool() {
-    for (void *q : ptrs) cudaFree(q);
+    for (void *q : ptrs) cudaFreeAsync(q, st);
   }
 };
 
-int grow(detlsh_index::QBuf &b, size_t bytes, bool *fresh = nullptr) {
+int grow(detlsh_index::QBuf &b, size_t bytes, cudaStream_t st, bool *fresh = nullptr) {
   if (fresh) *fresh = false;
   if (b.bytes >= bytes && b.p) return DETLSH_OK;
-  if (b.p) cudaFree(b.p);
+  if (b.p) cudaFreeAsync(b.p, st);
   b.p = nullptr;
   b.bytes = 0;
-  DL_CUDA(cudaMalloc(&b.p, bytes ? bytes : 1));
+  DL_TRY(pool_alloc(&b.p, bytes, st));
   b.bytes = bytes;
   if (fresh) *fresh = true;
   return DETLSH_OK;
@@ -188,9 +221,12 @@ void level_table(double eps2, double c, float *T) {
   T[NLEV - 1] = INFINITY;
 }
 
-__global__ void k_fill_minmax(uint32_t *mm, int LK) {
+__global__ void k_fill_minmax(uint32_t *mm, int LK, const float *B, int N_r) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < LK) { mm[2 * t] = 0xffffffffu; mm[2 * t + 1] = 0u; }
+  if (t < LK) {
+    mm[2 * t] = fkey(B[(int64_t)t * (N_r + 1) + 1] + 0.0f);
+    mm[2 * t + 1] = fkey(B[(int64_t)t * (N_r + 1) + N_r - 1] + 0.0f);
+  }
 }
 
 __global__ void k_iota(uint32_t *p, int64_t n) {
@@ -244,17 +280,17 @@ int validate_build(int64_t n, int32_t d, const detlsh_build_params *p) {
 int build_impl(detlsh_index *ix, const float *data, cudaStream_t st, const detlsh_build_params *p) {
   const int64_t n = ix->n;
   const int d = ix->d, L = ix->L, K = ix->K, LK = ix->LK, N_r = ix->N_r;
-  TempPool tp;
+  TempPool tp(st);
   DL_TRY(ensure_events(ix));
   const long long launches0 = g_launches.load();
   DL_CUDA(cudaEventRecord(ix->ev[0], st));
   // data copy (the index keeps its own FP32 rows for verification)
-  DL_TRY(dalloc(ix, &ix->X, (size_t)n * d));
+  DL_TRY(dalloc(ix, &ix->X, (size_t)n * d, st));
   DL_TRY(copy_in(ix->X, data, sizeof(float) * (size_t)n * d, st));
   // projection vectors (Eq. 1)
   std::vector<float> Ah((size_t)LK * d);
   projection_matrix(LK, d, ix->seed, Ah.data());
-  DL_TRY(dalloc(ix, &ix->A, (size_t)LK * d));
+  DL_TRY(dalloc(ix, &ix->A, (size_t)LK * d, st));
   DL_CUDA(cudaMemcpyAsync(ix->A, Ah.data(), sizeof(float) * Ah.size(), cudaMemcpyHostToDevice, st));
   // status words and the exact-path list
   int *err = nullptr;
@@ -273,7 +309,7 @@ int build_impl(detlsh_index *ix, const float *data, cudaStream_t st, const detls
   pa.fb_total = fb_total; pa.err = err;
 
   // ---- sample (Sec. III-A) ----
-  DL_TRY(dalloc(ix, &ix->sample, (size_t)n));
+  DL_TRY(dalloc(ix, &ix->sample, (size_t)n, st));
   uint32_t *blk = nullptr;
   DL_TRY(tp.get(&blk, sample_blocks(n) + 4));
   int64_t m = 0;
@@ -305,33 +341,49 @@ int build_impl(detlsh_index *ix, const float *data, cudaStream_t st, const detls
   DL_TRY(tp.get(&srt.vals_alt, (size_t)n));
   DL_TRY(tp.get(&srt.digit_base, (size_t)LK * 256));
   DL_TRY(segmented_sort(reinterpret_cast<uint32_t *>(Ps), nullptr, LK, m, 32, srt, st));
-  DL_TRY(dalloc(ix, &ix->B, (size_t)LK * (N_r + 1)));
+  DL_TRY(dalloc(ix, &ix->B, (size_t)LK * (N_r + 1), st));
   DL_TRY(extract_breakpoints(reinterpret_cast<uint32_t *>(Ps), LK, m, N_r, ix->B, st));
 
   DL_CUDA(cudaEventRecord(ix->ev[2], st));
   // ---- all projections, encoded (Alg. 1), and column min/max ----
-  DL_TRY(dalloc(ix, &ix->codes, (size_t)L * n * CODE_STRIDE));
+  DL_TRY(dalloc(ix, &ix->codes, (size_t)L * n * CODE_STRIDE, st));
   DL_CUDA(cudaMemsetAsync(ix->codes, 0, (size_t)L * n * CODE_STRIDE, st));
   uint32_t *minmax = nullptr;
   DL_TRY(tp.get(&minmax, (size_t)2 * LK));
-  k_fill_minmax<<<(unsigned)ceil_div(LK, 128), 128, 0, st>>>(minmax, LK);
+  // The column minimum is at most B[1] and the maximum at least B[N_r-1]
+  // (both are data values); points beyond them lie in the outer regions,
+  // which the encoder always recomputes exactly.
+  k_fill_minmax<<<(unsigned)ceil_div(LK, 128), 128, 0, st>>>(minmax, LK, ix->B, N_r);
   dl_count_launch();
+  // running bounds of the column extremes (same start as the extremes)
+  uint32_t *ubound = nullptr;
+  DL_TRY(tp.get(&ubound, (size_t)2 * LK));
+  DL_CUDA(cudaMemcpyAsync(ubound, minmax, sizeof(uint32_t) * 2 * LK, cudaMemcpyDeviceToDevice, st));
+  const double du = (double)d * 0x1p-24;
   ProjArgs pe = pa;
   pe.codes = ix->codes; pe.n = n; pe.B = ix->B; pe.N_r = N_r; pe.K = K; pe.minmax = minmax;
+  pe.ubound = ubound;
+  pe.gamma = std::nextafter((float)(0x1p-24 * (1.0 + 2.0 * du) * (1.0 + 1e-9)), INFINITY);
+  // uncertain or outer-region coordinates: a few per cent of n*LK
+  uint2 *fb_enc = nullptr;
+  const uint32_t fb_enc_cap = (uint32_t)std::min<int64_t>(std::max<int64_t>(n * LK / 16, 65536), 1 << 26);
+  DL_TRY(tp.get(&fb_enc, fb_enc_cap));
+  pe.fb_list = fb_enc;
+  pe.fb_cap = fb_enc_cap;
   DL_TRY(project_rows(ix->X, d, nullptr, n, d, ix->A, LK, 2, pe, st));
   e = check_err(err, st);
   if (e) return e;
   DL_TRY(finish_breakpoint_ends(minmax, LK, N_r, ix->B, st));
   DL_CUDA(cudaEventRecord(ix->ev[3], st));
   if (p->keep_projections) {
-    DL_TRY(dalloc(ix, &ix->P, (size_t)n * LK));
+    DL_TRY(dalloc(ix, &ix->P, (size_t)n * LK, st));
     ProjArgs pp = pa;
     pp.P = ix->P;
     pp.ldP = LK;
     DL_TRY(project_rows(ix->X, d, nullptr, n, d, ix->A, LK, 0, pp, st));
   }
   if (p->keep_bf16) {
-    DL_TRY(dalloc(ix, &ix->Xh, (size_t)n * d));
+    DL_TRY(dalloc(ix, &ix->Xh, (size_t)n * d, st));
     DL_TRY(dl::f32_to_bf16(ix->X, ix->Xh, n * (int64_t)d, st));
   }
   unsigned long long fbt = 0;
@@ -352,8 +404,8 @@ int build_impl(detlsh_index *ix, const float *data, cudaStream_t st, const detls
   DL_TRY(tp.get(&tt.leaf_base, (size_t)n));
   DL_TRY(tp.get(&tt.scalars, 8));
   tt.sort = srt;
-  DL_TRY(dalloc(ix, &ix->perm, (size_t)L * n));
-  DL_TRY(dalloc(ix, &ix->leaf_of, (size_t)L * n));
+  DL_TRY(dalloc(ix, &ix->perm, (size_t)L * n, st));
+  DL_TRY(dalloc(ix, &ix->leaf_of, (size_t)L * n, st));
   std::vector<uint32_t *> t_begin(L);
   std::vector<uint8_t *> t_box(L);
   uint32_t *lb_tmp = nullptr;
@@ -384,10 +436,10 @@ int build_impl(detlsh_index *ix, const float *data, cudaStream_t st, const detls
   int64_t tl = 0;
   for (int t = 0; t < L; ++t) { ix->leaf_off[t] = tl; tl += ix->nleaves[t]; }
   ix->leaf_off[L] = tl;
-  DL_TRY(dalloc(ix, &ix->leaf_begin, (size_t)tl + L));
-  DL_TRY(dalloc(ix, &ix->leaf_lo, (size_t)tl * 16));
-  DL_TRY(dalloc(ix, &ix->leaf_hi, (size_t)tl * 16));
-  DL_TRY(dalloc(ix, &ix->leaf_nb, (size_t)tl * 16));
+  DL_TRY(dalloc(ix, &ix->leaf_begin, (size_t)tl + L, st));
+  DL_TRY(dalloc(ix, &ix->leaf_lo, (size_t)tl * 16, st));
+  DL_TRY(dalloc(ix, &ix->leaf_hi, (size_t)tl * 16, st));
+  DL_TRY(dalloc(ix, &ix->leaf_nb, (size_t)tl * 16, st));
   for (int t = 0; t < L; ++t) {
     const int64_t nl = ix->nleaves[t], o = ix->leaf_off[t];
     DL_CUDA(cudaMemcpyAsync(ix->leaf_begin + o + t, t_begin[t], sizeof(uint32_t) * (nl + 1),
@@ -403,8 +455,8 @@ int build_impl(detlsh_index *ix, const float *data, cudaStream_t st, const detls
   for (int t = 0; t < L; ++t) { ix->blk_off[t] = tb; tb += ceil_div(ix->nleaves[t], LEAF_BLOCK); }
   ix->blk_off[L] = tb;
   for (int t = L + 1; t <= 16; ++t) ix->blk_off[t] = tb;
-  DL_TRY(dalloc(ix, &ix->blk_lo, (size_t)tb * 16));
-  DL_TRY(dalloc(ix, &ix->blk_hi, (size_t)tb * 16));
+  DL_TRY(dalloc(ix, &ix->blk_lo, (size_t)tb * 16, st));
+  DL_TRY(dalloc(ix, &ix->blk_hi, (size_t)tb * 16, st));
   for (int t = 0; t < L; ++t)
     DL_TRY(block_hulls(ix->leaf_lo + ix->leaf_off[t] * 16, ix->leaf_hi + ix->leaf_off[t] * 16,
                        ix->nleaves[t], ix->blk_lo + ix->blk_off[t] * 16,
@@ -424,12 +476,13 @@ int build_impl(detlsh_index *ix, const float *data, cudaStream_t st, const detls
 
 void free_index(detlsh_index *ix) {
   if (!ix) return;
-  for (void *q : ix->owned) cudaFree(q);
+  cudaDeviceSynchronize();  // no kernel of this index may still be running
+  for (void *q : ix->owned) cudaFreeAsync(q, 0);
   for (auto &e : ix->ev)
     if (e) cudaEventDestroy(e);
   for (auto *b : {&ix->qQ, &ix->qQh, &ix->qQp, &ix->qk, &ix->qids, &ix->qdists, &ix->qT,
                   &ix->qscratch, &ix->qstat, &ix->qS, &ix->qfb})
-    if (b->p) cudaFree(b->p);
+    if (b->p) cudaFreeAsync(b->p, 0);
   delete ix;
 }
 
@@ -475,12 +528,12 @@ int query_impl(detlsh_index *ix, const float *queries, int64_t m, const int32_t 
     for (int32_t v : kh)
       if (v < 1 || v > k_max) return DETLSH_ERR_INVALID_ARG;
   }
-  DL_TRY(grow(ix->qQ, sizeof(float) * (size_t)m * d));
-  DL_TRY(grow(ix->qQp, sizeof(float) * (size_t)m * LK));
-  DL_TRY(grow(ix->qids, sizeof(int64_t) * (size_t)m * k_max));
-  DL_TRY(grow(ix->qdists, sizeof(float) * (size_t)m * k_max));
-  DL_TRY(grow(ix->qT, sizeof(float) * 256));
-  DL_TRY(grow(ix->qstat, 256));
+  DL_TRY(grow(ix->qQ, sizeof(float) * (size_t)m * d, st));
+  DL_TRY(grow(ix->qQp, sizeof(float) * (size_t)m * LK, st));
+  DL_TRY(grow(ix->qids, sizeof(int64_t) * (size_t)m * k_max, st));
+  DL_TRY(grow(ix->qdists, sizeof(float) * (size_t)m * k_max, st));
+  DL_TRY(grow(ix->qT, sizeof(float) * 256, st));
+  DL_TRY(grow(ix->qstat, 256, st));
   float *Q = static_cast<float *>(ix->qQ.p);
   float *Qp = static_cast<float *>(ix->qQp.p);
   int *err = static_cast<int *>(ix->qstat.p);
@@ -492,14 +545,14 @@ int query_impl(detlsh_index *ix, const float *queries, int64_t m, const int32_t 
   DL_TRY(copy_in(Q, queries, sizeof(float) * (size_t)m * d, st));
   // exact query projections q'_i = H_i(q) (Alg. 5)
   const uint32_t fb_cap = (uint32_t)std::max<int64_t>(1024, m * LK / 64);
-  DL_TRY(grow(ix->qfb, sizeof(uint2) * fb_cap));
+  DL_TRY(grow(ix->qfb, sizeof(uint2) * fb_cap, st));
   ProjArgs pa;
   pa.P = Qp; pa.ldP = LK; pa.fb_count = fb_count; pa.fb_cap = fb_cap; pa.err = err;
   pa.fb_list = static_cast<uint2 *>(ix->qfb.p);
   DL_TRY(project_rows(Q, d, nullptr, m, d, ix->A, LK, 0, pa, st));
   const __nv_bfloat16 *Qh = nullptr;
   if (qp->precision == DETLSH_PREC_BF16_REFINE) {
-    DL_TRY(grow(ix->qQh, sizeof(__nv_bfloat16) * (size_t)m * d));
+    DL_TRY(grow(ix->qQh, sizeof(__nv_bfloat16) * (size_t)m * d, st));
     DL_TRY(dl::f32_to_bf16(Q, static_cast<__nv_bfloat16 *>(ix->qQh.p), m * (int64_t)d, st));
     Qh = static_cast<const __nv_bfloat16 *>(ix->qQh.p);
   }
@@ -509,7 +562,7 @@ int query_impl(detlsh_index *ix, const float *queries, int64_t m, const int32_t 
   DL_CUDA(cudaMemcpyAsync(ix->qT.p, Th, sizeof Th, cudaMemcpyHostToDevice, st));
   int32_t *kd = nullptr;
   if (kq) {
-    DL_TRY(grow(ix->qk, sizeof(int32_t) * (size_t)m));
+    DL_TRY(grow(ix->qk, sizeof(int32_t) * (size_t)m, st));
     kd = static_cast<int32_t *>(ix->qk.p);
     DL_CUDA(cudaMemcpyAsync(kd, kh.data(), sizeof(int32_t) * m, cudaMemcpyHostToDevice, st));
   }
@@ -527,7 +580,7 @@ int query_impl(detlsh_index *ix, const float *queries, int64_t m, const int32_t 
   qa.ids = static_cast<int64_t *>(ix->qids.p);
   qa.dists = static_cast<float *>(ix->qdists.p);
   if (S) {
-    DL_TRY(grow(ix->qS, sizeof(int64_t) * (size_t)m * S_cap + 3 * 8 * (size_t)m));
+    DL_TRY(grow(ix->qS, sizeof(int64_t) * (size_t)m * S_cap + 3 * 8 * (size_t)m, st));
     qa.S_out = static_cast<int64_t *>(ix->qS.p);
     qa.S_cap = S_cap;
     qa.S_size = qa.S_out + (size_t)m * S_cap;
@@ -544,7 +597,7 @@ int query_impl(detlsh_index *ix, const float *queries, int64_t m, const int32_t 
   DL_CUDA(cudaMemGetInfo(&freeb, &totb));
   while (slots > 1 && (size_t)slots * qa.slot_bytes > freeb / 4 + ix->qscratch.bytes) slots /= 2;
   bool fresh = false;
-  DL_TRY(grow(ix->qscratch, (size_t)slots * qa.slot_bytes, &fresh));
+  DL_TRY(grow(ix->qscratch, (size_t)slots * qa.slot_bytes, st, &fresh));
   // Leaf levels in the scratch carry a per-query epoch (base + query index);
   // start from zeroed scratch whenever it is new or the epochs would wrap.
   if (fresh || (uint64_t)ix->epoch_next + (uint64_t)m + 1 >= (1ull << 24)) {
@@ -845,9 +898,9 @@ int detlsh_project(const detlsh_index *cix, const float *rows, int64_t m, float 
   detlsh_index *ix = const_cast<detlsh_index *>(cix);
   std::lock_guard<std::mutex> g(ix->qmu);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  DL_TRY(grow(ix->qQ, sizeof(float) * (size_t)m * ix->d));
-  DL_TRY(grow(ix->qQp, sizeof(float) * (size_t)m * ix->LK));
-  DL_TRY(grow(ix->qstat, 256));
+  DL_TRY(grow(ix->qQ, sizeof(float) * (size_t)m * ix->d, st));
+  DL_TRY(grow(ix->qQp, sizeof(float) * (size_t)m * ix->LK, st));
+  DL_TRY(grow(ix->qstat, 256, st));
   DL_CUDA(cudaMemsetAsync(ix->qstat.p, 0, 256, st));
   float *Q = static_cast<float *>(ix->qQ.p);
   DL_TRY(copy_in(Q, rows, sizeof(float) * (size_t)m * ix->d, st));
@@ -857,7 +910,7 @@ int detlsh_project(const detlsh_index *cix, const float *rows, int64_t m, float 
   pa.err = static_cast<int *>(ix->qstat.p);
   pa.fb_count = reinterpret_cast<uint32_t *>(static_cast<char *>(ix->qstat.p) + 16);
   pa.fb_cap = (uint32_t)std::max<int64_t>(1024, m * ix->LK / 64);
-  DL_TRY(grow(ix->qfb, sizeof(uint2) * pa.fb_cap));
+  DL_TRY(grow(ix->qfb, sizeof(uint2) * pa.fb_cap, st));
   pa.fb_list = static_cast<uint2 *>(ix->qfb.p);
   DL_TRY(project_rows(Q, ix->d, nullptr, m, ix->d, ix->A, ix->LK, 0, pa, st));
   const int e = check_err(pa.err, st);

@@ -18,6 +18,8 @@ struct ProjArgs {
   const float *B = nullptr;  // [LK][N_r+1]
   int N_r = 0, K = 0;
   uint32_t *minmax = nullptr;  // [LK][2] order-preserving keys
+  uint32_t *ubound = nullptr;    // [LK][2] running bounds of column min/max (mode 2)
+  float gamma = 0.0f;            // u (1 + 2 d u), u = 2^-24, rounded up (mode 2)
   // outputs the compensated path cannot certify
   uint2 *fb_list = nullptr;
   uint32_t *fb_count = nullptr;

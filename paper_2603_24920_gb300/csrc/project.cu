@@ -15,6 +15,15 @@
 // |TwoSum error of (p + s)| + E stays below half the FP32 spacing at y.
 // Uncertified outputs (about 1e-5 of them) go to a list that an exact
 // big-integer kernel recomputes.
+//
+// Encoding (Alg. 1) needs only each coordinate's region, not its exact
+// value.  k_encode computes a plain FP32 FMA dot product y, whose distance
+// to the exact value is at most gamma_d * ||x|| * ||a|| (Higham's bound,
+// gamma_d = d u / (1 - d u), with Cauchy-Schwarz), widened by one unit in the
+// last place for the final rounding of the exact value.  When no breakpoint
+// lies in that interval the region is certain; otherwise -- and for the two
+// outer regions, which hold the column minimum and maximum -- the coordinate
+// is listed and recomputed exactly.
 #include "common.cuh"
 #include "kernels.h"
 
@@ -150,7 +159,6 @@ k_project(const float *__restrict__ X, int64_t ldx, const uint32_t *__restrict__
   // W = columns per tile, a multiple of K so that a tile never splits a tree
   __shared__ float Xs[PJ_ROWS][PJ_KC + 1];
   __shared__ float As[PJ_COLS][PJ_KC + 1];
-  extern __shared__ float dyn[];  // MODE 2: EncodeSmem + code staging
 
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
@@ -194,82 +202,6 @@ k_project(const float *__restrict__ X, int64_t ldx, const uint32_t *__restrict__
     }
   }
 
-  if constexpr (MODE == 2) {
-    // stage interior breakpoints of this tile's columns
-    float *Bs = dyn;                                                        // [64][BSTRIDE]
-    uint8_t *cst = reinterpret_cast<uint8_t *>(dyn + PJ_COLS * BSTRIDE);  // [64 rows][64 cols]
-    const int nint = o.N_r - 1;
-    __syncthreads();
-    for (int idx = tid; idx < PJ_COLS * 256; idx += PJ_THREADS) {
-      const int c = idx >> 8, z = idx & 255;
-      const int oc = col0 + c;
-      Bs[c * BSTRIDE + z] = (oc < LKt && z < nint) ? o.B[(int64_t)oc * (o.N_r + 1) + 1 + z] : 0.0f;
-    }
-    __syncthreads();
-    float cmin[4], cmax[4];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) { cmin[j] = __int_as_float(0x7f800000); cmax[j] = -cmin[j]; }
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int r = ty + 16 * i;
-      const int64_t rr = row0 + r;
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int c = tx + 16 * j;
-        const int oc = col0 + c;
-        float y;
-        const bool ok = dot2_finish(p[i][j], s[i][j], e[i][j], d, y);
-        uint8_t code = 0;
-        if (rr < nrows && oc < LKt) {
-          if (ok) {
-            code = (uint8_t)region_of(Bs + c * BSTRIDE, nint, y);
-            cmin[j] = fminf(cmin[j], y);
-            cmax[j] = fmaxf(cmax[j], y);
-          } else {
-            const uint32_t slot = atomicAdd(o.fb_count, 1u);
-            if (slot < o.fb_cap) o.fb_list[slot] = make_uint2((uint32_t)rr, (uint32_t)oc);
-          }
-        }
-        cst[r * PJ_COLS + c] = code;
-      }
-    }
-    // per-column min/max: reduce over the 16 row groups through shared memory
-    __syncthreads();
-    float *red = reinterpret_cast<float *>(cst + PJ_ROWS * PJ_COLS);  // [16][64][2]
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      red[(ty * PJ_COLS + tx + 16 * j) * 2 + 0] = cmin[j];
-      red[(ty * PJ_COLS + tx + 16 * j) * 2 + 1] = cmax[j];
-    }
-    __syncthreads();
-    if (tid < PJ_COLS && col0 + tid < LKt) {
-      float mn = red[tid * 2], mx = red[tid * 2 + 1];
-      for (int g = 1; g < 16; ++g) {
-        mn = fminf(mn, red[(g * PJ_COLS + tid) * 2]);
-        mx = fmaxf(mx, red[(g * PJ_COLS + tid) * 2 + 1]);
-      }
-      if (mn <= mx) {
-        atomicMin(&o.minmax[(col0 + tid) * 2 + 0], fkey(mn + 0.0f));
-        atomicMax(&o.minmax[(col0 + tid) * 2 + 1], fkey(mx + 0.0f));
-      }
-    }
-    // codes: 16 bytes per (tree, point); this tile covers trees col0/K ...
-    const int K = o.K;
-    const int ntree = (LKt - col0) / K;
-    const int t0 = col0 / K;
-    for (int idx = tid; idx < PJ_ROWS * ntree; idx += PJ_THREADS) {
-      const int r = idx / ntree, tt = idx % ntree;
-      const int64_t rr = row0 + r;
-      if (rr >= nrows) continue;
-      uint32_t w[4] = {0u, 0u, 0u, 0u};
-      for (int j = 0; j < K; ++j)
-        w[j >> 2] |= (uint32_t)cst[r * PJ_COLS + tt * K + j] << (8 * (j & 3));
-      uint4 *dst = reinterpret_cast<uint4 *>(o.codes + ((int64_t)(t0 + tt) * o.n + rr) * CODE_STRIDE);
-      *dst = make_uint4(w[0], w[1], w[2], w[3]);
-    }
-    return;
-  }
-
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
     const int64_t rr = row0 + ty + 16 * i;
@@ -291,38 +223,245 @@ k_project(const float *__restrict__ X, int64_t ldx, const uint32_t *__restrict__
   }
 }
 
-// Exact recomputation of the listed outputs.  The count is read on the
-// device, so no host synchronisation is needed; if the list overflowed, every
-// output is recomputed exactly (slow, but still exact).
+// Certified encoding: FP32 FMA estimate + rigorous a-posteriori bound.  Each
+// FMA s_k = fl(x_k a_k + s_{k-1}) errs by at most u |s_k|, so the estimate is
+// within u * sum_k |s_k| (+ an underflow allowance) of the exact product.  A
+// coordinate keeps its region when no breakpoint lies within that bound
+// widened by one unit in the last place (the rounding of the exact value);
+// otherwise it is listed.  Lowest- and highest-region coordinates are listed
+// only while they can still be the column minimum or maximum, tested against
+// running per-column bounds (init: B[1] and B[N_r-1], which are data values).
+__global__ void __launch_bounds__(PJ_THREADS, 2)
+k_encode(const float *__restrict__ X, int64_t ldx, int64_t nrows, int d,
+         const float *__restrict__ A, int LK, int W, ProjArgs o) {
+  __shared__ float Xs[PJ_ROWS][PJ_KC + 1];
+  __shared__ float As[PJ_COLS][PJ_KC + 1];
+  __shared__ uint32_t cmin[PJ_COLS], cmax[PJ_COLS];
+  extern __shared__ float dyn[];
+  uint8_t *cst = reinterpret_cast<uint8_t *>(dyn);  // [64 rows][64 cols] codes
+  const int tid = threadIdx.x;
+  const int tx = tid & 15, ty = tid >> 4;
+  const int col0 = blockIdx.y * W;
+  const int LKt = min(LK, col0 + W);
+  const int nint = o.N_r - 1;
+  const float eu = o.gamma;  // u (1 + 2 d u), rounded up
+  const float tiny = __fmul_rn((float)d, __uint_as_float(2u));  // d * 2^-148
+  const int K = o.K;
+  const int ntree = (LKt - col0) / K;
+  const int t0 = col0 / K;
+  const int64_t ntiles = ceil_div(nrows, PJ_ROWS);
+  // register prefetch of one tile chunk: 8 X values and 8 A values per thread
+  float px[8], pa[8];
+  auto fetch = [&](int64_t row0, int kc) {
+    const int kmax = min(PJ_KC, d - kc);
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int idx = tid + u * PJ_THREADS;
+      const int r = idx / PJ_KC, c = idx % PJ_KC;
+      const int64_t rr = row0 + r;
+      px[u] = (rr < nrows && c < kmax) ? X[rr * ldx + kc + c] : 0.0f;
+      const int oc = col0 + r;
+      pa[u] = (oc < LKt && c < kmax) ? A[(int64_t)oc * d + kc + c] : 0.0f;
+    }
+  };
+  auto stash = [&]() {
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int idx = tid + u * PJ_THREADS;
+      Xs[idx / PJ_KC][idx % PJ_KC] = px[u];
+      As[idx / PJ_KC][idx % PJ_KC] = pa[u];
+    }
+  };
+  int64_t tile = blockIdx.x;
+  if (tile < ntiles) fetch(tile * PJ_ROWS, 0);
+  for (; tile < ntiles; tile += gridDim.x) {
+    const int64_t row0 = tile * PJ_ROWS;
+    float acc[4][4], err[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[i][j] = err[i][j] = 0.0f;
+    for (int kc = 0; kc < d; kc += PJ_KC) {
+      const int kmax = min(PJ_KC, d - kc);
+      __syncthreads();
+      stash();
+      __syncthreads();
+      // prefetch the next chunk (or the first chunk of the next tile)
+      if (kc + PJ_KC < d) fetch(row0, kc + PJ_KC);
+      else if (tile + gridDim.x < ntiles) fetch((tile + gridDim.x) * PJ_ROWS, 0);
+#pragma unroll 4
+      for (int kk = 0; kk < kmax; ++kk) {
+        float xv[4], av[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) xv[i] = Xs[ty + 16 * i][kk];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) av[j] = As[tx + 16 * j][kk];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            acc[i][j] = __fmaf_rn(xv[i], av[j], acc[i][j]);
+            err[i][j] = __fadd_rn(err[i][j], fabsf(acc[i][j]));
+          }
+      }
+    }
+    if (tid < PJ_COLS) { cmin[tid] = 0xffffffffu; cmax[tid] = 0u; }
+    __syncthreads();
+    uint32_t flags = 0;  // bit i*4+j: output (i, j) goes to the exact list
+    float umin[4], lmax[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int oc = col0 + tx + 16 * j;
+      umin[j] = oc < LKt ? funkey(*(volatile uint32_t *)&o.ubound[oc * 2 + 0]) : 0.0f;
+      lmax[j] = oc < LKt ? funkey(*(volatile uint32_t *)&o.ubound[oc * 2 + 1]) : 0.0f;
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int r = ty + 16 * i;
+      const int64_t rr = row0 + r;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int c = tx + 16 * j;
+        const int oc = col0 + c;
+        uint8_t code = 0;
+        if (rr < nrows && oc < LKt) {
+          const float y = acc[i][j];
+          const float dlt = __fmaf_ru(eu, err[i][j], tiny);
+          const float dl2 = __fadd_ru(dlt, __fmul_ru(__fadd_ru(fabsf(y), dlt), 1.2e-7f));
+          const float lo = __fsub_rd(y, dl2), hi = __fadd_ru(y, dl2);
+          const float *Bc = o.B + (int64_t)oc * (o.N_r + 1) + 1;
+          const uint32_t reg = region_of(Bc, nint, y);
+          const bool finite = isfinite(y) && isfinite(dl2);
+          const bool sure = finite && (reg == 0 || Bc[reg - 1] < lo) &&
+                            (reg == (uint32_t)nint || Bc[reg] >= hi);
+          bool list = !sure;
+          if (reg == 0 && finite) {  // may be the column minimum?
+            list |= lo <= umin[j];
+            atomicMin(&cmin[c], fkey(hi));
+          }
+          if (reg == (uint32_t)nint && finite) {  // may be the column maximum?
+            list |= hi >= lmax[j];
+            atomicMax(&cmax[c], fkey(lo));
+          }
+          code = (uint8_t)reg;  // exact for sure coordinates; a hint for listed ones
+          if (list) flags |= 1u << (i * 4 + j);
+        }
+        cst[r * PJ_COLS + c] = code;
+      }
+    }
+    // one list reservation per warp: exclusive scan of the lanes' counts
+    {
+      const int lane = tid & 31;
+      const uint32_t cnt = __popc(flags);
+      uint32_t incl = cnt;
+#pragma unroll
+      for (int off = 1; off < 32; off <<= 1) {
+        const uint32_t y = __shfl_up_sync(FULL, incl, off);
+        if (lane >= off) incl += y;
+      }
+      uint32_t base = 0;
+      if (lane == 31 && incl) base = atomicAdd(o.fb_count, incl);
+      base = __shfl_sync(FULL, base, 31) + incl - cnt;
+      while (flags) {
+        const int b = __ffs(flags) - 1;
+        flags &= flags - 1;
+        const int64_t rr = row0 + ty + 16 * (b >> 2);
+        const int oc = col0 + tx + 16 * (b & 3);
+        const uint32_t hint = cst[(ty + 16 * (b >> 2)) * PJ_COLS + tx + 16 * (b & 3)];
+        if (base < o.fb_cap) o.fb_list[base] = make_uint2((uint32_t)rr, ((uint32_t)oc << 8) | hint);
+        ++base;
+      }
+    }
+    __syncthreads();
+    // tighten the running bounds: the column minimum is <= every hi seen in
+    // its lowest region, the maximum >= every lo seen in its highest region
+    if (tid < PJ_COLS && col0 + tid < LKt) {
+      if (cmin[tid] != 0xffffffffu) atomicMin(&o.ubound[(col0 + tid) * 2 + 0], cmin[tid]);
+      if (cmax[tid] != 0u) atomicMax(&o.ubound[(col0 + tid) * 2 + 1], cmax[tid]);
+    }
+    for (int idx = tid; idx < PJ_ROWS * ntree; idx += PJ_THREADS) {
+      const int r = idx / ntree, tt = idx % ntree;
+      const int64_t rr = row0 + r;
+      if (rr >= nrows) continue;
+      uint32_t w[4] = {0u, 0u, 0u, 0u};
+      for (int j = 0; j < K; ++j)
+        w[j >> 2] |= (uint32_t)cst[r * PJ_COLS + tt * K + j] << (8 * (j & 3));
+      uint4 *dst = reinterpret_cast<uint4 *>(o.codes + ((int64_t)(t0 + tt) * o.n + rr) * CODE_STRIDE);
+      *dst = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+  }
+}
+
+// Exact recomputation of the listed outputs, one warp per output.  Lanes
+// split the row (coalesced loads) and run the compensated recurrence on
+// their terms; lane 0 folds the 32 partial states (p_l, s_l, e_l) with the
+// same error-free TwoSum step, so the certificate of dot2_finish still
+// bounds the total error.  Uncertified outputs take the big-integer path.
+// The count is read on the device (no host synchronisation); if the list
+// overflowed, every output is recomputed.
 template <int MODE>
-__global__ void k_project_exact(const float *__restrict__ X, int64_t ldx,
-                                const uint32_t *__restrict__ rows, int64_t nrows, int d,
-                                const float *__restrict__ A, int LK, ProjArgs o) {
+__global__ void __launch_bounds__(256)
+k_project_exact(const float *__restrict__ X, int64_t ldx, const uint32_t *__restrict__ rows,
+                int64_t nrows, int d, const float *__restrict__ A, int LK, ProjArgs o) {
   const uint32_t cnt = *o.fb_count;
   if (cnt == 0) return;
   const bool all = cnt > o.fb_cap;
   if (blockIdx.x == 0 && threadIdx.x == 0 && o.fb_total)
     atomicAdd(o.fb_total, (unsigned long long)(all ? nrows * (int64_t)LK : (int64_t)cnt));
   const int64_t total = all ? nrows * (int64_t)LK : (int64_t)cnt;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
-       i += (int64_t)gridDim.x * blockDim.x) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < total; i += warps) {
     int64_t rr;
     int oc;
+    uint32_t hint = 0;
     if (all) { rr = i / LK; oc = (int)(i % LK); }
-    else { const uint2 f = o.fb_list[i]; rr = f.x; oc = (int)f.y; }
+    else {
+      const uint2 f = o.fb_list[i];
+      rr = f.x;
+      oc = MODE == 2 ? (int)(f.y >> 8) : (int)f.y;
+      hint = MODE == 2 ? (f.y & 255u) : 0u;
+    }
     const int64_t src = rows ? (int64_t)rows[rr] : rr;
+    const float *ar = A + (int64_t)oc * d;
+    const float *xr = X + src * ldx;
+    float p = 0.0f, sc = 0.0f, ec = 0.0f;
+    for (int k2 = lane; k2 < d; k2 += 32) dot2_step(p, sc, ec, xr[k2], ar[k2]);
+    // butterfly fold: (Pa,Sa,Ea) + (Pb,Sb,Eb) -> P = fl(Pa+Pb) with its exact
+    // TwoSum error q, S = fl(fl(Sa+Sb) + q), E gathers both bounds and the
+    // two new roundings; the true sum stays within u*E of P + S.
+    float P = p, S = sc, E = ec;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      const float pb = __shfl_xor_sync(FULL, P, off), sb = __shfl_xor_sync(FULL, S, off);
+      const float eb = __shfl_xor_sync(FULL, E, off);
+      const float t = __fadd_rn(P, pb);
+      const float z = __fsub_rn(t, P);
+      const float q = __fadd_rn(__fsub_rn(P, __fsub_rn(t, z)), __fsub_rn(pb, z));
+      const float w = __fadd_rn(S, sb);
+      const float s2 = __fadd_rn(w, q);
+      E = __fadd_rn(__fadd_rn(E, eb), __fadd_rn(fabsf(w), fabsf(s2)));
+      P = t;
+      S = s2;
+    }
+    if (lane != 0) continue;
+    float y;
     bool bad = false;
-    float y = exact_dot_rn(A + (int64_t)oc * d, X + src * ldx, d, &bad);
+    if (!dot2_finish(P, S, E, d + 32, y)) y = exact_dot_rn(ar, xr, d, &bad);
     if (bad) { atomicExch(o.err, (int)DETLSH_ERR_NONFINITE_INPUT); continue; }
     y = y + 0.0f;  // exact zero is +0
     if (MODE == 0) { o.P[rr * o.ldP + oc] = y; continue; }
     if (MODE == 1) { o.P[(int64_t)oc * o.ldP + rr] = y; continue; }
     const float *Bint = o.B + (int64_t)oc * (o.N_r + 1) + 1;
-    const uint32_t code = region_of(Bint, o.N_r - 1, y);
+    // walk from the estimated region to the exact one (#breakpoints < y)
+    uint32_t code = min(hint, (uint32_t)(o.N_r - 1));
+    while (code > 0 && !(Bint[code - 1] < y)) --code;
+    while (code < (uint32_t)(o.N_r - 1) && Bint[code] < y) ++code;
     const int t = oc / o.K, j = oc % o.K;
     o.codes[((int64_t)t * o.n + rr) * CODE_STRIDE + j] = (uint8_t)code;
-    atomicMin(&o.minmax[oc * 2 + 0], fkey(y));
-    atomicMax(&o.minmax[oc * 2 + 1], fkey(y));
+    // the column minimum (maximum) lies in the lowest (highest) region
+    if (code == 0) atomicMin(&o.minmax[oc * 2 + 0], fkey(y));
+    if (code == (uint32_t)(o.N_r - 1)) atomicMax(&o.minmax[oc * 2 + 1], fkey(y));
   }
 }
 
@@ -335,14 +474,23 @@ static int project_impl(const float *X, int64_t ldx, const uint32_t *rows, int64
   dim3 grid((unsigned)ceil_div(nrows, PJ_ROWS), (unsigned)ceil_div(LK, W));
   size_t dyn = 0;
   if (MODE == 2) {
-    dyn = sizeof(float) * PJ_COLS * BSTRIDE + PJ_ROWS * PJ_COLS + sizeof(float) * 16 * PJ_COLS * 2;
-    DL_CUDA(cudaFuncSetAttribute(k_project<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)dyn));
+    dyn = PJ_ROWS * PJ_COLS;
   }
-  k_project<MODE><<<grid, PJ_THREADS, dyn, st>>>(X, ldx, rows, nrows, d, A, LK, W, o);
+  if constexpr (MODE == 2) {
+    DL_CUDA(cudaFuncSetAttribute(k_encode, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+    int dev = 0, sms = 0, per = 0;
+    DL_CUDA(cudaGetDevice(&dev));
+    DL_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    DL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_encode, PJ_THREADS, dyn));
+    const int64_t gx = std::min<int64_t>(grid.x, (int64_t)sms * std::max(per, 1) / grid.y + 1);
+    dim3 pgrid((unsigned)std::max<int64_t>(gx, 1), grid.y);
+    k_encode<<<pgrid, PJ_THREADS, dyn, st>>>(X, ldx, nrows, d, A, LK, W, o);
+  } else {
+    k_project<MODE><<<grid, PJ_THREADS, dyn, st>>>(X, ldx, rows, nrows, d, A, LK, W, o);
+  }
   dl_count_launch();
   DL_CUDA(cudaGetLastError());
-  k_project_exact<MODE><<<256, 128, 0, st>>>(X, ldx, rows, nrows, d, A, LK, o);
+  k_project_exact<MODE><<<2048, 256, 0, st>>>(X, ldx, rows, nrows, d, A, LK, o);
   dl_count_launch();
   DL_CUDA(cudaGetLastError());
   return DETLSH_OK;
