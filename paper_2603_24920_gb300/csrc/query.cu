@@ -35,6 +35,7 @@ constexpr int QT = 256;
 constexpr int QW = QT / 32;
 constexpr int KMAX = 1024;
 constexpr int RR_MAX = 4096;  // re-rank pool of the BF16 path
+constexpr int FLC = 512;      // listed leaves per chunk of a flattened visit
 
 struct Slot {
   uint32_t *lev;    // [total_leaves] (epoch << 8) | level of expanded leaves
@@ -94,6 +95,7 @@ struct QShared {
   uint32_t cpos;
   int jchk;
 };
+static_assert(KMAX >= 1024, "the flattened visit borrows the top-k arrays");
 
 __device__ __forceinline__ uint32_t byte_of(const uint4 &c, int j) {
   const uint32_t w = j < 4 ? c.x : j < 8 ? c.y : j < 12 ? c.z : c.w;
@@ -434,34 +436,95 @@ __device__ __forceinline__ void build_level_hash(QCtx &c) {
   __syncthreads();
 }
 
+// ---- flattened visit of the points of listed leaves ------------------------
+// Threads are spread over points rather than leaves (leaves hold ~20 points
+// on average): per chunk of listed leaves, a block scan lays out the points of
+// the leaves selected by pred, and each thread finds its point's leaf by a
+// binary search in shared memory.  fn(valid, point, entry, level) is called
+// by every thread with a uniform trip count, so it may use warp collectives.
+// With count set, the points visited are added to the CTA's work counter.
+template <class Pred, class Fn>
+__device__ __forceinline__ void visit_points(QCtx &c, int t, Pred pred, Fn fn, bool count = false) {
+  const QueryIndexView &ix = c.ix;
+  QShared &sm = c.sm;
+  const int64_t nlist = sm.nlist[t];
+  const int64_t lo0 = ix.leaf_off[t];
+  const uint32_t *permt = ix.perm + (int64_t)t * ix.n;
+  // chunk layout in the top-k arrays (free until the top-k step of a query):
+  // point prefix [FLC + 1], leaf level bytes [FLC]; perm begin, list entry [FLC] each
+  uint32_t *fl_pre = sm.topk_key;
+  uint8_t *fl_lev = reinterpret_cast<uint8_t *>(sm.topk_key + 520);
+  uint32_t *fl_beg = sm.topk_id;
+  uint32_t *fl_ent = sm.topk_id + FLC;
+  for (int64_t e0 = 0; e0 < nlist; e0 += FLC) {
+    uint32_t q[2], sz[2], bg[2];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int64_t e = e0 + threadIdx.x * 2 + u;
+      q[u] = 0; sz[u] = 0; bg[u] = 0;
+      if (e < nlist && pred(e)) {
+        const uint32_t leaf = c.s.lleaf[lo0 + e];
+        bg[u] = leaf_begin_of(ix, t, leaf);
+        sz[u] = leaf_begin_of(ix, t, leaf + 1) - bg[u];
+        q[u] = 1;
+      }
+    }
+    uint32_t nq, np;
+    const uint32_t qs = block_exclusive_scan(q[0] + q[1], sm.wt, &nq);
+    const uint32_t ps = block_exclusive_scan(sz[0] + sz[1], sm.wt, &np);
+    {
+      uint32_t slot = qs, pre = ps;
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        if (q[u]) {
+          const int64_t e = e0 + threadIdx.x * 2 + u;
+          fl_pre[slot] = pre;
+          fl_beg[slot] = bg[u];
+          fl_ent[slot] = (uint32_t)e;
+          fl_lev[slot] = c.s.llev[lo0 + e];
+          ++slot;
+          pre += sz[u];
+        }
+      }
+    }
+    if (threadIdx.x == 0) {
+      fl_pre[nq] = np;
+      if (count) sm.n_visit += np;
+    }
+    __syncthreads();
+    for (uint32_t i0 = 0; i0 < np; i0 += QT) {
+      const uint32_t i = i0 + threadIdx.x;
+      const bool valid = i < np;
+      uint32_t p = 0, ent = 0, lev = 255u;
+      if (valid) {
+        int lo = 0, hi = (int)nq;  // last k with fl_pre[k] <= i
+        while (hi - lo > 1) {
+          const int mid = (lo + hi) >> 1;
+          if (fl_pre[mid] <= i) lo = mid; else hi = mid;
+        }
+        p = permt[fl_beg[lo] + (i - fl_pre[lo])];
+        ent = fl_ent[lo];
+        lev = fl_lev[lo];
+      }
+      fn(valid, p, ent, lev);
+    }
+    __syncthreads();
+  }
+}
+
 // ---- step 2: owner-rule union counts and per-tree new-point counts -------
 __device__ __forceinline__ void union_counts(QCtx &c) {
   const QueryIndexView &ix = c.ix;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const uint32_t jhi = (uint32_t)c.sm.jhi, ep = c.sm.epoch;
+  const uint32_t jhi = (uint32_t)c.sm.jhi;
   for (int t = 0; t < ix.L; ++t) {
-    const int64_t nlist = c.sm.nlist[t];
-    const uint32_t *permt = ix.perm + (int64_t)t * ix.n;
     const int64_t lo0 = ix.leaf_off[t];
-    for (int64_t chunk = (int64_t)warp * 32; chunk < nlist; chunk += QT) {
-      const int64_t e_ = chunk + lane;
-      const uint32_t mylv = e_ < nlist ? c.s.llev[lo0 + e_] : 255u;
-      const uint32_t myleaf = e_ < nlist ? c.s.lleaf[lo0 + e_] : 0u;
-      unsigned mask = __ballot_sync(FULL, e_ < nlist && mylv <= jhi);
-      while (mask) {
-        const int src = __ffs(mask) - 1;
-        mask &= mask - 1;
-        const uint32_t lq = __shfl_sync(FULL, myleaf, src);
-        const uint32_t lvt = __shfl_sync(FULL, mylv, src);
-        const uint32_t b = leaf_begin_of(ix, t, lq), e = leaf_begin_of(ix, t, lq + 1);
-        if (lane == 0) atomicAdd(&c.sm.n_visit, (unsigned long long)(e - b));
-        for (uint32_t base = b; base < e; base += 32) {
-          const uint32_t i = base + lane;
-          const bool valid = i < e;
+    uint32_t *Dt = reinterpret_cast<uint32_t *>(c.D + t * 256);
+    visit_points(
+        c, t, [&](int64_t e) { return c.s.llev[lo0 + e] <= jhi; },
+        [&](bool valid, uint32_t p, uint32_t, uint32_t lvt) {
           uint32_t m = 255u, f = 255u;
           int owner = -1;
           if (valid) {
-            const uint32_t p = permt[i];
             const uint32_t *lo = ix.leaf_of + (int64_t)p * ix.L;
             for (int u = 0; u < ix.L; ++u) {
               const uint32_t lv = (u == t) ? lvt : leaf_level_h(ix, c.s, c.sm, c.lut, u, lo[u]);
@@ -471,13 +534,10 @@ __device__ __forceinline__ void union_counts(QCtx &c) {
           }
           warp_bin_add(c.sm.H, valid && owner == t, m, 1u);
           // new in tree t for levels in [lvt, f)
-          const unsigned nw = __ballot_sync(FULL, valid && f > lvt);
-          if (lane == 0 && nw) atomicAdd(&c.D[t * 256 + lvt], (int)__popc(nw));
-          warp_bin_add(reinterpret_cast<uint32_t *>(c.D + t * 256), valid && f > lvt && f <= jhi,
-                       f, 0xffffffffu);  // adds -1 per point (two's complement)
-        }
-      }
-    }
+          warp_bin_add(Dt, valid && f > lvt, lvt, 1u);
+          warp_bin_add(Dt, valid && f > lvt && f <= jhi, f, 0xffffffffu);  // -1 (two's complement)
+        },
+        true);
   }
   __syncthreads();
 }
@@ -485,37 +545,27 @@ __device__ __forceinline__ void union_counts(QCtx &c) {
 // ---- step 3: candidate cut inside tree i* and candidate list -------------
 __device__ __forceinline__ void cut_and_collect(QCtx &c) {
   const QueryIndexView &ix = c.ix;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const uint32_t js = (uint32_t)c.sm.jstar, ep = c.sm.epoch;
+  const uint32_t js = (uint32_t)c.sm.jstar;
   const int is = c.sm.istar;
   const int64_t li0 = ix.leaf_off[is];
   const int64_t nli = c.sm.nlist[is];
-  const uint32_t *permi = ix.perm + (int64_t)is * ix.n;
   // new points of every qualifying listed leaf of tree i*
-  for (int64_t chunk = (int64_t)warp * 32; chunk < nli; chunk += QT) {
-    const int64_t e_ = chunk + lane;
-    const bool q = e_ < nli && c.s.llev[li0 + e_] <= js;
-    const uint32_t myleaf = e_ < nli ? c.s.lleaf[li0 + e_] : 0u;
-    if (e_ < nli) c.s.cval[e_] = 0;
-    unsigned mask = __ballot_sync(FULL, q);
-    while (mask) {
-      const int src = __ffs(mask) - 1;
-      mask &= mask - 1;
-      const uint32_t lq = __shfl_sync(FULL, myleaf, src);
-      const uint32_t b = leaf_begin_of(ix, is, lq), e = leaf_begin_of(ix, is, lq + 1);
-      uint32_t cnt = 0;
-      if (is == 0) {
-        cnt = e - b;
-      } else {
-        for (uint32_t base = b; base < e; base += 32) {
-          const uint32_t i = base + lane;
-          bool nw = false;
-          if (i < e) nw = min_level_before(ix, c.s, c.sm, c.lut, permi[i], is) > js;
-          cnt += __popc(__ballot_sync(FULL, nw));
-        }
-      }
-      if (lane == 0) c.s.cval[chunk + src] = cnt;
+  for (int64_t e = threadIdx.x; e < nli; e += QT) {
+    uint32_t v = 0;
+    if (is == 0 && c.s.llev[li0 + e] <= js) {
+      const uint32_t leaf = c.s.lleaf[li0 + e];
+      v = leaf_begin_of(ix, is, leaf + 1) - leaf_begin_of(ix, is, leaf);
     }
+    c.s.cval[e] = v;
+  }
+  __syncthreads();
+  if (is > 0) {
+    visit_points(
+        c, is, [&](int64_t e) { return c.s.llev[li0 + e] <= js; },
+        [&](bool valid, uint32_t p, uint32_t ent, uint32_t) {
+          const bool nw = valid && min_level_before(ix, c.s, c.sm, c.lut, p, is) > js;
+          warp_bin_add(c.s.cval, nw, ent, 1u);
+        });
   }
   __syncthreads();
   // priority order (LB^2, leaf index): smallest LB^2 value v reaching the
@@ -538,41 +588,26 @@ __device__ __forceinline__ void cut_and_collect(QCtx &c) {
   // collect S: trees before i* whole (new points only), tree i* up to the cut
   if (threadIdx.x == 0) c.sm.ncand = 0;
   __syncthreads();
+  const int lane = threadIdx.x & 31;
   for (int t = 0; t <= is; ++t) {
-    const int64_t nlist = c.sm.nlist[t];
     const int64_t lo0 = ix.leaf_off[t];
-    const uint32_t *permt = ix.perm + (int64_t)t * ix.n;
-    for (int64_t chunk = (int64_t)warp * 32; chunk < nlist; chunk += QT) {
-      const int64_t e_ = chunk + lane;
-      bool q = e_ < nlist && c.s.llev[lo0 + e_] <= js;
-      const uint32_t myleaf = e_ < nlist ? c.s.lleaf[lo0 + e_] : 0u;
-      if (q && t == is) {
-        const uint32_t kb = __float_as_uint(c.s.llb2[lo0 + e_]);
-        q = kb < v || (kb == v && myleaf <= cut);
-      }
-      unsigned mask = __ballot_sync(FULL, q);
-      while (mask) {
-        const int src = __ffs(mask) - 1;
-        mask &= mask - 1;
-        const uint32_t lq = __shfl_sync(FULL, myleaf, src);
-        const uint32_t b = leaf_begin_of(ix, t, lq), e = leaf_begin_of(ix, t, lq + 1);
-        for (uint32_t base = b; base < e; base += 32) {
-          const uint32_t i = base + lane;
-          bool take = false;
-          uint32_t p = 0;
-          if (i < e) {
-            p = permt[i];
-            take = (t == 0) || min_level_before(ix, c.s, c.sm, c.lut, p, t) > js;
-          }
+    visit_points(
+        c, t,
+        [&](int64_t e) {
+          if (c.s.llev[lo0 + e] > js) return false;
+          if (t < is) return true;
+          const uint32_t kb = __float_as_uint(c.s.llb2[lo0 + e]);
+          return kb < v || (kb == v && c.s.lleaf[lo0 + e] <= cut);
+        },
+        [&](bool valid, uint32_t p, uint32_t, uint32_t) {
+          const bool take = valid && (t == 0 || min_level_before(ix, c.s, c.sm, c.lut, p, t) > js);
           const unsigned tm = __ballot_sync(FULL, take);
           uint32_t pos0 = 0;
           if (lane == 0 && tm) pos0 = atomicAdd(&c.sm.ncand, (uint32_t)__popc(tm));
           pos0 = __shfl_sync(FULL, pos0, 0);
           const uint32_t pos = pos0 + __popc(tm & ((1u << lane) - 1u));
           if (take && pos < (uint32_t)c.qa.cand_cap) c.s.cand[pos] = p;
-        }
-      }
-    }
+        });
   }
   __syncthreads();
 }
