@@ -134,6 +134,14 @@ __device__ __forceinline__ void warp_bin_add(uint32_t *bins, bool active, uint32
   }
 }
 
+// Adds w to bins[v] for every active lane (w the same in every lane): lanes
+// holding the same v are grouped in one step and the lowest lane of each
+// group adds w times the group size.
+__device__ __forceinline__ void warp_bin_count(uint32_t *bins, bool active, uint32_t v, uint32_t w) {
+  const unsigned grp = __match_any_sync(FULL, active ? v : 0xffffffffu);
+  if (active && __ffs(grp) - 1 == (int)(threadIdx.x & 31)) atomicAdd(&bins[v], w * (uint32_t)__popc(grp));
+}
+
 // Warp 0 finds, over 256 bins, the first bin g with
 // below + sum(bins[0..g]) >= need, and writes g and the sum of the bins
 // before it (plus below) to shared memory.  Every thread of the block calls
@@ -202,7 +210,7 @@ struct QCtx {
   const QueryIndexView &ix;
   const QueryArgs &qa;
   QShared &sm;
-  float *lut;       // [16][N_r+1]
+  float *lut;       // [LUT_ROWS][LUT_STRIDE]
   uint32_t *hist;   // [L][256] point counts of expanded leaves by level
   int32_t *D;       // [L][256] new-point difference arrays
   Slot s;
@@ -248,15 +256,25 @@ __device__ __forceinline__ uint32_t min_level_before(const QueryIndexView &ix, c
   return f;
 }
 
+// The per-tree lookup table has 16 rows of LUT_STRIDE entries whatever K and
+// N_r are: rows j >= K are zero, so the padded code bytes (zero) add an exact
+// 0 to the sum, and every table offset is a compile-time constant.
+constexpr int LUT_STRIDE = 257;
+constexpr int LUT_ROWS = 16;
+
 // Squared lower bound of a box (Sec. IV-C) from the per-tree table
 // lut[j][z] = B_j[z] - q'_j: per dimension gap = max(0, B(lo) - q, q - B(hi+1)),
 // summed in FP32 over dimensions in order.
-__device__ __forceinline__ float box_lb2(const float *lut, int NR1, int K, const uint4 &lo,
-                                         const uint4 &hi) {
+__device__ __forceinline__ float box_lb2(const float *lut, const uint4 &lo, const uint4 &hi) {
+  const uint32_t wl[4] = {lo.x, lo.y, lo.z, lo.w};
+  const uint32_t wh[4] = {hi.x, hi.y, hi.z, hi.w};
   float acc = 0.0f;
-  for (int j = 0; j < K; ++j) {
-    const float a = lut[j * NR1 + byte_of(lo, j)];
-    const float b = -lut[j * NR1 + byte_of(hi, j) + 1];
+#pragma unroll
+  for (int j = 0; j < LUT_ROWS; ++j) {
+    const uint32_t zl = (wl[j >> 2] >> (8 * (j & 3))) & 255u;
+    const uint32_t zh = (wh[j >> 2] >> (8 * (j & 3))) & 255u;
+    const float a = lut[j * LUT_STRIDE + zl];
+    const float b = -lut[j * LUT_STRIDE + zh + 1];
     const float gap = fmaxf(fmaxf(a, b), 0.0f);
     acc = __fadd_rn(acc, __fmul_rn(gap, gap));
   }
@@ -281,9 +299,11 @@ __device__ __forceinline__ void expand_levels(QCtx &c) {
   if (threadIdx.x == 0) sm.jhi = NLEV - 1;
   __syncthreads();
   for (int t = 0; t < ix.L; ++t) {
-    for (int idx = threadIdx.x; idx < K * NR1; idx += QT) {
-      const int j = idx / NR1, z = idx % NR1;
-      c.lut[j * NR1 + z] = __fsub_rn(ix.B[(int64_t)(t * K + j) * NR1 + z], qp[t * K + j]);
+    for (int j = 0; j < LUT_ROWS; ++j) {
+      const float qj = j < K ? qp[t * K + j] : 0.0f;
+      const float *Bj = ix.B + (int64_t)(t * K + j) * NR1;
+      for (int z = threadIdx.x; z < LUT_STRIDE; z += QT)
+        c.lut[j * LUT_STRIDE + z] = (j < K && z < NR1) ? __fsub_rn(Bj[z], qj) : 0.0f;
     }
     sm.rh[threadIdx.x] = 0;
     if (threadIdx.x == 0) { sm.nlist[t] = 0; sm.cum = 0; sm.stop = 0; sm.jcur = NLEV; }
@@ -295,15 +315,15 @@ __device__ __forceinline__ void expand_levels(QCtx &c) {
     const uint4 *hhi = reinterpret_cast<const uint4 *>(ix.blk_hi) + ix.blk_off[t];
     uint8_t *blev = c.s.blev + ix.blk_off[t];
     if (threadIdx.x == 0) sm.n_blocks += (unsigned long long)nb;
-    for (int64_t b0 = 0; b0 < nb; b0 += QT) {  // uniform trip count for warp_bin_add
+    for (int64_t b0 = 0; b0 < nb; b0 += QT) {  // uniform trip count for the warp collectives
       const int64_t b = b0 + threadIdx.x;
       uint32_t lv = 255u;
       if (b < nb) {
-        lv = level_of(sm.T, box_lb2(c.lut, NR1, K, hlo[b], hhi[b]), c.qa.lg_eps2, c.qa.inv_2lg_c);
+        lv = level_of(sm.T, box_lb2(c.lut, hlo[b], hhi[b]), c.qa.lg_eps2, c.qa.inv_2lg_c);
         blev[b] = lv <= J0 ? (uint8_t)lv : (uint8_t)255;
         if (lv <= J0) atomicMin(&sm.jcur, (int)lv);
       }
-      warp_bin_add(sm.rh, b < nb && lv <= J0, lv, 1u);
+      warp_bin_count(sm.rh, b < nb && lv <= J0, lv, 1u);
     }
     __syncthreads();
     if (threadIdx.x < 32) {  // exclusive prefix of the per-level block counts
@@ -351,13 +371,13 @@ __device__ __forceinline__ void expand_levels(QCtx &c) {
         float lb = 0.0f;
         uint32_t sz = 0;
         if (valid) {
-          lb = box_lb2(c.lut, NR1, K, llo[l], lhi[l]);
+          lb = box_lb2(c.lut, llo[l], lhi[l]);
           lv = level_of(sm.T, lb, c.qa.lg_eps2, c.qa.inv_2lg_c);
           c.s.lev[ix.leaf_off[t] + l] = (ep << 8) | lv;
           sz = leaf_begin_of(ix, t, l + 1) - leaf_begin_of(ix, t, l);
         }
-        warp_bin_add(hist_t, valid, lv, sz);
         const bool keep = valid && lv <= Jnow;
+        warp_bin_add(hist_t, keep, lv, sz);  // levels above Jnow never reach a check
         const unsigned km = __ballot_sync(FULL, keep);
         const unsigned vm = __ballot_sync(FULL, valid);
         if (lane == 0) atomicAdd(&sm.n_leaves, (unsigned long long)__popc(vm));
@@ -397,7 +417,7 @@ __device__ __forceinline__ void build_level_hash(QCtx &c) {
   const QueryIndexView &ix = c.ix;
   QShared &sm = c.sm;
   const uint32_t jhi = (uint32_t)sm.jhi;
-  const uint32_t bytes = 16u * (uint32_t)(ix.N_r + 1) * 4u;
+  const uint32_t bytes = (uint32_t)(LUT_ROWS * LUT_STRIDE * sizeof(float));
   uint32_t bits = 0;
   while ((1u << (bits + 1)) * 5u <= bytes && bits + 1 <= 12) ++bits;
   if (threadIdx.x == 0) { sm.hash_count = 0; sm.hash_bits = bits; }
@@ -532,10 +552,10 @@ __device__ __forceinline__ void union_counts(QCtx &c) {
               if (u < t) f = min(f, lv);
             }
           }
-          warp_bin_add(c.sm.H, valid && owner == t, m, 1u);
+          warp_bin_count(c.sm.H, valid && owner == t, m, 1u);
           // new in tree t for levels in [lvt, f)
-          warp_bin_add(Dt, valid && f > lvt, lvt, 1u);
-          warp_bin_add(Dt, valid && f > lvt && f <= jhi, f, 0xffffffffu);  // -1 (two's complement)
+          warp_bin_count(Dt, valid && f > lvt, lvt, 1u);
+          warp_bin_count(Dt, valid && f > lvt && f <= jhi, f, 0xffffffffu);  // -1 (two's complement)
         },
         true);
   }
@@ -564,7 +584,7 @@ __device__ __forceinline__ void cut_and_collect(QCtx &c) {
         c, is, [&](int64_t e) { return c.s.llev[li0 + e] <= js; },
         [&](bool valid, uint32_t p, uint32_t ent, uint32_t) {
           const bool nw = valid && min_level_before(ix, c.s, c.sm, c.lut, p, is) > js;
-          warp_bin_add(c.s.cval, nw, ent, 1u);
+          warp_bin_count(c.s.cval, nw, ent, 1u);
         });
   }
   __syncthreads();
@@ -762,7 +782,7 @@ __global__ void __launch_bounds__(QT, 5) k_query(QueryIndexView ix, QueryArgs qa
   extern __shared__ __align__(16) uint8_t dsm[];
   QShared &sm = *reinterpret_cast<QShared *>(dsm);
   float *lut = reinterpret_cast<float *>(dsm + align_up(sizeof(QShared), 16));
-  uint32_t *hist = reinterpret_cast<uint32_t *>(lut + 16 * (ix.N_r + 1));
+  uint32_t *hist = reinterpret_cast<uint32_t *>(lut + LUT_ROWS * LUT_STRIDE);
   int32_t *D = reinterpret_cast<int32_t *>(hist + 256 * ix.L);
 
   uint8_t *base = qa.scratch + (int64_t)blockIdx.x * qa.slot_bytes;
@@ -944,7 +964,7 @@ __global__ void __launch_bounds__(QT, 5) k_query(QueryIndexView ix, QueryArgs qa
 }
 
 static size_t query_smem(const QueryIndexView &ix) {
-  return (size_t)align_up(sizeof(QShared), 16) + sizeof(float) * 16 * (ix.N_r + 1) +
+  return (size_t)align_up(sizeof(QShared), 16) + sizeof(float) * LUT_ROWS * LUT_STRIDE +
          sizeof(uint32_t) * 256 * ix.L * 2;
 }
 
