@@ -38,6 +38,7 @@ struct detlsh_index {
   // device arrays
   float *X = nullptr;
   __nv_bfloat16 *Xh = nullptr;
+  float *Xn = nullptr;  // squared norms of the BF16 rows (FP32)
   float *A = nullptr, *B = nullptr, *P = nullptr;
   uint8_t *codes = nullptr;
   uint32_t *sample = nullptr;
@@ -235,6 +236,24 @@ __global__ void k_iota(uint32_t *p, int64_t n) {
     p[i] = (uint32_t)i;
 }
 
+// BF16 copy of the data, one warp per row, with the FP32 squared norm of each
+// rounded row (the norm term of the tensor-core scores).
+__global__ void k_rows_to_bf16(const float *s, __nv_bfloat16 *h, float *nrm, int64_t n, int d) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < n; r += warps) {
+    float acc = 0.0f;
+    for (int j = lane; j < d; j += 32) {
+      const __nv_bfloat16 v = __float2bfloat16_rn(s[r * d + j]);
+      h[r * d + j] = v;
+      const float f = __bfloat162float(v);
+      acc = __fmaf_rn(f, f, acc);
+    }
+    for (int o = 16; o > 0; o >>= 1) acc = __fadd_rn(acc, __shfl_xor_sync(0xffffffffu, acc, o));
+    if (lane == 0) nrm[r] = acc;
+  }
+}
+
 __global__ void k_f32_to_bf16(const float *s, __nv_bfloat16 *d, int64_t count) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
        i += (int64_t)gridDim.x * blockDim.x)
@@ -384,7 +403,11 @@ int build_impl(detlsh_index *ix, const float *data, cudaStream_t st, const detls
   }
   if (p->keep_bf16) {
     DL_TRY(dalloc(ix, &ix->Xh, (size_t)n * d, st));
-    DL_TRY(dl::f32_to_bf16(ix->X, ix->Xh, n * (int64_t)d, st));
+    DL_TRY(dalloc(ix, &ix->Xn, (size_t)n, st));
+    k_rows_to_bf16<<<(unsigned)std::min<int64_t>(ceil_div(n, 8), 8192), 256, 0, st>>>(
+        ix->X, ix->Xh, ix->Xn, n, d);
+    dl_count_launch();
+    DL_CUDA(cudaGetLastError());
   }
   unsigned long long fbt = 0;
   DL_CUDA(cudaMemcpyAsync(&fbt, fb_total, sizeof fbt, cudaMemcpyDeviceToHost, st));
@@ -489,7 +512,7 @@ void free_index(detlsh_index *ix) {
 QueryIndexView view_of(const detlsh_index *ix) {
   QueryIndexView v;
   v.n = ix->n; v.d = ix->d; v.L = ix->L; v.K = ix->K; v.LK = ix->LK; v.N_r = ix->N_r;
-  v.X = ix->X; v.Xh = ix->Xh; v.B = ix->B; v.perm = ix->perm; v.leaf_begin = ix->leaf_begin;
+  v.X = ix->X; v.Xh = ix->Xh; v.Xn = ix->Xn; v.B = ix->B; v.perm = ix->perm; v.leaf_begin = ix->leaf_begin;
   v.leaf_lo = ix->leaf_lo; v.leaf_hi = ix->leaf_hi; v.leaf_of = ix->leaf_of;
   v.blk_lo = ix->blk_lo; v.blk_hi = ix->blk_hi;
   for (int t = 0; t <= 16; ++t) v.blk_off[t] = ix->blk_off[t];

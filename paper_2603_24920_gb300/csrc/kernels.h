@@ -93,6 +93,7 @@ struct QueryIndexView {
   int d, L, K, LK, N_r;
   const float *X;
   const __nv_bfloat16 *Xh;
+  const float *Xn;           // [n] squared norms of the BF16 rows
   const float *B;            // [LK][N_r+1]
   const uint32_t *perm;      // [L][n]
   const uint32_t *leaf_begin;  // concatenated, tree t at leaf_off[t] + t

@@ -84,7 +84,7 @@ struct QShared {
   // scalars
   int64_t qi;
   int jhi, jstar, istar, jcur, stop;
-  uint32_t need, ncand, sel_v, sel_below, nres, epoch;
+  uint32_t need, ncand, sel_v, sel_below, sel_at, nres, epoch;
   uint64_t cum;
   unsigned long long n_blocks, n_leaves, n_visit;  // work counters of this CTA
   int use_hash;
@@ -94,6 +94,7 @@ struct QShared {
   int64_t newt[16];
   uint32_t cpos;
   int jchk;
+  float qn;  // |q|^2 of the BF16 query
 };
 static_assert(KMAX >= 1024, "the flattened visit borrows the top-k arrays");
 
@@ -182,7 +183,8 @@ __device__ __forceinline__ void warp_first_crossing(const uint32_t *bins, uint64
 
 // Block-wide weighted radix select over 32-bit keys: finds the smallest key
 // v with W(key <= v) >= need, where item i has (key_i, weight_i) from get(i)
-// (weight 0 = absent).  Returns v in sm.sel_v and W(key < v) in sm.sel_below.
+// (weight 0 = absent).  Returns v in sm.sel_v, W(key < v) in sm.sel_below and
+// W(key == v) in sm.sel_at.
 template <class Get>
 __device__ __forceinline__ void block_select(int64_t N, Get get, uint32_t need, QShared &sm) {
   uint32_t prefix = 0, below = 0;
@@ -202,7 +204,7 @@ __device__ __forceinline__ void block_select(int64_t N, Get get, uint32_t need, 
     below = (uint32_t)sm.sel_bf;
     __syncthreads();
   }
-  if (threadIdx.x == 0) { sm.sel_v = prefix; sm.sel_below = below; }
+  if (threadIdx.x == 0) { sm.sel_v = prefix; sm.sel_below = below; sm.sel_at = sm.rh[prefix & 255u]; }
   __syncthreads();
 }
 
@@ -459,8 +461,9 @@ __device__ __forceinline__ void build_level_hash(QCtx &c) {
 // ---- flattened visit of the points of listed leaves ------------------------
 // Threads are spread over points rather than leaves (leaves hold ~20 points
 // on average): per chunk of listed leaves, a block scan lays out the points of
-// the leaves selected by pred, and each thread finds its point's leaf by a
-// binary search in shared memory.  fn(valid, point, entry, level) is called
+// the leaves selected by pred, and each warp walks a run of consecutive
+// points, a lane finding the leaf of its first point by a binary search in
+// shared memory.  fn(valid, point, entry, level) is called
 // by every thread with a uniform trip count, so it may use warp collectives.
 // With count set, the points visited are added to the CTA's work counter.
 template <class Pred, class Fn>
@@ -512,19 +515,28 @@ __device__ __forceinline__ void visit_points(QCtx &c, int t, Pred pred, Fn fn, b
       if (count) sm.n_visit += np;
     }
     __syncthreads();
-    for (uint32_t i0 = 0; i0 < np; i0 += QT) {
-      const uint32_t i = i0 + threadIdx.x;
+    // each warp walks a run of P * 32 consecutive points, lane-interleaved
+    // (coalesced): one search for the leaf of a lane's first point, then
+    // forward steps over leaf boundaries
+    const uint32_t P = (np + QT - 1) / QT;
+    const uint32_t i0 = (threadIdx.x >> 5) * P * 32u + (threadIdx.x & 31);
+    int cur = 0;
+    if (i0 < np) {
+      int hi = (int)nq;  // last k with fl_pre[k] <= i0
+      while (hi - cur > 1) {
+        const int mid = (cur + hi) >> 1;
+        if (fl_pre[mid] <= i0) cur = mid; else hi = mid;
+      }
+    }
+    for (uint32_t r = 0; r < P; ++r) {
+      const uint32_t i = i0 + r * 32u;
       const bool valid = i < np;
       uint32_t p = 0, ent = 0, lev = 255u;
       if (valid) {
-        int lo = 0, hi = (int)nq;  // last k with fl_pre[k] <= i
-        while (hi - lo > 1) {
-          const int mid = (lo + hi) >> 1;
-          if (fl_pre[mid] <= i) lo = mid; else hi = mid;
-        }
-        p = permt[fl_beg[lo] + (i - fl_pre[lo])];
-        ent = fl_ent[lo];
-        lev = fl_lev[lo];
+        while (fl_pre[cur + 1] <= i) ++cur;
+        p = permt[fl_beg[cur] + (i - fl_pre[cur])];
+        ent = fl_ent[cur];
+        lev = fl_lev[cur];
       }
       fn(valid, p, ent, lev);
     }
@@ -598,13 +610,16 @@ __device__ __forceinline__ void cut_and_collect(QCtx &c) {
   block_select(nli, get_lb, need, c.sm);
   const uint32_t v = c.sm.sel_v;
   const uint32_t need2 = need - c.sm.sel_below;
-  auto get_id = [&](int64_t i, uint32_t &k, uint32_t &w) {
-    const bool q = c.s.llev[li0 + i] <= js && __float_as_uint(c.s.llb2[li0 + i]) == v;
-    w = q ? c.s.cval[i] : 0u;
-    k = c.s.lleaf[li0 + i];
-  };
-  block_select(nli, get_id, need2, c.sm);
-  const uint32_t cut = c.sm.sel_v;
+  uint32_t cut = 0xffffffffu;  // every leaf at LB^2 == v when all of them are needed
+  if (need2 < c.sm.sel_at) {
+    auto get_id = [&](int64_t i, uint32_t &k, uint32_t &w) {
+      const bool q = c.s.llev[li0 + i] <= js && __float_as_uint(c.s.llb2[li0 + i]) == v;
+      w = q ? c.s.cval[i] : 0u;
+      k = c.s.lleaf[li0 + i];
+    };
+    block_select(nli, get_id, need2, c.sm);
+    cut = c.sm.sel_v;
+  }
   // collect S: trees before i* whole (new points only), tree i* up to the cut
   if (threadIdx.x == 0) c.sm.ncand = 0;
   __syncthreads();
@@ -633,91 +648,202 @@ __device__ __forceinline__ void cut_and_collect(QCtx &c) {
 }
 
 // ---- step 4: distances ----------------------------------------------------
-// FP32: one warp per candidate, lanes over float4 chunks (d % 4 == 0) or
-// scalars; butterfly reduction.  Four candidates per warp in flight.
-__device__ __forceinline__ void distances_fp32(QCtx &c, int64_t nc, bool allpts) {
-  const QueryIndexView &ix = c.ix;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int d = ix.d;
-  const float *q = c.qa.Q + c.qi * d;
-  const bool vec = (d & 3) == 0;
-  for (int64_t i0 = (int64_t)warp * 4; i0 < nc; i0 += QW * 4) {
-    float acc[4] = {0.f, 0.f, 0.f, 0.f};
-    uint32_t pid[4];
+// Sums NV per-lane values over aligned groups of W lanes in log2(W) shuffle
+// rounds: each round halves the values a lane holds by swapping half of them
+// with its partner, then a butterfly finishes.  Afterwards every lane holds
+// the group total of value index transpose_index<NV, W>(lane).
+template <int NV, int W>
+__device__ __forceinline__ float transpose_sum(float (&a)[NV], int lane) {
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int64_t i = i0 + u;
-      pid[u] = i < nc ? (allpts ? (uint32_t)i : c.s.cand[i]) : 0u;
+  for (int n = NV, off = W / 2; n > 1; n >>= 1, off >>= 1) {
+    const bool up = (lane & off) != 0;
+#pragma unroll
+    for (int i = 0; i < n / 2; ++i) {
+      const float send = up ? a[i] : a[i + n / 2];
+      const float keep = up ? a[i + n / 2] : a[i];
+      a[i] = __fadd_rn(keep, __shfl_xor_sync(FULL, send, off));
     }
-    if (vec) {
-      const int d4 = d >> 2;
-      for (int ch = lane; ch < d4; ch += 32) {
-        const float4 qv = reinterpret_cast<const float4 *>(q)[ch];
+  }
+  float v = a[0];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          if (i0 + u >= nc) continue;
-          const float4 xv = reinterpret_cast<const float4 *>(ix.X + (int64_t)pid[u] * d)[ch];
-          float t0 = __fsub_rn(qv.x, xv.x), t1 = __fsub_rn(qv.y, xv.y);
-          float t2 = __fsub_rn(qv.z, xv.z), t3 = __fsub_rn(qv.w, xv.w);
+  for (int off = W / NV / 2; off > 0; off >>= 1) v = __fadd_rn(v, __shfl_xor_sync(FULL, v, off));
+  return v;
+}
+template <int NV, int W>
+__device__ __forceinline__ int transpose_index(int lane) {
+  int idx = 0;
+#pragma unroll
+  for (int n = NV, off = W / 2; n > 1; n >>= 1, off >>= 1) idx = idx * 2 + ((lane & off) ? 1 : 0);
+  return idx;
+}
+
+// FP32 squared distances sum((q - x)^2) of rows get_id(0..nrows) into out[]
+// (as ordered uint32 keys).  A row is split over W lanes (float4 chunks when
+// d % 4 == 0, else scalars); a warp keeps 4 * (32 / W) rows in flight.
+template <int W, bool VEC, class GetId>
+__device__ __forceinline__ void dist_fp32_rows(const QueryIndexView &ix, const float *q,
+                                               int64_t nrows, GetId get_id, uint32_t *out) {
+  constexpr int NV = 4, PER = 32 / W, RPI = NV * PER;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int h = lane / W, cl = lane % W;
+  const int d = ix.d;
+  const int nch = VEC ? d >> 2 : d;
+  for (int64_t r0 = (int64_t)warp * RPI; r0 < nrows; r0 += QW * RPI) {
+    uint32_t myid = 0;
+    if (lane < RPI && r0 + lane < nrows) myid = get_id(r0 + lane);
+    // row ids of the lane's rows (the shuffles stay outside the chunk loop,
+    // whose trip count differs between lanes)
+    uint32_t pid[NV];
+#pragma unroll
+    for (int u = 0; u < NV; ++u) pid[u] = __shfl_sync(FULL, myid, u * PER + h);
+    float acc[NV];
+#pragma unroll
+    for (int u = 0; u < NV; ++u) acc[u] = 0.0f;
+    for (int ch = cl; ch < nch; ch += W) {
+      if (VEC) {
+        const float4 qv = reinterpret_cast<const float4 *>(q)[ch];
+        float4 xv[NV];
+#pragma unroll
+        for (int u = 0; u < NV; ++u)  // issue every row's load first
+          xv[u] = r0 + u * PER + h < nrows
+                      ? reinterpret_cast<const float4 *>(ix.X + (int64_t)pid[u] * d)[ch]
+                      : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int u = 0; u < NV; ++u) {
+          const float t0 = __fsub_rn(qv.x, xv[u].x), t1 = __fsub_rn(qv.y, xv[u].y);
+          const float t2 = __fsub_rn(qv.z, xv[u].z), t3 = __fsub_rn(qv.w, xv[u].w);
           acc[u] = __fmaf_rn(t0, t0, acc[u]);
           acc[u] = __fmaf_rn(t1, t1, acc[u]);
           acc[u] = __fmaf_rn(t2, t2, acc[u]);
           acc[u] = __fmaf_rn(t3, t3, acc[u]);
         }
-      }
-    } else {
-      for (int ch = lane; ch < d; ch += 32) {
+      } else {
         const float qv = q[ch];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          if (i0 + u >= nc) continue;
-          const float t0 = __fsub_rn(qv, ix.X[(int64_t)pid[u] * d + ch]);
+        for (int u = 0; u < NV; ++u) {
+          const float xv = r0 + u * PER + h < nrows ? ix.X[(int64_t)pid[u] * d + ch] : qv;
+          const float t0 = __fsub_rn(qv, xv);
           acc[u] = __fmaf_rn(t0, t0, acc[u]);
         }
       }
     }
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) acc[u] = __fadd_rn(acc[u], __shfl_xor_sync(FULL, acc[u], o));
-      if (lane == 0 && i0 + u < nc) c.s.key[i0 + u] = __float_as_uint(acc[u]);
-    }
+    const float v = transpose_sum<NV, W>(acc, cl);
+    const int64_t r = r0 + (int64_t)transpose_index<NV, W>(cl) * PER + h;
+    if ((cl & (W / NV - 1)) == 0 && r < nrows) out[r] = __float_as_uint(v);
+  }
+}
+
+template <class GetId>
+__device__ __forceinline__ void dist_fp32(const QueryIndexView &ix, const float *q, int64_t nrows,
+                                          GetId get_id, uint32_t *out) {
+  const int d = ix.d;
+  if ((d & 3) == 0) {
+    const int nch = d >> 2;
+    if (nch >= 32) dist_fp32_rows<32, true>(ix, q, nrows, get_id, out);
+    else if (nch >= 16) dist_fp32_rows<16, true>(ix, q, nrows, get_id, out);
+    else dist_fp32_rows<8, true>(ix, q, nrows, get_id, out);
+  } else {
+    if (d >= 32) dist_fp32_rows<32, false>(ix, q, nrows, get_id, out);
+    else if (d >= 16) dist_fp32_rows<16, false>(ix, q, nrows, get_id, out);
+    else dist_fp32_rows<8, false>(ix, q, nrows, get_id, out);
   }
   __syncthreads();
 }
 
-// BF16 scores: rows of 8-element uint4 chunks; a group of G lanes per
-// candidate (G = 8, 16 or 32 by d), 32/G candidates per warp at once.
+__device__ __forceinline__ void distances_fp32(QCtx &c, int64_t nc, bool allpts) {
+  const uint32_t *cand = c.s.cand;
+  dist_fp32(c.ix, c.qa.Q + c.qi * c.ix.d, nc,
+            [&](int64_t i) { return allpts ? (uint32_t)i : cand[i]; }, c.s.key);
+}
+
+// One m16n8k16 BF16 tensor-core product with FP32 accumulation (c += a b).
+__device__ __forceinline__ void mma_bf16_16816(float (&c)[4], uint32_t a0, uint32_t a1,
+                                               uint32_t a2, uint32_t a3, uint32_t b0,
+                                               uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
+      "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+// BF16 scores on the tensor cores: score(x) = |q|^2 + |x|^2 - 2 q.x with the
+// dot products of 16 candidate rows per warp and k-block of 16 from one
+// m16n8k16 MMA (the query is column 0 of B; columns 1-7 are zero).  The dot
+// product does not depend on the order of k, so each lane loads 4 consecutive
+// elements per row and k-block (8 bytes) and the same 4 query elements are
+// placed at the matching B positions: memory element 4t+{0,1,2,3} of a block
+// is MMA k-index {2t, 2t+1, 2t+8, 2t+9} for lane t = lane % 4.
 __device__ __forceinline__ void distances_bf16(QCtx &c, int64_t nc, bool allpts) {
   const QueryIndexView &ix = c.ix;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int d = ix.d;
-  const int d8 = d >> 3;  // d % 8 == 0 required for this path
-  const int G = d8 <= 8 ? 8 : (d8 <= 16 ? 16 : 32);
-  const int per = 32 / G;
-  const int g = lane / G, gl = lane % G;
-  const uint4 *q8 = reinterpret_cast<const uint4 *>(c.qa.Qh + c.qi * d);
-  for (int64_t i0 = (int64_t)warp * per; i0 < nc; i0 += QW * per) {
-    const int64_t i = i0 + g;
-    float acc = 0.f;
-    if (i < nc) {
-      const uint32_t p = allpts ? (uint32_t)i : c.s.cand[i];
-      const uint4 *x8 = reinterpret_cast<const uint4 *>(ix.Xh + (int64_t)p * d);
-      for (int ch = gl; ch < d8; ch += G) {
-        const uint4 qv = q8[ch], xv = x8[ch];
-        const __nv_bfloat162 *qa = reinterpret_cast<const __nv_bfloat162 *>(&qv);
-        const __nv_bfloat162 *xa = reinterpret_cast<const __nv_bfloat162 *>(&xv);
+  const int d = ix.d;  // d % 8 == 0 on this path
+  const int g = lane >> 2, t = lane & 3;
+  const __nv_bfloat16 *qh = c.qa.Qh + c.qi * d;
+  // |q|^2 of the BF16 query
+  if (warp == 0) {
+    float a = 0.0f;
+    for (int j = lane; j < d; j += 32) {
+      const float f = __bfloat162float(qh[j]);
+      a = __fmaf_rn(f, f, a);
+    }
+    for (int o = 16; o > 0; o >>= 1) a = __fadd_rn(a, __shfl_xor_sync(FULL, a, o));
+    if (lane == 0) c.sm.qn = a;
+  }
+  __syncthreads();
+  const float qn = c.sm.qn;
+  const int nblk = (d + 15) >> 4;
+  auto id_of = [&](int64_t r) -> uint32_t {
+    return (lane < 16 && r + lane < nc) ? (allpts ? (uint32_t)(r + lane) : c.s.cand[r + lane]) : 0u;
+  };
+  uint32_t myid = id_of((int64_t)warp * 16);
+  for (int64_t r0 = (int64_t)warp * 16; r0 < nc; r0 += QW * 16) {
+    const uint32_t p0 = __shfl_sync(FULL, myid, g), p1 = __shfl_sync(FULL, myid, g + 8);
+    const bool ok0 = r0 + g < nc, ok1 = r0 + g + 8 < nc;
+    // norms and the next rows' ids go out with this tile's row loads
+    float xn0 = 0.0f, xn1 = 0.0f;
+    if (t == 0) {
+      if (ok0) xn0 = ix.Xn[p0];
+      if (ok1) xn1 = ix.Xn[p1];
+    }
+    myid = id_of(r0 + QW * 16);
+    const __nv_bfloat16 *x0 = ix.Xh + (int64_t)p0 * d + 4 * t;
+    const __nv_bfloat16 *x1 = ix.Xh + (int64_t)p1 * d + 4 * t;
+    const __nv_bfloat16 *qt = qh + 4 * t;
+    float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    int b = 0;
+    for (; b + 4 <= nblk && (b + 4) * 16 <= d; b += 4) {  // four k-blocks: loads first
+      uint2 xa[4], xb[4], qv[4];
 #pragma unroll
-        for (int h = 0; h < 4; ++h) {
-          const float2 qf = __bfloat1622float2(qa[h]), xf = __bfloat1622float2(xa[h]);
-          const float t0 = qf.x - xf.x, t1 = qf.y - xf.y;
-          acc = __fmaf_rn(t0, t0, acc);
-          acc = __fmaf_rn(t1, t1, acc);
-        }
+      for (int u = 0; u < 4; ++u) {
+        const int e = (b + u) * 16;
+        xa[u] = ok0 ? *reinterpret_cast<const uint2 *>(x0 + e) : make_uint2(0u, 0u);
+        xb[u] = ok1 ? *reinterpret_cast<const uint2 *>(x1 + e) : make_uint2(0u, 0u);
+        qv[u] = g == 0 ? *reinterpret_cast<const uint2 *>(qt + e) : make_uint2(0u, 0u);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) mma_bf16_16816(acc, xa[u].x, xb[u].x, xa[u].y, xb[u].y, qv[u].x, qv[u].y);
+    }
+    for (; b < nblk; ++b) {
+      const int e = b * 16;
+      uint2 xa = make_uint2(0u, 0u), xb = make_uint2(0u, 0u), qv = make_uint2(0u, 0u);
+      if (e + 4 * t < d) {  // d % 4 == 0: the 4 elements are all in range
+        if (ok0) xa = *reinterpret_cast<const uint2 *>(x0 + e);
+        if (ok1) xb = *reinterpret_cast<const uint2 *>(x1 + e);
+        if (g == 0) qv = *reinterpret_cast<const uint2 *>(qt + e);
+      }
+      mma_bf16_16816(acc, xa.x, xb.x, xa.y, xb.y, qv.x, qv.y);
+    }
+    if (t == 0) {
+      if (ok0) {
+        const float s0 = __fadd_rn(__fadd_rn(qn, xn0), -2.0f * acc[0]);
+        c.s.key[r0 + g] = __float_as_uint(fmaxf(s0, 0.0f));
+      }
+      if (ok1) {
+        const float s1 = __fadd_rn(__fadd_rn(qn, xn1), -2.0f * acc[2]);
+        c.s.key[r0 + g + 8] = __float_as_uint(fmaxf(s1, 0.0f));
       }
     }
-    for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
-    if (gl == 0 && i < nc) c.s.key[i] = __float_as_uint(acc);
   }
   __syncthreads();
 }
@@ -731,15 +857,18 @@ __device__ __forceinline__ void topk_select(int64_t n, int kk, Get get, QShared 
   block_select(n, gk, (uint32_t)kk, sm);
   const uint32_t vk = sm.sel_v;
   const uint32_t below = sm.sel_below;
-  // ties at vk: the (kk - below) smallest ids
-  auto gi = [&](int64_t i, uint32_t &k, uint32_t &w) {
-    uint32_t key, id;
-    get(i, key, id);
-    k = id;
-    w = key == vk ? 1u : 0u;
-  };
-  block_select(n, gi, (uint32_t)kk - below, sm);
-  const uint32_t idcut = sm.sel_v;
+  // ties at vk: the (kk - below) smallest ids, unless all of them are needed
+  uint32_t idcut = 0xffffffffu;
+  if ((uint32_t)kk - below < sm.sel_at) {
+    auto gi = [&](int64_t i, uint32_t &k, uint32_t &w) {
+      uint32_t key, id;
+      get(i, key, id);
+      k = id;
+      w = key == vk ? 1u : 0u;
+    };
+    block_select(n, gi, (uint32_t)kk - below, sm);
+    idcut = sm.sel_v;
+  }
   if (threadIdx.x == 0) sm.nres = 0;
   __syncthreads();
   for (int64_t i = threadIdx.x; i < n; i += QT) {
@@ -885,14 +1014,17 @@ __global__ void __launch_bounds__(QT, 5) k_query(QueryIndexView ix, QueryArgs qa
       auto gk = [&](int64_t i, uint32_t &kk2, uint32_t &w) { uint32_t id; get_s(i, kk2, id); w = 1u; };
       block_select(nc, gk, (uint32_t)R, sm);
       const uint32_t vk = sm.sel_v, below = sm.sel_below;
-      auto gi = [&](int64_t i, uint32_t &kk2, uint32_t &w) {
-        uint32_t key, id;
-        get_s(i, key, id);
-        kk2 = id;
-        w = key == vk ? 1u : 0u;
-      };
-      block_select(nc, gi, (uint32_t)R - below, sm);
-      const uint32_t idcut = sm.sel_v;
+      uint32_t idcut = 0xffffffffu;
+      if ((uint32_t)R - below < sm.sel_at) {
+        auto gi = [&](int64_t i, uint32_t &kk2, uint32_t &w) {
+          uint32_t key, id;
+          get_s(i, key, id);
+          kk2 = id;
+          w = key == vk ? 1u : 0u;
+        };
+        block_select(nc, gi, (uint32_t)R - below, sm);
+        idcut = sm.sel_v;
+      }
       if (threadIdx.x == 0) sm.nres = 0;
       __syncthreads();
       for (int64_t i = threadIdx.x; i < nc; i += QT) {
@@ -905,35 +1037,7 @@ __global__ void __launch_bounds__(QT, 5) k_query(QueryIndexView ix, QueryArgs qa
       }
       __syncthreads();
       // exact FP32 distances of the re-rank pool
-      {
-        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-        const int d = ix.d;
-        const float *q = qa.Q + qi * d;
-        for (int r = warp; r < R; r += QW) {
-          const uint32_t p = s.rid[r];
-          float acc = 0.f;
-          if ((d & 3) == 0) {
-            for (int ch = lane; ch < (d >> 2); ch += 32) {
-              const float4 qv = reinterpret_cast<const float4 *>(q)[ch];
-              const float4 xv = reinterpret_cast<const float4 *>(ix.X + (int64_t)p * d)[ch];
-              float t0 = __fsub_rn(qv.x, xv.x), t1 = __fsub_rn(qv.y, xv.y);
-              float t2 = __fsub_rn(qv.z, xv.z), t3 = __fsub_rn(qv.w, xv.w);
-              acc = __fmaf_rn(t0, t0, acc);
-              acc = __fmaf_rn(t1, t1, acc);
-              acc = __fmaf_rn(t2, t2, acc);
-              acc = __fmaf_rn(t3, t3, acc);
-            }
-          } else {
-            for (int ch = lane; ch < d; ch += 32) {
-              const float t0 = __fsub_rn(q[ch], ix.X[(int64_t)p * d + ch]);
-              acc = __fmaf_rn(t0, t0, acc);
-            }
-          }
-          for (int o = 16; o > 0; o >>= 1) acc = __fadd_rn(acc, __shfl_xor_sync(FULL, acc, o));
-          if (lane == 0) s.rkey[r] = __float_as_uint(acc);
-        }
-        __syncthreads();
-      }
+      dist_fp32(ix, qa.Q + qi * ix.d, R, [&](int64_t i) { return s.rid[i]; }, s.rkey);
       auto get_r = [&](int64_t i, uint32_t &key, uint32_t &id) { key = s.rkey[i]; id = s.rid[i]; };
       topk_select(R, k, get_r, sm);
     } else {
