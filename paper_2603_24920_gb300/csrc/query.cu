@@ -248,13 +248,33 @@ __device__ __forceinline__ uint32_t leaf_level_h(const QueryIndexView &ix, const
   return (v >> 8) == sm.epoch ? (v & 255u) : 255u;
 }
 
+// Leaf of point p in tree u.  With LC = 4 (four trees) the point's four
+// leaf ids come from one 16-byte load; LC = 0 reads them one by one.
+template <int LC>
+struct PointLeaves {
+  uint32_t v[LC ? LC : 1];
+  const uint32_t *row;
+  __device__ __forceinline__ PointLeaves(const QueryIndexView &ix, uint32_t p) {
+    row = ix.leaf_of + (int64_t)p * ix.L;
+    if (LC == 4) {
+      const uint4 w = *reinterpret_cast<const uint4 *>(row);
+      v[0] = w.x; v[LC > 1 ? 1 : 0] = w.y; v[LC > 2 ? 2 : 0] = w.z; v[LC > 3 ? 3 : 0] = w.w;
+    }
+  }
+  __device__ __forceinline__ uint32_t operator[](int u) const { return LC == 4 ? v[u & 3] : row[u]; }
+};
+
 // Smallest level of point p over trees t' < tlim (255 if none).
+template <int LC>
 __device__ __forceinline__ uint32_t min_level_before(const QueryIndexView &ix, const Slot &s,
                                                      const QShared &sm, const float *lut,
                                                      uint32_t p, int tlim) {
   uint32_t f = 255u;
-  const uint32_t *lo = ix.leaf_of + (int64_t)p * ix.L;
-  for (int u = 0; u < tlim; ++u) f = min(f, leaf_level_h(ix, s, sm, lut, u, lo[u]));
+  const PointLeaves<LC> lf(ix, p);
+  const int L = LC ? LC : ix.L;
+#pragma unroll
+  for (int u = 0; u < L; ++u)
+    if (u < tlim) f = min(f, leaf_level_h(ix, s, sm, lut, u, lf[u]));
   return f;
 }
 
@@ -321,8 +341,10 @@ __device__ __forceinline__ void expand_levels(QCtx &c) {
       const int64_t b = b0 + threadIdx.x;
       uint32_t lv = 255u;
       if (b < nb) {
-        lv = level_of(sm.T, box_lb2(c.lut, hlo[b], hhi[b]), c.qa.lg_eps2, c.qa.inv_2lg_c);
-        blev[b] = lv <= J0 ? (uint8_t)lv : (uint8_t)255;
+        // level <= J0 exactly when LB^2 <= T[J0]; only those need their level
+        const float lb = box_lb2(c.lut, hlo[b], hhi[b]);
+        if (lb <= sm.T[J0]) lv = level_of(sm.T, lb, c.qa.lg_eps2, c.qa.inv_2lg_c);
+        blev[b] = (uint8_t)lv;
         if (lv <= J0) atomicMin(&sm.jcur, (int)lv);
       }
       warp_bin_count(sm.rh, b < nb && lv <= J0, lv, 1u);
@@ -374,12 +396,17 @@ __device__ __forceinline__ void expand_levels(QCtx &c) {
         uint32_t sz = 0;
         if (valid) {
           lb = box_lb2(c.lut, llo[l], lhi[l]);
-          lv = level_of(sm.T, lb, c.qa.lg_eps2, c.qa.inv_2lg_c);
-          c.s.lev[ix.leaf_off[t] + l] = (ep << 8) | lv;
-          sz = leaf_begin_of(ix, t, l + 1) - leaf_begin_of(ix, t, l);
+          // Leaves above Jnow are never needed again (every later test is
+          // against a bound <= Jnow), so only the others get their level,
+          // size and level-array entry; the rest read as level 255.
+          if (lb <= sm.T[Jnow]) {
+            lv = level_of(sm.T, lb, c.qa.lg_eps2, c.qa.inv_2lg_c);
+            c.s.lev[ix.leaf_off[t] + l] = (ep << 8) | lv;
+            sz = leaf_begin_of(ix, t, l + 1) - leaf_begin_of(ix, t, l);
+          }
         }
         const bool keep = valid && lv <= Jnow;
-        warp_bin_add(hist_t, keep, lv, sz);  // levels above Jnow never reach a check
+        warp_bin_add(hist_t, keep, lv, sz);
         const unsigned km = __ballot_sync(FULL, keep);
         const unsigned vm = __ballot_sync(FULL, valid);
         if (lane == 0) atomicAdd(&sm.n_leaves, (unsigned long long)__popc(vm));
@@ -545,10 +572,12 @@ __device__ __forceinline__ void visit_points(QCtx &c, int t, Pred pred, Fn fn, b
 }
 
 // ---- step 2: owner-rule union counts and per-tree new-point counts -------
-__device__ __forceinline__ void union_counts(QCtx &c) {
+template <int LC>
+__device__ __forceinline__ void union_counts_t(QCtx &c) {
   const QueryIndexView &ix = c.ix;
   const uint32_t jhi = (uint32_t)c.sm.jhi;
-  for (int t = 0; t < ix.L; ++t) {
+  const int L = LC ? LC : ix.L;
+  for (int t = 0; t < L; ++t) {
     const int64_t lo0 = ix.leaf_off[t];
     uint32_t *Dt = reinterpret_cast<uint32_t *>(c.D + t * 256);
     visit_points(
@@ -557,9 +586,10 @@ __device__ __forceinline__ void union_counts(QCtx &c) {
           uint32_t m = 255u, f = 255u;
           int owner = -1;
           if (valid) {
-            const uint32_t *lo = ix.leaf_of + (int64_t)p * ix.L;
-            for (int u = 0; u < ix.L; ++u) {
-              const uint32_t lv = (u == t) ? lvt : leaf_level_h(ix, c.s, c.sm, c.lut, u, lo[u]);
+            const PointLeaves<LC> lf(ix, p);
+#pragma unroll
+            for (int u = 0; u < L; ++u) {
+              const uint32_t lv = (u == t) ? lvt : leaf_level_h(ix, c.s, c.sm, c.lut, u, lf[u]);
               if (lv < m) { m = lv; owner = u; }
               if (u < t) f = min(f, lv);
             }
@@ -574,8 +604,14 @@ __device__ __forceinline__ void union_counts(QCtx &c) {
   __syncthreads();
 }
 
+__device__ __forceinline__ void union_counts(QCtx &c) {
+  if (c.ix.L == 4) union_counts_t<4>(c);
+  else union_counts_t<0>(c);
+}
+
 // ---- step 3: candidate cut inside tree i* and candidate list -------------
-__device__ __forceinline__ void cut_and_collect(QCtx &c) {
+template <int LC>
+__device__ __forceinline__ void cut_and_collect_t(QCtx &c) {
   const QueryIndexView &ix = c.ix;
   const uint32_t js = (uint32_t)c.sm.jstar;
   const int is = c.sm.istar;
@@ -595,7 +631,7 @@ __device__ __forceinline__ void cut_and_collect(QCtx &c) {
     visit_points(
         c, is, [&](int64_t e) { return c.s.llev[li0 + e] <= js; },
         [&](bool valid, uint32_t p, uint32_t ent, uint32_t) {
-          const bool nw = valid && min_level_before(ix, c.s, c.sm, c.lut, p, is) > js;
+          const bool nw = valid && min_level_before<LC>(ix, c.s, c.sm, c.lut, p, is) > js;
           warp_bin_count(c.s.cval, nw, ent, 1u);
         });
   }
@@ -635,7 +671,7 @@ __device__ __forceinline__ void cut_and_collect(QCtx &c) {
           return kb < v || (kb == v && c.s.lleaf[lo0 + e] <= cut);
         },
         [&](bool valid, uint32_t p, uint32_t, uint32_t) {
-          const bool take = valid && (t == 0 || min_level_before(ix, c.s, c.sm, c.lut, p, t) > js);
+          const bool take = valid && (t == 0 || min_level_before<LC>(ix, c.s, c.sm, c.lut, p, t) > js);
           const unsigned tm = __ballot_sync(FULL, take);
           uint32_t pos0 = 0;
           if (lane == 0 && tm) pos0 = atomicAdd(&c.sm.ncand, (uint32_t)__popc(tm));
@@ -645,6 +681,11 @@ __device__ __forceinline__ void cut_and_collect(QCtx &c) {
         });
   }
   __syncthreads();
+}
+
+__device__ __forceinline__ void cut_and_collect(QCtx &c) {
+  if (c.ix.L == 4) cut_and_collect_t<4>(c);
+  else cut_and_collect_t<0>(c);
 }
 
 // ---- step 4: distances ----------------------------------------------------
