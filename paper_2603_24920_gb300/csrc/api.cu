@@ -97,6 +97,18 @@ int pool_alloc(void **p, size_t bytes, cudaStream_t st) {
   return DETLSH_OK;
 }
 
+// Query scratch outlives its index: a freed index hands its slots (and the
+// epoch counter their level tags were written under) to the next index on
+// the same device, so rebuilding an index does not clear the slots again.
+// Epochs only grow, so tags left by earlier queries never match a later one.
+struct ScratchCache {
+  void *p = nullptr;
+  size_t bytes = 0;
+  uint32_t epoch_next = 1;
+};
+std::mutex g_scratch_mu;
+ScratchCache g_scratch[kPoolDevices];
+
 template <class T>
 int dalloc(detlsh_index *ix, T **p, size_t count, cudaStream_t st) {
   *p = nullptr;
@@ -504,8 +516,22 @@ void free_index(detlsh_index *ix) {
   for (auto &e : ix->ev)
     if (e) cudaEventDestroy(e);
   for (auto *b : {&ix->qQ, &ix->qQh, &ix->qQp, &ix->qk, &ix->qids, &ix->qdists, &ix->qT,
-                  &ix->qscratch, &ix->qstat, &ix->qS, &ix->qfb})
+                  &ix->qstat, &ix->qS, &ix->qfb})
     if (b->p) cudaFreeAsync(b->p, 0);
+  if (ix->qscratch.p) {  // keep the larger of this and the cached scratch
+    void *drop = ix->qscratch.p;
+    if (ix->device >= 0 && ix->device < kPoolDevices) {
+      std::lock_guard<std::mutex> g(g_scratch_mu);
+      ScratchCache &c = g_scratch[ix->device];
+      if (ix->qscratch.bytes >= c.bytes) {
+        drop = c.p;
+        c.p = ix->qscratch.p;
+        c.bytes = ix->qscratch.bytes;
+        c.epoch_next = ix->epoch_next;
+      }
+    }
+    if (drop) cudaFreeAsync(drop, 0);
+  }
   delete ix;
 }
 
@@ -619,6 +645,16 @@ int query_impl(detlsh_index *ix, const float *queries, int64_t m, const int32_t 
   size_t freeb = 0, totb = 0;
   DL_CUDA(cudaMemGetInfo(&freeb, &totb));
   while (slots > 1 && (size_t)slots * qa.slot_bytes > freeb / 4 + ix->qscratch.bytes) slots /= 2;
+  if (!ix->qscratch.p && ix->device >= 0 && ix->device < kPoolDevices) {
+    std::lock_guard<std::mutex> g(g_scratch_mu);
+    ScratchCache &c = g_scratch[ix->device];
+    if (c.p && c.bytes >= (size_t)slots * qa.slot_bytes) {  // adopt a freed index's slots
+      ix->qscratch.p = c.p;
+      ix->qscratch.bytes = c.bytes;
+      ix->epoch_next = c.epoch_next;
+      c = ScratchCache{};
+    }
+  }
   bool fresh = false;
   DL_TRY(grow(ix->qscratch, (size_t)slots * qa.slot_bytes, st, &fresh));
   // Leaf levels in the scratch carry a per-query epoch (base + query index);
