@@ -5,7 +5,7 @@ device-resident data, then one BF16+refine and one FP32 query call per
 repetition), without the recall check, the end-to-end pass or the CPU timing,
 so that a profiler sees few launches and little device memory.
 
-  python -m paper_2603_24920_gb300.profile_run --config c2 --reps 2 --beta 0.002
+  python -m paper_2603_24920_gb300.profile_run --config c2 --reps 2 --beta 0.0015
 
 Launch order per repetition: the build's kernels, then k_query (BF16+refine),
 then k_query (FP32).
@@ -23,7 +23,7 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--config", default="c2")
     ap.add_argument("--reps", type=int, default=2)
-    ap.add_argument("--beta", type=float, default=0.002)
+    ap.add_argument("--beta", type=float, default=0.0015)
     ap.add_argument("--c", type=float, default=1.5)
     ap.add_argument("--queries", type=int, default=0, help="first m queries (0 = all)")
     a = ap.parse_args()
