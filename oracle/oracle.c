@@ -735,6 +735,123 @@ static int64_t orc_union_size(const orc_index *ix, const float *qproj, float T, 
     return cnt;
 }
 
+/* ----------------------------------------------------------------------
+ * Alg. 3 as printed (before the optimisations of Sec. VI-B2) and Alg. 4.
+ * ---------------------------------------------------------------------- */
+
+/* Upper bound between q' and a node box (Sec. IV-C, Fig. 6): per dimension
+ * the distance from q'_j to the farther edge of the interval [B(lo), B(hi+1)],
+ * then the sum of squares.  FP32, dimensions in ascending order. */
+static float orc_ub2(const orc_index *ix, int t, const float *qp, const uint8_t *lo,
+                     const uint8_t *hi) {
+    float acc = 0.0f;
+    for (int j = 0; j < ix->K; j++) {
+        const float *Bt = ix->B + (int64_t)(t * ix->K + j) * (ix->N_r + 1);
+        float to_low = fabsf(Bt[lo[j]] - qp[j]);
+        float to_high = fabsf(Bt[hi[j] + 1] - qp[j]);
+        float far = to_low > to_high ? to_low : to_high;
+        acc = acc + far * far;
+    }
+    return acc;
+}
+
+/* Squared distance between a point's projection H_t(o) and q'_t in tree t's
+ * projected space: FP32, dimensions in ascending order. */
+static float orc_proj_dist2(const orc_index *ix, int t, const float *qp, int64_t p) {
+    const float *po = ix->P + p * (int64_t)(ix->L * ix->K) + (int64_t)t * ix->K;
+    float acc = 0.0f;
+    for (int j = 0; j < ix->K; j++) {
+        float dj = po[j] - qp[j];
+        acc = acc + dj * dj;
+    }
+    return acc;
+}
+
+/* Alg. 3 with the pruning rules of Sec. IV-C: a node whose lower bound
+ * exceeds r' is discarded; a leaf whose upper bound is within r' gives all
+ * its points; otherwise its points are examined one by one and those within
+ * r' of q' (projected distance) are added.  Squared values against R2. */
+static void orc_range_exact_rec(const orc_index *ix, int t, const float *qp, const onode *nd,
+                                float R2, int64_t *out, int64_t *nout) {
+    if (orc_lb2(ix, t, qp, nd->lo, nd->hi) > R2) return;
+    if (nd->split_dim < 0) {
+        int whole = orc_ub2(ix, t, qp, nd->lo, nd->hi) <= R2;
+        for (int64_t i = 0; i < nd->cnt; i++) {
+            int64_t p = nd->ids[i];
+            if (whole || orc_proj_dist2(ix, t, qp, p) <= R2) out[(*nout)++] = p;
+        }
+        return;
+    }
+    for (int b = 0; b < 2; b++)
+        if (nd->child[b]) orc_range_exact_rec(ix, t, qp, nd->child[b], R2, out, nout);
+}
+
+static void orc_query_proj(const orc_index *ix, const float *q, float *qproj) {
+    for (int t = 0; t < ix->L * ix->K; t++)
+        qproj[t] = orc_dot_rn32(ix->A + (int64_t)t * ix->d, q, ix->d);
+}
+
+int64_t orc_index_range_exact(const orc_index *ix, int t, const float *q, double r,
+                              int64_t *out) {
+    float qproj[256];
+    orc_query_proj(ix, q, qproj);
+    const float R2 = (float)(ix->eps2 * r * r); /* (eps r)^2, rounded once */
+    const otree *tr = &ix->trees[t];
+    int64_t nout = 0;
+    for (int64_t key = 0; key < ((int64_t)1 << ix->K); key++)
+        if (tr->first[key])
+            orc_range_exact_rec(ix, t, qproj + t * ix->K, tr->first[key], R2, out, &nout);
+    return nout;
+}
+
+void orc_index_leaf_ub2(const orc_index *ix, int t, const float *q, float *ub2) {
+    float qproj[256];
+    orc_query_proj(ix, q, qproj);
+    const otree *T = &ix->trees[t];
+    for (int64_t l = 0; l < T->nleaves; l++)
+        ub2[l] = orc_ub2(ix, t, qproj + t * ix->K, T->leaves[l]->lo, T->leaves[l]->hi);
+}
+
+int orc_index_rc_ann(const orc_index *ix, const float *q, double r, double beta, double c,
+                     int64_t *id, double *dist, int64_t *S_out, int64_t *S_size,
+                     int *tree_stop) {
+    const int64_t n = ix->n;
+    const int64_t need = (int64_t)ceil(beta * (double)n) + 1; /* beta*n + 1 */
+    float qproj[256];
+    orc_query_proj(ix, q, qproj);
+    const float R2 = (float)(ix->eps2 * r * r);
+    uint8_t *mark = (uint8_t *)calloc((size_t)n, 1);
+    int64_t *Rt = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n ? n : 1));
+    int64_t *S = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n ? n : 1));
+    int64_t ns = 0;
+    int stop = -1;
+    for (int t = 0; t < ix->L; t++) {
+        const otree *tr = &ix->trees[t];
+        int64_t nr = 0;
+        for (int64_t key = 0; key < ((int64_t)1 << ix->K); key++)
+            if (tr->first[key])
+                orc_range_exact_rec(ix, t, qproj + t * ix->K, tr->first[key], R2, Rt, &nr);
+        for (int64_t i = 0; i < nr; i++)
+            if (!mark[Rt[i]]) { mark[Rt[i]] = 1; S[ns++] = Rt[i]; }
+        if (ns >= need) { stop = t; break; }
+    }
+    /* the point of S closest to q (FP64 distances, ties by smaller id) */
+    int64_t best = -1;
+    double bd = INFINITY;
+    for (int64_t i = 0; i < ns; i++) {
+        double dd = orc_dist(q, ix->X + S[i] * ix->d, ix->d);
+        if (dd < bd || (dd == bd && S[i] < best)) { bd = dd; best = S[i]; }
+    }
+    if (stop < 0 && !(best >= 0 && bd <= c * r)) { best = -1; bd = INFINITY; }
+    *id = best;
+    *dist = bd;
+    if (S_out) for (int64_t i = 0; i < ns; i++) S_out[i] = S[i];
+    if (S_size) *S_size = ns;
+    if (tree_stop) *tree_stop = stop;
+    free(mark); free(Rt); free(S);
+    return 0;
+}
+
 int orc_index_query(const orc_index *ix, const float *q, int k, double beta, double c,
                     int64_t *ids, double *dists, int64_t *S_out, int64_t *S_size,
                     int *jstar, int *istar) {

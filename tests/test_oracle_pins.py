@@ -432,3 +432,112 @@ def test_guarantee_c2_k_ann():
             r = ix.query(Q[i], k, beta=beta, c=c, want_S=False)
             ok.append(bool(np.all(r["dists"] <= c * c * dists[i] + 1e-9)))
     assert np.mean(ok) >= 0.5 - 1.0 / np.e
+
+
+# ------------------------------------- Alg. 3 as printed, Alg. 4 (r,c)-ANN --
+def _proj_dist2(ix, arr, t, q):
+    """FP32 squared projected distances of every point in tree t (numpy)."""
+    K = ix.K
+    qp = oracle.project(q[None, :], arr["A"][t * K:(t + 1) * K])[0]
+    Pt = arr["P"][:, t * K:(t + 1) * K]
+    d2 = np.zeros(ix.n, np.float32)
+    for j in range(K):
+        diff = (Pt[:, j] - qp[j]).astype(np.float32)
+        d2 = (d2 + diff * diff).astype(np.float32)
+    return d2
+
+
+@pytest.mark.parametrize("box_mode", [0, 1])
+def test_upper_bound_is_sound(box_mode):
+    # Sec. IV-C / Fig. 6: the node upper bound is never below the projected
+    # distance of a point in the node, and never below the lower bound.
+    ix, X, Q = _small_index(box_mode=box_mode)
+    arr = ix.arrays()
+    for t in range(ix.L):
+        tr = ix.tree(t)
+        for q in Q[:4]:
+            ub2 = ix.leaf_ub2(t, q)
+            lb2 = ix.leaf_lb2(t, q)
+            d2 = _proj_dist2(ix, arr, t, q)
+            assert np.all(ub2[tr["leaf_of"]] >= d2)
+            assert np.all(ub2 >= lb2)
+
+
+@pytest.mark.parametrize("box_mode", [0, 1])
+def test_range_query_exact_is_projected_ball(box_mode):
+    # Alg. 3 (pruning by lower bound, whole leaves by upper bound, otherwise a
+    # per-point test) returns exactly the points whose projection lies within
+    # r' = eps*r of q' -- brute force over every point.
+    ix, X, Q = _small_index(box_mode=box_mode)
+    arr = ix.arrays()
+    e2 = oracle.eps2(ix.K, ix.L)
+    for t in range(ix.L):
+        for q in Q[:3]:
+            d2 = _proj_dist2(ix, arr, t, q)
+            for frac in (0.001, 0.01, 0.1):
+                # radius at which about frac*n points fall inside
+                r = float(np.sqrt(np.quantile(d2.astype(np.float64), frac) / e2))
+                got = np.sort(ix.range_exact(t, q, r))
+                R2 = np.float32(e2 * r * r)
+                assert np.array_equal(got, np.nonzero(d2 <= R2)[0])
+                assert got.size > 0
+
+
+def test_rc_ann_follows_alg4():
+    # Alg. 4 recomputed with numpy: S grows tree by tree; once |S| >= beta*n+1
+    # the closest point of S is returned; after all trees, the closest point
+    # of S only when it lies within c*r, else nothing.
+    ix, X, Q = _small_index(n=4000)
+    arr = ix.arrays()
+    e2 = oracle.eps2(ix.K, ix.L)
+    c = 1.5
+    seen_stop = seen_cond2 = seen_none = False
+    for q in Q[:6]:
+        d2s = [_proj_dist2(ix, arr, t, q) for t in range(ix.L)]
+        dist = np.sqrt(((X.astype(np.float64) - q.astype(np.float64)) ** 2).sum(1))
+        for beta in (0.005, 0.05):
+            for frac in (0.0005, 0.003, 0.02):
+                r = float(np.sqrt(np.quantile(d2s[0].astype(np.float64), frac) / e2))
+                R2 = np.float32(e2 * r * r)
+                need = int(np.ceil(beta * ix.n)) + 1
+                inS = np.zeros(ix.n, bool)
+                stop = -1
+                for t in range(ix.L):
+                    inS |= d2s[t] <= R2
+                    if inS.sum() >= need:
+                        stop = t
+                        break
+                got = ix.rc_ann(q, r, beta=beta, c=c)
+                assert got["tree_stop"] == stop
+                assert np.array_equal(np.sort(got["S"]), np.nonzero(inS)[0])
+                S = np.nonzero(inS)[0]
+                want = -1
+                if S.size:
+                    o = S[np.lexsort((S, dist[S]))[0]]
+                    if stop >= 0 or dist[o] <= c * r:
+                        want = o
+                assert got["id"] == want
+                if want >= 0:
+                    assert got["dist"] == pytest.approx(dist[want], rel=1e-12)
+                seen_stop |= stop >= 0
+                seen_cond2 |= stop < 0 and want >= 0
+                seen_none |= want < 0
+    assert seen_stop and seen_cond2 and seen_none
+
+
+def test_theorem1_rc_ann_guarantee():
+    # Theorem 1: when some point lies within r of q, Alg. 4 returns a point
+    # within c*r with probability >= 1/2 - 1/e (beta at its default 0.1).
+    c, beta = 1.5, 0.1
+    ok = []
+    for seed in range(4):
+        X, Q, _ = workloads.workload("c1", n=3000, m=10)
+        X = X[:, :32] + np.float32(seed)
+        Q = Q[:, :32] + np.float32(seed)
+        ix = oracle.Index(X, L=4, K=16, N_r=256, seed=seed, frac=0.1, M=64)
+        _, nn = oracle.bruteforce_knn(X, Q, 1)
+        for i in range(Q.shape[0]):
+            r = float(nn[i, 0]) if nn[i, 0] > 0 else 1e-3
+            got = ix.rc_ann(Q[i], r, beta=beta, c=c, want_S=False)
+            ok.append(got["id"] >= 0 and got["dist"] <= c * r + 1e-9)
+    assert np.mean(ok) >= 0.5 - 1.0 / np.e
