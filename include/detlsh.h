@@ -225,6 +225,30 @@ int detlsh_query_candidates(const detlsh_index *ix, const float *queries, int64_
                             const detlsh_query_params *qp, int64_t cap, int64_t *S,
                             int64_t *S_size, int32_t *jstar, int32_t *istar);
 
+/* (r,c)-ANN query, Alg. 4 of the paper (Sec. V-B), over the range query of
+ * Alg. 3 as printed (Sec. IV-C): for each tree in order, nodes whose lower
+ * bound exceeds r' = eps*r are pruned, a leaf whose upper bound is within r'
+ * gives all its points, and the points of any other reached leaf are tested
+ * one by one on their projected distance (FP32, dimensions in order, squared
+ * comparison against fp32(eps^2 r^2)).  S is the union over the trees so far;
+ * once |S| >= beta*n + 1 the point of S nearest to q is returned (tree_stop =
+ * that tree); after all L trees the nearest point of S is returned only if it
+ * lies within c*r (FP32 distance), else ids = -1 and dists = +inf (tree_stop
+ * = -1).  Nearest = smallest FP32 distance, ties by smaller id.
+ *   ix        index built with keep_projections = 1 (the per-point test reads
+ *             the stored projections); otherwise DETLSH_ERR_INVALID_ARG
+ *   queries   m x d FP32, row-major, host or device
+ *   r, beta, c  radius (> 0), false-positive budget (>= 0), ratio (> 1)
+ *   ids, dists  m entries each, caller-owned, host or device
+ *   tree_stop, S_size  m entries each, nullable
+ *   S         m x S_cap ids of S in arrival order (nullable; S_cap >= 1 when
+ *             given); entries past min(S_size, S_cap) are unspecified
+ * Errors: INVALID_ARG (arguments as above), NONFINITE_INPUT (a query holds NaN
+ * or Inf), OOM, CUDA.  Blocks until the results are written. */
+int detlsh_rc_ann(const detlsh_index *ix, const float *queries, int64_t m, double r,
+                  double beta, double c, void *stream, int64_t *ids, float *dists,
+                  int32_t *tree_stop, int64_t S_cap, int64_t *S, int64_t *S_size);
+
 #ifdef __cplusplus
 }
 #endif

@@ -56,7 +56,7 @@ struct detlsh_index {
     void *p = nullptr;
     size_t bytes = 0;
   };
-  QBuf qQ, qQh, qQp, qk, qids, qdists, qT, qscratch, qstat, qS, qfb;
+  QBuf qQ, qQh, qQp, qk, qids, qdists, qT, qscratch, qstat, qS, qfb, qrc, qrcs;
 };
 
 namespace {
@@ -516,7 +516,7 @@ void free_index(detlsh_index *ix) {
   for (auto &e : ix->ev)
     if (e) cudaEventDestroy(e);
   for (auto *b : {&ix->qQ, &ix->qQh, &ix->qQp, &ix->qk, &ix->qids, &ix->qdists, &ix->qT,
-                  &ix->qstat, &ix->qS, &ix->qfb})
+                  &ix->qstat, &ix->qS, &ix->qfb, &ix->qrc, &ix->qrcs})
     if (b->p) cudaFreeAsync(b->p, 0);
   if (ix->qscratch.p) {  // keep the larger of this and the cached scratch
     void *drop = ix->qscratch.p;
@@ -538,7 +538,7 @@ void free_index(detlsh_index *ix) {
 QueryIndexView view_of(const detlsh_index *ix) {
   QueryIndexView v;
   v.n = ix->n; v.d = ix->d; v.L = ix->L; v.K = ix->K; v.LK = ix->LK; v.N_r = ix->N_r;
-  v.X = ix->X; v.Xh = ix->Xh; v.Xn = ix->Xn; v.B = ix->B; v.perm = ix->perm; v.leaf_begin = ix->leaf_begin;
+  v.X = ix->X; v.Xh = ix->Xh; v.Xn = ix->Xn; v.P = ix->P; v.B = ix->B; v.perm = ix->perm; v.leaf_begin = ix->leaf_begin;
   v.leaf_lo = ix->leaf_lo; v.leaf_hi = ix->leaf_hi; v.leaf_of = ix->leaf_of;
   v.blk_lo = ix->blk_lo; v.blk_hi = ix->blk_hi;
   for (int t = 0; t <= 16; ++t) v.blk_off[t] = ix->blk_off[t];
@@ -837,6 +837,85 @@ int detlsh_query(const detlsh_index *ix, const float *queries, int64_t m, int32_
   detlsh_default_query_params(&qp);
   qp.c = c;
   return detlsh_query_ex(ix, queries, m, nullptr, k, &qp, nullptr, ids, dists);
+}
+
+int detlsh_rc_ann(const detlsh_index *cix, const float *queries, int64_t m, double r,
+                  double beta, double c, void *stream, int64_t *ids, float *dists,
+                  int32_t *tree_stop, int64_t S_cap, int64_t *S, int64_t *S_size) {
+  if (!cix || m < 0) return DETLSH_ERR_INVALID_ARG;
+  if (!(r > 0.0) || !std::isfinite(r) || !(beta >= 0.0) || !std::isfinite(beta) ||
+      !(c > 1.0) || !std::isfinite(c))
+    return DETLSH_ERR_INVALID_ARG;
+  if (S && S_cap < 1) return DETLSH_ERR_INVALID_ARG;
+  if (!cix->P) return DETLSH_ERR_INVALID_ARG;  // needs the projections kept at build
+  if (m == 0) return DETLSH_OK;
+  if (!queries || !ids || !dists) return DETLSH_ERR_INVALID_ARG;
+  detlsh_index *ix = const_cast<detlsh_index *>(cix);
+  std::lock_guard<std::mutex> g(ix->qmu);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int d = ix->d, LK = ix->LK;
+  DL_TRY(ensure_events(ix));
+  const long long launches0 = g_launches.load();
+  DL_TRY(grow(ix->qQ, sizeof(float) * (size_t)m * d, st));
+  DL_TRY(grow(ix->qQp, sizeof(float) * (size_t)m * LK, st));
+  DL_TRY(grow(ix->qstat, 256, st));
+  const int64_t scap = S ? S_cap : 0;
+  const size_t out_bytes = (size_t)m * (8 + 4 + 4 + 8) + (size_t)m * scap * 8 + 64;
+  DL_TRY(grow(ix->qrc, out_bytes, st));
+  float *Q = static_cast<float *>(ix->qQ.p);
+  float *Qp = static_cast<float *>(ix->qQp.p);
+  int *err = static_cast<int *>(ix->qstat.p);
+  uint32_t *fb_count = reinterpret_cast<uint32_t *>(static_cast<char *>(ix->qstat.p) + 16);
+  uint32_t *counter = reinterpret_cast<uint32_t *>(static_cast<char *>(ix->qstat.p) + 32);
+  DL_CUDA(cudaMemsetAsync(ix->qstat.p, 0, 256, st));
+  DL_CUDA(cudaEventRecord(ix->ev[5], st));
+  DL_TRY(copy_in(Q, queries, sizeof(float) * (size_t)m * d, st));
+  const uint32_t fb_cap = (uint32_t)std::max<int64_t>(1024, m * LK / 64);
+  DL_TRY(grow(ix->qfb, sizeof(uint2) * fb_cap, st));
+  ProjArgs pa;
+  pa.P = Qp; pa.ldP = LK; pa.fb_count = fb_count; pa.fb_cap = fb_cap; pa.err = err;
+  pa.fb_list = static_cast<uint2 *>(ix->qfb.p);
+  DL_TRY(project_rows(Q, d, nullptr, m, d, ix->A, LK, 0, pa, st));
+  int e = check_err(err, st);  // non-finite queries
+  if (e) return e;
+  QueryIndexView v = view_of(ix);
+  RcArgs a{};
+  a.Q = Q; a.Qp = Qp; a.m = m;
+  a.R2 = (float)(ix->eps2 * r * r);  // (eps r)^2 rounded once, as the radius grid
+  a.cr = (float)(c * r);
+  const double nb = std::ceil(beta * (double)ix->n);
+  a.need = nb > (double)ix->n ? ix->n + 1 : (int64_t)nb + 1;
+  char *ob = static_cast<char *>(ix->qrc.p);
+  a.ids = reinterpret_cast<int64_t *>(ob);
+  a.S_size = a.ids + m;
+  a.S = scap ? a.S_size + m : nullptr;
+  a.S_cap = scap;
+  a.dists = reinterpret_cast<float *>(ob + (size_t)m * 16 + (size_t)m * scap * 8);
+  a.tree_stop = reinterpret_cast<int32_t *>(a.dists + m);
+  a.slot_bytes = (int64_t)rcann_slot_bytes(v);
+  int slots = (int)std::min<int64_t>(rcann_slots(v), m);
+  size_t freeb = 0, totb = 0;
+  DL_CUDA(cudaMemGetInfo(&freeb, &totb));
+  while (slots > 1 && (size_t)slots * a.slot_bytes > freeb / 4 + ix->qrcs.bytes) slots /= 2;
+  DL_TRY(grow(ix->qrcs, (size_t)slots * a.slot_bytes, st));
+  a.scratch = static_cast<uint8_t *>(ix->qrcs.p);
+  a.nslots = slots;
+  a.work_counter = counter;
+  DL_CUDA(cudaEventRecord(ix->ev[6], st));
+  DL_TRY(run_rcann(v, a, st));
+  DL_CUDA(cudaEventRecord(ix->ev[7], st));
+  DL_TRY(copy_out(ids, a.ids, sizeof(int64_t) * (size_t)m, st));
+  DL_TRY(copy_out(dists, a.dists, sizeof(float) * (size_t)m, st));
+  if (tree_stop) DL_TRY(copy_out(tree_stop, a.tree_stop, sizeof(int32_t) * (size_t)m, st));
+  if (S_size) DL_TRY(copy_out(S_size, a.S_size, sizeof(int64_t) * (size_t)m, st));
+  if (S) DL_TRY(copy_out(S, a.S, sizeof(int64_t) * (size_t)m * scap, st));
+  DL_CUDA(cudaStreamSynchronize(st));
+  ix->timings.query_project_ms = ev_ms(ix->ev[5], ix->ev[6]);
+  ix->timings.query_kernel_ms = ev_ms(ix->ev[6], ix->ev[7]);
+  ix->timings.query_ms = ev_ms(ix->ev[5], ix->ev[7]);
+  ix->timings.query_launches = g_launches.load() - launches0;
+  ix->timings.query_count = m;
+  return DETLSH_OK;
 }
 
 int detlsh_query_candidates(const detlsh_index *cix, const float *queries, int64_t m, int32_t k,

@@ -94,6 +94,7 @@ struct QueryIndexView {
   const float *X;
   const __nv_bfloat16 *Xh;
   const float *Xn;           // [n] squared norms of the BF16 rows
+  const float *P;            // [n][LK] exact projections (null unless kept at build)
   const float *B;            // [LK][N_r+1]
   const uint32_t *perm;      // [L][n]
   const uint32_t *leaf_begin;  // concatenated, tree t at leaf_off[t] + t
@@ -138,6 +139,29 @@ size_t query_slot_bytes(const QueryIndexView &ix, int64_t cand_cap, int rerank_c
 void query_slot_offsets(const QueryIndexView &ix, int64_t cand_cap, int64_t off[12]);
 int query_slots(const QueryIndexView &ix);
 int run_queries(const QueryIndexView &ix, const QueryArgs &qa, cudaStream_t st);
+
+// (r,c)-ANN queries (Alg. 4) over the range query of Alg. 3 as printed.
+struct RcArgs {
+  const float *Q;            // [m][d]
+  const float *Qp;           // [m][LK] exact projections
+  int64_t m;
+  float R2;                  // fp32((eps r)^2)
+  float cr;                  // fp32(c r)
+  int64_t need;              // ceil(beta n) + 1
+  int64_t *ids;              // [m], -1 when nothing is returned
+  float *dists;              // [m], +inf when nothing is returned
+  int32_t *tree_stop;        // [m], tree where |S| reached need, -1 if none
+  int64_t *S_size;           // [m]
+  int64_t *S;                // [m][S_cap] (nullable)
+  int64_t S_cap;
+  uint8_t *scratch;          // nslots slots of rcann_slot_bytes
+  int64_t slot_bytes;
+  int nslots;
+  uint32_t *work_counter;    // zeroed by run_rcann
+};
+size_t rcann_slot_bytes(const QueryIndexView &ix);
+int rcann_slots(const QueryIndexView &ix);
+int run_rcann(const QueryIndexView &ix, const RcArgs &a, cudaStream_t st);
 
 // ---- misc (api.cu) ----------------------------------------------------------
 int f32_to_bf16(const float *src, __nv_bfloat16 *dst, int64_t count, cudaStream_t st);

@@ -26,6 +26,7 @@
 #include "common.cuh"
 #include "compact.cuh"
 #include "kernels.h"
+#include "lut.cuh"
 
 #include <algorithm>
 
@@ -278,31 +279,6 @@ __device__ __forceinline__ uint32_t min_level_before(const QueryIndexView &ix, c
   return f;
 }
 
-// The per-tree lookup table has 16 rows of LUT_STRIDE entries whatever K and
-// N_r are: rows j >= K are zero, so the padded code bytes (zero) add an exact
-// 0 to the sum, and every table offset is a compile-time constant.
-constexpr int LUT_STRIDE = 257;
-constexpr int LUT_ROWS = 16;
-
-// Squared lower bound of a box (Sec. IV-C) from the per-tree table
-// lut[j][z] = B_j[z] - q'_j: per dimension gap = max(0, B(lo) - q, q - B(hi+1)),
-// summed in FP32 over dimensions in order.
-__device__ __forceinline__ float box_lb2(const float *lut, const uint4 &lo, const uint4 &hi) {
-  const uint32_t wl[4] = {lo.x, lo.y, lo.z, lo.w};
-  const uint32_t wh[4] = {hi.x, hi.y, hi.z, hi.w};
-  float acc = 0.0f;
-#pragma unroll
-  for (int j = 0; j < LUT_ROWS; ++j) {
-    const uint32_t zl = (wl[j >> 2] >> (8 * (j & 3))) & 255u;
-    const uint32_t zh = (wh[j >> 2] >> (8 * (j & 3))) & 255u;
-    const float a = lut[j * LUT_STRIDE + zl];
-    const float b = -lut[j * LUT_STRIDE + zh + 1];
-    const float gap = fmaxf(fmaxf(a, b), 0.0f);
-    acc = __fadd_rn(acc, __fmul_rn(gap, gap));
-  }
-  return acc;
-}
-
 // ---- step 1: range-query levels, expanding leaf blocks in level order ----
 // For tree t: hull levels of every block; blocks at level <= the current
 // bound J are bucketed by level and expanded in ascending order.  A leaf's
@@ -321,12 +297,7 @@ __device__ __forceinline__ void expand_levels(QCtx &c) {
   if (threadIdx.x == 0) sm.jhi = NLEV - 1;
   __syncthreads();
   for (int t = 0; t < ix.L; ++t) {
-    for (int j = 0; j < LUT_ROWS; ++j) {
-      const float qj = j < K ? qp[t * K + j] : 0.0f;
-      const float *Bj = ix.B + (int64_t)(t * K + j) * NR1;
-      for (int z = threadIdx.x; z < LUT_STRIDE; z += QT)
-        c.lut[j * LUT_STRIDE + z] = (j < K && z < NR1) ? __fsub_rn(Bj[z], qj) : 0.0f;
-    }
+    build_lut(c.lut, ix.B, qp + t * K, t, K, NR1);
     sm.rh[threadIdx.x] = 0;
     if (threadIdx.x == 0) { sm.nlist[t] = 0; sm.cum = 0; sm.stop = 0; sm.jcur = NLEV; }
     __syncthreads();

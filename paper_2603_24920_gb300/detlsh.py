@@ -85,6 +85,7 @@ SIGNATURES = [
     ("detlsh_project", C.c_int, [_P, _P, _I64, _P, _P]),
     ("detlsh_query_candidates", C.c_int, [_P, _P, _I64, _I32, C.POINTER(QueryParams), _I64,
                                           _P, _P, _P, _P]),
+    ("detlsh_rc_ann", C.c_int, [_P, _P, _I64, _F64, _F64, _F64, _P, _P, _P, _P, _I64, _P, _P]),
 ]
 
 
@@ -309,6 +310,23 @@ def detlsh_query_candidates(h, queries, k, beta=0.1, c=1.5, cap=None):
                                          _ptr(ssz), _ptr(js), _ptr(ist)),
            "detlsh_query_candidates")
     return [S[r, :ssz[r]].copy() for r in range(m)], js, ist
+
+
+def detlsh_rc_ann(h, queries, r, beta=0.1, c=1.5, S_cap=0, stream=None):
+    """Alg. 4 (r,c)-ANN: ids (-1 = nothing), dists, tree_stop, S_size, and S
+    (list of id arrays) when S_cap > 0.  Host numpy or CUDA tensors in; numpy out."""
+    m = queries.shape[0]
+    ids = np.empty(m, np.int64)
+    dists = np.empty(m, np.float32)
+    stop = np.empty(m, np.int32)
+    ssz = np.empty(m, np.int64)
+    S = np.empty((m, S_cap), np.int64) if S_cap > 0 else None
+    _check(lib().detlsh_rc_ann(h, _ptr(queries), m, r, beta, c, _stream_ptr(stream), _ptr(ids),
+                               _ptr(dists), _ptr(stop), S_cap, _ptr(S) if S is not None else None,
+                               _ptr(ssz)),
+           "detlsh_rc_ann")
+    Sl = [S[i, :min(ssz[i], S_cap)].copy() for i in range(m)] if S is not None else None
+    return ids, dists, stop, ssz, Sl
 
 
 class Index:
