@@ -922,6 +922,68 @@ int orc_index_query(const orc_index *ix, const float *q, int k, double beta, dou
     return 0;
 }
 
+/* Alg. 5 run literally from a given r_min (no magic r_min): radii
+ * r_i = r_min c^i, i = 0, 1, ...; at each radius the trees in order, leaves
+ * of the range query entering S whole in ascending (LB^2, leaf id) order with
+ * the check |S| >= beta*n + k after each leaf (condition 1, lines 6-7); after
+ * the L trees, condition 2 (lines 8-9): at least k points of S within c*r
+ * (FP64 distances).  S accumulates across radii.  jstop = i of the radius
+ * that stopped, istop = the tree for condition 1, -1 for condition 2. */
+int orc_index_query_fixed(const orc_index *ix, const float *q, int k, double beta, double c,
+                          double r_min, int64_t *ids, double *dists, int64_t *S_out,
+                          int64_t *S_size, int *jstop, int *istop) {
+    int64_t n = ix->n;
+    if (k < 1 || k > n || !(r_min > 0.0)) return -1;
+    int64_t tau = (int64_t)ceil(beta * (double)n) + k;
+    float qproj[256];
+    orc_query_proj(ix, q, qproj);
+    uint8_t *mark = (uint8_t *)calloc((size_t)n, 1);
+    orc_cand *cand = (orc_cand *)malloc(sizeof(orc_cand) * (size_t)n);
+    orc_hits hits = {0};
+    int64_t ns = 0;
+    int js = -1, is = -1;
+    for (int i = 0; i < ORC_NLEV && js < 0; i++) {
+        const float Ti = (i == ORC_NLEV - 1) ? INFINITY
+                         : (float)(ix->eps2 * r_min * r_min * pow(c, 2.0 * (double)i));
+        for (int t = 0; t < ix->L && js < 0; t++) {
+            orc_range_query(ix, t, qproj + t * ix->K, Ti, &hits);
+            qsort(hits.v, (size_t)hits.n, sizeof(orc_hit), orc_cmp_hit);
+            for (int64_t h = 0; h < hits.n && js < 0; h++) {
+                const onode *lf = hits.v[h].leaf;
+                for (int64_t e = 0; e < lf->cnt; e++) {
+                    int64_t p = lf->ids[e];
+                    if (!mark[p]) {
+                        mark[p] = 1;
+                        cand[ns].id = p;
+                        cand[ns].dist = orc_dist(q, ix->X + p * ix->d, ix->d);
+                        if (S_out) S_out[ns] = p;
+                        ns++;
+                    }
+                }
+                if (ns >= tau) { js = i; is = t; }
+            }
+        }
+        if (js < 0) {
+            const double cr = c * (r_min * pow(c, (double)i));
+            int64_t within = 0;
+            for (int64_t e = 0; e < ns; e++) within += cand[e].dist <= cr;
+            if (within >= k) { js = i; is = -1; }
+        }
+    }
+    free(hits.v);
+    free(mark);
+    qsort(cand, (size_t)ns, sizeof(orc_cand), orc_cmp_cand);
+    for (int i = 0; i < k; i++) {
+        ids[i] = i < ns ? cand[i].id : -1;
+        dists[i] = i < ns ? cand[i].dist : INFINITY;
+    }
+    if (S_size) *S_size = ns;
+    if (jstop) *jstop = js;
+    if (istop) *istop = is;
+    free(cand);
+    return 0;
+}
+
 int orc_index_query_batch(const orc_index *ix, const float *Q, int64_t m, int k, double beta,
                           double c, int64_t *ids, double *dists, int64_t *S_sizes,
                           int nthreads) {

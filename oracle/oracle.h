@@ -85,6 +85,14 @@ void orc_index_level_table(const orc_index *ix, double c, float *T);
 int orc_index_query(const orc_index *ix, const float *q, int k, double beta, double c,
                     int64_t *ids, double *dists, int64_t *S_out, int64_t *S_size,
                     int *jstar, int *istar);
+/* Alg. 5 run literally from a fixed r_min (radii r_min c^i, i = 0, 1, ...;
+ * radius index i uses T'(i) = fp32(eps^2 r_min^2 c^(2i)), the last +inf),
+ * with condition 2 (at least k points of S within c*r, FP64) checked after
+ * each radius.  jstop = the stopping radius index, istop = the tree for
+ * condition 1 or -1 for condition 2.  S_out (capacity n, nullable). */
+int orc_index_query_fixed(const orc_index *ix, const float *q, int k, double beta, double c,
+                          double r_min, int64_t *ids, double *dists, int64_t *S_out,
+                          int64_t *S_size, int *jstop, int *istop);
 /* Same, over m queries, OpenMP over queries (nthreads <= 0: all cores). */
 int orc_index_query_batch(const orc_index *ix, const float *Q, int64_t m, int k, double beta,
                           double c, int64_t *ids, double *dists, int64_t *S_sizes,

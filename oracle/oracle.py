@@ -64,6 +64,11 @@ def lib():
                                       _i64p, _f64p, _i64p_n, C.POINTER(C.c_int64),
                                       C.POINTER(C.c_int), C.POINTER(C.c_int)]
         L.orc_index_query.restype = C.c_int
+        L.orc_index_query_fixed.argtypes = [C.c_void_p, _f32p, C.c_int, C.c_double, C.c_double,
+                                            C.c_double, _i64p, _f64p, _i64p_n,
+                                            C.POINTER(C.c_int64), C.POINTER(C.c_int),
+                                            C.POINTER(C.c_int)]
+        L.orc_index_query_fixed.restype = C.c_int
         L.orc_index_query_batch.argtypes = [C.c_void_p, _f32p, C.c_int64, C.c_int, C.c_double,
                                             C.c_double, _i64p, _f64p, _i64p, C.c_int]
         L.orc_index_query_batch.restype = C.c_int
@@ -232,6 +237,20 @@ class Index:
             raise ValueError("oracle query rejected its arguments")
         return dict(ids=ids, dists=dists, S=S[:ssz.value] if want_S else None,
                     S_size=ssz.value, jstar=js.value, istar=ist.value)
+
+    def query_fixed(self, q, k, r_min, beta=0.1, c=1.5, want_S=True):
+        """Alg. 5 from a fixed r_min with condition 2 (jstop: radius index,
+        istop: tree for condition 1, -1 for condition 2)."""
+        ids = np.zeros(k, np.int64)
+        dists = np.zeros(k, np.float64)
+        S = np.zeros(max(self.n, 1), np.int64) if want_S else None
+        ssz, js, ist = C.c_int64(0), C.c_int(0), C.c_int(0)
+        rc = lib().orc_index_query_fixed(self._h, _f32(q), k, beta, c, r_min, ids, dists, S,
+                                         C.byref(ssz), C.byref(js), C.byref(ist))
+        if rc != 0:
+            raise ValueError("oracle query rejected its arguments")
+        return dict(ids=ids, dists=dists, S=S[:ssz.value] if want_S else None,
+                    S_size=ssz.value, jstop=js.value, istop=ist.value)
 
     def query_batch(self, Q, k, beta=0.1, c=1.5, nthreads=0):
         Q = _f32(Q)

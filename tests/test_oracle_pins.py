@@ -541,3 +541,57 @@ def test_theorem1_rc_ann_guarantee():
             got = ix.rc_ann(Q[i], r, beta=beta, c=c, want_S=False)
             ok.append(got["id"] >= 0 and got["dist"] <= c * r + 1e-9)
     assert np.mean(ok) >= 0.5 - 1.0 / np.e
+
+
+# ------------------------------- Alg. 5 from a fixed r_min, condition 2 --
+def _fixed_grid(ix, r_min, c, i):
+    if i == oracle.NLEV - 1:
+        return np.float32(np.inf)
+    return np.float32(oracle.eps2(ix.K, ix.L) * r_min * r_min * c ** (2.0 * i))
+
+
+def test_query_fixed_rmin_follows_alg5():
+    # Alg. 5 literally, from a given r_min: the loop recomputed from the
+    # exported leaves (their lower bounds and members) with numpy, and the
+    # two stopping conditions checked as invariants at the stopping radius
+    # and the one before it.
+    ix, X, Q = _small_index(n=4000)
+    c, k = 1.5, 10
+    trees = [ix.tree(t) for t in range(ix.L)]
+    seen = set()
+    for q in Q[:5]:
+        dist = np.sqrt(((X.astype(np.float64) - q.astype(np.float64)) ** 2).sum(1))
+        lbs = [ix.leaf_lb2(t, q) for t in range(ix.L)]
+        for r_min in (0.3, 3.0, 30.0):
+            for beta in (0.002, 0.05):
+                tau = int(np.ceil(beta * ix.n)) + k
+                got = ix.query_fixed(q, k, r_min, beta=beta, c=c)
+                inS = np.zeros(ix.n, bool)
+                js = ist = None
+                for i in range(oracle.NLEV):
+                    T = _fixed_grid(ix, r_min, c, i)
+                    for t in range(ix.L):
+                        hit = np.nonzero(lbs[t] <= T)[0]
+                        hit = hit[np.lexsort((hit, lbs[t][hit]))]
+                        for lf in hit:
+                            inS[trees[t]["perm"][trees[t]["begin"][lf]:trees[t]["begin"][lf + 1]]] = True
+                            if inS.sum() >= tau:
+                                js, ist = i, t
+                                break
+                        if js is not None:
+                            break
+                    if js is not None:
+                        break
+                    if (dist[inS] <= c * r_min * c ** i).sum() >= k:
+                        js, ist = i, -1
+                        break
+                assert (got["jstop"], got["istop"]) == (js, ist)
+                S = got["S"]
+                assert np.array_equal(np.sort(S), np.nonzero(inS)[0])
+                order = np.lexsort((S, dist[S]))[:k]
+                assert np.array_equal(got["ids"], S[order])
+                if ist == -1:  # condition 2 holds here and neither held one radius before
+                    assert (dist[S] <= c * r_min * c ** js).sum() >= k
+                    assert S.size < tau
+                seen.add(ist == -1)
+    assert seen == {True, False}
