@@ -54,6 +54,15 @@ enum { DETLSH_PREC_FP32 = 0,        /* FP32 distances over every candidate  */
        DETLSH_PREC_BF16_REFINE = 1  /* BF16 scores, FP32 re-rank of the top
                                        rerank_mult * k                       */ };
 
+/* How Alg. 5 chooses its starting radius r_min (Sec. V-B1). */
+enum { DETLSH_RMIN_MAGIC = 0, /* the "magic" r_min: the smallest radius of the
+                                 grid c^j (j = -127..127) whose union over the
+                                 L trees holds beta*n + k points; condition 1
+                                 ends the first round                        */
+       DETLSH_RMIN_FIXED = 1  /* a given r_min: Alg. 5 runs its radius loop
+                                 r_min c^i (i = 0..253, then unbounded) with
+                                 condition 2 (k points of S within c*r)      */ };
+
 typedef struct detlsh_index detlsh_index;
 
 typedef struct {
@@ -76,6 +85,9 @@ typedef struct {
     int32_t precision;      /* DETLSH_PREC_FP32 (default) / DETLSH_PREC_BF16_REFINE */
     int32_t rerank_mult;    /* BF16 path: FP32 re-rank of the top rerank_mult*k
                                (default 4)                                         */
+    int32_t rmin_policy;    /* DETLSH_RMIN_MAGIC (default) / DETLSH_RMIN_FIXED     */
+    double r_min;           /* DETLSH_RMIN_FIXED: the starting radius (> 0); the
+                               FP32 path only (precision must be FP32)             */
 } detlsh_query_params;
 
 /* Fill *p with the defaults listed above (Sec. V-B1, Sec. VI-A). */
@@ -145,7 +157,7 @@ int detlsh_query_ex(const detlsh_index *ix, const float *queries, int64_t m,
  * calls that overlap on the GPU (other streams, other host threads) race:
  * serialise them.  Returns after the results are written.
  * Errors: as detlsh_query_ex, plus SCRATCH_LIMIT; INVALID_ARG for host
- * pointers.
+ * pointers and for rmin_policy other than DETLSH_RMIN_MAGIC.
  */
 int detlsh_query_noalloc(const detlsh_index *ix, const float *queries, int64_t m, int32_t k,
                          const detlsh_query_params *qp, void *stream, int64_t *ids,

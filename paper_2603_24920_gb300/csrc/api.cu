@@ -558,6 +558,11 @@ int validate_query(const detlsh_index *ix, int64_t m, int32_t k_max, const detls
   if (qp->precision == DETLSH_PREC_BF16_REFINE &&
       (!ix->Xh || (ix->d % 8) != 0 || qp->rerank_mult < 1))
     return DETLSH_ERR_INVALID_ARG;
+  if (qp->rmin_policy != DETLSH_RMIN_MAGIC && qp->rmin_policy != DETLSH_RMIN_FIXED)
+    return DETLSH_ERR_INVALID_ARG;
+  if (qp->rmin_policy == DETLSH_RMIN_FIXED &&
+      (!(qp->r_min > 0.0) || !std::isfinite(qp->r_min) || qp->precision != DETLSH_PREC_FP32))
+    return DETLSH_ERR_INVALID_ARG;
   return DETLSH_OK;
 }
 
@@ -581,7 +586,7 @@ int query_impl(detlsh_index *ix, const float *queries, int64_t m, const int32_t 
   DL_TRY(grow(ix->qQp, sizeof(float) * (size_t)m * LK, st));
   DL_TRY(grow(ix->qids, sizeof(int64_t) * (size_t)m * k_max, st));
   DL_TRY(grow(ix->qdists, sizeof(float) * (size_t)m * k_max, st));
-  DL_TRY(grow(ix->qT, sizeof(float) * 256, st));
+  DL_TRY(grow(ix->qT, sizeof(float) * 512, st));
   DL_TRY(grow(ix->qstat, 256, st));
   float *Q = static_cast<float *>(ix->qQ.p);
   float *Qp = static_cast<float *>(ix->qQp.p);
@@ -605,9 +610,23 @@ int query_impl(detlsh_index *ix, const float *queries, int64_t m, const int32_t 
     DL_TRY(dl::f32_to_bf16(Q, static_cast<__nv_bfloat16 *>(ix->qQh.p), m * (int64_t)d, st));
     Qh = static_cast<const __nv_bfloat16 *>(ix->qQh.p);
   }
-  float Th[256];
-  level_table(ix->eps2, qp->c, Th);
-  Th[255] = INFINITY;
+  // radius grid (and for a fixed r_min the condition-2 radii (c r_i)^2)
+  const bool fixed = qp->rmin_policy == DETLSH_RMIN_FIXED;
+  float Th[512];
+  if (fixed) {
+    const double r0 = qp->r_min, c = qp->c;
+    for (int i = 0; i < NLEV - 1; ++i) {
+      Th[i] = (float)(ix->eps2 * r0 * r0 * std::pow(c, 2.0 * (double)i));
+      const double cr = c * (r0 * std::pow(c, (double)i));
+      Th[256 + i] = (float)(cr * cr);
+    }
+    Th[NLEV - 1] = Th[255] = INFINITY;
+    Th[256 + NLEV - 1] = Th[511] = INFINITY;
+  } else {
+    level_table(ix->eps2, qp->c, Th);
+    Th[255] = INFINITY;
+    for (int i = 256; i < 512; ++i) Th[i] = INFINITY;
+  }
   DL_CUDA(cudaMemcpyAsync(ix->qT.p, Th, sizeof Th, cudaMemcpyHostToDevice, st));
   int32_t *kd = nullptr;
   if (kq) {
@@ -623,7 +642,12 @@ int query_impl(detlsh_index *ix, const float *queries, int64_t m, const int32_t 
   QueryArgs qa{};
   qa.Q = Q; qa.Qh = Qh; qa.Qp = Qp; qa.m = m; qa.kq = kd; qa.k_max = k_max;
   qa.tau_base = tau_base; qa.T = static_cast<const float *>(ix->qT.p);
-  qa.lg_eps2 = (float)std::log2(ix->eps2);
+  qa.Tc = static_cast<const float *>(ix->qT.p) + 256;
+  qa.policy = qp->rmin_policy;
+  // level estimate log2(T) -> index: grid c^j from j = -127, or r_min c^i from i = 0
+  qa.lg_eps2 = fixed ? (float)(std::log2(ix->eps2 * qp->r_min * qp->r_min) +
+                               254.0 * std::log2(qp->c))
+                     : (float)std::log2(ix->eps2);
   qa.inv_2lg_c = (float)(1.0 / (2.0 * std::log2(qp->c)));
   qa.precision = qp->precision; qa.rerank_mult = qp->rerank_mult;
   qa.ids = static_cast<int64_t *>(ix->qids.p);
@@ -638,7 +662,7 @@ int query_impl(detlsh_index *ix, const float *queries, int64_t m, const int32_t 
   }
   qa.cand_cap = cap;
   query_slot_offsets(v, cap, qa.off);
-  qa.slot_bytes = qa.off[11];  // total bytes of one slot
+  qa.slot_bytes = qa.off[12];  // total bytes of one slot
   int slots = query_slots(v);
   slots = (int)std::min<int64_t>(slots, std::max<int64_t>(m, 1));
   // keep the scratch within a quarter of the free device memory
@@ -756,6 +780,8 @@ int detlsh_default_query_params(detlsh_query_params *p) {
   p->c = 1.5;
   p->precision = DETLSH_PREC_FP32;
   p->rerank_mult = 4;
+  p->rmin_policy = DETLSH_RMIN_MAGIC;
+  p->r_min = 1.0;
   return DETLSH_OK;
 }
 

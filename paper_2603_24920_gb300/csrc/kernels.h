@@ -115,6 +115,8 @@ struct QueryArgs {
   int k_max;
   int64_t tau_base;          // ceil(beta * n)
   const float *T;            // [255] radius grid
+  const float *Tc;           // [255] fp32((c r_i)^2) (fixed r_min, condition 2)
+  int policy;                // DETLSH_RMIN_MAGIC / DETLSH_RMIN_FIXED
   float lg_eps2, inv_2lg_c;  // log2(eps^2), 1/(2 log2 c): level estimate before the exact fix-up
   int precision, rerank_mult;
   int64_t *ids;              // [m][k_max]
@@ -127,7 +129,7 @@ struct QueryArgs {
   // scratch: one slot per CTA, offsets from query_slot_offsets
   uint8_t *scratch;
   int64_t slot_bytes;
-  int64_t off[12];
+  int64_t off[13];
   int64_t cand_cap;
   uint32_t epoch_base;       // leaf levels are tagged (epoch << 8 | level), epoch = base + qi
   int nslots;
@@ -136,7 +138,7 @@ struct QueryArgs {
   unsigned long long *stats;  // [4]: candidates, leaves expanded, hull blocks, points visited
 };
 size_t query_slot_bytes(const QueryIndexView &ix, int64_t cand_cap, int rerank_cap);
-void query_slot_offsets(const QueryIndexView &ix, int64_t cand_cap, int64_t off[12]);
+void query_slot_offsets(const QueryIndexView &ix, int64_t cand_cap, int64_t off[13]);
 int query_slots(const QueryIndexView &ix);
 int run_queries(const QueryIndexView &ix, const QueryArgs &qa, cudaStream_t st);
 

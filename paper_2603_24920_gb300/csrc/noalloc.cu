@@ -73,6 +73,7 @@ extern "C" int detlsh_query_noalloc(const detlsh_index *ix, const float *queries
   detlsh_default_query_params(&def);
   if (!qp) qp = &def;
   DL_TRY(check_query_args(ix, m, k, qp));
+  if (qp->rmin_policy != DETLSH_RMIN_MAGIC) return DETLSH_ERR_INVALID_ARG;  // magic r_min only
   if (m == 0) return DETLSH_OK;
   if (!on_device(queries) || !on_device(ids) || !on_device(dists)) return DETLSH_ERR_INVALID_ARG;
   QueryIndexView v;
@@ -93,7 +94,7 @@ extern "C" int detlsh_query_noalloc(const detlsh_index *ix, const float *queries
   const int64_t o_slots = up256(o_qh + (bf16 ? 2 * m * v.d : 0));
   QueryArgs qa{};
   query_slot_offsets(v, cap, qa.off);
-  const int64_t slot = qa.off[11];
+  const int64_t slot = qa.off[12];
   if (o_slots + slot > (int64_t)kScratchBytes) return DETLSH_ERR_SCRATCH_LIMIT;
   int slots = query_slots(v);
   slots = (int)std::min<int64_t>({(int64_t)slots, m, ((int64_t)kScratchBytes - o_slots) / slot});

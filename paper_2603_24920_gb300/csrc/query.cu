@@ -50,26 +50,27 @@ struct Slot {
   uint32_t *key;    // [cap] order keys of distances
   uint32_t *rid;    // [RR_MAX] re-rank ids
   uint32_t *rkey;   // [RR_MAX]
+  uint8_t *cm;      // [cap] smallest level of each candidate (fixed r_min)
 };
 
 __host__ __device__ inline int64_t align_up(int64_t v, int64_t a) { return (v + a - 1) / a * a; }
 
-static void slot_layout(const QueryIndexView &ix, int64_t cap, int64_t off[12]) {
+static void slot_layout(const QueryIndexView &ix, int64_t cap, int64_t off[13]) {
   const int64_t tl = ix.leaf_off[ix.L], tb = ix.blk_off[ix.L];
-  const int64_t sz[11] = {4 * tl, tb, 4 * tb, 4 * tl, 4 * tl, tl, 4 * ix.max_leaves,
-                          4 * cap, 4 * cap, 4 * RR_MAX, 4 * RR_MAX};
+  const int64_t sz[12] = {4 * tl, tb, 4 * tb, 4 * tl, 4 * tl, tl, 4 * ix.max_leaves,
+                          4 * cap, 4 * cap, 4 * RR_MAX, 4 * RR_MAX, cap};
   int64_t o = 0;
-  for (int i = 0; i < 11; ++i) { off[i] = o; o = align_up(o + sz[i], 256); }
-  off[11] = o;
+  for (int i = 0; i < 12; ++i) { off[i] = o; o = align_up(o + sz[i], 256); }
+  off[12] = o;
 }
 
 size_t query_slot_bytes(const QueryIndexView &ix, int64_t cand_cap, int) {
-  int64_t off[12];
+  int64_t off[13];
   slot_layout(ix, cand_cap, off);
-  return (size_t)off[11];
+  return (size_t)off[12];
 }
 
-void query_slot_offsets(const QueryIndexView &ix, int64_t cand_cap, int64_t off[12]) {
+void query_slot_offsets(const QueryIndexView &ix, int64_t cand_cap, int64_t off[13]) {
   slot_layout(ix, cand_cap, off);
 }
 
@@ -547,6 +548,7 @@ template <int LC>
 __device__ __forceinline__ void union_counts_t(QCtx &c) {
   const QueryIndexView &ix = c.ix;
   const uint32_t jhi = (uint32_t)c.sm.jhi;
+  const bool fixed = c.qa.policy == DETLSH_RMIN_FIXED;
   const int L = LC ? LC : ix.L;
   for (int t = 0; t < L; ++t) {
     const int64_t lo0 = ix.leaf_off[t];
@@ -566,9 +568,12 @@ __device__ __forceinline__ void union_counts_t(QCtx &c) {
             }
           }
           warp_bin_count(c.sm.H, valid && owner == t, m, 1u);
-          // new in tree t for levels in [lvt, f)
-          warp_bin_count(Dt, valid && f > lvt, lvt, 1u);
-          warp_bin_count(Dt, valid && f > lvt && f <= jhi, f, 0xffffffffu);  // -1 (two's complement)
+          if (fixed) {  // points owned by tree t, by smallest level
+            warp_bin_count(Dt, valid && owner == t, m, 1u);
+          } else {      // new in tree t for levels in [lvt, f)
+            warp_bin_count(Dt, valid && f > lvt, lvt, 1u);
+            warp_bin_count(Dt, valid && f > lvt && f <= jhi, f, 0xffffffffu);  // -1 (two's complement)
+          }
         },
         true);
   }
@@ -919,6 +924,206 @@ __device__ __forceinline__ void topk_select(int64_t n, int kk, Get get, QShared 
   }
 }
 
+// ---- Alg. 5 from a fixed r_min, with condition 2 -------------------------
+// Radius index i stands for r_min c^i.  j1 = the first radius whose union
+// holds beta*n + k points (condition 1), if any.  Every radius before j1 is
+// passed whole, so at radius j1 the loop starts from S(j1 - 1) = the points
+// whose smallest level is below j1, and condition 2 can only stop it before
+// j1: at the first j < j1 where k points of S(j) lie within c r_j, i.e. k
+// points with max(smallest level, first radius covering their distance)
+// <= j.  Otherwise at j1 the trees add, in order, the points whose smallest
+// level is j1, each from the first tree attaining it; inside tree i* the
+// leaves enter by (LB^2, leaf index) until the count is reached.
+
+// Smallest level of p over trees u < t (fb) and over u > t (fa).
+template <int LC>
+__device__ __forceinline__ void levels_around(const QCtx &c, uint32_t p, int t, uint32_t &fb,
+                                              uint32_t &fa) {
+  const PointLeaves<LC> lf(c.ix, p);
+  const int L = LC ? LC : c.ix.L;
+  fb = 255u;
+  fa = 255u;
+#pragma unroll
+  for (int u = 0; u < L; ++u) {
+    if (u == t) continue;
+    const uint32_t lv = leaf_level_h(c.ix, c.s, c.sm, c.lut, u, lf[u]);
+    if (u < t) fb = min(fb, lv); else fa = min(fa, lv);
+  }
+}
+
+// Appends to the candidate list, warp-aggregated.
+__device__ __forceinline__ uint32_t warp_append(QCtx &c, bool take) {
+  const int lane = threadIdx.x & 31;
+  const unsigned tm = __ballot_sync(FULL, take);
+  uint32_t pos0 = 0;
+  if (lane == 0 && tm) pos0 = atomicAdd(&c.sm.ncand, (uint32_t)__popc(tm));
+  pos0 = __shfl_sync(FULL, pos0, 0);
+  return pos0 + __popc(tm & ((1u << lane) - 1u));
+}
+
+// S(js): every point whose smallest level is <= js, once (from the first
+// tree where its level is <= js), with that smallest level in cm[].
+template <int LC>
+__device__ __forceinline__ void collect_below(QCtx &c, uint32_t js) {
+  if (threadIdx.x == 0) c.sm.ncand = 0;
+  __syncthreads();
+  const int L = LC ? LC : c.ix.L;
+  for (int t = 0; t < L; ++t) {
+    const int64_t lo0 = c.ix.leaf_off[t];
+    visit_points(
+        c, t, [&](int64_t e) { return c.s.llev[lo0 + e] <= js; },
+        [&](bool valid, uint32_t p, uint32_t, uint32_t lvt) {
+          uint32_t fb = 0, fa = 0;
+          if (valid) levels_around<LC>(c, p, t, fb, fa);
+          const bool take = valid && fb > js;
+          const uint32_t pos = warp_append(c, take);
+          if (take && pos < (uint32_t)c.qa.cand_cap) {
+            c.s.cand[pos] = p;
+            c.s.cm[pos] = (uint8_t)min(lvt, fa);
+          }
+        });
+  }
+  __syncthreads();
+}
+
+// Condition 1 at radius j1 after S(j1 - 1): the cut in tree i* and the new
+// points of trees <= i*, appended after the ncA points already listed.
+template <int LC>
+__device__ __forceinline__ void cut_and_collect_fixed(QCtx &c, uint32_t j1) {
+  const QueryIndexView &ix = c.ix;
+  const int is = c.sm.istar;
+  const int64_t li0 = ix.leaf_off[is];
+  const int64_t nli = c.sm.nlist[is];
+  for (int64_t e = threadIdx.x; e < nli; e += QT) c.s.cval[e] = 0u;
+  __syncthreads();
+  // new points of tree i*'s leaves at level j1: smallest level j1, first tree
+  visit_points(
+      c, is, [&](int64_t e) { return c.s.llev[li0 + e] == j1; },
+      [&](bool valid, uint32_t p, uint32_t ent, uint32_t) {
+        uint32_t fb = 0, fa = 0;
+        if (valid) levels_around<LC>(c, p, is, fb, fa);
+        warp_bin_count(c.s.cval, valid && fb > j1 && fa >= j1, ent, 1u);
+      });
+  __syncthreads();
+  const uint32_t need = c.sm.need;
+  auto get_lb = [&](int64_t i, uint32_t &k, uint32_t &w) {
+    w = (c.s.llev[li0 + i] <= j1) ? c.s.cval[i] : 0u;
+    k = __float_as_uint(c.s.llb2[li0 + i]);
+  };
+  block_select(nli, get_lb, need, c.sm);
+  const uint32_t v = c.sm.sel_v;
+  const uint32_t need2 = need - c.sm.sel_below;
+  uint32_t cut = 0xffffffffu;
+  if (need2 < c.sm.sel_at) {
+    auto get_id = [&](int64_t i, uint32_t &k, uint32_t &w) {
+      const bool q = c.s.llev[li0 + i] <= j1 && __float_as_uint(c.s.llb2[li0 + i]) == v;
+      w = q ? c.s.cval[i] : 0u;
+      k = c.s.lleaf[li0 + i];
+    };
+    block_select(nli, get_id, need2, c.sm);
+    cut = c.sm.sel_v;
+  }
+  for (int t = 0; t <= is; ++t) {
+    const int64_t lo0 = ix.leaf_off[t];
+    visit_points(
+        c, t,
+        [&](int64_t e) {
+          if (c.s.llev[lo0 + e] != j1) return false;
+          if (t < is) return true;
+          const uint32_t kb = __float_as_uint(c.s.llb2[lo0 + e]);
+          return kb < v || (kb == v && c.s.lleaf[lo0 + e] <= cut);
+        },
+        [&](bool valid, uint32_t p, uint32_t, uint32_t) {
+          uint32_t fb = 0, fa = 0;
+          if (valid) levels_around<LC>(c, p, t, fb, fa);
+          const bool take = valid && fb > j1 && fa >= j1;
+          const uint32_t pos = warp_append(c, take);
+          if (take && pos < (uint32_t)c.qa.cand_cap) c.s.cand[pos] = p;
+        });
+  }
+  __syncthreads();
+}
+
+// The whole fixed-r_min resolution after the union counts: fills S, j and
+// the stopping tree (-1 = condition 2), and the top-k in sm.topk_*.
+template <int LC>
+__device__ __forceinline__ int64_t fixed_rmin_query(QCtx &c, int k) {
+  const QueryIndexView &ix = c.ix;
+  QShared &sm = c.sm;
+  const int64_t tau = c.tau;
+  const uint32_t j1 = (sm.sel_g <= sm.jhi) ? (uint32_t)sm.sel_g : (uint32_t)NLEV;
+  float *Tc = reinterpret_cast<float *>(sm.bstart);  // free after the expansion
+  for (int i = threadIdx.x; i < 256; i += QT) Tc[i] = c.qa.Tc[i];
+  const float *q = c.qa.Q + c.qi * ix.d;
+  const uint32_t *cand = c.s.cand;
+  int64_t ncA = 0;
+  if (j1 > 0) {
+    collect_below<LC>(c, j1 - 1);
+    ncA = min((int64_t)sm.ncand, c.qa.cand_cap);
+    dist_fp32(ix, q, ncA, [&](int64_t i) { return cand[i]; }, c.s.key);
+    // condition 2: first j < j1 with k points of max(level, covering radius) <= j
+    sm.rh[threadIdx.x] = 0;
+    __syncthreads();
+    for (int64_t i = threadIdx.x; i < ncA; i += QT) {
+      const float d2 = __uint_as_float(c.s.key[i]);
+      int lo = 0, hi = NLEV - 1;  // first radius index with d2 <= Tc (Tc[254] = inf)
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (d2 <= Tc[mid]) hi = mid; else lo = mid + 1;
+      }
+      const uint32_t b = max((uint32_t)lo, (uint32_t)c.s.cm[i]);
+      if (b < j1) atomicAdd(&sm.rh[b], 1u);
+    }
+    __syncthreads();
+    warp_first_crossing(sm.rh, 0, (uint64_t)k, &sm.sel_g, &sm.sel_bf);
+    __syncthreads();
+    const uint32_t j2 = (uint32_t)sm.sel_g;
+    if (j2 < j1 && sm.sel_g < 255) {
+      // stop by condition 2 at radius j2: S = S(j2), top-k of it
+      if (threadIdx.x == 0) { sm.jstar = (int)j2; sm.istar = -1; sm.nres = 0; }
+      __syncthreads();
+      int64_t* Sout = c.qa.S_out;
+      for (int64_t i = threadIdx.x; i < ncA; i += QT) {
+        if (c.s.cm[i] <= j2) {
+          const uint32_t pos = atomicAdd(&sm.nres, 1u);
+          if (Sout && pos < c.qa.S_cap) Sout[c.qi * c.qa.S_cap + pos] = cand[i];
+        }
+      }
+      __syncthreads();
+      const int64_t ns = sm.nres;
+      __syncthreads();
+      auto get_s = [&](int64_t i, uint32_t &key, uint32_t &id) {
+        key = c.s.cm[i] <= j2 ? c.s.key[i] : 0xffffffffu;
+        id = cand[i];
+      };
+      topk_select(ncA, k, get_s, sm);
+      return -ns - 1;  // negative: S was written here
+    }
+  }
+  // condition 1 at radius j1 (j1 < NLEV here: tau <= n)
+  if (threadIdx.x == 0) {
+    int64_t cum = ncA, basev = ncA;
+    int is = ix.L - 1;
+    for (int t = 0; t < ix.L; ++t) {
+      const int64_t nt = c.D[t * 256 + j1];
+      if (cum + nt >= tau) { is = t; basev = cum; break; }
+      cum += nt;
+    }
+    sm.jstar = (int)j1;
+    sm.istar = is;
+    sm.need = (uint32_t)(tau - basev);
+    sm.ncand = (uint32_t)ncA;
+  }
+  __syncthreads();
+  cut_and_collect_fixed<LC>(c, j1);
+  const int64_t nc = min((int64_t)sm.ncand, c.qa.cand_cap);
+  if (sm.ncand > c.qa.cand_cap && threadIdx.x == 0) atomicExch(c.qa.err, (int)DETLSH_ERR_CAPACITY);
+  dist_fp32(ix, q, nc - ncA, [&](int64_t i) { return cand[ncA + i]; }, c.s.key + ncA);
+  auto get_s = [&](int64_t i, uint32_t &key, uint32_t &id) { key = c.s.key[i]; id = cand[i]; };
+  topk_select(nc, k, get_s, sm);
+  return nc;
+}
+
 __global__ void __launch_bounds__(QT, 5) k_query(QueryIndexView ix, QueryArgs qa) {
   extern __shared__ __align__(16) uint8_t dsm[];
   QShared &sm = *reinterpret_cast<QShared *>(dsm);
@@ -939,6 +1144,7 @@ __global__ void __launch_bounds__(QT, 5) k_query(QueryIndexView ix, QueryArgs qa
   s.key = reinterpret_cast<uint32_t *>(base + qa.off[8]);
   s.rid = reinterpret_cast<uint32_t *>(base + qa.off[9]);
   s.rkey = reinterpret_cast<uint32_t *>(base + qa.off[10]);
+  s.cm = base + qa.off[11];
   for (int i = threadIdx.x; i < 256; i += QT) sm.T[i] = i < NLEV ? qa.T[i] : __int_as_float(0x7f800000);
   if (threadIdx.x == 0) { sm.n_blocks = 0; sm.n_leaves = 0; sm.n_visit = 0; }
   __syncthreads();
@@ -951,7 +1157,10 @@ __global__ void __launch_bounds__(QT, 5) k_query(QueryIndexView ix, QueryArgs qa
     const int k = qa.kq ? qa.kq[qi] : qa.k_max;
     const int64_t tau = qa.tau_base + k;
     QCtx c{ix, qa, sm, lut, hist, D, s, qi, tau};
-    const bool allpts = tau > ix.n;
+    bool fixed_done = false, s_written = false;  // fixed r_min: top-k (and S) done
+    // beta*n + k > n: with the magic r_min the budget is never met and S is
+    // every point; a fixed r_min still runs its radius loop (condition 2)
+    const bool allpts = tau > ix.n && qa.policy != DETLSH_RMIN_FIXED;
     int64_t nc;
     if (allpts) {
       // beta*n + k > n: the budget is never met; Alg. 5 stops through its
@@ -969,96 +1178,107 @@ __global__ void __launch_bounds__(QT, 5) k_query(QueryIndexView ix, QueryArgs qa
       // j* = first level whose union count reaches tau (<= jhi by construction)
       warp_first_crossing(sm.H, 0, (uint64_t)tau, &sm.sel_g, &sm.sel_bf);
       __syncthreads();
-      const int js = min(sm.sel_g, sm.jhi);
-      {  // points new in each tree at level j*: one warp per tree
-        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-        for (int t = warp; t < ix.L; t += QW) {
-          int64_t v = 0;
-          for (int j = lane; j <= js; j += 32) v += D[t * 256 + j];
+      if (qa.policy == DETLSH_RMIN_FIXED) {
+        const int64_t r = ix.L == 4 ? fixed_rmin_query<4>(c, k) : fixed_rmin_query<0>(c, k);
+        fixed_done = true;
+        s_written = r < 0;
+        nc = r < 0 ? -r - 1 : r;
+      } else {
+        const int js = min(sm.sel_g, sm.jhi);
+        {  // points new in each tree at level j*: one warp per tree
+          const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+          for (int t = warp; t < ix.L; t += QW) {
+            int64_t v = 0;
+            for (int j = lane; j <= js; j += 32) v += D[t * 256 + j];
 #pragma unroll
-          for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
-          if (lane == 0) sm.newt[t] = v;
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+            if (lane == 0) sm.newt[t] = v;
+          }
         }
-      }
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        int64_t cum = 0, basev = 0;
-        int is = ix.L - 1;
-        for (int t = 0; t < ix.L; ++t) {
-          if (cum + sm.newt[t] >= tau) { is = t; basev = cum; break; }
-          cum += sm.newt[t];
+        __syncthreads();
+        if (threadIdx.x == 0) {
+          int64_t cum = 0, basev = 0;
+          int is = ix.L - 1;
+          for (int t = 0; t < ix.L; ++t) {
+            if (cum + sm.newt[t] >= tau) { is = t; basev = cum; break; }
+            cum += sm.newt[t];
+          }
+          sm.jstar = js;
+          sm.istar = is;
+          sm.need = (uint32_t)(tau - basev);
         }
-        sm.jstar = js;
-        sm.istar = is;
-        sm.need = (uint32_t)(tau - basev);
-      }
-      __syncthreads();
-      cut_and_collect(c);
-      nc = sm.ncand;
-      if (nc > qa.cand_cap) {
-        // cannot happen for |S| < beta*n + k + largest leaf; report and skip
-        if (threadIdx.x == 0) atomicExch(qa.err, (int)DETLSH_ERR_CAPACITY);
-        nc = qa.cand_cap;
+        __syncthreads();
+        cut_and_collect(c);
+        nc = sm.ncand;
+        if (nc > qa.cand_cap) {
+          // cannot happen for |S| < beta*n + k + largest leaf; report and skip
+          if (threadIdx.x == 0) atomicExch(qa.err, (int)DETLSH_ERR_CAPACITY);
+          nc = qa.cand_cap;
+        }
       }
     }
     if (qa.S_out) {
-      for (int64_t i = threadIdx.x; i < nc && i < qa.S_cap; i += QT)
-        qa.S_out[qi * qa.S_cap + i] = allpts ? i : (int64_t)s.cand[i];
+      if (!s_written)
+        for (int64_t i = threadIdx.x; i < nc && i < qa.S_cap; i += QT)
+          qa.S_out[qi * qa.S_cap + i] = allpts ? i : (int64_t)s.cand[i];
       if (threadIdx.x == 0) {
         qa.S_size[qi] = nc;
-        qa.jstar[qi] = sm.jstar + JMIN;
+        // grid index j of r_min = c^j, or the radius index i of r_min c^i
+        qa.jstar[qi] = qa.policy == DETLSH_RMIN_FIXED ? sm.jstar : sm.jstar + JMIN;
         qa.istar[qi] = sm.istar;
         if (nc > qa.S_cap) atomicExch(qa.err, (int)DETLSH_ERR_CAPACITY);
       }
     }
-    // verification and top-k
-    if (qa.precision == DETLSH_PREC_BF16_REFINE) {
-      distances_bf16(c, nc, allpts);
-      int R = qa.rerank_mult * k;
-      if (R > RR_MAX) R = RR_MAX;
-      if (R > nc) R = (int)nc;
-      if (R < k) R = k;
-      auto get_s = [&](int64_t i, uint32_t &key, uint32_t &id) {
-        key = s.key[i];
-        id = allpts ? (uint32_t)i : s.cand[i];
-      };
-      // pick the R best BF16 scores (unsorted is enough): threshold select
-      auto gk = [&](int64_t i, uint32_t &kk2, uint32_t &w) { uint32_t id; get_s(i, kk2, id); w = 1u; };
-      block_select(nc, gk, (uint32_t)R, sm);
-      const uint32_t vk = sm.sel_v, below = sm.sel_below;
-      uint32_t idcut = 0xffffffffu;
-      if ((uint32_t)R - below < sm.sel_at) {
-        auto gi = [&](int64_t i, uint32_t &kk2, uint32_t &w) {
+    if (!fixed_done) {
+      // verification and top-k
+      if (qa.precision == DETLSH_PREC_BF16_REFINE) {
+        distances_bf16(c, nc, allpts);
+        int R = qa.rerank_mult * k;
+        if (R > RR_MAX) R = RR_MAX;
+        if (R > nc) R = (int)nc;
+        if (R < k) R = k;
+        auto get_s = [&](int64_t i, uint32_t &key, uint32_t &id) {
+          key = s.key[i];
+          id = allpts ? (uint32_t)i : s.cand[i];
+        };
+        // pick the R best BF16 scores (unsorted is enough): threshold select
+        auto gk = [&](int64_t i, uint32_t &kk2, uint32_t &w) { uint32_t id; get_s(i, kk2, id); w = 1u; };
+        block_select(nc, gk, (uint32_t)R, sm);
+        const uint32_t vk = sm.sel_v, below = sm.sel_below;
+        uint32_t idcut = 0xffffffffu;
+        if ((uint32_t)R - below < sm.sel_at) {
+          auto gi = [&](int64_t i, uint32_t &kk2, uint32_t &w) {
+            uint32_t key, id;
+            get_s(i, key, id);
+            kk2 = id;
+            w = key == vk ? 1u : 0u;
+          };
+          block_select(nc, gi, (uint32_t)R - below, sm);
+          idcut = sm.sel_v;
+        }
+        if (threadIdx.x == 0) sm.nres = 0;
+        __syncthreads();
+        for (int64_t i = threadIdx.x; i < nc; i += QT) {
           uint32_t key, id;
           get_s(i, key, id);
-          kk2 = id;
-          w = key == vk ? 1u : 0u;
-        };
-        block_select(nc, gi, (uint32_t)R - below, sm);
-        idcut = sm.sel_v;
-      }
-      if (threadIdx.x == 0) sm.nres = 0;
-      __syncthreads();
-      for (int64_t i = threadIdx.x; i < nc; i += QT) {
-        uint32_t key, id;
-        get_s(i, key, id);
-        if (key < vk || (key == vk && id <= idcut)) {
-          const uint32_t pos = atomicAdd(&sm.nres, 1u);
-          if (pos < RR_MAX) s.rid[pos] = id;
+          if (key < vk || (key == vk && id <= idcut)) {
+            const uint32_t pos = atomicAdd(&sm.nres, 1u);
+            if (pos < RR_MAX) s.rid[pos] = id;
+          }
         }
+        __syncthreads();
+        // exact FP32 distances of the re-rank pool
+        dist_fp32(ix, qa.Q + qi * ix.d, R, [&](int64_t i) { return s.rid[i]; }, s.rkey);
+        auto get_r = [&](int64_t i, uint32_t &key, uint32_t &id) { key = s.rkey[i]; id = s.rid[i]; };
+        topk_select(R, k, get_r, sm);
+      } else {
+        distances_fp32(c, nc, allpts);
+        auto get_s = [&](int64_t i, uint32_t &key, uint32_t &id) {
+          key = s.key[i];
+          id = allpts ? (uint32_t)i : s.cand[i];
+        };
+        topk_select(nc, k, get_s, sm);
       }
-      __syncthreads();
-      // exact FP32 distances of the re-rank pool
-      dist_fp32(ix, qa.Q + qi * ix.d, R, [&](int64_t i) { return s.rid[i]; }, s.rkey);
-      auto get_r = [&](int64_t i, uint32_t &key, uint32_t &id) { key = s.rkey[i]; id = s.rid[i]; };
-      topk_select(R, k, get_r, sm);
-    } else {
-      distances_fp32(c, nc, allpts);
-      auto get_s = [&](int64_t i, uint32_t &key, uint32_t &id) {
-        key = s.key[i];
-        id = allpts ? (uint32_t)i : s.cand[i];
-      };
-      topk_select(nc, k, get_s, sm);
     }
     if (threadIdx.x == 0 && qa.stats) atomicAdd(&qa.stats[0], (unsigned long long)nc);
     for (int r = threadIdx.x; r < qa.k_max; r += QT) {

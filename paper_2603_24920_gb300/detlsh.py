@@ -17,6 +17,7 @@ STATUS = {0: "OK", -1: "INVALID_ARG", -2: "NONFINITE_INPUT", -3: "OOM", -4: "CUD
           -5: "CAPACITY", -6: "NO_DEVICE", -7: "SCRATCH_LIMIT"}
 BOX_PREFIX, BOX_TIGHT = 0, 1
 PREC_FP32, PREC_BF16_REFINE = 0, 1
+RMIN_MAGIC, RMIN_FIXED = 0, 1
 
 
 class DetlshError(RuntimeError):
@@ -33,7 +34,7 @@ class BuildParams(C.Structure):
 
 class QueryParams(C.Structure):
     _fields_ = [("beta", C.c_double), ("c", C.c_double), ("precision", C.c_int32),
-                ("rerank_mult", C.c_int32)]
+                ("rerank_mult", C.c_int32), ("rmin_policy", C.c_int32), ("r_min", C.c_double)]
 
 
 class Info(C.Structure):
@@ -170,11 +171,14 @@ def detlsh_free(h):
 
 
 def detlsh_query_ex(h, queries, k, beta=0.1, c=1.5, precision=PREC_FP32, rerank_mult=4,
-                    k_per_query=None, stream=None, ids=None, dists=None):
-    """Returns (ids int64 (m, k), dists float32 (m, k)); torch CUDA if queries are."""
+                    k_per_query=None, stream=None, ids=None, dists=None, r_min=None):
+    """Returns (ids int64 (m, k), dists float32 (m, k)); torch CUDA if queries are.
+    r_min given: Alg. 5 from that radius with condition 2 (RMIN_FIXED)."""
     m = queries.shape[0]
     qp = detlsh_default_query_params()
     qp.beta, qp.c, qp.precision, qp.rerank_mult = beta, c, precision, rerank_mult
+    if r_min is not None:
+        qp.rmin_policy, qp.r_min = RMIN_FIXED, r_min
     if ids is None:
         if _is_cuda(queries):
             import torch
@@ -295,13 +299,16 @@ def detlsh_project(h, rows, stream=None):
     return out
 
 
-def detlsh_query_candidates(h, queries, k, beta=0.1, c=1.5, cap=None):
-    """Candidate sets of Alg. 5: list of id arrays, j*, i* per query."""
+def detlsh_query_candidates(h, queries, k, beta=0.1, c=1.5, cap=None, r_min=None):
+    """Candidate sets of Alg. 5: list of id arrays, j*, i* per query (with r_min:
+    the stopping radius index and tree, -1 for condition 2)."""
     i = detlsh_get_info(h)
     m = queries.shape[0]
     cap = i.n if cap is None else cap
     qp = detlsh_default_query_params()
     qp.beta, qp.c = beta, c
+    if r_min is not None:
+        qp.rmin_policy, qp.r_min = RMIN_FIXED, r_min
     S = np.empty((m, cap), np.int64)
     ssz = np.empty(m, np.int64)
     js = np.empty(m, np.int32)
