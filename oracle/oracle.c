@@ -234,6 +234,37 @@ void orc_breakpoints(const float *P, int64_t n, int LK, const int64_t *sample, i
     free(v);
 }
 
+/* Static encoding scheme (Sec. III-A): breakpoints b_1..b_{N_r-1} cut the
+ * N(0,1) density into N_r intervals of equal mass 1/N_r, b_0 = -inf and
+ * b_{N_r} = +inf, the same for every projected dimension.  The quantile is
+ * found by bisection on Phi(x) = erfc(-x/sqrt 2)/2 down to adjacent doubles
+ * in the left half (the right half by symmetry), keeping the one whose Phi is
+ * nearer to z/N_r, then rounded to FP32. */
+static double orc_norm_quantile(double p) {
+    /* symmetric: Phi^-1(1 - p) = -Phi^-1(p), Phi^-1(1/2) = 0 exactly (near 0
+     * the rounded Phi is flat over a relatively wide interval) */
+    if (p == 0.5) return 0.0;
+    if (p > 0.5) return -orc_norm_quantile(1.0 - p);
+    double lo = -40.0, hi = 0.0;
+    for (int it = 0; it < 2000; it++) {
+        double mid = 0.5 * (lo + hi);
+        if (mid <= lo || mid >= hi) break;
+        if (0.5 * erfc(-mid / sqrt(2.0)) < p) lo = mid; else hi = mid;
+    }
+    double elo = fabs(0.5 * erfc(-lo / sqrt(2.0)) - p);
+    double ehi = fabs(0.5 * erfc(-hi / sqrt(2.0)) - p);
+    return elo < ehi ? lo : hi;
+}
+
+void orc_static_breakpoints(int LK, int N_r, float *B) {
+    for (int t = 0; t < LK; t++) {
+        float *Bt = B + (int64_t)t * (N_r + 1);
+        for (int z = 1; z < N_r; z++) Bt[z] = (float)orc_norm_quantile((double)z / (double)N_r);
+        Bt[0] = -INFINITY;
+        Bt[N_r] = INFINITY;
+    }
+}
+
 /* ======================================================================
  * Alg. 1: find b with B(b) <= h <= B(b+1) and store the b-th symbol.  The
  * closed interval admits two b at a breakpoint; reading: the first such b,
@@ -544,7 +575,7 @@ static void orc_build_tree(orc_index *ix, int t, int insertion_order) {
 
 orc_index *orc_index_build(const float *X, int64_t n, int64_t d, int L, int K, int N_r,
                            uint64_t seed, double frac, int M, int box_mode,
-                           int insertion_order) {
+                           int insertion_order, int encoding) {
     orc_index *ix = (orc_index *)calloc(1, sizeof(orc_index));
     ix->n = n; ix->d = d; ix->L = L; ix->K = K; ix->N_r = N_r; ix->seed = seed;
     ix->frac = frac; ix->M = M; ix->box_mode = box_mode;
@@ -558,9 +589,14 @@ orc_index *orc_index_build(const float *X, int64_t n, int64_t d, int L, int K, i
     ix->P = (float *)malloc(sizeof(float) * (size_t)(n * LK));
     orc_project(ix->X, n, d, ix->A, LK, ix->P);
     ix->sample = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
-    ix->m = orc_sample(n, seed, frac, N_r, ix->sample);
     ix->B = (float *)malloc(sizeof(float) * (size_t)(LK * (N_r + 1)));
-    orc_breakpoints(ix->P, n, LK, ix->sample, ix->m, N_r, ix->B);
+    if (encoding == 1) {  /* static scheme: no sample */
+        ix->m = 0;
+        orc_static_breakpoints(LK, N_r, ix->B);
+    } else {              /* dynamic scheme */
+        ix->m = orc_sample(n, seed, frac, N_r, ix->sample);
+        orc_breakpoints(ix->P, n, LK, ix->sample, ix->m, N_r, ix->B);
+    }
     ix->codes = (uint8_t *)malloc((size_t)(n * LK));
     orc_encode(ix->P, n, LK, ix->B, N_r, ix->codes);
     ix->trees = (otree *)calloc((size_t)L, sizeof(otree));

@@ -46,6 +46,9 @@ int64_t orc_sample(int64_t n, uint64_t seed, double frac, int N_r, int64_t *ids)
 void orc_breakpoints(const float *P, int64_t n, int LK, const int64_t *sample, int64_t m,
                      int N_r, float *B);
 
+/* Static encoding scheme (Sec. III-A): equal-mass N(0,1) breakpoints,
+ * b_0 = -inf, b_{N_r} = +inf, every dimension alike. */
+void orc_static_breakpoints(int LK, int N_r, float *B);
 /* Alg. 1 (BinarySearch step): codes[p*LK + t] = region index of P[p*LK+t]. */
 void orc_encode(const float *P, int64_t n, int LK, const float *B, int N_r, uint8_t *codes);
 
@@ -63,10 +66,12 @@ typedef struct orc_index orc_index;
 
 /* box_mode 0 = prefix box (breakpoints dividing the node, Sec. IV-C),
  *          1 = tight min/max code box.
- * insertion_order 0 = canonical bulk build, 1 = literal Alg. 2 insertion. */
+ * insertion_order 0 = canonical bulk build, 1 = literal Alg. 2 insertion.
+ * encoding 0 = dynamic scheme (sampled equal-frequency breakpoints),
+ *          1 = static scheme (N(0,1) equal-mass breakpoints). */
 orc_index *orc_index_build(const float *X, int64_t n, int64_t d, int L, int K, int N_r,
                            uint64_t seed, double frac, int M, int box_mode,
-                           int insertion_order);
+                           int insertion_order, int encoding);
 void orc_index_free(orc_index *ix);
 int64_t orc_index_sample_size(const orc_index *ix);
 int64_t orc_index_num_leaves(const orc_index *ix, int t);

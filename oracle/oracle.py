@@ -49,7 +49,8 @@ def lib():
         L.orc_eps2.restype = C.c_double
         L.orc_level_table.argtypes = [C.c_double, C.c_double, _f32p]
         L.orc_index_build.argtypes = [_f32p, C.c_int64, C.c_int64, C.c_int, C.c_int, C.c_int,
-                                      C.c_uint64, C.c_double, C.c_int, C.c_int, C.c_int]
+                                      C.c_uint64, C.c_double, C.c_int, C.c_int, C.c_int, C.c_int]
+        L.orc_static_breakpoints.argtypes = [C.c_int, C.c_int, _f32p]
         L.orc_index_build.restype = C.c_void_p
         L.orc_index_free.argtypes = [C.c_void_p]
         L.orc_index_sample_size.argtypes = [C.c_void_p]
@@ -130,6 +131,13 @@ def breakpoints(P, sample_ids, N_r):
     return B
 
 
+def static_breakpoints(LK, N_r):
+    """Static encoding scheme (Sec. III-A): N(0,1) equal-mass breakpoints."""
+    B = np.zeros((LK, N_r + 1), np.float32)
+    lib().orc_static_breakpoints(LK, N_r, B)
+    return B
+
+
 def encode(P, B):
     P, B = _f32(P), _f32(B)
     n, LK = P.shape
@@ -156,13 +164,13 @@ class Index:
     """Oracle index: encoding (Alg. 1) + L pointer-based DE-Trees (Alg. 2)."""
 
     def __init__(self, X, L=4, K=16, N_r=256, seed=0, frac=0.1, M=64, box_mode=0,
-                 insertion_order=0):
+                 insertion_order=0, encoding=0):
         X = _f32(X)
         self.n, self.d = X.shape
         self.L, self.K, self.N_r, self.M = L, K, N_r, M
         self.X = X
         self._h = lib().orc_index_build(X, self.n, self.d, L, K, N_r, seed, frac, M,
-                                        box_mode, insertion_order)
+                                        box_mode, insertion_order, encoding)
 
     def __del__(self):
         if getattr(self, "_h", None):

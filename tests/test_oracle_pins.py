@@ -595,3 +595,31 @@ def test_query_fixed_rmin_follows_alg5():
                     assert S.size < tau
                 seen.add(ist == -1)
     assert seen == {True, False}
+
+
+# ------------------------------------------------ static encoding scheme --
+@pytest.mark.parametrize("N_r", [2, 16, 256])
+def test_static_breakpoints_are_normal_quantiles(N_r):
+    # Sec. III-A, static scheme: b_z = Phi^-1(z/N_r), b_0 = -inf, b_{N_r} = +inf
+    B = oracle.static_breakpoints(3, N_r)
+    want = st.norm.ppf(np.arange(1, N_r) / N_r).astype(np.float32)
+    for t in range(3):
+        assert np.array_equal(B[t, 1:N_r], want)
+        assert B[t, 0] == -np.inf and B[t, N_r] == np.inf
+
+
+def test_static_encoding_has_equal_mass_on_normal_data():
+    # each region holds probability 1/N_r under N(0,1): a chi-square test of
+    # the codes of N(0,1) samples, and the index built with the static
+    # scheme encodes its projections with those breakpoints
+    N_r = 16
+    B = oracle.static_breakpoints(1, N_r)
+    x = np.random.default_rng(3).normal(size=(200000, 1)).astype(np.float32)
+    codes = oracle.encode(x, B)[:, 0]
+    cnt = np.bincount(codes, minlength=N_r)
+    assert st.chisquare(cnt).pvalue > 1e-4
+    X, _, _ = workloads.workload("c4", n=3000, m=1)
+    ix = oracle.Index(X, L=2, K=8, N_r=N_r, seed=2, M=16, encoding=1)
+    arr = ix.arrays()
+    assert np.array_equal(arr["B"], oracle.static_breakpoints(16, N_r))
+    assert np.array_equal(arr["codes"], oracle.encode(arr["P"], arr["B"]))
