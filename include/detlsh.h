@@ -49,6 +49,12 @@ typedef enum {
 enum { DETLSH_BOX_PREFIX = 0, /* regions of the node's iSAX prefix (paper)   */
        DETLSH_BOX_TIGHT = 1 /* min/max code of the node's points           */ };
 
+/* Encoding scheme of the projected coordinates (Sec. III-A). */
+enum { DETLSH_ENC_DYNAMIC = 0, /* sampled equal-frequency breakpoints (paper) */
+       DETLSH_ENC_STATIC = 1   /* N(0,1) equal-mass breakpoints, ends -inf and
+                                  +inf, no sample (the iSAX scheme the paper
+                                  compares against)                         */ };
+
 /* Precision of the exact-distance verification step (Alg. 5, top-k). */
 enum { DETLSH_PREC_FP32 = 0,        /* FP32 distances over every candidate  */
        DETLSH_PREC_BF16_REFINE = 1  /* BF16 scores, FP32 re-rank of the top
@@ -76,6 +82,7 @@ typedef struct {
     int32_t box_mode;       /* DETLSH_BOX_PREFIX (default) or DETLSH_BOX_TIGHT     */
     int32_t keep_bf16;      /* 1: also keep a BF16 copy of the data (default 1)    */
     int32_t keep_projections; /* 1: keep the n x L*K projections (default 0)      */
+    int32_t encoding;       /* DETLSH_ENC_DYNAMIC (default) / DETLSH_ENC_STATIC    */
 } detlsh_build_params;
 
 typedef struct {
@@ -182,6 +189,7 @@ typedef struct {
     int64_t device_bytes;       /* device memory held by the index           */
     int64_t projection_fallbacks; /* projections computed by the exact
                                      big-integer path during the build       */
+    int32_t encoding;           /* DETLSH_ENC_DYNAMIC / DETLSH_ENC_STATIC     */
 } detlsh_info;
 
 int detlsh_get_info(const detlsh_index *ix, detlsh_info *info);

@@ -27,7 +27,7 @@ void dl_set_last_cuda_error(cudaError_t e, const char *what, const char *file, i
 struct detlsh_index {
   int device = 0;
   int64_t n = 0;
-  int d = 0, L = 0, K = 0, LK = 0, N_r = 0, bbits = 0, M = 0, box_mode = 0;
+  int d = 0, L = 0, K = 0, LK = 0, N_r = 0, bbits = 0, M = 0, box_mode = 0, encoding = 0;
   uint64_t seed = 0;
   double frac = 0.1, eps2 = 0.0;
   int64_t m_sample = 0;
@@ -234,6 +234,40 @@ void level_table(double eps2, double c, float *T) {
   T[NLEV - 1] = INFINITY;
 }
 
+// Static encoding scheme (Sec. III-A): the N(0,1) quantiles z/N_r.  Start
+// from the Abramowitz-Stegun 26.2.22 rational approximation (error < 3e-3)
+// and polish with Newton steps on Phi(x) = erfc(-x/sqrt 2)/2 to full double
+// precision; the upper half by symmetry, the median exactly 0.
+double normal_quantile(double p) {
+  if (p == 0.5) return 0.0;
+  if (p > 0.5) return -normal_quantile(1.0 - p);
+  const double t = std::sqrt(-2.0 * std::log(p));
+  double x = -(t - (2.30753 + 0.27061 * t) / (1.0 + t * (0.99229 + 0.04481 * t)));
+  for (int it = 0; it < 100; ++it) {
+    const double f = 0.5 * std::erfc(-x / std::sqrt(2.0)) - p;
+    const double dens = std::exp(-0.5 * x * x) / 2.5066282746310002;  // sqrt(2 pi)
+    const double step = f / dens;
+    x -= step;
+    if (std::fabs(step) <= 1e-17 * std::fabs(x)) break;
+  }
+  return x;
+}
+
+void static_breakpoints(int LK, int N_r, float *B) {
+  for (int t = 0; t < LK; ++t) {
+    float *Bt = B + (int64_t)t * (N_r + 1);
+    for (int z = 1; z < N_r; ++z) Bt[z] = (float)normal_quantile((double)z / (double)N_r);
+    Bt[0] = -INFINITY;
+    Bt[N_r] = INFINITY;
+  }
+}
+
+uint32_t host_fkey(float f) {
+  uint32_t b;
+  memcpy(&b, &f, sizeof b);
+  return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+
 __global__ void k_fill_minmax(uint32_t *mm, int LK, const float *B, int N_r) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t < LK) {
@@ -303,6 +337,8 @@ int validate_build(int64_t n, int32_t d, const detlsh_build_params *p) {
   if (p->N_r < 2 || p->N_r > 256 || (p->N_r & (p->N_r - 1))) return DETLSH_ERR_INVALID_ARG;
   if (p->max_size < 1) return DETLSH_ERR_INVALID_ARG;
   if (!(p->sample_frac > 0.0 && p->sample_frac <= 1.0)) return DETLSH_ERR_INVALID_ARG;
+  if (p->encoding != DETLSH_ENC_DYNAMIC && p->encoding != DETLSH_ENC_STATIC)
+    return DETLSH_ERR_INVALID_ARG;
   if (p->box_mode != DETLSH_BOX_PREFIX && p->box_mode != DETLSH_BOX_TIGHT)
     return DETLSH_ERR_INVALID_ARG;
   return DETLSH_OK;
@@ -339,42 +375,60 @@ int build_impl(detlsh_index *ix, const float *data, cudaStream_t st, const detls
   pa.fb_list = fb_list; pa.fb_count = fb_count; pa.fb_cap = fb_cap;
   pa.fb_total = fb_total; pa.err = err;
 
-  // ---- sample (Sec. III-A) ----
-  DL_TRY(dalloc(ix, &ix->sample, (size_t)n, st));
-  uint32_t *blk = nullptr;
-  DL_TRY(tp.get(&blk, sample_blocks(n) + 4));
-  int64_t m = 0;
-  DL_TRY(sample_ids(n, ix->seed, ix->frac, ix->sample, blk, &m, st));
-  if (m < 2 * (int64_t)N_r) {
-    k_iota<<<(unsigned)std::min<int64_t>(ceil_div(n, 256), 4096), 256, 0, st>>>(ix->sample, n);
-    dl_count_launch();
-    DL_CUDA(cudaGetLastError());
-    m = n;
+  const bool stat = ix->encoding == DETLSH_ENC_STATIC;
+  int e = 0;
+  SortTemp srt;  // the sample-column sort here, the first-layer key sort later
+  if (stat) {
+    const size_t cnt_cap = 256 * sort_tiles(n);
+    DL_TRY(tp.get(&srt.counts, cnt_cap));
+    srt.count_cap = cnt_cap;
+    DL_TRY(tp.get(&srt.keys_alt, (size_t)n));
+    DL_TRY(tp.get(&srt.vals_alt, (size_t)n));
+    DL_TRY(tp.get(&srt.digit_base, (size_t)256));
+    // ---- static scheme: fixed N(0,1) breakpoints, no sample ----
+    DL_TRY(dalloc(ix, &ix->sample, 1, st));
+    ix->m_sample = 0;
+    std::vector<float> Bh((size_t)LK * (N_r + 1));
+    static_breakpoints(LK, N_r, Bh.data());
+    DL_TRY(dalloc(ix, &ix->B, Bh.size(), st));
+    DL_CUDA(cudaMemcpyAsync(ix->B, Bh.data(), sizeof(float) * Bh.size(), cudaMemcpyHostToDevice, st));
+    DL_CUDA(cudaEventRecord(ix->ev[1], st));
+  } else {
+    // ---- sample (Sec. III-A) ----
+    DL_TRY(dalloc(ix, &ix->sample, (size_t)n, st));
+    uint32_t *blk = nullptr;
+    DL_TRY(tp.get(&blk, sample_blocks(n) + 4));
+    int64_t m = 0;
+    DL_TRY(sample_ids(n, ix->seed, ix->frac, ix->sample, blk, &m, st));
+    if (m < 2 * (int64_t)N_r) {
+      k_iota<<<(unsigned)std::min<int64_t>(ceil_div(n, 256), 4096), 256, 0, st>>>(ix->sample, n);
+      dl_count_launch();
+      DL_CUDA(cudaGetLastError());
+      m = n;
+    }
+    ix->m_sample = m;
+
+    // ---- breakpoints: sample projections, sorted per column ----
+    float *Ps = nullptr;
+    DL_TRY(tp.get(&Ps, (size_t)LK * m));
+    ProjArgs ps = pa;
+    ps.P = Ps;
+    ps.ldP = m;
+    DL_TRY(project_rows(ix->X, d, ix->sample, m, d, ix->A, LK, 1, ps, st));
+    e = check_err(err, st);
+    if (e) return e;
+    DL_CUDA(cudaEventRecord(ix->ev[1], st));
+    DL_TRY(float_to_keys(Ps, (int64_t)LK * m, st));
+    const size_t cnt_cap = std::max<size_t>((size_t)LK * 256 * sort_tiles(m), 256 * sort_tiles(n));
+    DL_TRY(tp.get(&srt.counts, cnt_cap));
+    srt.count_cap = cnt_cap;
+    DL_TRY(tp.get(&srt.keys_alt, std::max<size_t>((size_t)LK * m, (size_t)n)));
+    DL_TRY(tp.get(&srt.vals_alt, (size_t)n));
+    DL_TRY(tp.get(&srt.digit_base, (size_t)LK * 256));
+    DL_TRY(segmented_sort(reinterpret_cast<uint32_t *>(Ps), nullptr, LK, m, 32, srt, st));
+    DL_TRY(dalloc(ix, &ix->B, (size_t)LK * (N_r + 1), st));
+    DL_TRY(extract_breakpoints(reinterpret_cast<uint32_t *>(Ps), LK, m, N_r, ix->B, st));
   }
-  ix->m_sample = m;
-
-  // ---- breakpoints: sample projections, sorted per column ----
-  float *Ps = nullptr;
-  DL_TRY(tp.get(&Ps, (size_t)LK * m));
-  ProjArgs ps = pa;
-  ps.P = Ps;
-  ps.ldP = m;
-  DL_TRY(project_rows(ix->X, d, ix->sample, m, d, ix->A, LK, 1, ps, st));
-  int e = check_err(err, st);
-  if (e) return e;
-  DL_CUDA(cudaEventRecord(ix->ev[1], st));
-  DL_TRY(float_to_keys(Ps, (int64_t)LK * m, st));
-  SortTemp srt;
-  const size_t cnt_cap = std::max<size_t>((size_t)LK * 256 * sort_tiles(m), 256 * sort_tiles(n));
-  DL_TRY(tp.get(&srt.counts, cnt_cap));
-  srt.count_cap = cnt_cap;
-  DL_TRY(tp.get(&srt.keys_alt, std::max<size_t>((size_t)LK * m, (size_t)n)));
-  DL_TRY(tp.get(&srt.vals_alt, (size_t)n));
-  DL_TRY(tp.get(&srt.digit_base, (size_t)LK * 256));
-  DL_TRY(segmented_sort(reinterpret_cast<uint32_t *>(Ps), nullptr, LK, m, 32, srt, st));
-  DL_TRY(dalloc(ix, &ix->B, (size_t)LK * (N_r + 1), st));
-  DL_TRY(extract_breakpoints(reinterpret_cast<uint32_t *>(Ps), LK, m, N_r, ix->B, st));
-
   DL_CUDA(cudaEventRecord(ix->ev[2], st));
   // ---- all projections, encoded (Alg. 1), and column min/max ----
   DL_TRY(dalloc(ix, &ix->codes, (size_t)L * n * CODE_STRIDE, st));
@@ -389,7 +443,14 @@ int build_impl(detlsh_index *ix, const float *data, cudaStream_t st, const detls
   // running bounds of the column extremes (same start as the extremes)
   uint32_t *ubound = nullptr;
   DL_TRY(tp.get(&ubound, (size_t)2 * LK));
-  DL_CUDA(cudaMemcpyAsync(ubound, minmax, sizeof(uint32_t) * 2 * LK, cudaMemcpyDeviceToDevice, st));
+  if (stat) {  // fixed infinite ends: no column extreme is tracked
+    std::vector<uint32_t> ub((size_t)2 * LK);
+    for (int t = 0; t < LK; ++t) { ub[2 * t] = host_fkey(-INFINITY); ub[2 * t + 1] = host_fkey(INFINITY); }
+    DL_CUDA(cudaMemcpyAsync(ubound, ub.data(), sizeof(uint32_t) * ub.size(), cudaMemcpyHostToDevice, st));
+    DL_CUDA(cudaStreamSynchronize(st));  // ub is a host temporary
+  } else {
+    DL_CUDA(cudaMemcpyAsync(ubound, minmax, sizeof(uint32_t) * 2 * LK, cudaMemcpyDeviceToDevice, st));
+  }
   const double du = (double)d * 0x1p-24;
   ProjArgs pe = pa;
   pe.codes = ix->codes; pe.n = n; pe.B = ix->B; pe.N_r = N_r; pe.K = K; pe.minmax = minmax;
@@ -404,7 +465,7 @@ int build_impl(detlsh_index *ix, const float *data, cudaStream_t st, const detls
   DL_TRY(project_rows(ix->X, d, nullptr, n, d, ix->A, LK, 2, pe, st));
   e = check_err(err, st);
   if (e) return e;
-  DL_TRY(finish_breakpoint_ends(minmax, LK, N_r, ix->B, st));
+  if (!stat) DL_TRY(finish_breakpoint_ends(minmax, LK, N_r, ix->B, st));
   DL_CUDA(cudaEventRecord(ix->ev[3], st));
   if (p->keep_projections) {
     DL_TRY(dalloc(ix, &ix->P, (size_t)n * LK, st));
@@ -771,6 +832,7 @@ int detlsh_default_build_params(detlsh_build_params *p) {
   p->box_mode = DETLSH_BOX_PREFIX;
   p->keep_bf16 = 1;
   p->keep_projections = 0;
+  p->encoding = DETLSH_ENC_DYNAMIC;
   return DETLSH_OK;
 }
 
@@ -815,7 +877,7 @@ int detlsh_build_ex(const float *data, int64_t n, int32_t d, const detlsh_build_
   if (!ix) return DETLSH_ERR_OOM;
   cudaGetDevice(&ix->device);
   ix->n = n; ix->d = d; ix->L = p->L; ix->K = p->K; ix->LK = p->L * p->K; ix->N_r = p->N_r;
-  ix->M = p->max_size; ix->box_mode = p->box_mode; ix->seed = p->seed; ix->frac = p->sample_frac;
+  ix->M = p->max_size; ix->box_mode = p->box_mode; ix->encoding = p->encoding; ix->seed = p->seed; ix->frac = p->sample_frac;
   while ((1 << ix->bbits) < ix->N_r) ++ix->bbits;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const int s = build_impl(ix, data, st, p);
@@ -965,6 +1027,7 @@ int detlsh_get_info(const detlsh_index *ix, detlsh_info *info) {
   memset(info, 0, sizeof *info);
   info->n = ix->n; info->d = ix->d; info->L = ix->L; info->K = ix->K; info->N_r = ix->N_r;
   info->max_size = ix->M; info->box_mode = ix->box_mode; info->has_bf16 = ix->Xh != nullptr;
+  info->encoding = ix->encoding;
   info->sample_size = ix->m_sample;
   for (int t = 0; t < ix->L; ++t) info->num_leaves[t] = ix->nleaves[t];
   info->max_leaf_size = ix->max_leaf;

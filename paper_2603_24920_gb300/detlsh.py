@@ -18,6 +18,7 @@ STATUS = {0: "OK", -1: "INVALID_ARG", -2: "NONFINITE_INPUT", -3: "OOM", -4: "CUD
 BOX_PREFIX, BOX_TIGHT = 0, 1
 PREC_FP32, PREC_BF16_REFINE = 0, 1
 RMIN_MAGIC, RMIN_FIXED = 0, 1
+ENC_DYNAMIC, ENC_STATIC = 0, 1
 
 
 class DetlshError(RuntimeError):
@@ -29,7 +30,8 @@ class DetlshError(RuntimeError):
 class BuildParams(C.Structure):
     _fields_ = [("L", C.c_int32), ("K", C.c_int32), ("N_r", C.c_int32), ("max_size", C.c_int32),
                 ("seed", C.c_uint64), ("sample_frac", C.c_double), ("box_mode", C.c_int32),
-                ("keep_bf16", C.c_int32), ("keep_projections", C.c_int32)]
+                ("keep_bf16", C.c_int32), ("keep_projections", C.c_int32),
+                ("encoding", C.c_int32)]
 
 
 class QueryParams(C.Structure):
@@ -43,7 +45,7 @@ class Info(C.Structure):
                 ("has_bf16", C.c_int32), ("sample_size", C.c_int64),
                 ("num_leaves", C.c_int64 * 16), ("max_leaf_size", C.c_int64),
                 ("eps2", C.c_double), ("device_bytes", C.c_int64),
-                ("projection_fallbacks", C.c_int64)]
+                ("projection_fallbacks", C.c_int64), ("encoding", C.c_int32)]
 
 
 class Timings(C.Structure):
