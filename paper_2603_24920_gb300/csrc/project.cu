@@ -152,6 +152,18 @@ __device__ __forceinline__ uint32_t region_of(const float *__restrict__ Bint, in
   return (uint32_t)lo;
 }
 
+// The same count from a column's interior breakpoints staged in shared
+// memory, branch-free: power-of-two steps over the N_r - 1 sorted values.
+__device__ __forceinline__ uint32_t region_smem(const float *Bs, int N_r, float y) {
+  uint32_t pos = 0;
+#pragma unroll
+  for (int s = 7; s >= 0; --s) {
+    const uint32_t step = 1u << s;
+    if ((int)step < N_r && Bs[pos + step - 1] < y) pos += step;
+  }
+  return pos;
+}
+
 template <int MODE>
 __global__ void __launch_bounds__(PJ_THREADS)
 k_project(const float *__restrict__ X, int64_t ldx, const uint32_t *__restrict__ rows,
@@ -239,6 +251,7 @@ k_encode(const float *__restrict__ X, int64_t ldx, int64_t nrows, int d,
   __shared__ uint32_t cmin[PJ_COLS], cmax[PJ_COLS];
   extern __shared__ float dyn[];
   uint8_t *cst = reinterpret_cast<uint8_t *>(dyn);  // [64 rows][64 cols] codes
+  float *Bs = dyn + PJ_ROWS * PJ_COLS / 4;          // [64 cols][BSTRIDE] interior breakpoints
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
   const int col0 = blockIdx.y * W;
@@ -272,6 +285,10 @@ k_encode(const float *__restrict__ X, int64_t ldx, int64_t nrows, int d,
       As[idx / PJ_KC][idx % PJ_KC] = pa[u];
     }
   };
+  for (int idx = tid; idx < (LKt - col0) * BSTRIDE; idx += PJ_THREADS) {
+    const int c = idx / BSTRIDE, z = idx % BSTRIDE;
+    Bs[idx] = z < nint ? o.B[(int64_t)(col0 + c) * (o.N_r + 1) + 1 + z] : 0.0f;
+  }
   int64_t tile = blockIdx.x;
   if (tile < ntiles) fetch(tile * PJ_ROWS, 0);
   for (; tile < ntiles; tile += gridDim.x) {
@@ -329,8 +346,8 @@ k_encode(const float *__restrict__ X, int64_t ldx, int64_t nrows, int d,
           const float dlt = __fmaf_ru(eu, err[i][j], tiny);
           const float dl2 = __fadd_ru(dlt, __fmul_ru(__fadd_ru(fabsf(y), dlt), 1.2e-7f));
           const float lo = __fsub_rd(y, dl2), hi = __fadd_ru(y, dl2);
-          const float *Bc = o.B + (int64_t)oc * (o.N_r + 1) + 1;
-          const uint32_t reg = region_of(Bc, nint, y);
+          const float *Bc = Bs + c * BSTRIDE;
+          const uint32_t reg = region_smem(Bc, o.N_r, y);
           const bool finite = isfinite(y) && isfinite(dl2);
           const bool sure = finite && (reg == 0 || Bc[reg - 1] < lo) &&
                             (reg == (uint32_t)nint || Bc[reg] >= hi);
@@ -473,8 +490,8 @@ static int project_impl(const float *X, int64_t ldx, const uint32_t *rows, int64
   const int W = (MODE == 2) ? (PJ_COLS / o.K) * o.K : PJ_COLS;
   dim3 grid((unsigned)ceil_div(nrows, PJ_ROWS), (unsigned)ceil_div(LK, W));
   size_t dyn = 0;
-  if (MODE == 2) {
-    dyn = PJ_ROWS * PJ_COLS;
+  if (MODE == 2) {  // codes of a tile, then the tile's breakpoints
+    dyn = PJ_ROWS * PJ_COLS + sizeof(float) * PJ_COLS * BSTRIDE;
   }
   if constexpr (MODE == 2) {
     DL_CUDA(cudaFuncSetAttribute(k_encode, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
