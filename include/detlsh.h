@@ -245,6 +245,36 @@ int detlsh_query_candidates(const detlsh_index *ix, const float *queries, int64_
                             const detlsh_query_params *qp, int64_t cap, int64_t *S,
                             int64_t *S_size, int32_t *jstar, int32_t *istar);
 
+/*
+ * Queries that can be captured in a CUDA graph (batched serving: the paper has
+ * no counterpart; same results as detlsh_query_ex).
+ *
+ * detlsh_query_reserve fixes the query parameters (beta, c, precision,
+ * rerank_mult, r_min policy) and the largest batch (m_max queries, k <=
+ * k_max) and allocates every buffer the queries need, in buffers of their
+ * own.  It is synchronous; call it before any capture, and again whenever the
+ * parameters or sizes change (which invalidates graphs captured earlier).
+ * Errors: INVALID_ARG (as detlsh_query_ex, or m_max < 1), OOM, CUDA.
+ *
+ * detlsh_query_async enqueues one batch on `stream` and returns without
+ * waiting: it allocates nothing, copies nothing to or from the host and never
+ * synchronises, so the call can be captured and the graph replayed with new
+ * query contents in the same buffers.  queries (m x d FP32), k_per_query
+ * (nullable, m entries), ids (m x k_max) and dists (m x k_max) must be device
+ * memory, m <= m_max, k_max <= the reserved k_max.  Errors found on the host
+ * (INVALID_ARG: arguments as above or no reservation; CUDA) are returned;
+ * errors found on the device (NONFINITE_INPUT for a query holding NaN/Inf,
+ * INVALID_ARG for a per-query k outside [1, k_max], CAPACITY) are written to
+ * *status (one device int32, 0 = OK) when the batch completes; the outputs of
+ * a batch with a non-zero status are unspecified.  Calls on one index must
+ * not overlap on the GPU (one stream, or ordered by the caller).
+ */
+int detlsh_query_reserve(detlsh_index *ix, int64_t m_max, int32_t k_max,
+                         const detlsh_query_params *qp);
+int detlsh_query_async(const detlsh_index *ix, const float *queries, int64_t m,
+                       const int32_t *k_per_query, int32_t k_max, void *stream, int64_t *ids,
+                       float *dists, int32_t *status);
+
 /* (r,c)-ANN query, Alg. 4 of the paper (Sec. V-B), over the range query of
  * Alg. 3 as printed (Sec. IV-C): for each tree in order, nodes whose lower
  * bound exceeds r' = eps*r are pruned, a leaf whose upper bound is within r'

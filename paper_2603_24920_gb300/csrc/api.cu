@@ -46,7 +46,6 @@ struct detlsh_index {
   uint8_t *leaf_lo = nullptr, *leaf_hi = nullptr, *leaf_nb = nullptr;
   uint8_t *blk_lo = nullptr, *blk_hi = nullptr;  // hulls of LEAF_BLOCK-leaf runs
   int64_t blk_off[17] = {0};
-  uint32_t epoch_next = 1;  // query scratch tags leaf levels with per-query epochs
   cudaEvent_t ev[8] = {nullptr};
   detlsh_timings timings{};
   std::vector<void *> owned;
@@ -57,6 +56,18 @@ struct detlsh_index {
     size_t bytes = 0;
   };
   QBuf qQ, qQh, qQp, qk, qids, qdists, qT, qscratch, qstat, qS, qfb, qrc, qrcs;
+  // detlsh_query_reserve / detlsh_query_async: buffers of their own, so that a
+  // captured graph's pointers stay valid whatever other calls do
+  struct AsyncPlan {
+    bool ready = false;
+    detlsh_query_params qp{};
+    int64_t m_max = 0;
+    int32_t k_max = 0;
+    int slots = 0;
+    int64_t cap = 0, tau_base = 0;
+    int64_t off[13] = {0};
+  } plan;
+  QBuf aQp, aQh, afb, aT, astat, ascratch;
 };
 
 namespace {
@@ -97,14 +108,15 @@ int pool_alloc(void **p, size_t bytes, cudaStream_t st) {
   return DETLSH_OK;
 }
 
-// Query scratch outlives its index: a freed index hands its slots (and the
-// epoch counter their level tags were written under) to the next index on
-// the same device, so rebuilding an index does not clear the slots again.
-// Epochs only grow, so tags left by earlier queries never match a later one.
+// Query scratch outlives its index: a freed index hands its slots to the
+// next index on the same device, so rebuilding an index does not clear the
+// slots again.  The scratch starts with a device word that hands out the
+// per-query epochs its level tags carry; epochs only grow (56 bits), so tags
+// left by earlier queries never match a later one.
+constexpr size_t kScratchHeader = 256;
 struct ScratchCache {
   void *p = nullptr;
   size_t bytes = 0;
-  uint32_t epoch_next = 1;
 };
 std::mutex g_scratch_mu;
 ScratchCache g_scratch[kPoolDevices];
@@ -577,7 +589,8 @@ void free_index(detlsh_index *ix) {
   for (auto &e : ix->ev)
     if (e) cudaEventDestroy(e);
   for (auto *b : {&ix->qQ, &ix->qQh, &ix->qQp, &ix->qk, &ix->qids, &ix->qdists, &ix->qT,
-                  &ix->qstat, &ix->qS, &ix->qfb, &ix->qrc, &ix->qrcs})
+                  &ix->qstat, &ix->qS, &ix->qfb, &ix->qrc, &ix->qrcs, &ix->aQp, &ix->aQh,
+                  &ix->afb, &ix->aT, &ix->astat, &ix->ascratch})
     if (b->p) cudaFreeAsync(b->p, 0);
   if (ix->qscratch.p) {  // keep the larger of this and the cached scratch
     void *drop = ix->qscratch.p;
@@ -588,7 +601,6 @@ void free_index(detlsh_index *ix) {
         drop = c.p;
         c.p = ix->qscratch.p;
         c.bytes = ix->qscratch.bytes;
-        c.epoch_next = ix->epoch_next;
       }
     }
     if (drop) cudaFreeAsync(drop, 0);
@@ -730,27 +742,22 @@ int query_impl(detlsh_index *ix, const float *queries, int64_t m, const int32_t 
   size_t freeb = 0, totb = 0;
   DL_CUDA(cudaMemGetInfo(&freeb, &totb));
   while (slots > 1 && (size_t)slots * qa.slot_bytes > freeb / 4 + ix->qscratch.bytes) slots /= 2;
+  const size_t need_bytes = kScratchHeader + (size_t)slots * qa.slot_bytes;
   if (!ix->qscratch.p && ix->device >= 0 && ix->device < kPoolDevices) {
     std::lock_guard<std::mutex> g(g_scratch_mu);
     ScratchCache &c = g_scratch[ix->device];
-    if (c.p && c.bytes >= (size_t)slots * qa.slot_bytes) {  // adopt a freed index's slots
+    if (c.p && c.bytes >= need_bytes) {  // adopt a freed index's slots
       ix->qscratch.p = c.p;
       ix->qscratch.bytes = c.bytes;
-      ix->epoch_next = c.epoch_next;
       c = ScratchCache{};
     }
   }
   bool fresh = false;
-  DL_TRY(grow(ix->qscratch, (size_t)slots * qa.slot_bytes, st, &fresh));
-  // Leaf levels in the scratch carry a per-query epoch (base + query index);
-  // start from zeroed scratch whenever it is new or the epochs would wrap.
-  if (fresh || (uint64_t)ix->epoch_next + (uint64_t)m + 1 >= (1ull << 24)) {
-    DL_CUDA(cudaMemsetAsync(ix->qscratch.p, 0, ix->qscratch.bytes, st));
-    ix->epoch_next = 1;
-  }
-  qa.epoch_base = ix->epoch_next;
-  ix->epoch_next += (uint32_t)m;
-  qa.scratch = static_cast<uint8_t *>(ix->qscratch.p);
+  DL_TRY(grow(ix->qscratch, need_bytes, st, &fresh));
+  // new scratch: zero tags and epoch counter (epochs then start at 1)
+  if (fresh) DL_CUDA(cudaMemsetAsync(ix->qscratch.p, 0, ix->qscratch.bytes, st));
+  qa.epoch_counter = static_cast<unsigned long long *>(ix->qscratch.p);
+  qa.scratch = static_cast<uint8_t *>(ix->qscratch.p) + kScratchHeader;
   qa.nslots = slots;
   qa.work_counter = counter;
   qa.err = err;
@@ -925,6 +932,130 @@ int detlsh_query(const detlsh_index *ix, const float *queries, int64_t m, int32_
   detlsh_default_query_params(&qp);
   qp.c = c;
   return detlsh_query_ex(ix, queries, m, nullptr, k, &qp, nullptr, ids, dists);
+}
+
+namespace {
+// Radius grid (and for a fixed r_min the condition-2 radii) for qp, 512 floats.
+void query_tables(const detlsh_index *ix, const detlsh_query_params *qp, float Th[512]) {
+  if (qp->rmin_policy == DETLSH_RMIN_FIXED) {
+    const double r0 = qp->r_min, c = qp->c;
+    for (int i = 0; i < NLEV - 1; ++i) {
+      Th[i] = (float)(ix->eps2 * r0 * r0 * std::pow(c, 2.0 * (double)i));
+      const double cr = c * (r0 * std::pow(c, (double)i));
+      Th[256 + i] = (float)(cr * cr);
+    }
+    Th[NLEV - 1] = Th[255] = INFINITY;
+    Th[256 + NLEV - 1] = Th[511] = INFINITY;
+  } else {
+    level_table(ix->eps2, qp->c, Th);
+    Th[255] = INFINITY;
+    for (int i = 256; i < 512; ++i) Th[i] = INFINITY;
+  }
+}
+}  // namespace
+
+int detlsh_query_reserve(detlsh_index *ix, int64_t m_max, int32_t k_max,
+                         const detlsh_query_params *qp) {
+  detlsh_query_params def;
+  detlsh_default_query_params(&def);
+  if (!qp) qp = &def;
+  if (m_max < 1) return DETLSH_ERR_INVALID_ARG;
+  const int v = validate_query(ix, m_max, k_max, qp);
+  if (v) return v;
+  std::lock_guard<std::mutex> g(ix->qmu);
+  cudaStream_t st = nullptr;
+  auto &P = ix->plan;
+  P.ready = false;
+  const int d = ix->d, LK = ix->LK;
+  DL_TRY(grow(ix->aQp, sizeof(float) * (size_t)m_max * LK, st));
+  if (qp->precision == DETLSH_PREC_BF16_REFINE)
+    DL_TRY(grow(ix->aQh, sizeof(__nv_bfloat16) * (size_t)m_max * d, st));
+  const uint32_t fb_cap = (uint32_t)std::max<int64_t>(1024, m_max * LK / 64);
+  DL_TRY(grow(ix->afb, sizeof(uint2) * fb_cap, st));
+  DL_TRY(grow(ix->aT, sizeof(float) * 512, st));
+  DL_TRY(grow(ix->astat, 256, st));
+  float Th[512];
+  query_tables(ix, qp, Th);
+  DL_CUDA(cudaMemcpyAsync(ix->aT.p, Th, sizeof Th, cudaMemcpyHostToDevice, st));
+  const double tb = std::ceil(qp->beta * (double)ix->n);
+  P.tau_base = tb > (double)ix->n ? ix->n + 1 : (int64_t)tb;
+  P.cap = (P.tau_base + k_max > ix->n) ? ix->n
+                                        : std::min<int64_t>(ix->n, P.tau_base + k_max + ix->max_leaf);
+  QueryIndexView vw = view_of(ix);
+  query_slot_offsets(vw, P.cap, P.off);
+  int slots = (int)std::min<int64_t>(query_slots(vw), m_max);
+  size_t freeb = 0, totb = 0;
+  DL_CUDA(cudaMemGetInfo(&freeb, &totb));
+  while (slots > 1 && (size_t)slots * P.off[12] > freeb / 4 + ix->ascratch.bytes) slots /= 2;
+  bool fresh = false;
+  DL_TRY(grow(ix->ascratch, kScratchHeader + (size_t)slots * P.off[12], st, &fresh));
+  if (fresh) DL_CUDA(cudaMemsetAsync(ix->ascratch.p, 0, ix->ascratch.bytes, st));
+  DL_CUDA(cudaStreamSynchronize(st));
+  P.qp = *qp;
+  P.m_max = m_max;
+  P.k_max = k_max;
+  P.slots = slots;
+  P.ready = true;
+  return DETLSH_OK;
+}
+
+int detlsh_query_async(const detlsh_index *cix, const float *queries, int64_t m,
+                       const int32_t *k_per_query, int32_t k_max, void *stream, int64_t *ids,
+                       float *dists, int32_t *status) {
+  if (!cix || !queries || !ids || !dists || !status) return DETLSH_ERR_INVALID_ARG;
+  detlsh_index *ix = const_cast<detlsh_index *>(cix);
+  std::lock_guard<std::mutex> g(ix->qmu);
+  const auto &P = ix->plan;
+  if (!P.ready || m < 0 || m > P.m_max || k_max < 1 || k_max > P.k_max)
+    return DETLSH_ERR_INVALID_ARG;
+  if (!is_device_ptr(queries) || !is_device_ptr(ids) || !is_device_ptr(dists) ||
+      !is_device_ptr(status) || (k_per_query && !is_device_ptr(k_per_query)))
+    return DETLSH_ERR_INVALID_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int *err = static_cast<int *>(ix->astat.p);
+  DL_CUDA(cudaMemsetAsync(ix->astat.p, 0, 256, st));
+  if (m > 0) {
+    const int d = ix->d, LK = ix->LK;
+    float *Qp = static_cast<float *>(ix->aQp.p);
+    ProjArgs pa;
+    pa.P = Qp; pa.ldP = LK;
+    pa.fb_count = reinterpret_cast<uint32_t *>(static_cast<char *>(ix->astat.p) + 16);
+    pa.fb_cap = (uint32_t)(ix->afb.bytes / sizeof(uint2));
+    pa.fb_list = static_cast<uint2 *>(ix->afb.p);
+    pa.err = err;
+    DL_TRY(project_rows(queries, d, nullptr, m, d, ix->A, LK, 0, pa, st));
+    const __nv_bfloat16 *Qh = nullptr;
+    if (P.qp.precision == DETLSH_PREC_BF16_REFINE) {
+      DL_TRY(dl::f32_to_bf16(queries, static_cast<__nv_bfloat16 *>(ix->aQh.p), m * (int64_t)d, st));
+      Qh = static_cast<const __nv_bfloat16 *>(ix->aQh.p);
+    }
+    QueryIndexView v = view_of(ix);
+    QueryArgs qa{};
+    qa.Q = queries; qa.Qh = Qh; qa.Qp = Qp; qa.m = m; qa.kq = k_per_query; qa.k_max = k_max;
+    qa.tau_base = P.tau_base;
+    qa.T = static_cast<const float *>(ix->aT.p);
+    qa.Tc = qa.T + 256;
+    qa.policy = P.qp.rmin_policy;
+    const bool fixed = P.qp.rmin_policy == DETLSH_RMIN_FIXED;
+    qa.lg_eps2 = fixed ? (float)(std::log2(ix->eps2 * P.qp.r_min * P.qp.r_min) +
+                                 254.0 * std::log2(P.qp.c))
+                       : (float)std::log2(ix->eps2);
+    qa.inv_2lg_c = (float)(1.0 / (2.0 * std::log2(P.qp.c)));
+    qa.precision = P.qp.precision; qa.rerank_mult = P.qp.rerank_mult;
+    qa.ids = ids; qa.dists = dists;
+    qa.cand_cap = P.cap;
+    for (int i = 0; i < 13; ++i) qa.off[i] = P.off[i];
+    qa.slot_bytes = P.off[12];
+    qa.epoch_counter = static_cast<unsigned long long *>(ix->ascratch.p);
+    qa.scratch = static_cast<uint8_t *>(ix->ascratch.p) + kScratchHeader;
+    qa.nslots = P.slots;
+    qa.work_counter = reinterpret_cast<uint32_t *>(static_cast<char *>(ix->astat.p) + 32);
+    qa.err = err;
+    qa.stats = reinterpret_cast<unsigned long long *>(static_cast<char *>(ix->astat.p) + 64);
+    DL_TRY(run_queries(v, qa, st));
+  }
+  DL_CUDA(cudaMemcpyAsync(status, err, sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
+  return DETLSH_OK;
 }
 
 int detlsh_rc_ann(const detlsh_index *cix, const float *queries, int64_t m, double r,

@@ -131,7 +131,8 @@ struct QueryArgs {
   int64_t slot_bytes;
   int64_t off[13];
   int64_t cand_cap;
-  uint32_t epoch_base;       // leaf levels are tagged (epoch << 8 | level), epoch = base + qi
+  unsigned long long *epoch_counter;  // leaf levels are tagged (epoch << 8 | level); each
+                                      // query takes the next epoch from this device word
   int nslots;
   uint32_t *work_counter;
   int *err;

@@ -140,7 +140,7 @@ extern "C" int detlsh_query_noalloc(const detlsh_index *ix, const float *queries
   qa.work_counter = counter;
   qa.err = err;
   qa.stats = stats;
-  qa.epoch_base = 1;  // level tags were cleared above
+  qa.epoch_counter = reinterpret_cast<unsigned long long *>(base + o_status + 128);  // cleared above
   DL_TRY(run_queries(v, qa, st));
   int h = 0;
   DL_CUDA(cudaMemcpyAsync(&h, err, sizeof h, cudaMemcpyDeviceToHost, st));

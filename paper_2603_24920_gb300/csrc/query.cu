@@ -39,7 +39,7 @@ constexpr int RR_MAX = 4096;  // re-rank pool of the BF16 path
 constexpr int FLC = 512;      // listed leaves per chunk of a flattened visit
 
 struct Slot {
-  uint32_t *lev;    // [total_leaves] (epoch << 8) | level of expanded leaves
+  unsigned long long *lev;  // [total_leaves] (epoch << 8) | level of expanded leaves
   uint8_t *blev;    // [total_blocks] block levels (255 = beyond the bound)
   uint32_t *border; // [total_blocks] block ids ordered by level
   uint32_t *lleaf;  // [total_leaves] per-tree lists of expanded leaves (at leaf_off[t])
@@ -57,7 +57,7 @@ __host__ __device__ inline int64_t align_up(int64_t v, int64_t a) { return (v + 
 
 static void slot_layout(const QueryIndexView &ix, int64_t cap, int64_t off[13]) {
   const int64_t tl = ix.leaf_off[ix.L], tb = ix.blk_off[ix.L];
-  const int64_t sz[12] = {4 * tl, tb, 4 * tb, 4 * tl, 4 * tl, tl, 4 * ix.max_leaves,
+  const int64_t sz[12] = {8 * tl, tb, 4 * tb, 4 * tl, 4 * tl, tl, 4 * ix.max_leaves,
                           4 * cap, 4 * cap, 4 * RR_MAX, 4 * RR_MAX, cap};
   int64_t o = 0;
   for (int i = 0; i < 12; ++i) { off[i] = o; o = align_up(o + sz[i], 256); }
@@ -86,7 +86,8 @@ struct QShared {
   // scalars
   int64_t qi;
   int jhi, jstar, istar, jcur, stop;
-  uint32_t need, ncand, sel_v, sel_below, sel_at, nres, epoch;
+  uint32_t need, ncand, sel_v, sel_below, sel_at, nres;
+  unsigned long long epoch;  // this query's tag for the leaf levels in the slot
   uint64_t cum;
   unsigned long long n_blocks, n_leaves, n_visit;  // work counters of this CTA
   int use_hash;
@@ -246,8 +247,8 @@ __device__ __forceinline__ uint32_t leaf_level_h(const QueryIndexView &ix, const
       h = (h + 1u) & mask;
     }
   }
-  const uint32_t v = s.lev[ix.leaf_off[u] + l];
-  return (v >> 8) == sm.epoch ? (v & 255u) : 255u;
+  const unsigned long long v = s.lev[ix.leaf_off[u] + l];
+  return (v >> 8) == sm.epoch ? (uint32_t)(v & 255u) : 255u;
 }
 
 // Leaf of point p in tree u.  With LC = 4 (four trees) the point's four
@@ -294,7 +295,7 @@ __device__ __forceinline__ void expand_levels(QCtx &c) {
   const int K = ix.K, NR1 = ix.N_r + 1;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const float *qp = c.qa.Qp + c.qi * ix.LK;
-  const uint32_t ep = sm.epoch;
+  const unsigned long long ep = sm.epoch;
   if (threadIdx.x == 0) sm.jhi = NLEV - 1;
   __syncthreads();
   for (int t = 0; t < ix.L; ++t) {
@@ -1133,7 +1134,7 @@ __global__ void __launch_bounds__(QT, 5) k_query(QueryIndexView ix, QueryArgs qa
 
   uint8_t *base = qa.scratch + (int64_t)blockIdx.x * qa.slot_bytes;
   Slot s;
-  s.lev = reinterpret_cast<uint32_t *>(base + qa.off[0]);
+  s.lev = reinterpret_cast<unsigned long long *>(base + qa.off[0]);
   s.blev = base + qa.off[1];
   s.border = reinterpret_cast<uint32_t *>(base + qa.off[2]);
   s.lleaf = reinterpret_cast<uint32_t *>(base + qa.off[3]);
@@ -1154,7 +1155,11 @@ __global__ void __launch_bounds__(QT, 5) k_query(QueryIndexView ix, QueryArgs qa
     __syncthreads();
     const int64_t qi = sm.qi;
     if (qi >= qa.m) break;
-    const int k = qa.kq ? qa.kq[qi] : qa.k_max;
+    int k = qa.kq ? qa.kq[qi] : qa.k_max;
+    if (k < 1 || k > qa.k_max) {  // per-query k outside [1, k_max]: report, clamp
+      if (threadIdx.x == 0) atomicExch(qa.err, (int)DETLSH_ERR_INVALID_ARG);
+      k = k < 1 ? 1 : qa.k_max;
+    }
     const int64_t tau = qa.tau_base + k;
     QCtx c{ix, qa, sm, lut, hist, D, s, qi, tau};
     bool fixed_done = false, s_written = false;  // fixed r_min: top-k (and S) done
@@ -1170,7 +1175,9 @@ __global__ void __launch_bounds__(QT, 5) k_query(QueryIndexView ix, QueryArgs qa
     } else {
       for (int i = threadIdx.x; i < 256 * ix.L; i += QT) { hist[i] = 0; D[i] = 0; }
       sm.H[threadIdx.x] = 0;
-      if (threadIdx.x == 0) sm.epoch = qa.epoch_base + (uint32_t)qi;
+      // a fresh tag from the slot area's counter: no tag left by an earlier
+      // query (or an earlier launch) can match it
+      if (threadIdx.x == 0) sm.epoch = atomicAdd(qa.epoch_counter, 1ull) + 1ull;
       __syncthreads();
       expand_levels(c);
       build_level_hash(c);

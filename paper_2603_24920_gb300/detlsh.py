@@ -88,6 +88,8 @@ SIGNATURES = [
     ("detlsh_project", C.c_int, [_P, _P, _I64, _P, _P]),
     ("detlsh_query_candidates", C.c_int, [_P, _P, _I64, _I32, C.POINTER(QueryParams), _I64,
                                           _P, _P, _P, _P]),
+    ("detlsh_query_reserve", C.c_int, [_P, _I64, _I32, C.POINTER(QueryParams)]),
+    ("detlsh_query_async", C.c_int, [_P, _P, _I64, _P, _I32, _P, _P, _P, _P]),
     ("detlsh_rc_ann", C.c_int, [_P, _P, _I64, _F64, _F64, _F64, _P, _P, _P, _P, _I64, _P, _P]),
 ]
 
@@ -319,6 +321,24 @@ def detlsh_query_candidates(h, queries, k, beta=0.1, c=1.5, cap=None, r_min=None
                                          _ptr(ssz), _ptr(js), _ptr(ist)),
            "detlsh_query_candidates")
     return [S[r, :ssz[r]].copy() for r in range(m)], js, ist
+
+
+def detlsh_query_reserve(h, m_max, k_max, beta=0.1, c=1.5, precision=PREC_FP32, rerank_mult=4,
+                         r_min=None):
+    """Fix the parameters and sizes of detlsh_query_async and allocate its buffers."""
+    qp = detlsh_default_query_params()
+    qp.beta, qp.c, qp.precision, qp.rerank_mult = beta, c, precision, rerank_mult
+    if r_min is not None:
+        qp.rmin_policy, qp.r_min = RMIN_FIXED, r_min
+    _check(lib().detlsh_query_reserve(h, m_max, k_max, C.byref(qp)), "detlsh_query_reserve")
+
+
+def detlsh_query_async(h, queries, k_max, ids, dists, status, k_per_query=None, stream=None):
+    """Enqueue one batch (device tensors only); capturable in a CUDA graph.
+    Device-side errors land in status (int32 tensor of one element)."""
+    _check(lib().detlsh_query_async(h, _ptr(queries), queries.shape[0], _ptr(k_per_query), k_max,
+                                    _stream_ptr(stream), _ptr(ids), _ptr(dists), _ptr(status)),
+           "detlsh_query_async")
 
 
 def detlsh_rc_ann(h, queries, r, beta=0.1, c=1.5, S_cap=0, stream=None):
