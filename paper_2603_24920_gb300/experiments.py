@@ -6,6 +6,8 @@ the recall knobs, the paper's query variants and the encoding ablation.
   python -m paper_2603_24920_gb300.experiments lk         # L x K on c2
   python -m paper_2603_24920_gb300.experiments variants   # r_min policy, (r,c)-ANN,
                                                           # static vs dynamic encoding
+  python -m paper_2603_24920_gb300.experiments stream     # c5: uneven batches through
+                                                          # captured CUDA graphs
 
 Every number is device time from CUDA events (the library's own timings) on
 device-resident inputs, after one warm-up call.  Recall@10 (or recall@k for
@@ -222,12 +224,107 @@ def cmd_variants(a):
         torch.cuda.empty_cache()
 
 
+def cmd_stream(a):
+    """c5's serving pattern: a stream of 100,000 queries in uneven batches
+    (sizes 1..4096), k in {1, 10, 100}, answered by detlsh_query_async replayed
+    from CUDA graphs (one per power-of-two batch bucket, captured on first use;
+    a batch is padded to its bucket with copies of its last query).  Each batch
+    is copied in from pinned host memory and its results copied back."""
+    torch = _torch()
+    import workloads
+    from paper_2603_24920_gb300 import detlsh as D
+    cfg = workloads.CONFIGS["c5"]
+    n = a.n or cfg["n"]
+    t0 = time.time()
+    X = workloads.generate(cfg["kind"], n, cfg["d"], cfg["seed"], 0)
+    Q = workloads.generate(cfg["kind"], cfg["m"], cfg["d"], cfg["seed"], 1)
+    kq = np.asarray(workloads._rng(cfg["seed"], 4).choice(np.asarray(cfg["k"], np.int32), cfg["m"]),
+                    np.int32)
+    sizes = workloads.batch_sizes(cfg["m"])
+    gen_s = time.time() - t0
+    Xd = torch.from_numpy(X).cuda()
+    del X
+    h = D.detlsh_build(Xd, L=4, K=16, N_r=256, seed=0, max_size=64)
+    D.detlsh_free(h)
+    h = D.detlsh_build(Xd, L=4, K=16, N_r=256, seed=0, max_size=64)
+    tb = D.detlsh_get_timings(h).build_ms
+    kmax = int(kq.max())
+    D.detlsh_query_reserve(h, 4096, kmax, beta=a.beta, precision=D.PREC_BF16_REFINE)
+    st = torch.cuda.Stream()
+    Qh = torch.from_numpy(Q).pin_memory()
+    Kh = torch.from_numpy(kq).pin_memory()
+    ids_h = torch.empty((cfg["m"], kmax), dtype=torch.int64).pin_memory()
+    d_h = torch.empty((cfg["m"], kmax), dtype=torch.float32).pin_memory()
+    graphs = {}
+
+    def bucket(s):
+        b = 1
+        while b < s:
+            b *= 2
+        return b
+
+    def get_graph(B):
+        if B not in graphs:
+            qb = torch.zeros((B, cfg["d"]), dtype=torch.float32, device="cuda")
+            kb = torch.ones(B, dtype=torch.int32, device="cuda")
+            ib = torch.empty((B, kmax), dtype=torch.int64, device="cuda")
+            db = torch.empty((B, kmax), dtype=torch.float32, device="cuda")
+            sb = torch.zeros(1, dtype=torch.int32, device="cuda")
+            with torch.cuda.stream(st):
+                D.detlsh_query_async(h, qb, kmax, ib, db, sb, k_per_query=kb, stream=st)
+            st.synchronize()
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, stream=st):
+                D.detlsh_query_async(h, qb, kmax, ib, db, sb, k_per_query=kb, stream=st)
+            graphs[B] = (g, qb, kb, ib, db, sb)
+        return graphs[B]
+
+    def run_stream():
+        pos = 0
+        with torch.cuda.stream(st):
+            for s in sizes:
+                g, qb, kb, ib, db, sb = get_graph(bucket(s))
+                B = qb.shape[0]
+                qb[:s].copy_(Qh[pos:pos + s], non_blocking=True)
+                kb[:s].copy_(Kh[pos:pos + s], non_blocking=True)
+                if B > s:
+                    qb[s:].copy_(qb[s - 1:s].expand(B - s, -1))
+                    kb[s:].fill_(1)
+                g.replay()
+                ids_h[pos:pos + s].copy_(ib[:s], non_blocking=True)
+                d_h[pos:pos + s].copy_(db[:s], non_blocking=True)
+                pos += s
+        st.synchronize()
+
+    run_stream()  # captures the graphs, warms up
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    w0 = time.time()
+    e0.record(st)
+    run_stream()
+    e1.record(st)
+    st.synchronize()
+    wall = time.time() - w0
+    ms = e0.elapsed_time(e1)
+    gt = exact_knn(Xd, Q, 10, nq=200)
+    rec = recall(ids_h.numpy()[:200], gt, kq[:200])
+    print("c5 stream: n = %d x %d (data generated on the host in %.0f s), build %.1f ms "
+          "(%.0f M points/s)" % (n, cfg["d"], gen_s, tb, n / tb / 1e3))
+    row("queries", "batches", "graphs", "beta", "stream ms (device)", "queries/s",
+        "wall s", "recall@min(k,10)")
+    row(cfg["m"], len(sizes), len(graphs), a.beta, "%.1f" % ms, "%.0f" % (cfg["m"] / ms * 1e3),
+        "%.2f" % wall, "%.3f" % rec)
+    D.detlsh_free(h)
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("what", choices=["configs", "sweep", "lk", "variants"])
+    ap.add_argument("what", choices=["configs", "sweep", "lk", "variants", "stream"])
     ap.add_argument("--c5-n", type=int, default=0, help="also run the first N points of c5")
+    ap.add_argument("--n", type=int, default=0, help="stream: points of c5 (0 = all 1e8)")
+    ap.add_argument("--beta", type=float, default=5e-5, help="stream: beta")
     a = ap.parse_args()
-    {"configs": cmd_configs, "sweep": cmd_sweep, "lk": cmd_lk, "variants": cmd_variants}[a.what](a)
+    {"configs": cmd_configs, "sweep": cmd_sweep, "lk": cmd_lk, "variants": cmd_variants,
+     "stream": cmd_stream}[a.what](a)
 
 
 if __name__ == "__main__":
