@@ -1020,6 +1020,80 @@ int orc_index_query_fixed(const orc_index *ix, const float *q, int k, double bet
     return 0;
 }
 
+static int orc_cmp_float_asc(const void *a, const void *b) {
+    float x = *(const float *)a, y = *(const float *)b;
+    return (x > y) - (x < y);
+}
+
+/* Alg. 5 at the smallest continuous r_min: every point's smallest lower bound
+ * over the trees, m(o) = min_t LB^2_t(leaf_t(o)); the threshold v* is the
+ * (beta*n + k)-th smallest m(o), the least squared radius (eps r)^2 at which
+ * the union of the L range queries holds beta*n + k points.  Then the loop of
+ * Alg. 5 at that radius: trees in order, leaves with LB^2 <= v* in ascending
+ * (LB^2, leaf id) order, the check after each leaf.  eps and c cancel: only
+ * the order of the lower bounds matters.  *vstar = v* (+inf when beta*n+k > n,
+ * S = every point). */
+int orc_index_query_magic_min(const orc_index *ix, const float *q, int k, double beta,
+                              int64_t *ids, double *dists, int64_t *S_out, int64_t *S_size,
+                              float *vstar, int *istar) {
+    int64_t n = ix->n;
+    if (k < 1 || k > n) return -1;
+    int64_t tau = (int64_t)ceil(beta * (double)n) + k;
+    orc_cand *cand = (orc_cand *)malloc(sizeof(orc_cand) * (size_t)n);
+    int64_t ns = 0;
+    int is = -1;
+    float vs = INFINITY;
+    if (tau > n) {
+        for (int64_t p = 0; p < n; p++) { cand[ns].id = p; if (S_out) S_out[ns] = p; ns++; }
+    } else {
+        float qproj[256];
+        orc_query_proj(ix, q, qproj);
+        float *mo = (float *)malloc(sizeof(float) * (size_t)n);
+        for (int64_t p = 0; p < n; p++) mo[p] = INFINITY;
+        for (int t = 0; t < ix->L; t++) {
+            const otree *tr = &ix->trees[t];
+            for (int64_t l = 0; l < tr->nleaves; l++) {
+                const onode *lf = tr->leaves[l];
+                float lb = orc_lb2(ix, t, qproj + t * ix->K, lf->lo, lf->hi);
+                for (int64_t i = 0; i < lf->cnt; i++)
+                    if (lb < mo[lf->ids[i]]) mo[lf->ids[i]] = lb;
+            }
+        }
+        qsort(mo, (size_t)n, sizeof(float), orc_cmp_float_asc);
+        vs = mo[tau - 1];
+        free(mo);
+        uint8_t *mark = (uint8_t *)calloc((size_t)n, 1);
+        orc_hits hits = {0};
+        for (int t = 0; t < ix->L && ns < tau; t++) {
+            orc_range_query(ix, t, qproj + t * ix->K, vs, &hits);
+            qsort(hits.v, (size_t)hits.n, sizeof(orc_hit), orc_cmp_hit);
+            for (int64_t h = 0; h < hits.n && ns < tau; h++) {
+                const onode *lf = hits.v[h].leaf;
+                for (int64_t i = 0; i < lf->cnt; i++) {
+                    int64_t p = lf->ids[i];
+                    if (!mark[p]) {
+                        mark[p] = 1;
+                        if (S_out) S_out[ns] = p;
+                        cand[ns++].id = p;
+                    }
+                }
+                if (ns >= tau) is = t;
+            }
+        }
+        free(hits.v);
+        free(mark);
+    }
+    for (int64_t i = 0; i < ns; i++)
+        cand[i].dist = orc_dist(q, ix->X + cand[i].id * ix->d, ix->d);
+    qsort(cand, (size_t)ns, sizeof(orc_cand), orc_cmp_cand);
+    for (int i = 0; i < k; i++) { ids[i] = cand[i].id; dists[i] = cand[i].dist; }
+    if (S_size) *S_size = ns;
+    if (vstar) *vstar = vs;
+    if (istar) *istar = is;
+    free(cand);
+    return 0;
+}
+
 int orc_index_query_batch(const orc_index *ix, const float *Q, int64_t m, int k, double beta,
                           double c, int64_t *ids, double *dists, int64_t *S_sizes,
                           int nthreads) {

@@ -98,6 +98,13 @@ int orc_index_query(const orc_index *ix, const float *q, int k, double beta, dou
 int orc_index_query_fixed(const orc_index *ix, const float *q, int k, double beta, double c,
                           double r_min, int64_t *ids, double *dists, int64_t *S_out,
                           int64_t *S_size, int *jstop, int *istop);
+/* Alg. 5 at the smallest continuous r_min (no radius grid): v* = the
+ * (beta*n + k)-th smallest of the points' smallest leaf lower bound over the
+ * trees; then Alg. 5's first round at that squared radius.  *vstar = v*,
+ * istar as orc_index_query.  S_out (capacity n, nullable). */
+int orc_index_query_magic_min(const orc_index *ix, const float *q, int k, double beta,
+                              int64_t *ids, double *dists, int64_t *S_out, int64_t *S_size,
+                              float *vstar, int *istar);
 /* Same, over m queries, OpenMP over queries (nthreads <= 0: all cores). */
 int orc_index_query_batch(const orc_index *ix, const float *Q, int64_t m, int k, double beta,
                           double c, int64_t *ids, double *dists, int64_t *S_sizes,

@@ -70,6 +70,10 @@ def lib():
                                             C.POINTER(C.c_int64), C.POINTER(C.c_int),
                                             C.POINTER(C.c_int)]
         L.orc_index_query_fixed.restype = C.c_int
+        L.orc_index_query_magic_min.argtypes = [C.c_void_p, _f32p, C.c_int, C.c_double, _i64p,
+                                                _f64p, _i64p_n, C.POINTER(C.c_int64),
+                                                C.POINTER(C.c_float), C.POINTER(C.c_int)]
+        L.orc_index_query_magic_min.restype = C.c_int
         L.orc_index_query_batch.argtypes = [C.c_void_p, _f32p, C.c_int64, C.c_int, C.c_double,
                                             C.c_double, _i64p, _f64p, _i64p, C.c_int]
         L.orc_index_query_batch.restype = C.c_int
@@ -259,6 +263,19 @@ class Index:
             raise ValueError("oracle query rejected its arguments")
         return dict(ids=ids, dists=dists, S=S[:ssz.value] if want_S else None,
                     S_size=ssz.value, jstop=js.value, istop=ist.value)
+
+    def query_magic_min(self, q, k, beta=0.1, want_S=True):
+        """Alg. 5 at the smallest continuous r_min (vstar: the squared threshold)."""
+        ids = np.zeros(k, np.int64)
+        dists = np.zeros(k, np.float64)
+        S = np.zeros(max(self.n, 1), np.int64) if want_S else None
+        ssz, vs, ist = C.c_int64(0), C.c_float(0.0), C.c_int(0)
+        rc = lib().orc_index_query_magic_min(self._h, _f32(q), k, beta, ids, dists, S,
+                                             C.byref(ssz), C.byref(vs), C.byref(ist))
+        if rc != 0:
+            raise ValueError("oracle query rejected its arguments")
+        return dict(ids=ids, dists=dists, S=S[:ssz.value] if want_S else None,
+                    S_size=ssz.value, vstar=vs.value, istar=ist.value)
 
     def query_batch(self, Q, k, beta=0.1, c=1.5, nthreads=0):
         Q = _f32(Q)

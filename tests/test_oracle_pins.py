@@ -623,3 +623,38 @@ def test_static_encoding_has_equal_mass_on_normal_data():
     arr = ix.arrays()
     assert np.array_equal(arr["B"], oracle.static_breakpoints(16, N_r))
     assert np.array_equal(arr["codes"], oracle.encode(arr["P"], arr["B"]))
+
+
+# ------------------------------------------- Alg. 5 at the continuous r_min --
+def test_query_magic_min_is_smallest_radius():
+    # the smallest continuous r_min: |S(v*)| >= beta*n + k and every smaller
+    # lower-bound value leaves fewer points; S and i* recomputed from the
+    # exported leaves; the result equals the grid query whenever v* falls on
+    # the same leaves (a radius grid that is fine enough)
+    ix, X, Q = _small_index(n=5000)
+    trees = [ix.tree(t) for t in range(ix.L)]
+    for q in Q[:5]:
+        lbs = [ix.leaf_lb2(t, q) for t in range(ix.L)]
+        mo = np.min([lbs[t][trees[t]["leaf_of"]] for t in range(ix.L)], axis=0)
+        for beta, k in ((0.01, 10), (0.1, 5)):
+            tau = int(np.ceil(beta * ix.n)) + k
+            got = ix.query_magic_min(q, k, beta=beta)
+            v = np.float32(got["vstar"])
+            assert (mo <= v).sum() >= tau
+            assert (mo < v).sum() < tau  # no smaller lower-bound value reaches tau
+            inS = np.zeros(ix.n, bool)
+            ist = -1
+            for t in range(ix.L):
+                hit = np.nonzero(lbs[t] <= v)[0]
+                hit = hit[np.lexsort((hit, lbs[t][hit]))]
+                for lf in hit:
+                    inS[trees[t]["perm"][trees[t]["begin"][lf]:trees[t]["begin"][lf + 1]]] = True
+                    if inS.sum() >= tau:
+                        ist = t
+                        break
+                if ist >= 0:
+                    break
+            assert got["istar"] == ist
+            assert np.array_equal(np.sort(got["S"]), np.nonzero(inS)[0])
+            wi, wd = _numpy_knn(X[got["S"]], q, k)
+            assert np.array_equal(got["ids"], got["S"][wi])
