@@ -65,9 +65,14 @@ enum { DETLSH_RMIN_MAGIC = 0, /* the "magic" r_min: the smallest radius of the
                                  grid c^j (j = -127..127) whose union over the
                                  L trees holds beta*n + k points; condition 1
                                  ends the first round                        */
-       DETLSH_RMIN_FIXED = 1  /* a given r_min: Alg. 5 runs its radius loop
+       DETLSH_RMIN_FIXED = 1, /* a given r_min: Alg. 5 runs its radius loop
                                  r_min c^i (i = 0..253, then unbounded) with
-                                 condition 2 (k points of S within c*r)      */ };
+                                 condition 2 (k points of S within c*r)      */
+       DETLSH_RMIN_CONTINUOUS = 2 /* the smallest r_min off any grid: the
+                                 squared radius is the (beta*n + k)-th
+                                 smallest of the points' smallest leaf lower
+                                 bound over the trees, so eps and c cancel;
+                                 condition 1 ends the first round           */ };
 
 typedef struct detlsh_index detlsh_index;
 

@@ -631,7 +631,8 @@ int validate_query(const detlsh_index *ix, int64_t m, int32_t k_max, const detls
   if (qp->precision == DETLSH_PREC_BF16_REFINE &&
       (!ix->Xh || (ix->d % 8) != 0 || qp->rerank_mult < 1))
     return DETLSH_ERR_INVALID_ARG;
-  if (qp->rmin_policy != DETLSH_RMIN_MAGIC && qp->rmin_policy != DETLSH_RMIN_FIXED)
+  if (qp->rmin_policy != DETLSH_RMIN_MAGIC && qp->rmin_policy != DETLSH_RMIN_FIXED &&
+      qp->rmin_policy != DETLSH_RMIN_CONTINUOUS)
     return DETLSH_ERR_INVALID_ARG;
   if (qp->rmin_policy == DETLSH_RMIN_FIXED &&
       (!(qp->r_min > 0.0) || !std::isfinite(qp->r_min) || qp->precision != DETLSH_PREC_FP32))

@@ -1125,6 +1125,183 @@ __device__ __forceinline__ int64_t fixed_rmin_query(QCtx &c, int k) {
   return nc;
 }
 
+// ---- Alg. 5 at the smallest continuous r_min -----------------------------
+// v* = the (beta*n + k)-th smallest of m(p) = min over trees of the lower
+// bound of p's leaf: N(T(j*-1)) < beta*n + k <= N(T(j*)) on the grid, so v*
+// lies in (T(j*-1), T(j*)] and is found among the points whose smallest level
+// is j*.  A leaf of level < j* is within v*, one of level > j* is not; for
+// level j* the exact lower bound decides.  Then Alg. 5's first round at v*.
+
+// Lower bound of leaf l of tree u, from the breakpoints and q' in global
+// memory: the same FP32 operations in the same order as box_lb2 on the table.
+__device__ __forceinline__ float leaf_lb2_direct(const QueryIndexView &ix, const float *qp,
+                                                 int u, uint32_t l) {
+  const int64_t g = ix.leaf_off[u] + l;
+  const uint4 lo = reinterpret_cast<const uint4 *>(ix.leaf_lo)[g];
+  const uint4 hi = reinterpret_cast<const uint4 *>(ix.leaf_hi)[g];
+  const uint32_t wl[4] = {lo.x, lo.y, lo.z, lo.w}, wh[4] = {hi.x, hi.y, hi.z, hi.w};
+  const int NR1 = ix.N_r + 1;
+  float acc = 0.0f;
+  for (int j = 0; j < ix.K; ++j) {
+    const uint32_t zl = (wl[j >> 2] >> (8 * (j & 3))) & 255u;
+    const uint32_t zh = (wh[j >> 2] >> (8 * (j & 3))) & 255u;
+    const float *Bj = ix.B + (int64_t)(u * ix.K + j) * NR1;
+    const float q = qp[u * ix.K + j];
+    const float a = __fsub_rn(Bj[zl], q);
+    const float b = -__fsub_rn(Bj[zh + 1], q);
+    const float gap = fmaxf(fmaxf(a, b), 0.0f);
+    acc = __fadd_rn(acc, __fmul_rn(gap, gap));
+  }
+  return acc;
+}
+
+// Is p (visited in tree t's leaf of level lvt and lower bound lbt) within the
+// squared radius v, and does no earlier tree hold it within v?  The smallest
+// lower bound of p over all trees goes to *m (trees of level j* recomputed).
+template <int LC>
+__device__ __forceinline__ bool new_at_v(const QCtx &c, uint32_t p, int t, uint32_t js,
+                                         float v, bool want_m, float lbt, float *m) {
+  const PointLeaves<LC> lf(c.ix, p);
+  const int L = LC ? LC : c.ix.L;
+  const float *qp = c.qa.Qp + c.qi * c.ix.LK;
+  bool blocked = false;
+  float mm = lbt;
+#pragma unroll
+  for (int u = 0; u < L; ++u) {
+    if (u == t || (u > t && !want_m)) continue;
+    const uint32_t lv = leaf_level_h(c.ix, c.s, c.sm, c.lut, u, lf[u]);
+    if (lv > js) continue;
+    const float lb = (lv < js) ? 0.0f : leaf_lb2_direct(c.ix, qp, u, lf[u]);
+    if (u < t && (lv < js || lb <= v)) blocked = true;
+    if (lv == js) mm = fminf(mm, lb);
+  }
+  if (m) *m = mm;
+  return !blocked;
+}
+
+template <int LC>
+__device__ __forceinline__ void magic_min_resolve(QCtx &c) {
+  const QueryIndexView &ix = c.ix;
+  QShared &sm = c.sm;
+  const int L = LC ? LC : ix.L;
+  const uint32_t js = (uint32_t)min(sm.sel_g, sm.jhi);
+  const uint32_t need0 = (uint32_t)(c.tau - (int64_t)sm.sel_bf);  // beyond N(j* - 1)
+  // v*: radix select over m(p) of the points whose smallest level is j*,
+  // each counted once (from the first tree at level j*)
+  uint32_t prefix = 0, below = 0;
+  for (int shift = 24; shift >= 0; shift -= 8) {
+    sm.rh[threadIdx.x] = 0;
+    __syncthreads();
+    const uint32_t hmask = (shift == 24) ? 0u : (0xffffffffu << (shift + 8));
+    for (int t = 0; t < L; ++t) {
+      const int64_t lo0 = ix.leaf_off[t];
+      visit_points(
+          c, t, [&](int64_t e) { return c.s.llev[lo0 + e] == js; },
+          [&](bool valid, uint32_t p, uint32_t ent, uint32_t) {
+            bool take = false;
+            uint32_t key = 0;
+            if (valid) {
+              uint32_t fb = 0, fa = 0;
+              levels_around<LC>(c, p, t, fb, fa);
+              if (fb > js && fa >= js) {  // first tree at level j*, none below
+                float m;
+                new_at_v<LC>(c, p, t, js, 0.0f, true, c.s.llb2[lo0 + ent], &m);
+                key = __float_as_uint(m);
+                take = (key & hmask) == (prefix & hmask);
+              }
+            }
+            warp_bin_count(sm.rh, take, (key >> shift) & 255u, 1u);
+          });
+    }
+    __syncthreads();
+    warp_first_crossing(sm.rh, below, need0, &sm.sel_g, &sm.sel_bf);
+    __syncthreads();
+    prefix |= (uint32_t)sm.sel_g << shift;
+    below = (uint32_t)sm.sel_bf;
+    __syncthreads();
+  }
+  const float v = __uint_as_float(prefix);
+  // new points per tree at v, i*, the count still needed inside tree i*
+  if (threadIdx.x < 16) sm.newt[threadIdx.x] = 0;
+  __syncthreads();
+  for (int t = 0; t < L; ++t) {
+    const int64_t lo0 = ix.leaf_off[t];
+    visit_points(
+        c, t, [&](int64_t e) { return c.s.llev[lo0 + e] <= js && c.s.llb2[lo0 + e] <= v; },
+        [&](bool valid, uint32_t p, uint32_t, uint32_t) {
+          const bool nw = valid && new_at_v<LC>(c, p, t, js, v, false, 0.0f, nullptr);
+          const unsigned bm = __ballot_sync(FULL, nw);
+          if ((threadIdx.x & 31) == 0 && bm)
+            atomicAdd(reinterpret_cast<unsigned long long *>(&sm.newt[t]), (unsigned long long)__popc(bm));
+        });
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int64_t cum = 0, basev = 0;
+    int is = L - 1;
+    for (int t = 0; t < L; ++t) {
+      if (cum + sm.newt[t] >= c.tau) { is = t; basev = cum; break; }
+      cum += sm.newt[t];
+    }
+    sm.jstar = (int)js;
+    sm.istar = is;
+    sm.need = (uint32_t)(c.tau - basev);
+  }
+  __syncthreads();
+  const int is = sm.istar;
+  const int64_t li0 = ix.leaf_off[is];
+  const int64_t nli = sm.nlist[is];
+  for (int64_t e = threadIdx.x; e < nli; e += QT) c.s.cval[e] = 0u;
+  __syncthreads();
+  auto inside = [&](int64_t lo0, int64_t e) {
+    return c.s.llev[lo0 + e] <= js && c.s.llb2[lo0 + e] <= v;
+  };
+  visit_points(
+      c, is, [&](int64_t e) { return inside(li0, e); },
+      [&](bool valid, uint32_t p, uint32_t ent, uint32_t) {
+        const bool nw = valid && new_at_v<LC>(c, p, is, js, v, false, 0.0f, nullptr);
+        warp_bin_count(c.s.cval, nw, ent, 1u);
+      });
+  __syncthreads();
+  const uint32_t need = sm.need;
+  auto get_lb = [&](int64_t i, uint32_t &k, uint32_t &w) {
+    w = inside(li0, i) ? c.s.cval[i] : 0u;
+    k = __float_as_uint(c.s.llb2[li0 + i]);
+  };
+  block_select(nli, get_lb, need, sm);
+  const uint32_t vb = sm.sel_v;
+  const uint32_t need2 = need - sm.sel_below;
+  uint32_t cut = 0xffffffffu;
+  if (need2 < sm.sel_at) {
+    auto get_id = [&](int64_t i, uint32_t &k, uint32_t &w) {
+      const bool q = inside(li0, i) && __float_as_uint(c.s.llb2[li0 + i]) == vb;
+      w = q ? c.s.cval[i] : 0u;
+      k = c.s.lleaf[li0 + i];
+    };
+    block_select(nli, get_id, need2, sm);
+    cut = sm.sel_v;
+  }
+  if (threadIdx.x == 0) sm.ncand = 0;
+  __syncthreads();
+  for (int t = 0; t <= is; ++t) {
+    const int64_t lo0 = ix.leaf_off[t];
+    visit_points(
+        c, t,
+        [&](int64_t e) {
+          if (!inside(lo0, e)) return false;
+          if (t < is) return true;
+          const uint32_t kb = __float_as_uint(c.s.llb2[lo0 + e]);
+          return kb < vb || (kb == vb && c.s.lleaf[lo0 + e] <= cut);
+        },
+        [&](bool valid, uint32_t p, uint32_t, uint32_t) {
+          const bool take = valid && new_at_v<LC>(c, p, t, js, v, false, 0.0f, nullptr);
+          const uint32_t pos = warp_append(c, take);
+          if (take && pos < (uint32_t)c.qa.cand_cap) c.s.cand[pos] = p;
+        });
+  }
+  __syncthreads();
+}
+
 __global__ void __launch_bounds__(QT, 5) k_query(QueryIndexView ix, QueryArgs qa) {
   extern __shared__ __align__(16) uint8_t dsm[];
   QShared &sm = *reinterpret_cast<QShared *>(dsm);
@@ -1190,6 +1367,13 @@ __global__ void __launch_bounds__(QT, 5) k_query(QueryIndexView ix, QueryArgs qa
         fixed_done = true;
         s_written = r < 0;
         nc = r < 0 ? -r - 1 : r;
+      } else if (qa.policy == DETLSH_RMIN_CONTINUOUS) {
+        if (ix.L == 4) magic_min_resolve<4>(c); else magic_min_resolve<0>(c);
+        nc = sm.ncand;
+        if (nc > qa.cand_cap) {
+          if (threadIdx.x == 0) atomicExch(qa.err, (int)DETLSH_ERR_CAPACITY);
+          nc = qa.cand_cap;
+        }
       } else {
         const int js = min(sm.sel_g, sm.jhi);
         {  // points new in each tree at level j*: one warp per tree

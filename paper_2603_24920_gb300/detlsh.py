@@ -17,7 +17,7 @@ STATUS = {0: "OK", -1: "INVALID_ARG", -2: "NONFINITE_INPUT", -3: "OOM", -4: "CUD
           -5: "CAPACITY", -6: "NO_DEVICE", -7: "SCRATCH_LIMIT"}
 BOX_PREFIX, BOX_TIGHT = 0, 1
 PREC_FP32, PREC_BF16_REFINE = 0, 1
-RMIN_MAGIC, RMIN_FIXED = 0, 1
+RMIN_MAGIC, RMIN_FIXED, RMIN_CONTINUOUS = 0, 1, 2
 ENC_DYNAMIC, ENC_STATIC = 0, 1
 
 
@@ -175,14 +175,18 @@ def detlsh_free(h):
 
 
 def detlsh_query_ex(h, queries, k, beta=0.1, c=1.5, precision=PREC_FP32, rerank_mult=4,
-                    k_per_query=None, stream=None, ids=None, dists=None, r_min=None):
+                    k_per_query=None, stream=None, ids=None, dists=None, r_min=None,
+                    rmin_policy=None):
     """Returns (ids int64 (m, k), dists float32 (m, k)); torch CUDA if queries are.
-    r_min given: Alg. 5 from that radius with condition 2 (RMIN_FIXED)."""
+    r_min given: Alg. 5 from that radius with condition 2 (RMIN_FIXED);
+    rmin_policy=RMIN_CONTINUOUS: the smallest r_min off the grid."""
     m = queries.shape[0]
     qp = detlsh_default_query_params()
     qp.beta, qp.c, qp.precision, qp.rerank_mult = beta, c, precision, rerank_mult
     if r_min is not None:
         qp.rmin_policy, qp.r_min = RMIN_FIXED, r_min
+    if rmin_policy is not None:
+        qp.rmin_policy = rmin_policy
     if ids is None:
         if _is_cuda(queries):
             import torch
@@ -303,7 +307,8 @@ def detlsh_project(h, rows, stream=None):
     return out
 
 
-def detlsh_query_candidates(h, queries, k, beta=0.1, c=1.5, cap=None, r_min=None):
+def detlsh_query_candidates(h, queries, k, beta=0.1, c=1.5, cap=None, r_min=None,
+                            rmin_policy=None):
     """Candidate sets of Alg. 5: list of id arrays, j*, i* per query (with r_min:
     the stopping radius index and tree, -1 for condition 2)."""
     i = detlsh_get_info(h)
@@ -313,6 +318,8 @@ def detlsh_query_candidates(h, queries, k, beta=0.1, c=1.5, cap=None, r_min=None
     qp.beta, qp.c = beta, c
     if r_min is not None:
         qp.rmin_policy, qp.r_min = RMIN_FIXED, r_min
+    if rmin_policy is not None:
+        qp.rmin_policy = rmin_policy
     S = np.empty((m, cap), np.int64)
     ssz = np.empty(m, np.int64)
     js = np.empty(m, np.int32)
