@@ -1302,6 +1302,9 @@ __device__ __forceinline__ void magic_min_resolve(QCtx &c) {
   __syncthreads();
 }
 
+// One instantiation per r_min policy, so the common (magic grid) kernel
+// carries none of the other policies' code or register pressure.
+template <int POL>
 __global__ void __launch_bounds__(QT, 5) k_query(QueryIndexView ix, QueryArgs qa) {
   extern __shared__ __align__(16) uint8_t dsm[];
   QShared &sm = *reinterpret_cast<QShared *>(dsm);
@@ -1362,12 +1365,12 @@ __global__ void __launch_bounds__(QT, 5) k_query(QueryIndexView ix, QueryArgs qa
       // j* = first level whose union count reaches tau (<= jhi by construction)
       warp_first_crossing(sm.H, 0, (uint64_t)tau, &sm.sel_g, &sm.sel_bf);
       __syncthreads();
-      if (qa.policy == DETLSH_RMIN_FIXED) {
+      if constexpr (POL == DETLSH_RMIN_FIXED) {
         const int64_t r = ix.L == 4 ? fixed_rmin_query<4>(c, k) : fixed_rmin_query<0>(c, k);
         fixed_done = true;
         s_written = r < 0;
         nc = r < 0 ? -r - 1 : r;
-      } else if (qa.policy == DETLSH_RMIN_CONTINUOUS) {
+      } else if constexpr (POL == DETLSH_RMIN_CONTINUOUS) {
         if (ix.L == 4) magic_min_resolve<4>(c); else magic_min_resolve<0>(c);
         nc = sm.ncand;
         if (nc > qa.cand_cap) {
@@ -1500,8 +1503,9 @@ int query_slots(const QueryIndexView &ix) {
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const size_t smem = query_smem(ix);
-  cudaFuncSetAttribute(k_query, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_query, QT, smem);
+  cudaFuncSetAttribute(k_query<DETLSH_RMIN_MAGIC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_query<DETLSH_RMIN_MAGIC>, QT, smem);
   if (per < 1) per = 1;
   return sms * per;
 }
@@ -1509,10 +1513,13 @@ int query_slots(const QueryIndexView &ix) {
 int run_queries(const QueryIndexView &ix, const QueryArgs &qa, cudaStream_t st) {
   if (qa.m <= 0) return DETLSH_OK;
   const size_t smem = query_smem(ix);
-  DL_CUDA(cudaFuncSetAttribute(k_query, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  auto kern = qa.policy == DETLSH_RMIN_FIXED        ? k_query<DETLSH_RMIN_FIXED>
+              : qa.policy == DETLSH_RMIN_CONTINUOUS ? k_query<DETLSH_RMIN_CONTINUOUS>
+                                                    : k_query<DETLSH_RMIN_MAGIC>;
+  DL_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   DL_CUDA(cudaMemsetAsync(qa.work_counter, 0, sizeof(uint32_t), st));
   const int grid = (int)std::min<int64_t>(qa.nslots, qa.m);
-  k_query<<<grid, QT, smem, st>>>(ix, qa);
+  kern<<<grid, QT, smem, st>>>(ix, qa);
   dl_count_launch();
   DL_CUDA(cudaGetLastError());
   return DETLSH_OK;
