@@ -301,8 +301,9 @@ int detlsh_query_async(const detlsh_index *ix, const float *queries, int64_t m,
  * Errors: INVALID_ARG (arguments as above), NONFINITE_INPUT (a query holds NaN
  * or Inf), OOM, CUDA.  Blocks until the results are written. */
 int detlsh_rc_ann(const detlsh_index *ix, const float *queries, int64_t m, double r,
-                  double beta, double c, void *stream, int64_t *ids, float *dists,
-                  int32_t *tree_stop, int64_t S_cap, int64_t *S, int64_t *S_size);
+                  double beta, double c, int32_t optimised, void *stream, int64_t *ids,
+                  float *dists, int32_t *tree_stop, int64_t S_cap, int64_t *S,
+                  int64_t *S_size);
 
 #ifdef __cplusplus
 }

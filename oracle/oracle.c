@@ -849,8 +849,8 @@ void orc_index_leaf_ub2(const orc_index *ix, int t, const float *q, float *ub2) 
 }
 
 int orc_index_rc_ann(const orc_index *ix, const float *q, double r, double beta, double c,
-                     int64_t *id, double *dist, int64_t *S_out, int64_t *S_size,
-                     int *tree_stop) {
+                     int optimised, int64_t *id, double *dist, int64_t *S_out,
+                     int64_t *S_size, int *tree_stop) {
     const int64_t n = ix->n;
     const int64_t need = (int64_t)ceil(beta * (double)n) + 1; /* beta*n + 1 */
     float qproj[256];
@@ -864,9 +864,17 @@ int orc_index_rc_ann(const orc_index *ix, const float *q, double r, double beta,
     for (int t = 0; t < ix->L; t++) {
         const otree *tr = &ix->trees[t];
         int64_t nr = 0;
-        for (int64_t key = 0; key < ((int64_t)1 << ix->K); key++)
-            if (tr->first[key])
-                orc_range_exact_rec(ix, t, qproj + t * ix->K, tr->first[key], R2, Rt, &nr);
+        if (optimised) {  /* optimisation (1) of Sec. VI-B2: leaves whole by lower bound */
+            orc_hits hits = {0};
+            orc_range_query(ix, t, qproj + t * ix->K, R2, &hits);
+            for (int64_t h = 0; h < hits.n; h++)
+                for (int64_t i = 0; i < hits.v[h].leaf->cnt; i++) Rt[nr++] = hits.v[h].leaf->ids[i];
+            free(hits.v);
+        } else {
+            for (int64_t key = 0; key < ((int64_t)1 << ix->K); key++)
+                if (tr->first[key])
+                    orc_range_exact_rec(ix, t, qproj + t * ix->K, tr->first[key], R2, Rt, &nr);
+        }
         for (int64_t i = 0; i < nr; i++)
             if (!mark[Rt[i]]) { mark[Rt[i]] = 1; S[ns++] = Rt[i]; }
         if (ns >= need) { stop = t; break; }

@@ -121,14 +121,16 @@ int64_t orc_index_range_exact(const orc_index *ix, int t, const float *q, double
                               int64_t *out);
 /* Upper bound of every leaf of tree t to query q (FP32, Sec. IV-C). */
 void orc_index_leaf_ub2(const orc_index *ix, int t, const float *q, float *ub2);
-/* Alg. 4, (r,c)-ANN: trees in order, S = union of the exact range queries;
+/* Alg. 4, (r,c)-ANN: trees in order, S = union of the range queries (Alg. 3
+ * as printed, or with optimised = 1 optimisation (1) of Sec. VI-B2: every
+ * leaf whose lower bound is within r' whole);
  * once |S| >= beta*n + 1 the point of S closest to q is returned (tree_stop =
  * that tree); after all L trees, the closest point of S if it lies within
  * c*r, else id = -1 (tree_stop = -1).  FP64 distances, ties by smaller id.
  * S_out (capacity n, nullable) receives S in arrival order. */
 int orc_index_rc_ann(const orc_index *ix, const float *q, double r, double beta, double c,
-                     int64_t *id, double *dist, int64_t *S_out, int64_t *S_size,
-                     int *tree_stop);
+                     int optimised, int64_t *id, double *dist, int64_t *S_out,
+                     int64_t *S_size, int *tree_stop);
 /* Exact kNN by brute force, FP64 distances, ties by smaller id. */
 void orc_bruteforce_knn(const float *X, int64_t n, int64_t d, const float *Q, int64_t m,
                         int k, int64_t *ids, double *dists, int nthreads);

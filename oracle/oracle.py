@@ -82,7 +82,7 @@ def lib():
         L.orc_index_range_exact.argtypes = [C.c_void_p, C.c_int, _f32p, C.c_double, _i64p]
         L.orc_index_range_exact.restype = C.c_int64
         L.orc_index_rc_ann.argtypes = [C.c_void_p, _f32p, C.c_double, C.c_double, C.c_double,
-                                       C.POINTER(C.c_int64), C.POINTER(C.c_double), _i64p_n,
+                                       C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_double), _i64p_n,
                                        C.POINTER(C.c_int64), C.POINTER(C.c_int)]
         L.orc_index_rc_ann.restype = C.c_int
         L.orc_bruteforce_knn.argtypes = [_f32p, C.c_int64, C.c_int64, _f32p, C.c_int64, C.c_int,
@@ -227,12 +227,14 @@ class Index:
         cnt = lib().orc_index_range_exact(self._h, t, _f32(q), r, out)
         return out[:cnt]
 
-    def rc_ann(self, q, r, beta=0.1, c=1.5, want_S=True):
-        """Alg. 4: (r,c)-ANN.  id -1 when the query returns nothing."""
+    def rc_ann(self, q, r, beta=0.1, c=1.5, want_S=True, optimised=False):
+        """Alg. 4: (r,c)-ANN.  id -1 when the query returns nothing.  optimised:
+        whole leaves by lower bound (Sec. VI-B2 (1)) instead of Alg. 3 as printed."""
         pid, dist = C.c_int64(0), C.c_double(0.0)
         ssz, stop = C.c_int64(0), C.c_int(0)
         S = np.zeros(max(self.n, 1), np.int64) if want_S else None
-        lib().orc_index_rc_ann(self._h, _f32(q), r, beta, c, C.byref(pid), C.byref(dist), S,
+        lib().orc_index_rc_ann(self._h, _f32(q), r, beta, c, int(optimised), C.byref(pid),
+                               C.byref(dist), S,
                                C.byref(ssz), C.byref(stop))
         return dict(id=pid.value, dist=dist.value, S=S[:ssz.value] if want_S else None,
                     S_size=ssz.value, tree_stop=stop.value)

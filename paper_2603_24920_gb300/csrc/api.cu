@@ -1060,14 +1060,16 @@ int detlsh_query_async(const detlsh_index *cix, const float *queries, int64_t m,
 }
 
 int detlsh_rc_ann(const detlsh_index *cix, const float *queries, int64_t m, double r,
-                  double beta, double c, void *stream, int64_t *ids, float *dists,
-                  int32_t *tree_stop, int64_t S_cap, int64_t *S, int64_t *S_size) {
+                  double beta, double c, int32_t optimised, void *stream, int64_t *ids,
+                  float *dists, int32_t *tree_stop, int64_t S_cap, int64_t *S,
+                  int64_t *S_size) {
   if (!cix || m < 0) return DETLSH_ERR_INVALID_ARG;
   if (!(r > 0.0) || !std::isfinite(r) || !(beta >= 0.0) || !std::isfinite(beta) ||
       !(c > 1.0) || !std::isfinite(c))
     return DETLSH_ERR_INVALID_ARG;
   if (S && S_cap < 1) return DETLSH_ERR_INVALID_ARG;
-  if (!cix->P) return DETLSH_ERR_INVALID_ARG;  // needs the projections kept at build
+  if (optimised != 0 && optimised != 1) return DETLSH_ERR_INVALID_ARG;
+  if (!optimised && !cix->P) return DETLSH_ERR_INVALID_ARG;  // per-point tests read P
   if (m == 0) return DETLSH_OK;
   if (!queries || !ids || !dists) return DETLSH_ERR_INVALID_ARG;
   detlsh_index *ix = const_cast<detlsh_index *>(cix);
@@ -1100,7 +1102,7 @@ int detlsh_rc_ann(const detlsh_index *cix, const float *queries, int64_t m, doub
   if (e) return e;
   QueryIndexView v = view_of(ix);
   RcArgs a{};
-  a.Q = Q; a.Qp = Qp; a.m = m;
+  a.Q = Q; a.Qp = Qp; a.m = m; a.optimised = optimised;
   a.R2 = (float)(ix->eps2 * r * r);  // (eps r)^2 rounded once, as the radius grid
   a.cr = (float)(c * r);
   const double nb = std::ceil(beta * (double)ix->n);

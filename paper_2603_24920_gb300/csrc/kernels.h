@@ -151,6 +151,7 @@ struct RcArgs {
   float R2;                  // fp32((eps r)^2)
   float cr;                  // fp32(c r)
   int64_t need;              // ceil(beta n) + 1
+  int optimised;             // 1: leaves whole by lower bound (Sec. VI-B2 (1))
   int64_t *ids;              // [m], -1 when nothing is returned
   float *dists;              // [m], +inf when nothing is returned
   int32_t *tree_stop;        // [m], tree where |S| reached need, -1 if none

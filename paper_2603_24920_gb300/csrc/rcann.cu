@@ -1,5 +1,6 @@
 // rcann.cu -- (r,c)-ANN queries (Alg. 4) over the DE-Trees with the range
-// query of Alg. 3 as printed (Sec. IV-C pruning, no Sec. VI-B2 shortcuts).
+// query of Alg. 3 as printed (Sec. IV-C pruning), or with optimisation (1)
+// of Sec. VI-B2 (every leaf whose lower bound is within r' taken whole).
 //
 // One persistent launch, one CTA per query at a time.  For each tree in
 // order: the leaf-run hulls and then the leaves whose lower bound is within
@@ -80,6 +81,27 @@ __device__ __forceinline__ float point_d2(const QueryIndexView &ix, const float 
   return acc;
 }
 
+// Lower bound of leaf l of tree u from the breakpoints and q' (the table's
+// operations in the table's order, so it equals box_lb2 on the table).
+__device__ __forceinline__ float leaf_lb2_of(const QueryIndexView &ix, const float *qp, int u,
+                                             uint32_t l) {
+  const int64_t g = ix.leaf_off[u] + l;
+  const uint4 lo = reinterpret_cast<const uint4 *>(ix.leaf_lo)[g];
+  const uint4 hi = reinterpret_cast<const uint4 *>(ix.leaf_hi)[g];
+  const uint32_t wl[4] = {lo.x, lo.y, lo.z, lo.w}, wh[4] = {hi.x, hi.y, hi.z, hi.w};
+  const int NR1 = ix.N_r + 1;
+  float acc = 0.0f;
+  for (int j = 0; j < ix.K; ++j) {
+    const uint32_t zl = (wl[j >> 2] >> (8 * (j & 3))) & 255u;
+    const uint32_t zh = (wh[j >> 2] >> (8 * (j & 3))) & 255u;
+    const float *Bj = ix.B + (int64_t)(u * ix.K + j) * NR1;
+    const float q = qp[u * ix.K + j];
+    const float gap = fmaxf(fmaxf(__fsub_rn(Bj[zl], q), -__fsub_rn(Bj[zh + 1], q)), 0.0f);
+    acc = __fadd_rn(acc, __fmul_rn(gap, gap));
+  }
+  return acc;
+}
+
 __global__ void __launch_bounds__(RT) k_rcann(QueryIndexView ix, RcArgs a) {
   extern __shared__ __align__(16) uint8_t dsm[];
   float *lut = reinterpret_cast<float *>(dsm);
@@ -120,7 +142,7 @@ __global__ void __launch_bounds__(RT) k_rcann(QueryIndexView ix, RcArgs a) {
         bool keep = false, whole = false;
         if (l < nl) {
           keep = box_lb2(lut, llo[l], lhi[l]) <= a.R2;
-          whole = keep && box_ub2(lut, llo[l], lhi[l]) <= a.R2;
+          whole = keep && (a.optimised || box_ub2(lut, llo[l], lhi[l]) <= a.R2);
         }
         const unsigned km = __ballot_sync(FULL, keep);
         uint32_t p0 = 0;
@@ -167,8 +189,13 @@ __global__ void __launch_bounds__(RT) k_rcann(QueryIndexView ix, RcArgs a) {
           const uint32_t fb = sm.fl_beg[lo];
           const uint32_t p = permt[(fb & 0x7fffffffu) + (i - sm.fl_pre[lo])];
           bool in = (fb >> 31) || proj_d2(ix, sm.qp, p, t) <= a.R2;
-          for (int u = 0; in && u < t; ++u)
-            if (proj_d2(ix, sm.qp, p, u) <= a.R2) in = false;  // returned by an earlier tree
+          for (int u = 0; in && u < t; ++u) {  // returned by an earlier tree?
+            if (a.optimised) {
+              if (leaf_lb2_of(ix, sm.qp, u, ix.leaf_of[(int64_t)p * ix.L + u]) <= a.R2) in = false;
+            } else if (proj_d2(ix, sm.qp, p, u) <= a.R2) {
+              in = false;
+            }
+          }
           if (in) {
             const unsigned long long pos = atomicAdd(&sm.count, 1ull);
             if (a.S && (int64_t)pos < a.S_cap) a.S[qi * a.S_cap + (int64_t)pos] = p;

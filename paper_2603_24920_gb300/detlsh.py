@@ -90,7 +90,8 @@ SIGNATURES = [
                                           _P, _P, _P, _P]),
     ("detlsh_query_reserve", C.c_int, [_P, _I64, _I32, C.POINTER(QueryParams)]),
     ("detlsh_query_async", C.c_int, [_P, _P, _I64, _P, _I32, _P, _P, _P, _P]),
-    ("detlsh_rc_ann", C.c_int, [_P, _P, _I64, _F64, _F64, _F64, _P, _P, _P, _P, _I64, _P, _P]),
+    ("detlsh_rc_ann", C.c_int, [_P, _P, _I64, _F64, _F64, _F64, _I32, _P, _P, _P, _P, _I64, _P,
+                                _P]),
 ]
 
 
@@ -348,7 +349,7 @@ def detlsh_query_async(h, queries, k_max, ids, dists, status, k_per_query=None, 
            "detlsh_query_async")
 
 
-def detlsh_rc_ann(h, queries, r, beta=0.1, c=1.5, S_cap=0, stream=None):
+def detlsh_rc_ann(h, queries, r, beta=0.1, c=1.5, S_cap=0, stream=None, optimised=False):
     """Alg. 4 (r,c)-ANN: ids (-1 = nothing), dists, tree_stop, S_size, and S
     (list of id arrays) when S_cap > 0.  Host numpy or CUDA tensors in; numpy out."""
     m = queries.shape[0]
@@ -357,7 +358,8 @@ def detlsh_rc_ann(h, queries, r, beta=0.1, c=1.5, S_cap=0, stream=None):
     stop = np.empty(m, np.int32)
     ssz = np.empty(m, np.int64)
     S = np.empty((m, S_cap), np.int64) if S_cap > 0 else None
-    _check(lib().detlsh_rc_ann(h, _ptr(queries), m, r, beta, c, _stream_ptr(stream), _ptr(ids),
+    _check(lib().detlsh_rc_ann(h, _ptr(queries), m, r, beta, c, int(optimised),
+                               _stream_ptr(stream), _ptr(ids),
                                _ptr(dists), _ptr(stop), S_cap, _ptr(S) if S is not None else None,
                                _ptr(ssz)),
            "detlsh_rc_ann")

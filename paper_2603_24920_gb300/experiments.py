@@ -189,18 +189,23 @@ def cmd_variants(a):
                          compute_mode="donot_use_mm_for_euclid_dist")
         nn.append(dd.min(1).values.cpu().numpy())
     nn = np.concatenate(nn)
-    print("(r,c)-ANN (Alg. 4, Alg. 3 as printed), c2, c = 1.5, 200 queries:")
-    row("r / NN distance", "beta", "kernel ms per query", "answered within c*r", "mean S size")
+    print("(r,c)-ANN (Alg. 4), c2, c = 1.5, 200 queries: Alg. 3 as printed vs optimisation (1)"
+          " of Sec. VI-B2 (whole leaves):")
+    row("range query", "r / NN distance", "beta", "kernel ms per query", "answered within c*r",
+        "returns the true NN", "mean S size")
     r_med = float(np.median(nn))
-    for f in (1.0, 1.5):
-        for beta in (0.0015, 0.01):
-            r = f * r_med
-            D.detlsh_rc_ann(h, Qn, r, beta=beta)
-            ids, dists, stop, ssz, _ = D.detlsh_rc_ann(h, Qn, r, beta=beta)
-            t = D.detlsh_get_timings(h)
-            ok = np.mean((ids >= 0) & (dists <= 1.5 * r * (1 + 1e-6)))
-            row("%.1f x median (r = %.1f)" % (f, r), beta, "%.4f" % (t.query_kernel_ms / 200),
-                "%.3f" % ok, "%.0f" % ssz.mean())
+    nn_id = exact_knn(Xd, Qn, 1, nq=200)[:, 0]
+    for opt in (False, True):
+        for f in (1.0, 1.5):
+            for beta in (0.0015, 0.01):
+                r = f * r_med
+                D.detlsh_rc_ann(h, Qn, r, beta=beta, optimised=opt)
+                ids, dists, stop, ssz, _ = D.detlsh_rc_ann(h, Qn, r, beta=beta, optimised=opt)
+                t = D.detlsh_get_timings(h)
+                ok = np.mean((ids >= 0) & (dists <= 1.5 * r * (1 + 1e-6)))
+                row("whole leaves" if opt else "as printed", "%.1f x median (r = %.1f)" % (f, r),
+                    beta, "%.4f" % (t.query_kernel_ms / 200), "%.3f" % ok,
+                    "%.3f" % np.mean(ids == nn_id), "%.0f" % ssz.mean())
     D.detlsh_free(h)
     del Xd, Qd
     torch.cuda.empty_cache()

@@ -1,5 +1,6 @@
-"""(r,c)-ANN (Alg. 4) over the range query of Alg. 3 as printed: CUDA path vs
-the CPU oracle through the C-ABI.
+"""(r,c)-ANN (Alg. 4) over the range query of Alg. 3 as printed, and with
+optimisation (1) of Sec. VI-B2 (whole leaves): CUDA path vs the CPU oracle
+through the C-ABI.
 
 Bit-exact: the candidate set S (union of the per-tree exact range queries up
 to the stopping tree) and the stopping tree.  The returned point: the same id
@@ -52,8 +53,9 @@ def _radii(ox, q, K, L):
     return [float(np.sqrt(np.quantile(d2, f) / e2)) for f in (0.0005, 0.003, 0.02)]
 
 
+@pytest.mark.parametrize("optimised", [False, True])
 @pytest.mark.parametrize("beta", [0.005, 0.05])
-def test_rc_ann_matches_oracle(pair, beta):
+def test_rc_ann_matches_oracle(pair, beta, optimised):
     h, ox, X, Q, n = pair["h"], pair["ox"], pair["X"], pair["Q"], pair["n"]
     c = 1.5
     outcomes = set()
@@ -61,8 +63,9 @@ def test_rc_ann_matches_oracle(pair, beta):
         q = Q[i]
         dist = np.sqrt(((X.astype(np.float64) - q.astype(np.float64)) ** 2).sum(1))
         for r in _radii(ox, q, pair["K"], pair["L"]):
-            want = ox.rc_ann(q, r, beta=beta, c=c)
-            ids, dists, stop, ssz, S = D.detlsh_rc_ann(h, Q[i:i + 1], r, beta=beta, c=c, S_cap=n)
+            want = ox.rc_ann(q, r, beta=beta, c=c, optimised=optimised)
+            ids, dists, stop, ssz, S = D.detlsh_rc_ann(h, Q[i:i + 1], r, beta=beta, c=c, S_cap=n,
+                                                       optimised=optimised)
             assert stop[0] == want["tree_stop"], (i, r)
             assert ssz[0] == want["S_size"]
             assert np.array_equal(np.sort(S[0]), np.sort(want["S"]))
@@ -102,6 +105,7 @@ def test_rc_ann_argument_errors():
     q = np.ascontiguousarray(Q[:, :16])
     with pytest.raises(D.DetlshError):
         D.detlsh_rc_ann(h, q, 1.0)
+    D.detlsh_rc_ann(h, q, 1.0, optimised=True)  # whole leaves need no projections
     D.detlsh_free(h)
     h = D.detlsh_build(np.ascontiguousarray(X[:, :16]), L=2, K=4, N_r=16, seed=1,
                        keep_projections=1)

@@ -658,3 +658,37 @@ def test_query_magic_min_is_smallest_radius():
             assert np.array_equal(np.sort(got["S"]), np.nonzero(inS)[0])
             wi, wd = _numpy_knn(X[got["S"]], q, k)
             assert np.array_equal(got["ids"], got["S"][wi])
+
+
+def test_rc_ann_optimised_takes_whole_leaves():
+    # optimisation (1) of Sec. VI-B2 inside Alg. 4: a tree returns every point
+    # of every leaf whose lower bound is within r' (numpy from the exported
+    # leaves), a superset of Alg. 3 as printed at the same radius
+    ix, X, Q = _small_index(n=4000)
+    arr = ix.arrays()
+    e2 = oracle.eps2(ix.K, ix.L)
+    trees = [ix.tree(t) for t in range(ix.L)]
+    for q in Q[:4]:
+        dist = np.sqrt(((X.astype(np.float64) - q.astype(np.float64)) ** 2).sum(1))
+        d2 = _proj_dist2(ix, arr, 0, q)
+        for frac in (0.001, 0.01):
+            r = float(np.sqrt(np.quantile(d2.astype(np.float64), frac) / e2))
+            R2 = np.float32(e2 * r * r)
+            for beta in (0.005, 0.05):
+                need = int(np.ceil(beta * ix.n)) + 1
+                inS = np.zeros(ix.n, bool)
+                stop = -1
+                for t in range(ix.L):
+                    inS |= ix.leaf_lb2(t, q)[trees[t]["leaf_of"]] <= R2
+                    if inS.sum() >= need:
+                        stop = t
+                        break
+                got = ix.rc_ann(q, r, beta=beta, optimised=True)
+                assert got["tree_stop"] == stop
+                assert np.array_equal(np.sort(got["S"]), np.nonzero(inS)[0])
+                exact = ix.rc_ann(q, r, beta=beta)
+                if exact["tree_stop"] < 0 and stop < 0:
+                    assert set(exact["S"].tolist()) <= set(got["S"].tolist())
+                S = got["S"]
+                if S.size and (stop >= 0 or dist[S].min() <= 1.5 * r):
+                    assert got["id"] == S[np.lexsort((S, dist[S]))[0]]
