@@ -46,6 +46,8 @@ struct detlsh_index {
   uint8_t *leaf_lo = nullptr, *leaf_hi = nullptr, *leaf_nb = nullptr;
   uint8_t *blk_lo = nullptr, *blk_hi = nullptr;  // hulls of LEAF_BLOCK-leaf runs
   int64_t blk_off[17] = {0};
+  uint8_t *sblk_lo = nullptr, *sblk_hi = nullptr;  // hulls of LEAF_BLOCK-hull runs
+  int64_t sblk_off[17] = {0};
   cudaEvent_t ev[8] = {nullptr};
   detlsh_timings timings{};
   std::vector<void *> owned;
@@ -569,6 +571,19 @@ int build_impl(detlsh_index *ix, const float *data, cudaStream_t st, const detls
     DL_TRY(block_hulls(ix->leaf_lo + ix->leaf_off[t] * 16, ix->leaf_hi + ix->leaf_off[t] * 16,
                        ix->nleaves[t], ix->blk_lo + ix->blk_off[t] * 16,
                        ix->blk_hi + ix->blk_off[t] * 16, st));
+  // and hulls of runs of LEAF_BLOCK hulls (LEAF_BLOCK^2 leaves)
+  int64_t ts = 0;
+  for (int t = 0; t < L; ++t) {
+    ix->sblk_off[t] = ts;
+    ts += ceil_div(ix->blk_off[t + 1] - ix->blk_off[t], LEAF_BLOCK);
+  }
+  for (int t = L; t <= 16; ++t) ix->sblk_off[t] = ts;
+  DL_TRY(dalloc(ix, &ix->sblk_lo, (size_t)ts * 16, st));
+  DL_TRY(dalloc(ix, &ix->sblk_hi, (size_t)ts * 16, st));
+  for (int t = 0; t < L; ++t)
+    DL_TRY(block_hulls(ix->blk_lo + ix->blk_off[t] * 16, ix->blk_hi + ix->blk_off[t] * 16,
+                       ix->blk_off[t + 1] - ix->blk_off[t], ix->sblk_lo + ix->sblk_off[t] * 16,
+                       ix->sblk_hi + ix->sblk_off[t] * 16, st));
   DL_CUDA(cudaEventRecord(ix->ev[4], st));
   DL_CUDA(cudaStreamSynchronize(st));
   ix->fb_total = (int64_t)fbt;
@@ -615,6 +630,8 @@ QueryIndexView view_of(const detlsh_index *ix) {
   v.leaf_lo = ix->leaf_lo; v.leaf_hi = ix->leaf_hi; v.leaf_of = ix->leaf_of;
   v.blk_lo = ix->blk_lo; v.blk_hi = ix->blk_hi;
   for (int t = 0; t <= 16; ++t) v.blk_off[t] = ix->blk_off[t];
+  v.sblk_lo = ix->sblk_lo; v.sblk_hi = ix->sblk_hi;
+  for (int t = 0; t <= 16; ++t) v.sblk_off[t] = ix->sblk_off[t];
   for (int t = 0; t <= 16; ++t) v.leaf_off[t] = t <= ix->L ? ix->leaf_off[t] : ix->leaf_off[ix->L];
   v.max_leaves = ix->max_leaves;
   v.max_leaf_size = ix->max_leaf;

@@ -103,6 +103,8 @@ struct QueryIndexView {
   const uint8_t *blk_lo, *blk_hi;  // [total_blocks][16] hulls of LEAF_BLOCK leaves
   int64_t leaf_off[17];      // leaf index offset of each tree (prefix)
   int64_t blk_off[17];       // block index offset of each tree (prefix)
+  const uint8_t *sblk_lo, *sblk_hi;  // [total_sblocks][16] hulls of LEAF_BLOCK blocks
+  int64_t sblk_off[17];      // super-block index offset of each tree (prefix)
   int64_t max_leaves;        // max leaves of one tree
   int64_t max_leaf_size;
 };

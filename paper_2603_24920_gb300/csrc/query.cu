@@ -309,9 +309,31 @@ __device__ __forceinline__ void expand_levels(QCtx &c) {
     const uint4 *hlo = reinterpret_cast<const uint4 *>(ix.blk_lo) + ix.blk_off[t];
     const uint4 *hhi = reinterpret_cast<const uint4 *>(ix.blk_hi) + ix.blk_off[t];
     uint8_t *blev = c.s.blev + ix.blk_off[t];
-    if (threadIdx.x == 0) sm.n_blocks += (unsigned long long)nb;
-    for (int64_t b0 = 0; b0 < nb; b0 += QT) {  // uniform trip count for the warp collectives
-      const int64_t b = b0 + threadIdx.x;
+    // Once a bound J0 is known (every tree after the first), the hulls of
+    // runs of LEAF_BLOCK hulls prune the hull scan: a run whose hull lies
+    // beyond T[J0] holds no hull, leaf or point within it.  The scan then
+    // covers the hulls of the listed runs (listed in the cut-count array,
+    // free until the cut).
+    const bool prune = J0 < (uint32_t)(NLEV - 1);
+    uint32_t *slist = c.s.cval;
+    int64_t nscan = nb;
+    if (prune) {
+      const int64_t ns = ix.sblk_off[t + 1] - ix.sblk_off[t];
+      const uint4 *slo = reinterpret_cast<const uint4 *>(ix.sblk_lo) + ix.sblk_off[t];
+      const uint4 *shi = reinterpret_cast<const uint4 *>(ix.sblk_hi) + ix.sblk_off[t];
+      if (threadIdx.x == 0) { sm.cpos = 0; sm.n_blocks += (unsigned long long)ns; }
+      __syncthreads();
+      for (int64_t u = threadIdx.x; u < ns; u += QT)
+        if (box_lb2(c.lut, slo[u], shi[u]) <= sm.T[J0]) slist[atomicAdd(&sm.cpos, 1u)] = (uint32_t)u;
+      __syncthreads();
+      nscan = (int64_t)sm.cpos * LEAF_BLOCK;
+    }
+    auto blk = [&](int64_t i) -> int64_t {  // i-th hull of the scan
+      return prune ? (int64_t)slist[i / LEAF_BLOCK] * LEAF_BLOCK + (i % LEAF_BLOCK) : i;
+    };
+    for (int64_t b0 = 0; b0 < nscan; b0 += QT) {  // uniform trip count for the warp collectives
+      const int64_t i = b0 + threadIdx.x;
+      const int64_t b = i < nscan ? blk(i) : nb;
       uint32_t lv = 255u;
       if (b < nb) {
         // level <= J0 exactly when LB^2 <= T[J0]; only those need their level
@@ -320,6 +342,8 @@ __device__ __forceinline__ void expand_levels(QCtx &c) {
         blev[b] = (uint8_t)lv;
         if (lv <= J0) atomicMin(&sm.jcur, (int)lv);
       }
+      const unsigned vm = __ballot_sync(FULL, b < nb);
+      if ((threadIdx.x & 31) == 0) atomicAdd(&sm.n_blocks, (unsigned long long)__popc(vm));
       warp_bin_count(sm.rh, b < nb && lv <= J0, lv, 1u);
     }
     __syncthreads();
@@ -338,8 +362,10 @@ __device__ __forceinline__ void expand_levels(QCtx &c) {
       for (int i = 0; i < 8; ++i) { sm.bstart[lane * 8 + i] = acc; acc += v[i]; }
     }
     __syncthreads();
-    // bucket the blocks by level (ids in border[bstart[lv] ...])
-    for (int64_t b = threadIdx.x; b < nb; b += QT) {
+    // bucket the scanned blocks by level (ids in border[bstart[lv] ...])
+    for (int64_t i = threadIdx.x; i < nscan; i += QT) {
+      const int64_t b = blk(i);
+      if (b >= nb) continue;
       const uint32_t lv = blev[b];
       if (lv <= J0) {
         const uint32_t pos = atomicAdd(&sm.bstart[lv], 1u);
