@@ -98,6 +98,7 @@ struct QShared {
   uint32_t cpos;
   int jchk;
   float qn;  // |q|^2 of the BF16 query
+  int jguess, crossed;  // bound guessed from this CTA's previous query; tree crossed tau
 };
 static_assert(KMAX >= 1024, "the flattened visit borrows the top-k arrays");
 
@@ -296,12 +297,19 @@ __device__ __forceinline__ void expand_levels(QCtx &c) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const float *qp = c.qa.Qp + c.qi * ix.LK;
   const unsigned long long ep = sm.epoch;
-  if (threadIdx.x == 0) sm.jhi = NLEV - 1;
+  // The first tree starts from a guessed bound (this CTA's previous final
+  // bound plus a margin) so that the second hull level can prune its scan as
+  // well.  If the tree does not reach beta*n + k within the guess, it is
+  // expanded again without one; either way every leaf at or below its
+  // crossing level is listed and counted, so the results do not depend on it.
+  if (threadIdx.x == 0) sm.jhi = min(NLEV - 1, sm.jguess + 3);
   __syncthreads();
   for (int t = 0; t < ix.L; ++t) {
     build_lut(c.lut, ix.B, qp + t * K, t, K, NR1);
     sm.rh[threadIdx.x] = 0;
-    if (threadIdx.x == 0) { sm.nlist[t] = 0; sm.cum = 0; sm.stop = 0; sm.jcur = NLEV; }
+    if (threadIdx.x == 0) {
+      sm.nlist[t] = 0; sm.cum = 0; sm.stop = 0; sm.jcur = NLEV; sm.crossed = 0;
+    }
     __syncthreads();
     const uint32_t J0 = (uint32_t)sm.jhi;
     const int64_t nb = ix.blk_off[t + 1] - ix.blk_off[t];
@@ -425,7 +433,7 @@ __device__ __forceinline__ void expand_levels(QCtx &c) {
         int j = sm.jchk;
         for (; j < jnext && j <= sm.jhi; ++j) {
           sm.cum += hist_t[j];
-          if (sm.cum >= (uint64_t)c.tau) { sm.jhi = j; sm.stop = 1; break; }
+          if (sm.cum >= (uint64_t)c.tau) { sm.jhi = j; sm.stop = 1; sm.crossed = 1; break; }
         }
         sm.jchk = j;  // first level not yet added
         if (jnext > sm.jhi || p1c >= nsel) sm.stop = 1;
@@ -435,7 +443,16 @@ __device__ __forceinline__ void expand_levels(QCtx &c) {
       if (sm.stop) break;
     }
     __syncthreads();
+    if (t == 0 && !sm.crossed && J0 < (uint32_t)(NLEV - 1)) {
+      // the guessed bound was too low: expand the first tree again without it
+      for (int i = threadIdx.x; i < 256; i += QT) hist_t[i] = 0;
+      if (threadIdx.x == 0) sm.jhi = NLEV - 1;
+      __syncthreads();
+      t = -1;
+      continue;
+    }
   }
+  if (threadIdx.x == 0) sm.jguess = sm.jhi;
 }
 
 // ---- step 1b: shared-memory table of the levels at or below the bound ----
@@ -1353,7 +1370,7 @@ __global__ void __launch_bounds__(QT, 5) k_query(QueryIndexView ix, QueryArgs qa
   s.rkey = reinterpret_cast<uint32_t *>(base + qa.off[10]);
   s.cm = base + qa.off[11];
   for (int i = threadIdx.x; i < 256; i += QT) sm.T[i] = i < NLEV ? qa.T[i] : __int_as_float(0x7f800000);
-  if (threadIdx.x == 0) { sm.n_blocks = 0; sm.n_leaves = 0; sm.n_visit = 0; }
+  if (threadIdx.x == 0) { sm.n_blocks = 0; sm.n_leaves = 0; sm.n_visit = 0; sm.jguess = NLEV - 1; }
   __syncthreads();
 
   while (true) {
