@@ -511,6 +511,7 @@ int build_impl(detlsh_index *ix, const float *data, cudaStream_t st, const detls
   DL_TRY(tp.get(&tt.block_counts, sample_blocks(n) + 4));
   DL_TRY(tp.get(&tt.tmp_begin, (size_t)n));
   DL_TRY(tp.get(&tt.tmp_box, (size_t)n * 48));
+  DL_TRY(tp.get(&tt.lists, (size_t)n * 4));
   DL_TRY(tp.get(&tt.leaf_base, (size_t)n));
   DL_TRY(tp.get(&tt.scalars, 8));
   tt.sort = srt;

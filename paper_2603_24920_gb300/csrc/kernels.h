@@ -73,8 +73,9 @@ struct TreeTemp {
   uint4 *codesA = nullptr, *codesB = nullptr;
   uint32_t *idsB = nullptr;
   uint32_t *node_begin = nullptr, *node_count = nullptr, *block_counts = nullptr;
-  uint32_t *tmp_begin = nullptr;
-  uint8_t *tmp_box = nullptr;  // [n][48]: lo, hi, nb
+  uint32_t *tmp_begin = nullptr;  // [n] leaf start flags
+  uint8_t *tmp_box = nullptr;  // [n][48]: lo, hi, nb of the leaf starting there
+  uint4 *lists = nullptr;      // [2n][2]: the open nodes of two levels
   uint32_t *leaf_base = nullptr;
   uint32_t *scalars = nullptr;
   SortTemp sort;

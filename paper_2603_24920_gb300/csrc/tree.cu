@@ -7,12 +7,15 @@
 // before child 1; points inside a leaf in ascending id order.
 //
 // Build: (1) stable radix sort of the point ids by their K-bit first-layer
-// key (the root's 2^K children); (2) one CTA per non-empty first-layer node
-// builds that node's binary subtree depth-first, choosing at every node the
-// dimension that splits it most evenly and stably partitioning the node's
-// range between two ping-pong buffers (first-layer subtrees are independent,
-// as the paper's parallel indexing phase notes in Sec. IV-B); (3) leaves are
-// numbered by a scan over first-layer nodes and written out in order.
+// key (the root's 2^K children); (2) the subtrees of the first-layer nodes,
+// level by level: a CTA takes the first-layer nodes that start in its range
+// of points (first-layer subtrees are independent, as the paper's parallel
+// indexing phase notes in Sec. IV-B) and, at each level, its warps take the
+// open nodes one each, choosing the dimension that splits a node most evenly
+// and stably partitioning its range between two ping-pong buffers; a leaf is
+// recorded at the position where its points start; (3) leaves are numbered
+// by a scan over first-layer nodes and written out in position order, which
+// is depth-first order (child 0 holds the lower part of its parent's range).
 //
 // Reading of Alg. 2 (insertion order and max_size are left open): a node is
 // split iff it holds more than max_size points and some dimension has prefix
@@ -27,8 +30,6 @@
 
 namespace dl {
 
-constexpr int TB_THREADS = 256;
-constexpr int TB_STACK = 128;  // > K * (bits - 1) + 1 for K <= 16, bits <= 8
 
 __global__ void k_first_keys(const uint8_t *__restrict__ codes, int64_t n, int K, int bbits,
                              uint32_t *keys, uint32_t *vals) {
@@ -63,229 +64,186 @@ __device__ __forceinline__ uint32_t code_byte(const uint4 &c, int j) {
   return (w >> (8 * (j & 3))) & 255u;
 }
 
-struct StackEntry {
-  uint32_t b, e;
-  uint8_t nb[16];
-  uint32_t par;
+struct NodeEntry {
+  uint32_t b, e, par, f;  // range, buffer holding it, first-layer node
+  uint4 nb;               // prefix length per dimension, one byte each
 };
 
 struct SubtreeArgs {
   int64_t n;
   int K, bbits, M, box_mode;
+  uint32_t F;
   const uint32_t *node_begin;  // [F+1]
   uint4 *codesA, *codesB;
   uint32_t *idsA, *idsB;
   uint32_t *perm;
-  uint32_t *node_count;        // leaves per first-layer node
-  uint32_t *tmp_begin;         // [n] leaf begin by slot
-  uint8_t *tmp_box;            // [n][48]
+  uint32_t *node_count;        // leaves per first-layer node (zeroed)
+  uint32_t *leaf_flag;         // [n] 1 where a leaf starts (zeroed)
+  uint8_t *tmp_box;            // [n][48] box of the leaf starting there
+  NodeEntry *listA, *listB;    // [n] each: open nodes of a level
   int *err;
 };
 
+constexpr int TB_THREADS = 256;
+constexpr int TB_WARPS = TB_THREADS / 32;
+constexpr int TB_POINTS = 2048;  // first-layer nodes starting in a CTA's range of points
+
 __global__ void __launch_bounds__(TB_THREADS) k_subtree(SubtreeArgs a) {
-  __shared__ StackEntry stk[TB_STACK];
-  __shared__ int sp;
-  __shared__ uint32_t nleaf;
-  __shared__ uint32_t wpart[TB_THREADS / 32][16];
-  __shared__ uint32_t n1s[16];
-  __shared__ int split_dim, degenerate;
-  __shared__ StackEntry cur;
-  __shared__ uint32_t wz[TB_THREADS / 32], wo[TB_THREADS / 32];
-  __shared__ uint32_t boxv[2][16];
-
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  __shared__ uint32_t ncur, nnext, f_lo, f_hi;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int K = a.K, bb = a.bbits;
-  const uint32_t b0 = a.node_begin[blockIdx.x], e0 = a.node_begin[blockIdx.x + 1];
-
-  if (tid == 0) {
-    StackEntry r;
-    r.b = b0; r.e = e0; r.par = 0;
-    for (int j = 0; j < 16; ++j) r.nb[j] = j < K ? 1 : (uint8_t)bb;
-    stk[0] = r;
-    sp = 1;
-    nleaf = 0;
+  const unsigned lt = (1u << lane) - 1u;
+  const uint32_t P0 = blockIdx.x * (uint32_t)TB_POINTS;
+  if (threadIdx.x == 0) {  // first-layer nodes f with node_begin[f] in [P0, P0 + TB_POINTS)
+    uint32_t lo = 0, hi = a.F;
+    while (lo < hi) { const uint32_t mid = (lo + hi) >> 1; if (a.node_begin[mid] < P0) lo = mid + 1; else hi = mid; }
+    f_lo = lo;
+    hi = a.F;
+    while (lo < hi) {
+      const uint32_t mid = (lo + hi) >> 1;
+      if (a.node_begin[mid] < P0 + (uint32_t)TB_POINTS) lo = mid + 1; else hi = mid;
+    }
+    f_hi = lo;
+    ncur = f_hi - f_lo;
   }
   __syncthreads();
-
-  while (true) {
-    if (tid == 0) {
-      if (sp > 0) cur = stk[--sp];
-      else cur.e = cur.b;  // signals done with b == e below (never a real node)
-    }
+  if (ncur == 0) return;
+  // this CTA's lists live at the positions of its points: nodes of a level
+  // are disjoint and non-empty, so a level never holds more of them
+  const uint32_t lbase = a.node_begin[f_lo];
+  NodeEntry *cur = a.listA + lbase, *nxt = a.listB + lbase;
+  uint32_t root_nb[4] = {0u, 0u, 0u, 0u};
+  for (int j = 0; j < 16; ++j) root_nb[j >> 2] |= (uint32_t)(j < K ? 1 : bb) << (8 * (j & 3));
+  for (uint32_t f = f_lo + threadIdx.x; f < f_hi; f += TB_THREADS) {
+    NodeEntry r;
+    r.b = a.node_begin[f]; r.e = a.node_begin[f + 1]; r.par = 0; r.f = f;
+    r.nb = make_uint4(root_nb[0], root_nb[1], root_nb[2], root_nb[3]);
+    cur[f - f_lo] = r;
+  }
+  __syncthreads();
+  while (ncur > 0) {  // one level per pass
+    if (threadIdx.x == 0) nnext = 0;
     __syncthreads();
-    const uint32_t b = cur.b, e = cur.e, par = cur.par;
-    if (e <= b) break;  // uniform
-    const uint32_t cnt = e - b;
-    const uint4 *src = par ? a.codesB : a.codesA;
-    const uint32_t *srcid = par ? a.idsB : a.idsA;
-
-    bool eligible_any = false;
-    for (int j = 0; j < K; ++j) eligible_any |= cur.nb[j] < bb;
-
-    if (cnt > (uint32_t)a.M && eligible_any) {
-      // count the next bit of every dimension with bits left
-      uint32_t c1[16], shj[16];
-      uint32_t elig = 0;
+    const uint32_t nc = ncur;
+    for (uint32_t i = w; i < nc; i += TB_WARPS) {
+      const NodeEntry ent = cur[i];
+      const uint32_t b = ent.b, e = ent.e, par = ent.par;
+      const uint4 nbv = ent.nb;
+      const uint32_t cnt = e - b;
+      const uint4 *src = par ? a.codesB : a.codesA;
+      const uint32_t *srcid = par ? a.idsB : a.idsA;
+      bool eligible_any = false;
+      for (int j = 0; j < K; ++j) eligible_any |= (int)code_byte(nbv, j) < bb;
+      if (cnt > (uint32_t)a.M && eligible_any) {
+        uint32_t c1[16];
 #pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        c1[j] = 0;
-        const bool el = j < K && cur.nb[j] < bb;
-        elig |= (el ? 1u : 0u) << j;
-        shj[j] = el ? (uint32_t)(bb - 1 - cur.nb[j]) : 0u;
-      }
-      for (uint32_t i = b + tid; i < e; i += TB_THREADS) {
-        const uint4 c = src[i];
+        for (int j = 0; j < 16; ++j) c1[j] = 0u;
+        for (uint32_t x = b + lane; x < e; x += 32) {
+          const uint4 c = src[x];
 #pragma unroll
-        for (int j = 0; j < 16; ++j)
-          if (elig & (1u << j)) c1[j] += (code_byte(c, j) >> shj[j]) & 1u;
-      }
-#pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        uint32_t v = c1[j];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
-        if (lane == 0) wpart[warp][j] = v;
-      }
-      __syncthreads();
-      if (tid < 16) {
-        uint32_t v = 0;
-        for (int w = 0; w < TB_THREADS / 32; ++w) v += wpart[w][tid];
-        n1s[tid] = v;
-      }
-      __syncthreads();
-      if (tid == 0) {
+          for (int j = 0; j < 16; ++j) {
+            const int nbj = (int)code_byte(nbv, j);
+            if (j < K && nbj < bb) c1[j] += (code_byte(c, j) >> (bb - 1 - nbj)) & 1u;
+          }
+        }
+        // most even split, ties to the smallest dimension
         int best = -1;
         int64_t bestd = 0;
-        for (int j = 0; j < K; ++j) {
-          if (cur.nb[j] >= bb) continue;
-          int64_t dd = (int64_t)cnt - 2 * (int64_t)n1s[j];
-          if (dd < 0) dd = -dd;
-          if (best < 0 || dd < bestd) { best = j; bestd = dd; }
+        uint32_t n1 = 0;
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const uint32_t v = __reduce_add_sync(FULL, c1[j]);
+          if (j < K && (int)code_byte(nbv, j) < bb) {
+            int64_t dd = (int64_t)cnt - 2 * (int64_t)v;
+            if (dd < 0) dd = -dd;
+            if (best < 0 || dd < bestd) { best = j; bestd = dd; n1 = v; }
+          }
         }
-        split_dim = best;
-        degenerate = (n1s[best] == 0u || n1s[best] == cnt);
-        if (degenerate) {
+        uint32_t wv[4] = {nbv.x, nbv.y, nbv.z, nbv.w};
+        const uint32_t nbbest = code_byte(nbv, best);
+        wv[best >> 2] += 1u << (8 * (best & 3));  // one more prefix bit in the split dimension
+        const uint4 nbc = make_uint4(wv[0], wv[1], wv[2], wv[3]);
+        if (n1 == 0u || n1 == cnt) {
           // one side empty: the only child has the same points, one more bit
-          StackEntry ch = cur;
-          ch.nb[best] = (uint8_t)(cur.nb[best] + 1);
-          if (sp < TB_STACK) stk[sp++] = ch;
-          else atomicExch(a.err, (int)DETLSH_ERR_CAPACITY);
+          if (lane == 0) {
+            NodeEntry ch = ent;
+            ch.nb = nbc;
+            nxt[atomicAdd(&nnext, 1u)] = ch;
+          }
+          continue;
+        }
+        const uint32_t n0 = cnt - n1;
+        const uint32_t sh = (uint32_t)(bb - 1) - nbbest;
+        uint4 *dst = par ? a.codesA : a.codesB;
+        uint32_t *dstid = par ? a.idsA : a.idsB;
+        uint32_t zrun = 0, orun = 0;
+        for (uint32_t base = b; base < e; base += 32) {
+          const uint32_t x = base + lane;
+          const bool valid = x < e;
+          uint4 c = make_uint4(0, 0, 0, 0);
+          uint32_t id = 0, bit = 0;
+          if (valid) { c = src[x]; id = srcid[x]; bit = (code_byte(c, best) >> sh) & 1u; }
+          const unsigned ones = __ballot_sync(FULL, valid && bit);
+          const unsigned zeros = __ballot_sync(FULL, valid && !bit);
+          if (valid) {
+            const uint32_t pos = bit ? (b + n0 + orun + __popc(ones & lt)) : (b + zrun + __popc(zeros & lt));
+            dst[pos] = c;
+            dstid[pos] = id;
+          }
+          zrun += __popc(zeros);
+          orun += __popc(ones);
+        }
+        if (lane == 0) {
+          const uint32_t q = atomicAdd(&nnext, 2u);
+          NodeEntry c0 = ent, c1e = ent;
+          c0.nb = c1e.nb = nbc;
+          c0.par = c1e.par = par ^ 1u;
+          c0.e = b + n0;
+          c1e.b = b + n0;
+          nxt[q] = c0;
+          nxt[q + 1] = c1e;
+        }
+        continue;
+      }
+      // ---- leaf: ids to perm, box and flag at the leaf's first position ----
+      for (uint32_t x = b + lane; x < e; x += 32) a.perm[x] = srcid[x];
+      uint32_t lo = 255u, hi = 0u;
+      if (a.box_mode == DETLSH_BOX_TIGHT) {  // lane j < 16 gathers dimension j
+        for (uint32_t x = b; x < e; ++x) {
+          const uint32_t v = code_byte(src[x], lane & 15);
+          lo = min(lo, v);
+          hi = max(hi, v);
         }
       }
-      __syncthreads();
-      if (degenerate) continue;
-      const int js = split_dim;
-      const uint32_t n0 = cnt - n1s[js];
-      const uint32_t sh = (uint32_t)(bb - 1 - cur.nb[js]);
-      uint4 *dst = par ? a.codesA : a.codesB;
-      uint32_t *dstid = par ? a.idsA : a.idsB;
-      uint32_t zrun = 0, orun = 0;
-      const unsigned lt = (1u << lane) - 1u;
-      for (uint32_t base = b; base < e; base += TB_THREADS) {
-        const uint32_t i = base + tid;
-        const bool valid = i < e;
-        uint4 c = make_uint4(0, 0, 0, 0);
-        uint32_t id = 0, bit = 0;
-        if (valid) { c = src[i]; id = srcid[i]; bit = (code_byte(c, js) >> sh) & 1u; }
-        const unsigned ones = __ballot_sync(FULL, valid && bit);
-        const unsigned zeros = __ballot_sync(FULL, valid && !bit);
-        if (lane == 0) { wz[warp] = __popc(zeros); wo[warp] = __popc(ones); }
-        __syncthreads();
-        uint32_t zb = 0, ob = 0, zt = 0, ot = 0;
-        for (int w = 0; w < TB_THREADS / 32; ++w) {
-          if (w < warp) { zb += wz[w]; ob += wo[w]; }
-          zt += wz[w]; ot += wo[w];
+      if (lane < 16) {
+        uint8_t blo = 0, bhi = 0;
+        if (lane < K) {
+          const uint32_t freeb = (uint32_t)bb - code_byte(nbv, lane);
+          const uint32_t pre = code_byte(src[b], lane) >> freeb;
+          blo = (uint8_t)(pre << freeb);
+          bhi = (uint8_t)((pre << freeb) + (1u << freeb) - 1u);
+          if (a.box_mode == DETLSH_BOX_TIGHT) { blo = (uint8_t)lo; bhi = (uint8_t)hi; }
         }
-        if (valid) {
-          const uint32_t pos = bit ? (b + n0 + orun + ob + __popc(ones & lt))
-                                   : (b + zrun + zb + __popc(zeros & lt));
-          dst[pos] = c;
-          dstid[pos] = id;
-        }
-        zrun += zt;
-        orun += ot;
-        __syncthreads();
+        a.tmp_box[(int64_t)b * 48 + lane] = blo;
+        a.tmp_box[(int64_t)b * 48 + 16 + lane] = bhi;
+        a.tmp_box[(int64_t)b * 48 + 32 + lane] = lane < K ? (uint8_t)code_byte(nbv, lane) : 0;
       }
-      if (tid == 0) {
-        StackEntry c0 = cur, c1e = cur;
-        c0.nb[js] = c1e.nb[js] = (uint8_t)(cur.nb[js] + 1);
-        c0.par = c1e.par = par ^ 1u;
-        c0.e = b + n0;
-        c1e.b = b + n0;
-        // child 1 below child 0: DFS visits child 0 first.  Depth is bounded
-        // by K*(bits-1)+1 < TB_STACK; the guard only reports, never overflows.
-        if (sp + 2 > TB_STACK) {
-          atomicExch(a.err, (int)DETLSH_ERR_CAPACITY);
-        } else {
-          if (c1e.e > c1e.b) stk[sp++] = c1e;
-          if (c0.e > c0.b) stk[sp++] = c0;
-        }
-      }
-      __syncthreads();
-      continue;
-    }
-
-    // ---- leaf: ids to perm, box to the slot of this first-layer node ----
-    for (uint32_t i = b + tid; i < e; i += TB_THREADS) a.perm[i] = srcid[i];
-    const uint32_t slot = b0 + nleaf;
-    __syncthreads();  // every thread has read nleaf before thread 0 advances it
-    if (a.box_mode == DETLSH_BOX_TIGHT) {
-      uint32_t mn[16], mx[16];
-#pragma unroll
-      for (int j = 0; j < 16; ++j) { mn[j] = 255u; mx[j] = 0u; }
-      for (uint32_t i = b + tid; i < e; i += TB_THREADS) {
-        const uint4 c = src[i];
-#pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          const uint32_t v = code_byte(c, j);
-          mn[j] = min(mn[j], v);
-          mx[j] = max(mx[j], v);
-        }
-      }
-#pragma unroll
-      for (int j = 0; j < 16; ++j) {
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          mn[j] = min(mn[j], __shfl_xor_sync(FULL, mn[j], o));
-          mx[j] = max(mx[j], __shfl_xor_sync(FULL, mx[j], o));
-        }
-      }
-      if (tid < 16) { boxv[0][tid] = 255u; boxv[1][tid] = 0u; }
-      __syncthreads();
       if (lane == 0) {
-        for (int j = 0; j < 16; ++j) {
-          atomicMin(&boxv[0][j], mn[j]);
-          atomicMax(&boxv[1][j], mx[j]);
-        }
+        a.leaf_flag[b] = 1u;
+        atomicAdd(&a.node_count[ent.f], 1u);
       }
-      __syncthreads();
     }
-    if (tid < 16) {
-      uint8_t lo = 0, hi = 0;
-      if (tid < K) {
-        const uint32_t freeb = (uint32_t)(bb - cur.nb[tid]);
-        const uint32_t pre = code_byte(src[b], tid) >> freeb;
-        lo = (uint8_t)(pre << freeb);
-        hi = (uint8_t)((pre << freeb) + (1u << freeb) - 1u);
-        if (a.box_mode == DETLSH_BOX_TIGHT) { lo = (uint8_t)boxv[0][tid]; hi = (uint8_t)boxv[1][tid]; }
-      }
-      a.tmp_box[(int64_t)slot * 48 + tid] = lo;
-      a.tmp_box[(int64_t)slot * 48 + 16 + tid] = hi;
-      a.tmp_box[(int64_t)slot * 48 + 32 + tid] = tid < K ? cur.nb[tid] : 0;
-    }
-    if (tid == 0) {
-      a.tmp_begin[slot] = b;
-      nleaf = nleaf + 1;
-    }
+    __syncthreads();  // this level's partitions and children are complete
+    if (threadIdx.x == 0) ncur = nnext;
+    NodeEntry *t = cur; cur = nxt; nxt = t;
     __syncthreads();
   }
-  if (tid == 0) a.node_count[blockIdx.x] = nleaf;
 }
 
 struct LeafWriteArgs {
   int64_t n;
   int L, t;
-  const uint32_t *node_begin, *node_count, *leaf_base, *tmp_begin, *perm;
+  const uint32_t *node_begin, *leaf_base, *leaf_flag, *perm;
   const uint8_t *tmp_box;
   uint32_t *leaf_begin;
   uint8_t *leaf_lo, *leaf_hi, *leaf_nb;
@@ -293,31 +251,39 @@ struct LeafWriteArgs {
   uint32_t *max_leaf;
 };
 
-// One warp per first-layer node: number its leaves, copy their records and
-// write leaf_of for their points.
+// One warp per first-layer node: its leaves in position order (= depth-first
+// order), numbered from the node's base; records copied, leaf_of written.
 __global__ void k_leaf_write(LeafWriteArgs a, int64_t F) {
   const int64_t f = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (f >= F) return;
   const uint32_t nb0 = a.node_begin[f], ne = a.node_begin[f + 1];
-  const uint32_t cnt = a.node_count[f], base = a.leaf_base[f];
-  for (uint32_t l = 0; l < cnt; ++l) {
-    const uint32_t slot = nb0 + l;
-    const uint32_t g = base + l;
-    const uint32_t lb = a.tmp_begin[slot];
-    const uint32_t le = (l + 1 < cnt) ? a.tmp_begin[slot + 1] : ne;
+  uint32_t g = a.leaf_base[f];
+  auto emit = [&](uint32_t lb, uint32_t le) {
     if (lane < 16) {
-      a.leaf_lo[(int64_t)g * 16 + lane] = a.tmp_box[(int64_t)slot * 48 + lane];
-      a.leaf_hi[(int64_t)g * 16 + lane] = a.tmp_box[(int64_t)slot * 48 + 16 + lane];
-      a.leaf_nb[(int64_t)g * 16 + lane] = a.tmp_box[(int64_t)slot * 48 + 32 + lane];
+      a.leaf_lo[(int64_t)g * 16 + lane] = a.tmp_box[(int64_t)lb * 48 + lane];
+      a.leaf_hi[(int64_t)g * 16 + lane] = a.tmp_box[(int64_t)lb * 48 + 16 + lane];
+      a.leaf_nb[(int64_t)g * 16 + lane] = a.tmp_box[(int64_t)lb * 48 + 32 + lane];
     }
     if (lane == 0) {
       a.leaf_begin[g] = lb;
       atomicMax(a.max_leaf, le - lb);
     }
-    for (uint32_t i = lb + lane; i < le; i += 32)
-      a.leaf_of[(int64_t)a.perm[i] * a.L + a.t] = g;
+    for (uint32_t i = lb + lane; i < le; i += 32) a.leaf_of[(int64_t)a.perm[i] * a.L + a.t] = g;
+    ++g;
+  };
+  int64_t pend = -1;  // a leaf start whose end is the next start
+  for (uint32_t c0 = nb0; c0 < ne; c0 += 32) {
+    const uint32_t p = c0 + lane;
+    unsigned m = __ballot_sync(FULL, p < ne && a.leaf_flag[p] != 0u);
+    while (m) {
+      const uint32_t st = c0 + (uint32_t)(__ffs(m) - 1);
+      m &= m - 1u;
+      if (pend >= 0) emit((uint32_t)pend, st);
+      pend = st;
+    }
   }
+  if (pend >= 0) emit((uint32_t)pend, ne);
 }
 
 __global__ void k_set_u32(uint32_t *p, uint32_t v) { *p = v; }
@@ -382,15 +348,20 @@ int build_tree(const TreeBuildArgs &A, TreeTemp &T, int64_t *nleaves, int64_t *m
   dl_count_launch();
   SubtreeArgs sa;
   sa.n = n; sa.K = A.K; sa.bbits = A.bbits; sa.M = A.M; sa.box_mode = A.box_mode;
+  sa.F = F;
   sa.node_begin = T.node_begin;
   sa.codesA = T.codesA; sa.codesB = T.codesB;
   sa.idsA = T.vals; sa.idsB = T.idsB;
   sa.perm = A.perm;
   sa.node_count = T.node_count;
-  sa.tmp_begin = T.tmp_begin;
+  sa.leaf_flag = T.tmp_begin;
   sa.tmp_box = T.tmp_box;
+  sa.listA = reinterpret_cast<NodeEntry *>(T.lists);
+  sa.listB = reinterpret_cast<NodeEntry *>(T.lists) + n;
   sa.err = reinterpret_cast<int *>(T.scalars + 2);
-  k_subtree<<<F, TB_THREADS, 0, st>>>(sa);
+  DL_CUDA(cudaMemsetAsync(T.node_count, 0, sizeof(uint32_t) * F, st));
+  DL_CUDA(cudaMemsetAsync(T.tmp_begin, 0, sizeof(uint32_t) * (size_t)n, st));
+  k_subtree<<<(unsigned)ceil_div(n, TB_POINTS), TB_THREADS, 0, st>>>(sa);
   dl_count_launch();
   DL_CUDA(cudaGetLastError());
   // leaf numbering
@@ -401,8 +372,8 @@ int build_tree(const TreeBuildArgs &A, TreeTemp &T, int64_t *nleaves, int64_t *m
   DL_CUDA(cudaMemsetAsync(T.scalars + 3, 0, sizeof(uint32_t), st));
   LeafWriteArgs lw;
   lw.n = n; lw.L = A.L; lw.t = A.t;
-  lw.node_begin = T.node_begin; lw.node_count = T.node_count; lw.leaf_base = T.leaf_base;
-  lw.tmp_begin = T.tmp_begin; lw.perm = A.perm; lw.tmp_box = T.tmp_box;
+  lw.node_begin = T.node_begin; lw.leaf_base = T.leaf_base; lw.leaf_flag = T.tmp_begin;
+  lw.perm = A.perm; lw.tmp_box = T.tmp_box;
   lw.leaf_begin = A.leaf_begin; lw.leaf_lo = A.leaf_lo; lw.leaf_hi = A.leaf_hi;
   lw.leaf_nb = A.leaf_nb; lw.leaf_of = A.leaf_of; lw.max_leaf = T.scalars + 3;
   k_leaf_write<<<(unsigned)ceil_div((int64_t)F * 32, 256), 256, 0, st>>>(lw, F);
