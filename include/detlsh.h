@@ -100,6 +100,11 @@ typedef struct {
     int32_t rmin_policy;    /* DETLSH_RMIN_MAGIC (default) / DETLSH_RMIN_FIXED     */
     double r_min;           /* DETLSH_RMIN_FIXED: the starting radius (> 0); the
                                FP32 path only (precision must be FP32)             */
+    int32_t per_tree;       /* 0 (default): leaves join S in (LB^2, leaf) order with
+                               the budget checked after each leaf (the priority
+                               queue of Sec. VI-B2); 1: Alg. 5 as printed, each
+                               tree's range query whole, checked after each tree
+                               (DETLSH_RMIN_MAGIC only; candidate buffers of n)  */
 } detlsh_query_params;
 
 /* Fill *p with the defaults listed above (Sec. V-B1, Sec. VI-A). */

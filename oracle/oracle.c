@@ -896,9 +896,22 @@ int orc_index_rc_ann(const orc_index *ix, const float *q, double r, double beta,
     return 0;
 }
 
+int orc_index_query_ex(const orc_index *ix, const float *q, int k, double beta, double c,
+                       int per_tree, int64_t *ids, double *dists, int64_t *S_out,
+                       int64_t *S_size, int *jstar, int *istar);
+
 int orc_index_query(const orc_index *ix, const float *q, int k, double beta, double c,
                     int64_t *ids, double *dists, int64_t *S_out, int64_t *S_size,
                     int *jstar, int *istar) {
+    return orc_index_query_ex(ix, q, k, beta, c, 0, ids, dists, S_out, S_size, jstar, istar);
+}
+
+/* per_tree = 1: Alg. 5 without the priority queue of Sec. VI-B2: a tree's
+ * range query joins S whole and the budget is checked after each tree
+ * (lines 5-6 as printed). */
+int orc_index_query_ex(const orc_index *ix, const float *q, int k, double beta, double c,
+                       int per_tree, int64_t *ids, double *dists, int64_t *S_out,
+                       int64_t *S_size, int *jstar, int *istar) {
     int64_t n = ix->n;
     if (k < 1 || k > n) return -1;
     int LK = ix->L * ix->K;
@@ -935,7 +948,7 @@ int orc_index_query(const orc_index *ix, const float *q, int k, double beta, dou
         for (int t = 0; t < ix->L && ns < tau; t++) {
             orc_range_query(ix, t, qproj + t * ix->K, T[hi], &hits);
             qsort(hits.v, (size_t)hits.n, sizeof(orc_hit), orc_cmp_hit);
-            for (int64_t h = 0; h < hits.n && ns < tau; h++) {
+            for (int64_t h = 0; h < hits.n && (per_tree || ns < tau); h++) {
                 const onode *lf = hits.v[h].leaf;
                 for (int64_t i = 0; i < lf->cnt; i++) {
                     int64_t p = lf->ids[i];
@@ -945,8 +958,9 @@ int orc_index_query(const orc_index *ix, const float *q, int k, double beta, dou
                         cand[ns++].id = p;
                     }
                 }
-                if (ns >= tau) is = t;
+                if (!per_tree && ns >= tau) is = t;
             }
+            if (per_tree && ns >= tau) is = t;
         }
         free(hits.v);
         free(mark);

@@ -105,6 +105,12 @@ int orc_index_query_fixed(const orc_index *ix, const float *q, int k, double bet
 int orc_index_query_magic_min(const orc_index *ix, const float *q, int k, double beta,
                               int64_t *ids, double *dists, int64_t *S_out, int64_t *S_size,
                               float *vstar, int *istar);
+/* As orc_index_query; per_tree = 1 drops the priority queue: each tree's
+ * range query joins S whole and |S| >= beta*n + k is checked after each tree
+ * (Alg. 5 as printed). */
+int orc_index_query_ex(const orc_index *ix, const float *q, int k, double beta, double c,
+                       int per_tree, int64_t *ids, double *dists, int64_t *S_out,
+                       int64_t *S_size, int *jstar, int *istar);
 /* Same, over m queries, OpenMP over queries (nthreads <= 0: all cores). */
 int orc_index_query_batch(const orc_index *ix, const float *Q, int64_t m, int k, double beta,
                           double c, int64_t *ids, double *dists, int64_t *S_sizes,

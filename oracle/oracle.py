@@ -65,6 +65,10 @@ def lib():
                                       _i64p, _f64p, _i64p_n, C.POINTER(C.c_int64),
                                       C.POINTER(C.c_int), C.POINTER(C.c_int)]
         L.orc_index_query.restype = C.c_int
+        L.orc_index_query_ex.argtypes = [C.c_void_p, _f32p, C.c_int, C.c_double, C.c_double,
+                                         C.c_int, _i64p, _f64p, _i64p_n, C.POINTER(C.c_int64),
+                                         C.POINTER(C.c_int), C.POINTER(C.c_int)]
+        L.orc_index_query_ex.restype = C.c_int
         L.orc_index_query_fixed.argtypes = [C.c_void_p, _f32p, C.c_int, C.c_double, C.c_double,
                                             C.c_double, _i64p, _f64p, _i64p_n,
                                             C.POINTER(C.c_int64), C.POINTER(C.c_int),
@@ -239,14 +243,14 @@ class Index:
         return dict(id=pid.value, dist=dist.value, S=S[:ssz.value] if want_S else None,
                     S_size=ssz.value, tree_stop=stop.value)
 
-    def query(self, q, k, beta=0.1, c=1.5, want_S=True):
+    def query(self, q, k, beta=0.1, c=1.5, want_S=True, per_tree=False):
         ids = np.zeros(k, np.int64)
         dists = np.zeros(k, np.float64)
         S = np.zeros(self.n, np.int64) if want_S else np.zeros(1, np.int64)
         ssz, js, ist = C.c_int64(0), C.c_int(0), C.c_int(0)
-        rc = lib().orc_index_query(self._h, _f32(q), k, beta, c, ids, dists,
-                                   S if want_S else None, C.byref(ssz), C.byref(js),
-                                   C.byref(ist))
+        rc = lib().orc_index_query_ex(self._h, _f32(q), k, beta, c, int(per_tree), ids, dists,
+                                      S if want_S else None, C.byref(ssz), C.byref(js),
+                                      C.byref(ist))
         if rc != 0:
             raise ValueError("oracle query rejected its arguments")
         return dict(ids=ids, dists=dists, S=S[:ssz.value] if want_S else None,

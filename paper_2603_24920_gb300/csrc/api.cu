@@ -652,6 +652,8 @@ int validate_query(const detlsh_index *ix, int64_t m, int32_t k_max, const detls
   if (qp->rmin_policy != DETLSH_RMIN_MAGIC && qp->rmin_policy != DETLSH_RMIN_FIXED &&
       qp->rmin_policy != DETLSH_RMIN_CONTINUOUS)
     return DETLSH_ERR_INVALID_ARG;
+  if (qp->per_tree != 0 && qp->per_tree != 1) return DETLSH_ERR_INVALID_ARG;
+  if (qp->per_tree && qp->rmin_policy != DETLSH_RMIN_MAGIC) return DETLSH_ERR_INVALID_ARG;
   if (qp->rmin_policy == DETLSH_RMIN_FIXED &&
       (!(qp->r_min > 0.0) || !std::isfinite(qp->r_min) || qp->precision != DETLSH_PREC_FP32))
     return DETLSH_ERR_INVALID_ARG;
@@ -728,8 +730,9 @@ int query_impl(detlsh_index *ix, const float *queries, int64_t m, const int32_t 
   }
   const double tb = std::ceil(qp->beta * (double)ix->n);
   const int64_t tau_base = tb > (double)ix->n ? ix->n + 1 : (int64_t)tb;
-  int64_t cap = (tau_base + k_max > ix->n) ? ix->n
-                                            : std::min<int64_t>(ix->n, tau_base + k_max + ix->max_leaf);
+  int64_t cap = (tau_base + k_max > ix->n || qp->per_tree)
+                    ? ix->n
+                    : std::min<int64_t>(ix->n, tau_base + k_max + ix->max_leaf);
   QueryIndexView v = view_of(ix);
   QueryArgs qa{};
   qa.Q = Q; qa.Qh = Qh; qa.Qp = Qp; qa.m = m; qa.kq = kd; qa.k_max = k_max;
@@ -742,6 +745,7 @@ int query_impl(detlsh_index *ix, const float *queries, int64_t m, const int32_t 
                      : (float)std::log2(ix->eps2);
   qa.inv_2lg_c = (float)(1.0 / (2.0 * std::log2(qp->c)));
   qa.precision = qp->precision; qa.rerank_mult = qp->rerank_mult;
+  qa.per_tree = qp->per_tree;
   qa.ids = static_cast<int64_t *>(ix->qids.p);
   qa.dists = static_cast<float *>(ix->qdists.p);
   if (S) {
@@ -870,6 +874,7 @@ int detlsh_default_query_params(detlsh_query_params *p) {
   p->rerank_mult = 4;
   p->rmin_policy = DETLSH_RMIN_MAGIC;
   p->r_min = 1.0;
+  p->per_tree = 0;
   return DETLSH_OK;
 }
 
@@ -998,8 +1003,9 @@ int detlsh_query_reserve(detlsh_index *ix, int64_t m_max, int32_t k_max,
   DL_CUDA(cudaMemcpyAsync(ix->aT.p, Th, sizeof Th, cudaMemcpyHostToDevice, st));
   const double tb = std::ceil(qp->beta * (double)ix->n);
   P.tau_base = tb > (double)ix->n ? ix->n + 1 : (int64_t)tb;
-  P.cap = (P.tau_base + k_max > ix->n) ? ix->n
-                                        : std::min<int64_t>(ix->n, P.tau_base + k_max + ix->max_leaf);
+  P.cap = (P.tau_base + k_max > ix->n || qp->per_tree)
+              ? ix->n
+              : std::min<int64_t>(ix->n, P.tau_base + k_max + ix->max_leaf);
   QueryIndexView vw = view_of(ix);
   query_slot_offsets(vw, P.cap, P.off);
   int slots = (int)std::min<int64_t>(query_slots(vw), m_max);
@@ -1061,6 +1067,7 @@ int detlsh_query_async(const detlsh_index *cix, const float *queries, int64_t m,
                        : (float)std::log2(ix->eps2);
     qa.inv_2lg_c = (float)(1.0 / (2.0 * std::log2(P.qp.c)));
     qa.precision = P.qp.precision; qa.rerank_mult = P.qp.rerank_mult;
+    qa.per_tree = P.qp.per_tree;
     qa.ids = ids; qa.dists = dists;
     qa.cand_cap = P.cap;
     for (int i = 0; i < 13; ++i) qa.off[i] = P.off[i];

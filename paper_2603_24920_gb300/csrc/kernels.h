@@ -119,7 +119,8 @@ struct QueryArgs {
   int64_t tau_base;          // ceil(beta * n)
   const float *T;            // [255] radius grid
   const float *Tc;           // [255] fp32((c r_i)^2) (fixed r_min, condition 2)
-  int policy;                // DETLSH_RMIN_MAGIC / DETLSH_RMIN_FIXED
+  int policy;                // DETLSH_RMIN_MAGIC / DETLSH_RMIN_FIXED / _CONTINUOUS
+  int per_tree;              // 1: whole trees join S (no priority queue)
   float lg_eps2, inv_2lg_c;  // log2(eps^2), 1/(2 log2 c): level estimate before the exact fix-up
   int precision, rerank_mult;
   int64_t *ids;              // [m][k_max]

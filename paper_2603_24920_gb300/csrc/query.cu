@@ -657,24 +657,27 @@ __device__ __forceinline__ void cut_and_collect_t(QCtx &c) {
   }
   __syncthreads();
   // priority order (LB^2, leaf index): smallest LB^2 value v reaching the
-  // count still needed, then the smallest leaf index among LB^2 == v
+  // count still needed, then the smallest leaf index among LB^2 == v (with
+  // whole trees joining S, tree i* is taken whole)
   const uint32_t need = c.sm.need;
-  auto get_lb = [&](int64_t i, uint32_t &k, uint32_t &w) {
-    w = (c.s.llev[li0 + i] <= js) ? c.s.cval[i] : 0u;
-    k = __float_as_uint(c.s.llb2[li0 + i]);
-  };
-  block_select(nli, get_lb, need, c.sm);
-  const uint32_t v = c.sm.sel_v;
-  const uint32_t need2 = need - c.sm.sel_below;
-  uint32_t cut = 0xffffffffu;  // every leaf at LB^2 == v when all of them are needed
-  if (need2 < c.sm.sel_at) {
-    auto get_id = [&](int64_t i, uint32_t &k, uint32_t &w) {
-      const bool q = c.s.llev[li0 + i] <= js && __float_as_uint(c.s.llb2[li0 + i]) == v;
-      w = q ? c.s.cval[i] : 0u;
-      k = c.s.lleaf[li0 + i];
+  uint32_t v = 0xffffffffu, cut = 0xffffffffu;
+  if (!c.qa.per_tree) {
+    auto get_lb = [&](int64_t i, uint32_t &k, uint32_t &w) {
+      w = (c.s.llev[li0 + i] <= js) ? c.s.cval[i] : 0u;
+      k = __float_as_uint(c.s.llb2[li0 + i]);
     };
-    block_select(nli, get_id, need2, c.sm);
-    cut = c.sm.sel_v;
+    block_select(nli, get_lb, need, c.sm);
+    v = c.sm.sel_v;
+    const uint32_t need2 = need - c.sm.sel_below;
+    if (need2 < c.sm.sel_at) {  // else every leaf at LB^2 == v is needed
+      auto get_id = [&](int64_t i, uint32_t &k, uint32_t &w) {
+        const bool q = c.s.llev[li0 + i] <= js && __float_as_uint(c.s.llb2[li0 + i]) == v;
+        w = q ? c.s.cval[i] : 0u;
+        k = c.s.lleaf[li0 + i];
+      };
+      block_select(nli, get_id, need2, c.sm);
+      cut = c.sm.sel_v;
+    }
   }
   // collect S: trees before i* whole (new points only), tree i* up to the cut
   if (threadIdx.x == 0) c.sm.ncand = 0;

@@ -36,7 +36,8 @@ class BuildParams(C.Structure):
 
 class QueryParams(C.Structure):
     _fields_ = [("beta", C.c_double), ("c", C.c_double), ("precision", C.c_int32),
-                ("rerank_mult", C.c_int32), ("rmin_policy", C.c_int32), ("r_min", C.c_double)]
+                ("rerank_mult", C.c_int32), ("rmin_policy", C.c_int32), ("r_min", C.c_double),
+                ("per_tree", C.c_int32)]
 
 
 class Info(C.Structure):
@@ -177,7 +178,7 @@ def detlsh_free(h):
 
 def detlsh_query_ex(h, queries, k, beta=0.1, c=1.5, precision=PREC_FP32, rerank_mult=4,
                     k_per_query=None, stream=None, ids=None, dists=None, r_min=None,
-                    rmin_policy=None):
+                    rmin_policy=None, per_tree=False):
     """Returns (ids int64 (m, k), dists float32 (m, k)); torch CUDA if queries are.
     r_min given: Alg. 5 from that radius with condition 2 (RMIN_FIXED);
     rmin_policy=RMIN_CONTINUOUS: the smallest r_min off the grid."""
@@ -188,6 +189,7 @@ def detlsh_query_ex(h, queries, k, beta=0.1, c=1.5, precision=PREC_FP32, rerank_
         qp.rmin_policy, qp.r_min = RMIN_FIXED, r_min
     if rmin_policy is not None:
         qp.rmin_policy = rmin_policy
+    qp.per_tree = int(per_tree)
     if ids is None:
         if _is_cuda(queries):
             import torch
@@ -309,7 +311,7 @@ def detlsh_project(h, rows, stream=None):
 
 
 def detlsh_query_candidates(h, queries, k, beta=0.1, c=1.5, cap=None, r_min=None,
-                            rmin_policy=None):
+                            rmin_policy=None, per_tree=False):
     """Candidate sets of Alg. 5: list of id arrays, j*, i* per query (with r_min:
     the stopping radius index and tree, -1 for condition 2)."""
     i = detlsh_get_info(h)
@@ -321,6 +323,7 @@ def detlsh_query_candidates(h, queries, k, beta=0.1, c=1.5, cap=None, r_min=None
         qp.rmin_policy, qp.r_min = RMIN_FIXED, r_min
     if rmin_policy is not None:
         qp.rmin_policy = rmin_policy
+    qp.per_tree = int(per_tree)
     S = np.empty((m, cap), np.int64)
     ssz = np.empty(m, np.int64)
     js = np.empty(m, np.int32)

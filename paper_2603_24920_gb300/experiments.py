@@ -189,6 +189,13 @@ def cmd_variants(a):
                          compute_mode="donot_use_mm_for_euclid_dist")
         nn.append(dd.min(1).values.cpu().numpy())
     nn = np.concatenate(nn)
+    print("Alg. 5 with and without the priority queue of Sec. VI-B2, c2, beta = 0.0015, k = 50:")
+    row("budget check", "kernel ms", "recall@10", "S per query")
+    for pt in (False, True):
+        ids, _, t = run_query(D, h, Qd, 50, beta=0.0015, per_tree=pt)
+        row("after each tree (as printed)" if pt else "after each leaf (priority queue)",
+            "%.2f" % t.query_kernel_ms, "%.3f" % recall(ids.cpu().numpy()[:200], gt, 10),
+            "%.0f" % (t.query_candidates / t.query_count))
     print("(r,c)-ANN (Alg. 4), c2, c = 1.5, 200 queries: Alg. 3 as printed vs optimisation (1)"
           " of Sec. VI-B2 (whole leaves):")
     row("range query", "r / NN distance", "beta", "kernel ms per query", "answered within c*r",

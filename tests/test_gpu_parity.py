@@ -259,3 +259,18 @@ def test_query_argument_errors():
         assert ids.shape == (0, 3)
     finally:
         D.detlsh_free(h)
+
+
+@pytest.mark.parametrize("beta,k", [(0.01, 10), (0.1, 5)])
+def test_query_per_tree_check(pair, beta, k):
+    # Alg. 5 as printed (whole trees, budget checked after each tree)
+    h, ox, X = pair["h"], pair["ox"], pair["X"]
+    k = min(k, pair["n"])
+    Q = _queries(pair["d"])
+    S_g, js, ist = D.detlsh_query_candidates(h, Q, k, beta=beta, per_tree=True)
+    ids, dists = D.detlsh_query_ex(h, Q, k, beta=beta, per_tree=True)
+    for i in range(Q.shape[0]):
+        r = ox.query(Q[i], k, beta=beta, per_tree=True)
+        assert np.array_equal(np.sort(S_g[i]), np.sort(r["S"])), i
+        assert js[i] == r["jstar"] and ist[i] == r["istar"]
+        _check_topk(ids[i], dists[i], r["S"], X, Q[i], k)

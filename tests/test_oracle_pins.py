@@ -692,3 +692,26 @@ def test_rc_ann_optimised_takes_whole_leaves():
                 S = got["S"]
                 if S.size and (stop >= 0 or dist[S].min() <= 1.5 * r):
                     assert got["id"] == S[np.lexsort((S, dist[S]))[0]]
+
+
+def test_query_per_tree_check_takes_whole_trees():
+    # Alg. 5 without the priority queue: S is the union of whole range
+    # queries, trees in order, up to the first tree where |S| >= beta*n + k;
+    # it contains the per-leaf S and shares j* and i*
+    ix, X, Q = _small_index(n=5000)
+    trees = [ix.tree(t) for t in range(ix.L)]
+    c = 1.5
+    T = ix.level_table(c)
+    for q in Q[:5]:
+        for beta, k in ((0.01, 10), (0.1, 5)):
+            tau = int(np.ceil(beta * ix.n)) + k
+            leafwise = ix.query(q, k, beta=beta, c=c)
+            got = ix.query(q, k, beta=beta, c=c, per_tree=True)
+            assert got["jstar"] == leafwise["jstar"] and got["istar"] == leafwise["istar"]
+            thr = T[got["jstar"] - oracle.JMIN]
+            inS = np.zeros(ix.n, bool)
+            for t in range(got["istar"] + 1):
+                inS |= ix.leaf_lb2(t, q)[trees[t]["leaf_of"]] <= thr
+            assert np.array_equal(np.sort(got["S"]), np.nonzero(inS)[0])
+            assert set(leafwise["S"].tolist()) <= set(got["S"].tolist())
+            assert got["S"].size >= tau
