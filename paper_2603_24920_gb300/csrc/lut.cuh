@@ -41,6 +41,26 @@ __device__ __forceinline__ float box_lb2(const float *lut, const uint4 &lo, cons
   return acc;
 }
 
+// The same sum over dimensions [J0, J1) only, continuing from acc (the
+// terms are non-negative and FP32 addition is monotone, so a partial sum
+// above a threshold shows the whole sum is above it too).
+template <int J0, int J1>
+__device__ __forceinline__ float box_lb2_part(const float *lut, const uint4 &lo, const uint4 &hi,
+                                              float acc) {
+  const uint32_t wl[4] = {lo.x, lo.y, lo.z, lo.w};
+  const uint32_t wh[4] = {hi.x, hi.y, hi.z, hi.w};
+#pragma unroll
+  for (int j = J0; j < J1; ++j) {
+    const uint32_t zl = (wl[j >> 2] >> (8 * (j & 3))) & 255u;
+    const uint32_t zh = (wh[j >> 2] >> (8 * (j & 3))) & 255u;
+    const float a = lut[j * LUT_STRIDE + zl];
+    const float b = -lut[j * LUT_STRIDE + zh + 1];
+    const float gap = fmaxf(fmaxf(a, b), 0.0f);
+    acc = __fadd_rn(acc, __fmul_rn(gap, gap));
+  }
+  return acc;
+}
+
 // Squared upper bound of a box (Sec. IV-C, Fig. 6): per dimension the
 // distance to the farther edge, max(|B(lo) - q|, |B(hi+1) - q|), summed in
 // FP32 over dimensions in order.

@@ -401,12 +401,18 @@ __device__ __forceinline__ void expand_levels(QCtx &c) {
         uint32_t lv = 255u;
         float lb = 0.0f;
         uint32_t sz = 0;
-        if (valid) {
-          lb = box_lb2(c.lut, llo[l], lhi[l]);
+        // Half the dimensions first: when every leaf of the run is already
+        // above T[Jnow] the rest is skipped (partial sums only grow).
+        const float thr = sm.T[Jnow];
+        uint4 blo = make_uint4(0, 0, 0, 0), bhi = make_uint4(0, 0, 0, 0);
+        if (valid) { blo = llo[l]; bhi = lhi[l]; lb = box_lb2_part<0, LUT_ROWS / 2>(c.lut, blo, bhi, 0.0f); }
+        const bool more = __any_sync(FULL, valid && lb <= thr);
+        if (valid && more) lb = box_lb2_part<LUT_ROWS / 2, LUT_ROWS>(c.lut, blo, bhi, lb);
+        if (valid && more) {
           // Leaves above Jnow are never needed again (every later test is
           // against a bound <= Jnow), so only the others get their level,
           // size and level-array entry; the rest read as level 255.
-          if (lb <= sm.T[Jnow]) {
+          if (lb <= thr) {
             lv = level_of(sm.T, lb, c.qa.lg_eps2, c.qa.inv_2lg_c);
             c.s.lev[ix.leaf_off[t] + l] = (ep << 8) | lv;
             sz = leaf_begin_of(ix, t, l + 1) - leaf_begin_of(ix, t, l);
