@@ -17,9 +17,9 @@
 // big-integer kernel recomputes.
 //
 // Encoding (Alg. 1) needs only each coordinate's region, not its exact
-// value.  k_encode computes a plain FP32 FMA dot product y, whose distance
-// to the exact value is at most gamma_d * ||x|| * ||a|| (Higham's bound,
-// gamma_d = d u / (1 - d u), with Cauchy-Schwarz), widened by one unit in the
+// value.  k_encode computes a plain FP32 FMA dot product y and a rigorous
+// bound on its distance to the exact value (a running chunked term plus a
+// Cauchy-Schwarz term, detailed at the kernel), widened by one unit in the
 // last place for the final rounding of the exact value.  When no breakpoint
 // lies in that interval the region is certain; otherwise -- and for the two
 // outer regions, which hold the column minimum and maximum -- the coordinate
@@ -28,6 +28,7 @@
 #include "kernels.h"
 
 #include <algorithm>
+#include <cmath>
 
 namespace dl {
 
@@ -142,25 +143,14 @@ __device__ float exact_dot_rn(const float *__restrict__ a, const float *__restri
 // 257 floats so that the 16 columns a warp searches fall in distinct banks.
 constexpr int BSTRIDE = 257;
 
-__device__ __forceinline__ uint32_t region_of(const float *__restrict__ Bint, int nint, float y) {
-  // number of interior breakpoints strictly below y (Alg. 1, lowest region on ties)
-  int lo = 0, hi = nint;
-  while (lo < hi) {
-    const int mid = (lo + hi) >> 1;
-    if (Bint[mid] < y) lo = mid + 1; else hi = mid;
-  }
-  return (uint32_t)lo;
-}
-
-// The same count from a column's interior breakpoints staged in shared
-// memory, branch-free: power-of-two steps over the N_r - 1 sorted values.
-__device__ __forceinline__ uint32_t region_smem(const float *Bs, int N_r, float y) {
+// Number of interior breakpoints strictly below y (Alg. 1, lowest region on
+// ties), from a column staged in shared memory and padded with +inf up to 255
+// entries: eight power-of-two steps, branch-free.
+__device__ __forceinline__ uint32_t region_smem(const float *Bs, float y) {
   uint32_t pos = 0;
 #pragma unroll
-  for (int s = 7; s >= 0; --s) {
-    const uint32_t step = 1u << s;
-    if ((int)step < N_r && Bs[pos + step - 1] < y) pos += step;
-  }
+  for (int s = 7; s >= 0; --s)
+    if (Bs[pos + (1u << s) - 1] < y) pos += 1u << s;
   return pos;
 }
 
@@ -235,140 +225,234 @@ k_project(const float *__restrict__ X, int64_t ldx, const uint32_t *__restrict__
   }
 }
 
-// Certified encoding: FP32 FMA estimate + rigorous a-posteriori bound.  Each
-// FMA s_k = fl(x_k a_k + s_{k-1}) errs by at most u |s_k|, so the estimate is
-// within u * sum_k |s_k| (+ an underflow allowance) of the exact product.  A
-// coordinate keeps its region when no breakpoint lies within that bound
-// widened by one unit in the last place (the rounding of the exact value);
-// otherwise it is listed.  Lowest- and highest-region coordinates are listed
-// only while they can still be the column minimum or maximum, tested against
-// running per-column bounds (init: B[1] and B[N_r-1], which are data values).
-__global__ void __launch_bounds__(PJ_THREADS, 2)
+// Certified encoding: FP32 FMA estimate + rigorous a-posteriori bound.
+//
+// Each FMA s_k = fl(x_k a_k + s_{k-1}) errs by at most u |s_k| (+ an
+// underflow allowance), so the estimate is within u * sum_k |s_k| of the
+// exact product.  That sum is bounded in chunks of EN_CH terms: inside a
+// chunk c that starts from s_c, |s_k| <= (|s_c| + T_c) / (1 - EN_CH u) with
+// T_c = sum_{i in c} |x_i a_i|, so a chunk adds at most
+// EN_CH (|s_c| + T_c) / (1 - EN_CH u); and sum_c T_c <= ||x|| ||a||
+// (Cauchy-Schwarz).  The kernel therefore keeps one running term per output,
+// E = sum_c EN_CH |s_c| (rounded up), and the bound is
+//   gamma * (E + EN_CH ||x|| ||a||) + d 2^-148,  gamma >= u / (1 - EN_CH u),
+// with ||x||, ||a|| upper bounds from round-up arithmetic.  A coordinate
+// keeps its region when no breakpoint lies within that bound widened by one
+// unit in the last place (the rounding of the exact value); otherwise it is
+// listed.  Lowest- and highest-region coordinates are listed only while they
+// can still be the column minimum or maximum, tested against running
+// per-column bounds (init: B[1] and B[N_r-1], which are data values).
+//
+// Tiling: a CTA of 512 threads owns one column tile (<= 64 columns) and
+// walks 256-row tiles; a thread accumulates 8 rows x 4 columns.  Chunks of 32
+// terms are staged in shared memory k-major by cp.async (double-buffered), so
+// the inner step is three 16-byte shared loads and 32 FMAs.  Row r of term k
+// sits at float (k, ((r >> 2) ^ (k & 7)) * 4 + (r & 3)), which makes the
+// copies' shared stores bank-conflict-free and keeps every 16-byte read whole.
+constexpr int EN_ROWS = 256;
+constexpr int EN_COLS = 64;
+constexpr int EN_KC = 32;
+constexpr int EN_CH = 8;
+constexpr int EN_THREADS = 512;
+constexpr int EN_CST = 18;  // codes: words per staged row (conflict-free stores)
+
+__host__ __device__ constexpr size_t encode_smem_bytes() {
+  return sizeof(float) * (2 * EN_KC * EN_ROWS + 2 * EN_KC * EN_COLS + EN_COLS * BSTRIDE +
+                          EN_ROWS + EN_COLS) +
+         sizeof(uint32_t) * (EN_ROWS * EN_CST + 2 * EN_COLS);
+}
+
+__device__ __forceinline__ void cp_async4(float *dst, const float *src, bool valid) {
+  const uint32_t s = (uint32_t)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(s), "l"(src),
+               "r"(valid ? 4 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// EN_CH terms (k = kb .. kb + EN_CH - 1, kb a multiple of 8) of a thread's
+// 8 x 4 outputs, after adding the chunk's EN_CH |s_c| to E.
+__device__ __forceinline__ void encode_terms(float (&s)[8][4], float (&E)[8][4], const float *xs,
+                                             const float *as, int kb, int ty, int tx) {
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) E[i][j] = __fmaf_ru((float)EN_CH, fabsf(s[i][j]), E[i][j]);
+#pragma unroll
+  for (int u = 0; u < EN_CH; ++u) {
+    const int k = kb + u;
+    const float4 x0 = *reinterpret_cast<const float4 *>(xs + k * EN_ROWS + (((2 * ty) ^ u) << 2));
+    const float4 x1 = *reinterpret_cast<const float4 *>(xs + k * EN_ROWS + (((2 * ty + 1) ^ u) << 2));
+    const float4 a4 = *reinterpret_cast<const float4 *>(as + k * EN_COLS + ((tx ^ u) << 2));
+    const float xv[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+    const float av[4] = {a4.x, a4.y, a4.z, a4.w};
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) s[i][j] = __fmaf_rn(xv[i], av[j], s[i][j]);
+  }
+}
+
+__global__ void __launch_bounds__(EN_THREADS, 1)
 k_encode(const float *__restrict__ X, int64_t ldx, int64_t nrows, int d,
          const float *__restrict__ A, int LK, int W, ProjArgs o) {
-  __shared__ float Xs[PJ_ROWS][PJ_KC + 1];
-  __shared__ float As[PJ_COLS][PJ_KC + 1];
-  __shared__ uint32_t cmin[PJ_COLS], cmax[PJ_COLS];
   extern __shared__ float dyn[];
-  uint8_t *cst = reinterpret_cast<uint8_t *>(dyn);  // [64 rows][64 cols] codes
-  float *Bs = dyn + PJ_ROWS * PJ_COLS / 4;          // [64 cols][BSTRIDE] interior breakpoints
+  float *Xs = dyn;                                  // [2][EN_KC][EN_ROWS], swizzled
+  float *As = Xs + 2 * EN_KC * EN_ROWS;             // [2][EN_KC][EN_COLS], swizzled
+  float *Bs = As + 2 * EN_KC * EN_COLS;             // [64 slots][BSTRIDE] interior breakpoints
+  float *nxs = Bs + EN_COLS * BSTRIDE;              // [EN_ROWS] row norms (rounded up)
+  float *nas = nxs + EN_ROWS;                       // [EN_COLS] column norms (rounded up)
+  uint32_t *cst = reinterpret_cast<uint32_t *>(nas + EN_COLS);  // [EN_ROWS][EN_CST] codes
+  uint32_t *cmin = cst + EN_ROWS * EN_CST, *cmax = cmin + EN_COLS;
+  const uint8_t *cst8 = reinterpret_cast<const uint8_t *>(cst);
+
   const int tid = threadIdx.x;
-  const int tx = tid & 15, ty = tid >> 4;
+  const int lane = tid & 31, warp = tid >> 5;
+  const int tx = tid & 15, ty = tid >> 4;           // columns 4tx.., rows 8ty..
   const int col0 = blockIdx.y * W;
   const int LKt = min(LK, col0 + W);
+  const int ncol = LKt - col0;
   const int nint = o.N_r - 1;
-  const float eu = o.gamma;  // u (1 + 2 d u), rounded up
+  const float gam = o.gamma;                        // >= u / (1 - EN_CH u), rounded up
   const float tiny = __fmul_rn((float)d, __uint_as_float(2u));  // d * 2^-148
   const int K = o.K;
-  const int ntree = (LKt - col0) / K;
+  const int ntree = ncol / K;
   const int t0 = col0 / K;
-  const int64_t ntiles = ceil_div(nrows, PJ_ROWS);
-  // register prefetch of one tile chunk: 8 X values and 8 A values per thread
-  float px[8], pa[8];
-  auto fetch = [&](int64_t row0, int kc) {
-    const int kmax = min(PJ_KC, d - kc);
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int idx = tid + u * PJ_THREADS;
-      const int r = idx / PJ_KC, c = idx % PJ_KC;
-      const int64_t rr = row0 + r;
-      px[u] = (rr < nrows && c < kmax) ? X[rr * ldx + kc + c] : 0.0f;
-      const int oc = col0 + r;
-      pa[u] = (oc < LKt && c < kmax) ? A[(int64_t)oc * d + kc + c] : 0.0f;
-    }
-  };
-  auto stash = [&]() {
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int idx = tid + u * PJ_THREADS;
-      Xs[idx / PJ_KC][idx % PJ_KC] = px[u];
-      As[idx / PJ_KC][idx % PJ_KC] = pa[u];
-    }
-  };
-  for (int idx = tid; idx < (LKt - col0) * BSTRIDE; idx += PJ_THREADS) {
+  const int64_t ntiles = ceil_div(nrows, EN_ROWS);
+  const int nchunk = (d + EN_KC - 1) / EN_KC;
+  // breakpoint slot of column c: columns 4tx + j of a warp land in 16 consecutive slots
+  auto bslot = [](int c) { return (c & 3) * 16 + (c >> 2); };
+
+  for (int idx = tid; idx < ncol * BSTRIDE; idx += EN_THREADS) {
     const int c = idx / BSTRIDE, z = idx % BSTRIDE;
-    Bs[idx] = z < nint ? o.B[(int64_t)(col0 + c) * (o.N_r + 1) + 1 + z] : 0.0f;
+    Bs[bslot(c) * BSTRIDE + z] = z < nint ? o.B[(int64_t)(col0 + c) * (o.N_r + 1) + 1 + z] : INFINITY;
   }
-  int64_t tile = blockIdx.x;
-  if (tile < ntiles) fetch(tile * PJ_ROWS, 0);
-  for (; tile < ntiles; tile += gridDim.x) {
-    const int64_t row0 = tile * PJ_ROWS;
-    float acc[4][4], err[4][4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-      for (int j = 0; j < 4; ++j) acc[i][j] = err[i][j] = 0.0f;
-    for (int kc = 0; kc < d; kc += PJ_KC) {
-      const int kmax = min(PJ_KC, d - kc);
-      __syncthreads();
-      stash();
-      __syncthreads();
-      // prefetch the next chunk (or the first chunk of the next tile)
-      if (kc + PJ_KC < d) fetch(row0, kc + PJ_KC);
-      else if (tile + gridDim.x < ntiles) fetch((tile + gridDim.x) * PJ_ROWS, 0);
-#pragma unroll 4
-      for (int kk = 0; kk < kmax; ++kk) {
-        float xv[4], av[4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) xv[i] = Xs[ty + 16 * i][kk];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) av[j] = As[tx + 16 * j][kk];
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-#pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            acc[i][j] = __fmaf_rn(xv[i], av[j], acc[i][j]);
-            err[i][j] = __fadd_rn(err[i][j], fabsf(acc[i][j]));
-          }
-      }
+  if (tid < EN_COLS) {  // ||a|| per column, rounded up
+    float s2 = 0.0f;
+    if (tid < ncol) {
+      const float *ar = A + (int64_t)(col0 + tid) * d;
+      for (int k = 0; k < d; ++k) s2 = __fmaf_ru(ar[k], ar[k], s2);
     }
-    if (tid < PJ_COLS) { cmin[tid] = 0xffffffffu; cmax[tid] = 0u; }
-    __syncthreads();
-    uint32_t flags = 0;  // bit i*4+j: output (i, j) goes to the exact list
-    float umin[4], lmax[4];
+    nas[tid] = __fsqrt_ru(s2);
+  }
+
+  // cp.async of one chunk (tile, kc) into stage st: 16 X and 4 A words per thread
+  auto load = [&](int64_t tile, int kc, int st) {
+    const int64_t row0 = tile * EN_ROWS;
+    const int kmax = min(EN_KC, d - kc);
+    const int r3 = lane & 3, kq = lane >> 2;
+    float *xs = Xs + st * EN_KC * EN_ROWS;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int oc = col0 + tx + 16 * j;
-      umin[j] = oc < LKt ? funkey(*(volatile uint32_t *)&o.ubound[oc * 2 + 0]) : 0.0f;
-      lmax[j] = oc < LKt ? funkey(*(volatile uint32_t *)&o.ubound[oc * 2 + 1]) : 0.0f;
-    }
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int r = ty + 16 * i;
+    for (int it = 0; it < 16; ++it) {
+      const int cell = warp * 16 + it;              // 64 row groups x 4 k groups
+      const int rg = cell >> 2, k = (cell & 3) * 8 + kq;
+      const int r = rg * 4 + r3;
       const int64_t rr = row0 + r;
+      const bool v = rr < nrows && k < kmax;
+      cp_async4(xs + k * EN_ROWS + ((rg ^ kq) << 2) + r3, v ? X + rr * ldx + kc + k : X, v);
+    }
+    float *as = As + st * EN_KC * EN_COLS;
+#pragma unroll
+    for (int it = 0; it < 4; ++it) {
+      const int cell = warp * 4 + it;               // 16 column groups x 4 k groups
+      const int cg = cell >> 2, k = (cell & 3) * 8 + kq;
+      const int c = cg * 4 + r3;
+      const bool v = c < ncol && k < kmax;
+      cp_async4(as + k * EN_COLS + ((cg ^ kq) << 2) + r3, v ? A + (int64_t)(col0 + c) * d + kc + k : A, v);
+    }
+  };
+
+  int64_t tile = blockIdx.x;
+  int st = 0;
+  if (tile < ntiles) load(tile, 0, 0);
+  cp_async_commit();
+  for (; tile < ntiles; tile += gridDim.x) {
+    const int64_t row0 = tile * EN_ROWS;
+    float s[8][4], E[8][4];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) s[i][j] = E[i][j] = 0.0f;
+    // row norm^2 of row tid >> 1: this thread takes the terms with bit 2 of
+    // k equal to tid & 1 (the pair's loads then fall in distinct banks)
+    float nx2 = 0.0f;
+    for (int q = 0; q < nchunk; ++q) {
+      const int kc = q * EN_KC;
+      __syncthreads();  // stage st ^ 1 is free
+      if (q + 1 < nchunk) load(tile, kc + EN_KC, st ^ 1);
+      else if (tile + gridDim.x < ntiles) load(tile + gridDim.x, 0, st ^ 1);
+      cp_async_commit();
+      cp_async_wait1();
+      __syncthreads();  // stage st is visible
+      const float *xs = Xs + st * EN_KC * EN_ROWS;
+      const float *as = As + st * EN_KC * EN_COLS;
+      {
+        const int r = tid >> 1, h = tid & 1;
+#pragma unroll
+        for (int e = 0; e < 16; ++e) {
+          const int k = (e >> 2) * 8 + h * 4 + (e & 3);
+          const float v = xs[k * EN_ROWS + (((r >> 2) ^ (k & 7)) << 2) + (r & 3)];
+          nx2 = __fmaf_ru(v, v, nx2);
+        }
+      }
+      if (d - kc >= EN_KC) {  // a full chunk: every address is a constant offset
+#pragma unroll
+        for (int kb = 0; kb < EN_KC; kb += EN_CH) encode_terms(s, E, xs, as, kb, ty, tx);
+      } else {
+        const int kpad = (d - kc + EN_CH - 1) & ~(EN_CH - 1);
+        for (int kb = 0; kb < kpad; kb += EN_CH) encode_terms(s, E, xs, as, kb, ty, tx);
+      }
+      st ^= 1;
+    }
+    nx2 = __fadd_ru(nx2, __shfl_xor_sync(FULL, nx2, 1));
+    if ((tid & 1) == 0) nxs[tid >> 1] = __fsqrt_ru(nx2);
+    if (tid < EN_COLS) { cmin[tid] = 0xffffffffu; cmax[tid] = 0u; }
+    __syncthreads();
+    uint32_t flags = 0;  // bit i*4+j: output (row 8ty+i, column 4tx+j) goes to the exact list
+    float na[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) na[j] = nas[4 * tx + j];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int r = 8 * ty + i;
+      const bool rowok = row0 + r < nrows;
+      const float nx = nxs[r];
+      // the row's four regions first (independent searches), then the certificates
+      uint32_t word = 0;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) word |= region_smem(Bs + bslot(4 * tx + j) * BSTRIDE, s[i][j]) << (8 * j);
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
-        const int c = tx + 16 * j;
-        const int oc = col0 + c;
-        uint8_t code = 0;
-        if (rr < nrows && oc < LKt) {
-          const float y = acc[i][j];
-          const float dlt = __fmaf_ru(eu, err[i][j], tiny);
-          const float dl2 = __fadd_ru(dlt, __fmul_ru(__fadd_ru(fabsf(y), dlt), 1.2e-7f));
-          const float lo = __fsub_rd(y, dl2), hi = __fadd_ru(y, dl2);
-          const float *Bc = Bs + c * BSTRIDE;
-          const uint32_t reg = region_smem(Bc, o.N_r, y);
-          const bool finite = isfinite(y) && isfinite(dl2);
-          const bool sure = finite && (reg == 0 || Bc[reg - 1] < lo) &&
-                            (reg == (uint32_t)nint || Bc[reg] >= hi);
-          bool list = !sure;
-          if (reg == 0 && finite) {  // may be the column minimum?
-            list |= lo <= umin[j];
+        const int c = 4 * tx + j;
+        const float y = s[i][j];
+        const uint32_t reg = (word >> (8 * j)) & 255u;
+        const float tot = __fmaf_ru((float)EN_CH, __fmul_ru(nx, na[j]), E[i][j]);
+        const float dlt = __fmaf_ru(gam, tot, tiny);
+        const float dl2 = __fadd_ru(dlt, __fmul_ru(__fadd_ru(fabsf(y), dlt), 1.2e-7f));
+        const float lo = __fsub_rd(y, dl2), hi = __fadd_ru(y, dl2);
+        const float *Bc = Bs + bslot(c) * BSTRIDE;
+        const bool finite = isfinite(y) && isfinite(dl2);
+        const float below = reg == 0 ? -INFINITY : Bc[reg - 1];
+        const float above = reg == (uint32_t)nint ? INFINITY : Bc[reg];
+        bool list = !(finite && below < lo && above >= hi);
+        if (finite && (reg == 0 || reg == (uint32_t)nint) && rowok && c < ncol) {
+          if (reg == 0) {  // may be the column minimum?
+            list |= lo <= funkey(*(volatile uint32_t *)&o.ubound[(col0 + c) * 2 + 0]);
             atomicMin(&cmin[c], fkey(hi));
           }
-          if (reg == (uint32_t)nint && finite) {  // may be the column maximum?
-            list |= hi >= lmax[j];
+          if (reg == (uint32_t)nint) {  // may be the column maximum?
+            list |= hi >= funkey(*(volatile uint32_t *)&o.ubound[(col0 + c) * 2 + 1]);
             atomicMax(&cmax[c], fkey(lo));
           }
-          code = (uint8_t)reg;  // exact for sure coordinates; a hint for listed ones
-          if (list) flags |= 1u << (i * 4 + j);
         }
-        cst[r * PJ_COLS + c] = code;
+        if (list && rowok && c < ncol) flags |= 1u << (i * 4 + j);
       }
+      cst[r * EN_CST + tx] = word;  // exact for sure coordinates; hints for listed ones
     }
     // one list reservation per warp: exclusive scan of the lanes' counts
     {
-      const int lane = tid & 31;
       const uint32_t cnt = __popc(flags);
       uint32_t incl = cnt;
 #pragma unroll
@@ -382,31 +466,42 @@ k_encode(const float *__restrict__ X, int64_t ldx, int64_t nrows, int d,
       while (flags) {
         const int b = __ffs(flags) - 1;
         flags &= flags - 1;
-        const int64_t rr = row0 + ty + 16 * (b >> 2);
-        const int oc = col0 + tx + 16 * (b & 3);
-        const uint32_t hint = cst[(ty + 16 * (b >> 2)) * PJ_COLS + tx + 16 * (b & 3)];
-        if (base < o.fb_cap) o.fb_list[base] = make_uint2((uint32_t)rr, ((uint32_t)oc << 8) | hint);
+        const int r = 8 * ty + (b >> 2), c = 4 * tx + (b & 3);
+        const uint32_t hint = cst8[r * EN_CST * 4 + c];
+        if (base < o.fb_cap) o.fb_list[base] = make_uint2((uint32_t)(row0 + r), ((uint32_t)(col0 + c) << 8) | hint);
         ++base;
       }
     }
     __syncthreads();
     // tighten the running bounds: the column minimum is <= every hi seen in
     // its lowest region, the maximum >= every lo seen in its highest region
-    if (tid < PJ_COLS && col0 + tid < LKt) {
+    if (tid < ncol) {
       if (cmin[tid] != 0xffffffffu) atomicMin(&o.ubound[(col0 + tid) * 2 + 0], cmin[tid]);
       if (cmax[tid] != 0u) atomicMax(&o.ubound[(col0 + tid) * 2 + 1], cmax[tid]);
     }
-    for (int idx = tid; idx < PJ_ROWS * ntree; idx += PJ_THREADS) {
+    for (int idx = tid; idx < EN_ROWS * ntree; idx += EN_THREADS) {
       const int r = idx / ntree, tt = idx % ntree;
       const int64_t rr = row0 + r;
       if (rr >= nrows) continue;
-      uint32_t w[4] = {0u, 0u, 0u, 0u};
-      for (int j = 0; j < K; ++j)
-        w[j >> 2] |= (uint32_t)cst[r * PJ_COLS + tt * K + j] << (8 * (j & 3));
-      uint4 *dst = reinterpret_cast<uint4 *>(o.codes + ((int64_t)(t0 + tt) * o.n + rr) * CODE_STRIDE);
-      *dst = make_uint4(w[0], w[1], w[2], w[3]);
+      uint4 w;
+      if (K == 16) {
+        const uint32_t *src = cst + r * EN_CST + tt * 4;
+        w = make_uint4(src[0], src[1], src[2], src[3]);
+      } else {
+        const uint8_t *src = cst8 + r * EN_CST * 4 + tt * K;
+        auto pack = [&](int j0) {
+          uint32_t v = 0;
+#pragma unroll
+          for (int b = 0; b < 4; ++b)
+            if (j0 + b < K) v |= (uint32_t)src[j0 + b] << (8 * b);
+          return v;
+        };
+        w = make_uint4(pack(0), pack(4), pack(8), pack(12));
+      }
+      *reinterpret_cast<uint4 *>(o.codes + ((int64_t)(t0 + tt) * o.n + rr) * CODE_STRIDE) = w;
     }
   }
+  cp_async_wait0();  // only empty groups can remain; drain them before exit
 }
 
 // Exact recomputation of the listed outputs, one warp per output.  Lanes
@@ -487,23 +582,23 @@ static int project_impl(const float *X, int64_t ldx, const uint32_t *rows, int64
                         const float *A, int LK, ProjArgs o, cudaStream_t st) {
   if (nrows <= 0) return DETLSH_OK;
   DL_CUDA(cudaMemsetAsync(o.fb_count, 0, sizeof(uint32_t), st));
-  const int W = (MODE == 2) ? (PJ_COLS / o.K) * o.K : PJ_COLS;
-  dim3 grid((unsigned)ceil_div(nrows, PJ_ROWS), (unsigned)ceil_div(LK, W));
-  size_t dyn = 0;
-  if (MODE == 2) {  // codes of a tile, then the tile's breakpoints
-    dyn = PJ_ROWS * PJ_COLS + sizeof(float) * PJ_COLS * BSTRIDE;
-  }
+  const int W = (MODE == 2) ? (EN_COLS / o.K) * o.K : PJ_COLS;
   if constexpr (MODE == 2) {
+    // gamma >= u / (1 - EN_CH u), u = 2^-24, rounded up
+    o.gamma = std::nextafter((float)(0x1p-24 * (1.0 + 2.0 * EN_CH * 0x1p-24) * (1.0 + 1e-9)), INFINITY);
+    const size_t dyn = encode_smem_bytes();
     DL_CUDA(cudaFuncSetAttribute(k_encode, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
     int dev = 0, sms = 0, per = 0;
     DL_CUDA(cudaGetDevice(&dev));
     DL_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    DL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_encode, PJ_THREADS, dyn));
-    const int64_t gx = std::min<int64_t>(grid.x, (int64_t)sms * std::max(per, 1) / grid.y + 1);
-    dim3 pgrid((unsigned)std::max<int64_t>(gx, 1), grid.y);
-    k_encode<<<pgrid, PJ_THREADS, dyn, st>>>(X, ldx, nrows, d, A, LK, W, o);
+    DL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_encode, EN_THREADS, dyn));
+    const int64_t ny = ceil_div(LK, W), tiles = ceil_div(nrows, EN_ROWS);
+    // persistent: one wave of CTAs, split over the column tiles
+    const int64_t gx = std::min<int64_t>(tiles, std::max<int64_t>((int64_t)sms * std::max(per, 1) / ny, 1));
+    k_encode<<<dim3((unsigned)gx, (unsigned)ny), EN_THREADS, dyn, st>>>(X, ldx, nrows, d, A, LK, W, o);
   } else {
-    k_project<MODE><<<grid, PJ_THREADS, dyn, st>>>(X, ldx, rows, nrows, d, A, LK, W, o);
+    dim3 grid((unsigned)ceil_div(nrows, PJ_ROWS), (unsigned)ceil_div(LK, W));
+    k_project<MODE><<<grid, PJ_THREADS, 0, st>>>(X, ldx, rows, nrows, d, A, LK, W, o);
   }
   dl_count_launch();
   DL_CUDA(cudaGetLastError());

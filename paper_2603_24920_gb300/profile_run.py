@@ -47,8 +47,10 @@ def main():
         D.detlsh_query_ex(h, Qd, k, beta=a.beta, c=a.c, precision=D.PREC_FP32, stream=st)
         torch.cuda.synchronize()
         t = D.detlsh_get_timings(h)
-        print("build %.3f ms  query kernel %.3f ms  |S|/q %.0f" %
-              (t.build_ms, t.query_kernel_ms, t.query_candidates / max(1, t.query_count)),
+        print("build %.3f ms (sample %.3f, breakpoints %.3f, encode %.3f, trees %.3f)  "
+              "query kernel %.3f ms  |S|/q %.0f" %
+              (t.build_ms, t.sample_ms, t.breakpoints_ms, t.encode_ms, t.trees_ms,
+               t.query_kernel_ms, t.query_candidates / max(1, t.query_count)),
               flush=True)
         D.detlsh_free(h)
 
