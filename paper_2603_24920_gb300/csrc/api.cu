@@ -465,11 +465,9 @@ int build_impl(detlsh_index *ix, const float *data, cudaStream_t st, const detls
   } else {
     DL_CUDA(cudaMemcpyAsync(ubound, minmax, sizeof(uint32_t) * 2 * LK, cudaMemcpyDeviceToDevice, st));
   }
-  const double du = (double)d * 0x1p-24;
   ProjArgs pe = pa;
   pe.codes = ix->codes; pe.n = n; pe.B = ix->B; pe.N_r = N_r; pe.K = K; pe.minmax = minmax;
   pe.ubound = ubound;
-  pe.gamma = std::nextafter((float)(0x1p-24 * (1.0 + 2.0 * du) * (1.0 + 1e-9)), INFINITY);
   // uncertain or outer-region coordinates: a few per cent of n*LK
   uint2 *fb_enc = nullptr;
   const uint32_t fb_enc_cap = (uint32_t)std::min<int64_t>(std::max<int64_t>(n * LK / 16, 65536), 1 << 26);
@@ -513,36 +511,37 @@ int build_impl(detlsh_index *ix, const float *data, cudaStream_t st, const detls
   DL_TRY(tp.get(&tt.tmp_box, (size_t)n * 48));
   DL_TRY(tp.get(&tt.lists, (size_t)n * 4));
   DL_TRY(tp.get(&tt.leaf_base, (size_t)n));
-  DL_TRY(tp.get(&tt.scalars, 8));
   tt.sort = srt;
   DL_TRY(dalloc(ix, &ix->perm, (size_t)L * n, st));
   DL_TRY(dalloc(ix, &ix->leaf_of, (size_t)L * n, st));
-  std::vector<uint32_t *> t_begin(L);
-  std::vector<uint8_t *> t_box(L);
-  uint32_t *lb_tmp = nullptr;
-  uint8_t *lo_tmp = nullptr, *hi_tmp = nullptr, *nb_tmp = nullptr;
-  DL_TRY(tp.get(&lb_tmp, (size_t)n + 1));
-  DL_TRY(tp.get(&lo_tmp, (size_t)n * 16));
-  DL_TRY(tp.get(&hi_tmp, (size_t)n * 16));
-  DL_TRY(tp.get(&nb_tmp, (size_t)n * 16));
+  // every tree writes its leaves to its own worst-case (n leaves) region, so
+  // the L builds are enqueued back to back and the host waits once
+  uint32_t *lb_tmp = nullptr, *scal = nullptr;
+  uint8_t *box_tmp = nullptr;
+  DL_TRY(tp.get(&lb_tmp, (size_t)L * (n + 1)));
+  DL_TRY(tp.get(&box_tmp, (size_t)L * n * 48));
+  DL_TRY(tp.get(&scal, (size_t)4 * L));
   for (int t = 0; t < L; ++t) {
     TreeBuildArgs a;
     a.n = n; a.K = K; a.bbits = ix->bbits; a.M = ix->M; a.box_mode = ix->box_mode;
     a.codes_t = ix->codes + (size_t)t * n * CODE_STRIDE;
     a.perm = ix->perm + (size_t)t * n;
-    a.leaf_begin = lb_tmp; a.leaf_lo = lo_tmp; a.leaf_hi = hi_tmp; a.leaf_nb = nb_tmp;
+    a.leaf_begin = lb_tmp + (size_t)t * (n + 1);
+    a.leaf_lo = box_tmp + (size_t)t * n * 48;
+    a.leaf_hi = a.leaf_lo + (size_t)n * 16;
+    a.leaf_nb = a.leaf_lo + (size_t)n * 32;
     a.leaf_of = ix->leaf_of; a.L = L; a.t = t;
-    int64_t nl = 0, ml = 0;
-    DL_TRY(build_tree(a, tt, &nl, &ml, st));
-    ix->nleaves[t] = nl;
-    ix->max_leaf = std::max(ix->max_leaf, ml);
-    ix->max_leaves = std::max(ix->max_leaves, nl);
-    DL_TRY(tp.get(&t_begin[t], (size_t)nl + 1));
-    DL_TRY(tp.get(&t_box[t], (size_t)nl * 48));
-    DL_CUDA(cudaMemcpyAsync(t_begin[t], lb_tmp, sizeof(uint32_t) * (nl + 1), cudaMemcpyDeviceToDevice, st));
-    DL_CUDA(cudaMemcpyAsync(t_box[t], lo_tmp, (size_t)nl * 16, cudaMemcpyDeviceToDevice, st));
-    DL_CUDA(cudaMemcpyAsync(t_box[t] + nl * 16, hi_tmp, (size_t)nl * 16, cudaMemcpyDeviceToDevice, st));
-    DL_CUDA(cudaMemcpyAsync(t_box[t] + nl * 32, nb_tmp, (size_t)nl * 16, cudaMemcpyDeviceToDevice, st));
+    a.scalars = scal + 4 * t;
+    DL_TRY(build_tree(a, tt, st));
+  }
+  std::vector<uint32_t> hs((size_t)4 * L);
+  DL_CUDA(cudaMemcpyAsync(hs.data(), scal, sizeof(uint32_t) * hs.size(), cudaMemcpyDeviceToHost, st));
+  DL_CUDA(cudaStreamSynchronize(st));
+  for (int t = 0; t < L; ++t) {
+    if (hs[4 * t + 2] != 0) return (int)hs[4 * t + 2];
+    ix->nleaves[t] = hs[4 * t + 1];
+    ix->max_leaf = std::max<int64_t>(ix->max_leaf, hs[4 * t + 3]);
+    ix->max_leaves = std::max<int64_t>(ix->max_leaves, hs[4 * t + 1]);
   }
   int64_t tl = 0;
   for (int t = 0; t < L; ++t) { ix->leaf_off[t] = tl; tl += ix->nleaves[t]; }
@@ -553,12 +552,13 @@ int build_impl(detlsh_index *ix, const float *data, cudaStream_t st, const detls
   DL_TRY(dalloc(ix, &ix->leaf_nb, (size_t)tl * 16, st));
   for (int t = 0; t < L; ++t) {
     const int64_t nl = ix->nleaves[t], o = ix->leaf_off[t];
-    DL_CUDA(cudaMemcpyAsync(ix->leaf_begin + o + t, t_begin[t], sizeof(uint32_t) * (nl + 1),
+    const uint8_t *bx = box_tmp + (size_t)t * n * 48;
+    DL_CUDA(cudaMemcpyAsync(ix->leaf_begin + o + t, lb_tmp + (size_t)t * (n + 1), sizeof(uint32_t) * (nl + 1),
                             cudaMemcpyDeviceToDevice, st));
-    DL_CUDA(cudaMemcpyAsync(ix->leaf_lo + o * 16, t_box[t], (size_t)nl * 16, cudaMemcpyDeviceToDevice, st));
-    DL_CUDA(cudaMemcpyAsync(ix->leaf_hi + o * 16, t_box[t] + nl * 16, (size_t)nl * 16,
+    DL_CUDA(cudaMemcpyAsync(ix->leaf_lo + o * 16, bx, (size_t)nl * 16, cudaMemcpyDeviceToDevice, st));
+    DL_CUDA(cudaMemcpyAsync(ix->leaf_hi + o * 16, bx + (size_t)n * 16, (size_t)nl * 16,
                             cudaMemcpyDeviceToDevice, st));
-    DL_CUDA(cudaMemcpyAsync(ix->leaf_nb + o * 16, t_box[t] + nl * 32, (size_t)nl * 16,
+    DL_CUDA(cudaMemcpyAsync(ix->leaf_nb + o * 16, bx + (size_t)n * 32, (size_t)nl * 16,
                             cudaMemcpyDeviceToDevice, st));
   }
   // hulls of runs of LEAF_BLOCK leaves, the coarse level of the range query

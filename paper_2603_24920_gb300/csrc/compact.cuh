@@ -51,7 +51,9 @@ __global__ void k_compact_count(int64_t n, Flag f, uint32_t *block_counts) {
 }
 
 // In-place exclusive scan of nb counts by one CTA; total to *total.
-__global__ void k_scan_counts(uint32_t *counts, int64_t nb, uint32_t *total);
+// Exclusive scan of counts[0 .. nb) in place (nb read from *nb_dev when that
+// is given); *total (optional) receives the sum.
+__global__ void k_scan_counts(uint32_t *counts, int64_t nb, const uint32_t *nb_dev, uint32_t *total);
 
 template <class Flag>
 __global__ void k_compact_write(int64_t n, Flag f, const uint32_t *block_offsets, uint32_t *out) {
@@ -80,7 +82,7 @@ int compact(int64_t n, Flag f, uint32_t *block_counts, uint32_t *out, uint32_t *
   }
   k_compact_count<<<(unsigned)nb, CP_THREADS, 0, st>>>(n, f, block_counts);
   dl_count_launch();
-  k_scan_counts<<<1, 1024, 0, st>>>(block_counts, nb, count);
+  k_scan_counts<<<1, 1024, 0, st>>>(block_counts, nb, nullptr, count);
   dl_count_launch();
   k_compact_write<<<(unsigned)nb, CP_THREADS, 0, st>>>(n, f, block_counts, out);
   dl_count_launch();

@@ -19,7 +19,7 @@ struct ProjArgs {
   int N_r = 0, K = 0;
   uint32_t *minmax = nullptr;  // [LK][2] order-preserving keys
   uint32_t *ubound = nullptr;    // [LK][2] running bounds of column min/max (mode 2)
-  float gamma = 0.0f;            // u (1 + 2 d u), u = 2^-24, rounded up (mode 2)
+  float gamma = 0.0f;            // encoder error factor (mode 2; set by project_rows)
   // outputs the compensated path cannot certify
   uint2 *fb_list = nullptr;
   uint32_t *fb_count = nullptr;
@@ -66,6 +66,7 @@ struct TreeBuildArgs {
   uint32_t *leaf_begin;    // [nleaves+1]
   uint8_t *leaf_lo, *leaf_hi, *leaf_nb;  // [nleaves][16]
   uint32_t *leaf_of;       // [n][L] (column t)
+  uint32_t *scalars;       // [4] (device): first-layer nodes, leaves, error, largest leaf
   int L, t;
 };
 struct TreeTemp {
@@ -77,13 +78,11 @@ struct TreeTemp {
   uint8_t *tmp_box = nullptr;  // [n][48]: lo, hi, nb of the leaf starting there
   uint4 *lists = nullptr;      // [2n][2]: the open nodes of two levels
   uint32_t *leaf_base = nullptr;
-  uint32_t *scalars = nullptr;
   SortTemp sort;
 };
-// Builds one tree; returns the number of leaves through *nleaves.  The leaf
-// arrays must hold n entries (n+1 for leaf_begin).
-int build_tree(const TreeBuildArgs &a, TreeTemp &tmp, int64_t *nleaves, int64_t *max_leaf,
-               cudaStream_t st);
+// Enqueues the build of one tree (no host synchronisation); the counts land
+// in a.scalars.  The leaf arrays must hold n entries (n+1 for leaf_begin).
+int build_tree(const TreeBuildArgs &a, TreeTemp &tmp, cudaStream_t st);
 // Hull boxes of runs of LEAF_BLOCK leaves: [ceil(nleaves/LEAF_BLOCK)][16] each.
 int block_hulls(const uint8_t *lo, const uint8_t *hi, int64_t nleaves, uint8_t *hlo, uint8_t *hhi,
                 cudaStream_t st);

@@ -142,8 +142,9 @@ int segmented_sort(uint32_t *keys, uint32_t *vals, int nseg, int64_t len, int nb
 }
 
 // ---- compaction scan ----------------------------------------------------------
-__global__ void k_scan_counts(uint32_t *counts, int64_t nb, uint32_t *total) {
+__global__ void k_scan_counts(uint32_t *counts, int64_t nb, const uint32_t *nb_dev, uint32_t *total) {
   __shared__ uint32_t wt[32];
+  if (nb_dev) nb = *nb_dev;  // the count lives on the device (no host round trip)
   uint32_t carry = 0;
   for (int64_t base = 0; base < nb; base += blockDim.x) {
     const int64_t i = base + threadIdx.x;

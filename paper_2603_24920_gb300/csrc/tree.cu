@@ -72,7 +72,7 @@ struct NodeEntry {
 struct SubtreeArgs {
   int64_t n;
   int K, bbits, M, box_mode;
-  uint32_t F;
+  const uint32_t *F;           // number of first-layer nodes (device)
   const uint32_t *node_begin;  // [F+1]
   uint4 *codesA, *codesB;
   uint32_t *idsA, *idsB;
@@ -95,10 +95,11 @@ __global__ void __launch_bounds__(TB_THREADS) k_subtree(SubtreeArgs a) {
   const unsigned lt = (1u << lane) - 1u;
   const uint32_t P0 = blockIdx.x * (uint32_t)TB_POINTS;
   if (threadIdx.x == 0) {  // first-layer nodes f with node_begin[f] in [P0, P0 + TB_POINTS)
-    uint32_t lo = 0, hi = a.F;
+    const uint32_t F = *a.F;
+    uint32_t lo = 0, hi = F;
     while (lo < hi) { const uint32_t mid = (lo + hi) >> 1; if (a.node_begin[mid] < P0) lo = mid + 1; else hi = mid; }
     f_lo = lo;
-    hi = a.F;
+    hi = F;
     while (lo < hi) {
       const uint32_t mid = (lo + hi) >> 1;
       if (a.node_begin[mid] < P0 + (uint32_t)TB_POINTS) lo = mid + 1; else hi = mid;
@@ -253,10 +254,10 @@ struct LeafWriteArgs {
 
 // One warp per first-layer node: its leaves in position order (= depth-first
 // order), numbered from the node's base; records copied, leaf_of written.
-__global__ void k_leaf_write(LeafWriteArgs a, int64_t F) {
+__global__ void k_leaf_write(LeafWriteArgs a, const uint32_t *F) {
   const int64_t f = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
-  if (f >= F) return;
+  if (f >= *F) return;
   const uint32_t nb0 = a.node_begin[f], ne = a.node_begin[f + 1];
   uint32_t g = a.leaf_base[f];
   auto emit = [&](uint32_t lb, uint32_t le) {
@@ -287,6 +288,8 @@ __global__ void k_leaf_write(LeafWriteArgs a, int64_t F) {
 }
 
 __global__ void k_set_u32(uint32_t *p, uint32_t v) { *p = v; }
+// base[*idx] = v, the index read on the device
+__global__ void k_set_at(uint32_t *base, const uint32_t *idx, uint32_t v) { base[*idx] = v; }
 
 // Hull boxes of consecutive runs of LEAF_BLOCK leaves (in canonical order):
 // per dimension the smallest lo and largest hi of the run.  A hull contains
@@ -325,11 +328,14 @@ int block_hulls(const uint8_t *lo, const uint8_t *hi, int64_t nleaves, uint8_t *
   return DETLSH_OK;
 }
 
-int build_tree(const TreeBuildArgs &A, TreeTemp &T, int64_t *nleaves, int64_t *max_leaf,
-               cudaStream_t st) {
+int build_tree(const TreeBuildArgs &A, TreeTemp &T, cudaStream_t st) {
   const int64_t n = A.n;
   const int gs = (int)std::min<int64_t>(ceil_div(n, 256), 4096);
-  DL_CUDA(cudaMemsetAsync(T.scalars, 0, 4 * sizeof(uint32_t), st));
+  // no host round trip: counts stay on the device, launches are sized by
+  // their upper bounds (at most min(n, 2^K) first-layer nodes)
+  const int64_t Fmax = std::min<int64_t>(n, (int64_t)1 << A.K);
+  uint32_t *S = A.scalars;  // [0] F, [1] leaves, [2] error, [3] largest leaf
+  DL_CUDA(cudaMemsetAsync(S, 0, 4 * sizeof(uint32_t), st));
   k_first_keys<<<gs, 256, 0, st>>>(A.codes_t, n, A.K, A.bbits, T.keys, T.vals);
   dl_count_launch();
   DL_CUDA(cudaGetLastError());
@@ -339,16 +345,12 @@ int build_tree(const TreeBuildArgs &A, TreeTemp &T, int64_t *nleaves, int64_t *m
   dl_count_launch();
   DL_CUDA(cudaGetLastError());
   // first-layer nodes = runs of equal keys
-  uint32_t *F_dev = T.scalars;
-  DL_TRY(compact(n, BoundaryFlag{T.keys}, T.block_counts, T.node_begin, F_dev, st));
-  uint32_t F = 0;
-  DL_CUDA(cudaMemcpyAsync(&F, F_dev, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
-  DL_CUDA(cudaStreamSynchronize(st));
-  k_set_u32<<<1, 1, 0, st>>>(T.node_begin + F, (uint32_t)n);
+  DL_TRY(compact(n, BoundaryFlag{T.keys}, T.block_counts, T.node_begin, S + 0, st));
+  k_set_at<<<1, 1, 0, st>>>(T.node_begin, S + 0, (uint32_t)n);
   dl_count_launch();
   SubtreeArgs sa;
   sa.n = n; sa.K = A.K; sa.bbits = A.bbits; sa.M = A.M; sa.box_mode = A.box_mode;
-  sa.F = F;
+  sa.F = S + 0;
   sa.node_begin = T.node_begin;
   sa.codesA = T.codesA; sa.codesB = T.codesB;
   sa.idsA = T.vals; sa.idsB = T.idsB;
@@ -358,36 +360,29 @@ int build_tree(const TreeBuildArgs &A, TreeTemp &T, int64_t *nleaves, int64_t *m
   sa.tmp_box = T.tmp_box;
   sa.listA = reinterpret_cast<NodeEntry *>(T.lists);
   sa.listB = reinterpret_cast<NodeEntry *>(T.lists) + n;
-  sa.err = reinterpret_cast<int *>(T.scalars + 2);
-  DL_CUDA(cudaMemsetAsync(T.node_count, 0, sizeof(uint32_t) * F, st));
+  sa.err = reinterpret_cast<int *>(S + 2);
+  DL_CUDA(cudaMemsetAsync(T.node_count, 0, sizeof(uint32_t) * Fmax, st));
   DL_CUDA(cudaMemsetAsync(T.tmp_begin, 0, sizeof(uint32_t) * (size_t)n, st));
   k_subtree<<<(unsigned)ceil_div(n, TB_POINTS), TB_THREADS, 0, st>>>(sa);
   dl_count_launch();
   DL_CUDA(cudaGetLastError());
   // leaf numbering
-  DL_CUDA(cudaMemcpyAsync(T.leaf_base, T.node_count, sizeof(uint32_t) * F,
+  DL_CUDA(cudaMemcpyAsync(T.leaf_base, T.node_count, sizeof(uint32_t) * Fmax,
                           cudaMemcpyDeviceToDevice, st));
-  k_scan_counts<<<1, 1024, 0, st>>>(T.leaf_base, F, T.scalars + 1);
+  k_scan_counts<<<1, 1024, 0, st>>>(T.leaf_base, Fmax, S + 0, S + 1);
   dl_count_launch();
-  DL_CUDA(cudaMemsetAsync(T.scalars + 3, 0, sizeof(uint32_t), st));
   LeafWriteArgs lw;
   lw.n = n; lw.L = A.L; lw.t = A.t;
   lw.node_begin = T.node_begin; lw.leaf_base = T.leaf_base; lw.leaf_flag = T.tmp_begin;
   lw.perm = A.perm; lw.tmp_box = T.tmp_box;
   lw.leaf_begin = A.leaf_begin; lw.leaf_lo = A.leaf_lo; lw.leaf_hi = A.leaf_hi;
-  lw.leaf_nb = A.leaf_nb; lw.leaf_of = A.leaf_of; lw.max_leaf = T.scalars + 3;
-  k_leaf_write<<<(unsigned)ceil_div((int64_t)F * 32, 256), 256, 0, st>>>(lw, F);
+  lw.leaf_nb = A.leaf_nb; lw.leaf_of = A.leaf_of; lw.max_leaf = S + 3;
+  k_leaf_write<<<(unsigned)ceil_div(Fmax * 32, 256), 256, 0, st>>>(lw, S + 0);
   dl_count_launch();
   DL_CUDA(cudaGetLastError());
-  uint32_t hs[4];
-  DL_CUDA(cudaMemcpyAsync(hs, T.scalars, sizeof(hs), cudaMemcpyDeviceToHost, st));
-  DL_CUDA(cudaStreamSynchronize(st));
-  if (hs[2] != 0) return (int)hs[2];
-  k_set_u32<<<1, 1, 0, st>>>(A.leaf_begin + hs[1], (uint32_t)n);
+  k_set_at<<<1, 1, 0, st>>>(A.leaf_begin, S + 1, (uint32_t)n);
   dl_count_launch();
   DL_CUDA(cudaGetLastError());
-  *nleaves = hs[1];
-  *max_leaf = hs[3];
   return DETLSH_OK;
 }
 
