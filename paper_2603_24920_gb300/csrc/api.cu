@@ -391,14 +391,8 @@ int build_impl(detlsh_index *ix, const float *data, cudaStream_t st, const detls
 
   const bool stat = ix->encoding == DETLSH_ENC_STATIC;
   int e = 0;
-  SortTemp srt;  // the sample-column sort here, the first-layer key sort later
+  SortTemp srt;  // the sample-column sort
   if (stat) {
-    const size_t cnt_cap = 256 * sort_tiles(n);
-    DL_TRY(tp.get(&srt.counts, cnt_cap));
-    srt.count_cap = cnt_cap;
-    DL_TRY(tp.get(&srt.keys_alt, (size_t)n));
-    DL_TRY(tp.get(&srt.vals_alt, (size_t)n));
-    DL_TRY(tp.get(&srt.digit_base, (size_t)256));
     // ---- static scheme: fixed N(0,1) breakpoints, no sample ----
     DL_TRY(dalloc(ix, &ix->sample, 1, st));
     ix->m_sample = 0;
@@ -433,11 +427,10 @@ int build_impl(detlsh_index *ix, const float *data, cudaStream_t st, const detls
     if (e) return e;
     DL_CUDA(cudaEventRecord(ix->ev[1], st));
     DL_TRY(float_to_keys(Ps, (int64_t)LK * m, st));
-    const size_t cnt_cap = std::max<size_t>((size_t)LK * 256 * sort_tiles(m), 256 * sort_tiles(n));
+    const size_t cnt_cap = (size_t)LK * 256 * sort_tiles(m);
     DL_TRY(tp.get(&srt.counts, cnt_cap));
     srt.count_cap = cnt_cap;
-    DL_TRY(tp.get(&srt.keys_alt, std::max<size_t>((size_t)LK * m, (size_t)n)));
-    DL_TRY(tp.get(&srt.vals_alt, (size_t)n));
+    DL_TRY(tp.get(&srt.keys_alt, (size_t)LK * m));
     DL_TRY(tp.get(&srt.digit_base, (size_t)LK * 256));
     DL_TRY(segmented_sort(reinterpret_cast<uint32_t *>(Ps), nullptr, LK, m, 32, srt, st));
     DL_TRY(dalloc(ix, &ix->B, (size_t)LK * (N_r + 1), st));
@@ -498,50 +491,76 @@ int build_impl(detlsh_index *ix, const float *data, cudaStream_t st, const detls
   DL_CUDA(cudaMemcpyAsync(&fbt, fb_total, sizeof fbt, cudaMemcpyDeviceToHost, st));
 
   // ---- DE-Trees (Alg. 2) ----
-  TreeTemp tt;
-  DL_TRY(tp.get(&tt.keys, (size_t)n));
-  DL_TRY(tp.get(&tt.vals, (size_t)n));
-  DL_TRY(tp.get(&tt.codesA, (size_t)n));
-  DL_TRY(tp.get(&tt.codesB, (size_t)n));
-  DL_TRY(tp.get(&tt.idsB, (size_t)n));
-  DL_TRY(tp.get(&tt.node_begin, (size_t)n + 1));
-  DL_TRY(tp.get(&tt.node_count, (size_t)n));
-  DL_TRY(tp.get(&tt.block_counts, sample_blocks(n) + 4));
-  DL_TRY(tp.get(&tt.tmp_begin, (size_t)n));
-  DL_TRY(tp.get(&tt.tmp_box, (size_t)n * 48));
-  DL_TRY(tp.get(&tt.lists, (size_t)n * 4));
-  DL_TRY(tp.get(&tt.leaf_base, (size_t)n));
-  tt.sort = srt;
+  // Trees are built G at a time (every kernel runs over G * n positions);
+  // G is L unless the temporaries would crowd the device or the positions
+  // would overflow 32 bits.  Each group writes its leaves to its own
+  // worst-case region, so all groups are enqueued back to back and the host
+  // waits once.
   DL_TRY(dalloc(ix, &ix->perm, (size_t)L * n, st));
   DL_TRY(dalloc(ix, &ix->leaf_of, (size_t)L * n, st));
-  // every tree writes its leaves to its own worst-case (n leaves) region, so
-  // the L builds are enqueued back to back and the host waits once
-  uint32_t *lb_tmp = nullptr, *scal = nullptr;
-  uint8_t *box_tmp = nullptr;
-  DL_TRY(tp.get(&lb_tmp, (size_t)L * (n + 1)));
-  DL_TRY(tp.get(&box_tmp, (size_t)L * n * 48));
-  DL_TRY(tp.get(&scal, (size_t)4 * L));
-  for (int t = 0; t < L; ++t) {
-    TreeBuildArgs a;
-    a.n = n; a.K = K; a.bbits = ix->bbits; a.M = ix->M; a.box_mode = ix->box_mode;
-    a.codes_t = ix->codes + (size_t)t * n * CODE_STRIDE;
-    a.perm = ix->perm + (size_t)t * n;
-    a.leaf_begin = lb_tmp + (size_t)t * (n + 1);
-    a.leaf_lo = box_tmp + (size_t)t * n * 48;
-    a.leaf_hi = a.leaf_lo + (size_t)n * 16;
-    a.leaf_nb = a.leaf_lo + (size_t)n * 32;
-    a.leaf_of = ix->leaf_of; a.L = L; a.t = t;
-    a.scalars = scal + 4 * t;
-    DL_TRY(build_tree(a, tt, st));
+  int G = L;
+  {
+    size_t freeb = 0, totb = 0;
+    DL_CUDA(cudaMemGetInfo(&freeb, &totb));
+    const size_t per_tree = (size_t)n * 240;  // group temporaries per tree, bytes
+    while (G > 1 && ((size_t)G * per_tree > freeb / 2 || (int64_t)G * n + G > (int64_t)UINT32_MAX)) --G;
   }
-  std::vector<uint32_t> hs((size_t)4 * L);
+  const int ngroups = (L + G - 1) / G;
+  const int64_t N = (int64_t)G * n;
+  TreeTemp tt;
+  DL_TRY(tp.get(&tt.keys, (size_t)N));
+  DL_TRY(tp.get(&tt.vals, (size_t)N));
+  DL_TRY(tp.get(&tt.codesA, (size_t)N));
+  DL_TRY(tp.get(&tt.codesB, (size_t)N));
+  DL_TRY(tp.get(&tt.idsB, (size_t)N));
+  DL_TRY(tp.get(&tt.node_begin, (size_t)N + 1));
+  DL_TRY(tp.get(&tt.node_count, (size_t)N));
+  DL_TRY(tp.get(&tt.block_counts, sample_blocks(N) + 4));
+  DL_TRY(tp.get(&tt.tmp_begin, (size_t)N));
+  DL_TRY(tp.get(&tt.tmp_box, (size_t)N * 48));
+  DL_TRY(tp.get(&tt.lists, (size_t)N * 4));
+  DL_TRY(tp.get(&tt.leaf_base, (size_t)N));
+  {
+    const size_t cnt_cap = (size_t)G * 256 * sort_tiles(n);
+    DL_TRY(tp.get(&tt.sort.counts, cnt_cap));
+    tt.sort.count_cap = cnt_cap;
+    DL_TRY(tp.get(&tt.sort.keys_alt, (size_t)N));
+    DL_TRY(tp.get(&tt.sort.vals_alt, (size_t)N));
+    DL_TRY(tp.get(&tt.sort.digit_base, (size_t)G * 256));
+  }
+  constexpr int SCAL = 32;  // scalars per group: 4 counts + up to 17 tree offsets
+  uint32_t *scal = nullptr;
+  DL_TRY(tp.get(&scal, (size_t)SCAL * ngroups));
+  std::vector<uint32_t *> g_begin(ngroups);
+  std::vector<uint8_t *> g_box(ngroups);
+  for (int g = 0; g < ngroups; ++g) {
+    const int t0 = g * G, Gg = std::min(G, L - t0);
+    DL_TRY(tp.get(&g_begin[g], (size_t)Gg * (n + 1)));
+    DL_TRY(tp.get(&g_box[g], (size_t)Gg * n * 48));
+    TreeBuildArgs a;
+    a.n = n; a.G = Gg; a.K = K; a.bbits = ix->bbits; a.M = ix->M; a.box_mode = ix->box_mode;
+    a.codes = ix->codes + (size_t)t0 * n * CODE_STRIDE;
+    a.perm = ix->perm + (size_t)t0 * n;
+    a.leaf_begin = g_begin[g];
+    a.leaf_lo = g_box[g];
+    a.leaf_hi = a.leaf_lo + (size_t)Gg * n * 16;
+    a.leaf_nb = a.leaf_lo + (size_t)Gg * n * 32;
+    a.leaf_of = ix->leaf_of; a.L = L; a.t0 = t0;
+    a.scalars = scal + SCAL * g;
+    DL_TRY(build_trees(a, tt, st));
+  }
+  std::vector<uint32_t> hs((size_t)SCAL * ngroups);
   DL_CUDA(cudaMemcpyAsync(hs.data(), scal, sizeof(uint32_t) * hs.size(), cudaMemcpyDeviceToHost, st));
   DL_CUDA(cudaStreamSynchronize(st));
-  for (int t = 0; t < L; ++t) {
-    if (hs[4 * t + 2] != 0) return (int)hs[4 * t + 2];
-    ix->nleaves[t] = hs[4 * t + 1];
-    ix->max_leaf = std::max<int64_t>(ix->max_leaf, hs[4 * t + 3]);
-    ix->max_leaves = std::max<int64_t>(ix->max_leaves, hs[4 * t + 1]);
+  for (int g = 0; g < ngroups; ++g) {
+    const uint32_t *h = hs.data() + SCAL * g;
+    if (h[2] != 0) return (int)h[2];
+    const int t0 = g * G, Gg = std::min(G, L - t0);
+    for (int u = 0; u < Gg; ++u) {
+      ix->nleaves[t0 + u] = (int64_t)h[4 + u + 1] - h[4 + u];
+      ix->max_leaves = std::max(ix->max_leaves, ix->nleaves[t0 + u]);
+    }
+    ix->max_leaf = std::max<int64_t>(ix->max_leaf, h[3]);
   }
   int64_t tl = 0;
   for (int t = 0; t < L; ++t) { ix->leaf_off[t] = tl; tl += ix->nleaves[t]; }
@@ -550,15 +569,16 @@ int build_impl(detlsh_index *ix, const float *data, cudaStream_t st, const detls
   DL_TRY(dalloc(ix, &ix->leaf_lo, (size_t)tl * 16, st));
   DL_TRY(dalloc(ix, &ix->leaf_hi, (size_t)tl * 16, st));
   DL_TRY(dalloc(ix, &ix->leaf_nb, (size_t)tl * 16, st));
-  for (int t = 0; t < L; ++t) {
-    const int64_t nl = ix->nleaves[t], o = ix->leaf_off[t];
-    const uint8_t *bx = box_tmp + (size_t)t * n * 48;
-    DL_CUDA(cudaMemcpyAsync(ix->leaf_begin + o + t, lb_tmp + (size_t)t * (n + 1), sizeof(uint32_t) * (nl + 1),
+  for (int g = 0; g < ngroups; ++g) {  // a group's leaves are contiguous in the final layout
+    const int t0 = g * G, Gg = std::min(G, L - t0);
+    const int64_t nl = ix->leaf_off[t0 + Gg] - ix->leaf_off[t0], o = ix->leaf_off[t0];
+    const uint8_t *bx = g_box[g];
+    DL_CUDA(cudaMemcpyAsync(ix->leaf_begin + o + t0, g_begin[g], sizeof(uint32_t) * (nl + Gg),
                             cudaMemcpyDeviceToDevice, st));
     DL_CUDA(cudaMemcpyAsync(ix->leaf_lo + o * 16, bx, (size_t)nl * 16, cudaMemcpyDeviceToDevice, st));
-    DL_CUDA(cudaMemcpyAsync(ix->leaf_hi + o * 16, bx + (size_t)n * 16, (size_t)nl * 16,
+    DL_CUDA(cudaMemcpyAsync(ix->leaf_hi + o * 16, bx + (size_t)Gg * n * 16, (size_t)nl * 16,
                             cudaMemcpyDeviceToDevice, st));
-    DL_CUDA(cudaMemcpyAsync(ix->leaf_nb + o * 16, bx + (size_t)n * 32, (size_t)nl * 16,
+    DL_CUDA(cudaMemcpyAsync(ix->leaf_nb + o * 16, bx + (size_t)Gg * n * 32, (size_t)nl * 16,
                             cudaMemcpyDeviceToDevice, st));
   }
   // hulls of runs of LEAF_BLOCK leaves, the coarse level of the range query

@@ -59,15 +59,17 @@ int finish_breakpoint_ends(const uint32_t *minmax, int LK, int N_r, float *B, cu
 // ---- DE-Tree layout (tree.cu) ----------------------------------------------
 struct TreeBuildArgs {
   int64_t n;
+  int G;                   // trees built together: t0 .. t0 + G - 1
   int K, bbits, M, box_mode;
-  const uint8_t *codes_t;  // codes of this tree, [n][16]
+  const uint8_t *codes;    // codes of tree t0, then the next G - 1 trees: [G][n][16]
   // outputs
-  uint32_t *perm;          // [n] point ids leaf by leaf
-  uint32_t *leaf_begin;    // [nleaves+1]
-  uint8_t *leaf_lo, *leaf_hi, *leaf_nb;  // [nleaves][16]
-  uint32_t *leaf_of;       // [n][L] (column t)
-  uint32_t *scalars;       // [4] (device): first-layer nodes, leaves, error, largest leaf
-  int L, t;
+  uint32_t *perm;          // [G][n] point ids leaf by leaf (the trees' rows of perm)
+  uint32_t *leaf_begin;    // [leaves + G]: each tree's starts (within the tree) and end n
+  uint8_t *leaf_lo, *leaf_hi, *leaf_nb;  // [leaves][16], trees one after another
+  uint32_t *leaf_of;       // [n][L] (columns t0 ..)
+  uint32_t *scalars;       // [4 + G + 1] (device): first-layer nodes, leaves, error,
+                           // largest leaf, first leaf of every tree and the total
+  int L, t0;
 };
 struct TreeTemp {
   uint32_t *keys = nullptr, *vals = nullptr;
@@ -80,9 +82,10 @@ struct TreeTemp {
   uint32_t *leaf_base = nullptr;
   SortTemp sort;
 };
-// Enqueues the build of one tree (no host synchronisation); the counts land
-// in a.scalars.  The leaf arrays must hold n entries (n+1 for leaf_begin).
-int build_tree(const TreeBuildArgs &a, TreeTemp &tmp, cudaStream_t st);
+// Enqueues the build of G trees (no host synchronisation); the counts land in
+// a.scalars.  Temporaries hold G n entries; the leaf arrays G n (G n + G for
+// leaf_begin).
+int build_trees(const TreeBuildArgs &a, TreeTemp &tmp, cudaStream_t st);
 // Hull boxes of runs of LEAF_BLOCK leaves: [ceil(nleaves/LEAF_BLOCK)][16] each.
 int block_hulls(const uint8_t *lo, const uint8_t *hi, int64_t nleaves, uint8_t *hlo, uint8_t *hhi,
                 cudaStream_t st);

@@ -6,8 +6,10 @@
 // layer key ascending (dimension 0 is the most significant bit), then child 0
 // before child 1; points inside a leaf in ascending id order.
 //
-// Build: (1) stable radix sort of the point ids by their K-bit first-layer
-// key (the root's 2^K children); (2) the subtrees of the first-layer nodes,
+// Build, for a group of G trees at once (every kernel runs over the G * n
+// positions of the group; tree g owns positions [g n, (g + 1) n)): (1) stable
+// radix sort of the point ids by their K-bit first-layer key (the root's 2^K
+// children), one segment per tree; (2) the subtrees of the first-layer nodes,
 // level by level: a CTA takes the first-layer nodes that start in its range
 // of points (first-layer subtrees are independent, as the paper's parallel
 // indexing phase notes in Sec. IV-B) and, at each level, its warps take the
@@ -31,9 +33,10 @@
 namespace dl {
 
 
-__global__ void k_first_keys(const uint8_t *__restrict__ codes, int64_t n, int K, int bbits,
+// keys and point ids of G trees: position i is point i % n of tree i / n
+__global__ void k_first_keys(const uint8_t *__restrict__ codes, int64_t n, int64_t N, int K, int bbits,
                              uint32_t *keys, uint32_t *vals) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
        i += (int64_t)gridDim.x * blockDim.x) {
     const uint4 c = reinterpret_cast<const uint4 *>(codes)[i];
     const uint32_t w[4] = {c.x, c.y, c.z, c.w};
@@ -43,20 +46,22 @@ __global__ void k_first_keys(const uint8_t *__restrict__ codes, int64_t n, int K
       key |= ((byte >> (bbits - 1)) & 1u) << (K - 1 - j);
     }
     keys[i] = key;
-    vals[i] = (uint32_t)i;
+    vals[i] = (uint32_t)(i % n);
   }
 }
 
 __global__ void k_gather_codes(const uint4 *__restrict__ codes, const uint32_t *__restrict__ ids,
-                               int64_t n, uint4 *out) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+                               int64_t n, int64_t N, uint4 *out) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
        i += (int64_t)gridDim.x * blockDim.x)
-    out[i] = codes[ids[i]];
+    out[i] = codes[(i / n) * n + ids[i]];
 }
 
+// a first-layer node starts at every change of key and at every tree start
 struct BoundaryFlag {
   const uint32_t *keys;
-  __device__ bool operator()(int64_t i) const { return i == 0 || keys[i] != keys[i - 1]; }
+  int64_t n;
+  __device__ bool operator()(int64_t i) const { return i % n == 0 || keys[i] != keys[i - 1]; }
 };
 
 __device__ __forceinline__ uint32_t code_byte(const uint4 &c, int j) {
@@ -243,8 +248,9 @@ __global__ void __launch_bounds__(TB_THREADS) k_subtree(SubtreeArgs a) {
 
 struct LeafWriteArgs {
   int64_t n;
-  int L, t;
+  int L, t0;
   const uint32_t *node_begin, *leaf_base, *leaf_flag, *perm;
+  const uint32_t *tree_leaf_off;  // [G+1] first leaf of every tree of the group
   const uint8_t *tmp_box;
   uint32_t *leaf_begin;
   uint8_t *leaf_lo, *leaf_hi, *leaf_nb;
@@ -254,11 +260,16 @@ struct LeafWriteArgs {
 
 // One warp per first-layer node: its leaves in position order (= depth-first
 // order), numbered from the node's base; records copied, leaf_of written.
+// Leaf g of the group (tree t = its position / n) goes to record g and to
+// leaf_begin[g + t] (each tree's leaf_begin has one end entry more); leaf_of
+// gets the number within the tree, g - tree_leaf_off[t].
 __global__ void k_leaf_write(LeafWriteArgs a, const uint32_t *F) {
   const int64_t f = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (f >= *F) return;
   const uint32_t nb0 = a.node_begin[f], ne = a.node_begin[f + 1];
+  const uint32_t t = (uint32_t)(nb0 / a.n), pos0 = (uint32_t)(t * a.n);
+  const uint32_t g0 = a.tree_leaf_off[t];
   uint32_t g = a.leaf_base[f];
   auto emit = [&](uint32_t lb, uint32_t le) {
     if (lane < 16) {
@@ -267,10 +278,10 @@ __global__ void k_leaf_write(LeafWriteArgs a, const uint32_t *F) {
       a.leaf_nb[(int64_t)g * 16 + lane] = a.tmp_box[(int64_t)lb * 48 + 32 + lane];
     }
     if (lane == 0) {
-      a.leaf_begin[g] = lb;
+      a.leaf_begin[g + t] = lb - pos0;
       atomicMax(a.max_leaf, le - lb);
     }
-    for (uint32_t i = lb + lane; i < le; i += 32) a.leaf_of[(int64_t)a.perm[i] * a.L + a.t] = g;
+    for (uint32_t i = lb + lane; i < le; i += 32) a.leaf_of[(int64_t)a.perm[i] * a.L + a.t0 + t] = g - g0;
     ++g;
   };
   int64_t pend = -1;  // a leaf start whose end is the next start
@@ -290,6 +301,24 @@ __global__ void k_leaf_write(LeafWriteArgs a, const uint32_t *F) {
 __global__ void k_set_u32(uint32_t *p, uint32_t v) { *p = v; }
 // base[*idx] = v, the index read on the device
 __global__ void k_set_at(uint32_t *base, const uint32_t *idx, uint32_t v) { base[*idx] = v; }
+
+// First leaf of every tree of the group (its first first-layer node starts
+// at position t n), the total, and each tree's end entry of leaf_begin.
+__global__ void k_tree_leaf_offsets(const uint32_t *node_begin, const uint32_t *F,
+                                    const uint32_t *leaf_base, const uint32_t *total, int64_t n,
+                                    int G, uint32_t *off, uint32_t *leaf_begin) {
+  const int t = threadIdx.x;
+  if (t > G) return;
+  uint32_t o = *total;
+  if (t < G) {
+    uint32_t lo = 0, hi = *F;
+    const uint32_t key = (uint32_t)(t * n);
+    while (lo < hi) { const uint32_t mid = (lo + hi) >> 1; if (node_begin[mid] < key) lo = mid + 1; else hi = mid; }
+    o = leaf_base[lo];
+  }
+  off[t] = o;
+  if (t > 0) leaf_begin[o + (uint32_t)t - 1] = (uint32_t)n;  // end of tree t - 1
+}
 
 // Hull boxes of consecutive runs of LEAF_BLOCK leaves (in canonical order):
 // per dimension the smallest lo and largest hi of the run.  A hull contains
@@ -328,28 +357,28 @@ int block_hulls(const uint8_t *lo, const uint8_t *hi, int64_t nleaves, uint8_t *
   return DETLSH_OK;
 }
 
-int build_tree(const TreeBuildArgs &A, TreeTemp &T, cudaStream_t st) {
-  const int64_t n = A.n;
-  const int gs = (int)std::min<int64_t>(ceil_div(n, 256), 4096);
+int build_trees(const TreeBuildArgs &A, TreeTemp &T, cudaStream_t st) {
+  const int64_t n = A.n, N = (int64_t)A.G * n;
+  const int gs = (int)std::min<int64_t>(ceil_div(N, 256), 4096);
   // no host round trip: counts stay on the device, launches are sized by
-  // their upper bounds (at most min(n, 2^K) first-layer nodes)
-  const int64_t Fmax = std::min<int64_t>(n, (int64_t)1 << A.K);
-  uint32_t *S = A.scalars;  // [0] F, [1] leaves, [2] error, [3] largest leaf
+  // their upper bounds (at most min(n, 2^K) first-layer nodes per tree)
+  const int64_t Fmax = A.G * std::min<int64_t>(n, (int64_t)1 << A.K);
+  uint32_t *S = A.scalars;  // [0] F, [1] leaves, [2] error, [3] largest leaf, [4..] tree offsets
   DL_CUDA(cudaMemsetAsync(S, 0, 4 * sizeof(uint32_t), st));
-  k_first_keys<<<gs, 256, 0, st>>>(A.codes_t, n, A.K, A.bbits, T.keys, T.vals);
+  k_first_keys<<<gs, 256, 0, st>>>(A.codes, n, N, A.K, A.bbits, T.keys, T.vals);
   dl_count_launch();
   DL_CUDA(cudaGetLastError());
-  DL_TRY(segmented_sort(T.keys, T.vals, 1, n, A.K, T.sort, st));
-  k_gather_codes<<<gs, 256, 0, st>>>(reinterpret_cast<const uint4 *>(A.codes_t), T.vals, n,
+  DL_TRY(segmented_sort(T.keys, T.vals, A.G, n, A.K, T.sort, st));
+  k_gather_codes<<<gs, 256, 0, st>>>(reinterpret_cast<const uint4 *>(A.codes), T.vals, n, N,
                                      T.codesA);
   dl_count_launch();
   DL_CUDA(cudaGetLastError());
-  // first-layer nodes = runs of equal keys
-  DL_TRY(compact(n, BoundaryFlag{T.keys}, T.block_counts, T.node_begin, S + 0, st));
-  k_set_at<<<1, 1, 0, st>>>(T.node_begin, S + 0, (uint32_t)n);
+  // first-layer nodes = runs of equal keys within a tree
+  DL_TRY(compact(N, BoundaryFlag{T.keys, n}, T.block_counts, T.node_begin, S + 0, st));
+  k_set_at<<<1, 1, 0, st>>>(T.node_begin, S + 0, (uint32_t)N);
   dl_count_launch();
   SubtreeArgs sa;
-  sa.n = n; sa.K = A.K; sa.bbits = A.bbits; sa.M = A.M; sa.box_mode = A.box_mode;
+  sa.n = N; sa.K = A.K; sa.bbits = A.bbits; sa.M = A.M; sa.box_mode = A.box_mode;
   sa.F = S + 0;
   sa.node_begin = T.node_begin;
   sa.codesA = T.codesA; sa.codesB = T.codesB;
@@ -359,11 +388,11 @@ int build_tree(const TreeBuildArgs &A, TreeTemp &T, cudaStream_t st) {
   sa.leaf_flag = T.tmp_begin;
   sa.tmp_box = T.tmp_box;
   sa.listA = reinterpret_cast<NodeEntry *>(T.lists);
-  sa.listB = reinterpret_cast<NodeEntry *>(T.lists) + n;
+  sa.listB = reinterpret_cast<NodeEntry *>(T.lists) + N;
   sa.err = reinterpret_cast<int *>(S + 2);
   DL_CUDA(cudaMemsetAsync(T.node_count, 0, sizeof(uint32_t) * Fmax, st));
-  DL_CUDA(cudaMemsetAsync(T.tmp_begin, 0, sizeof(uint32_t) * (size_t)n, st));
-  k_subtree<<<(unsigned)ceil_div(n, TB_POINTS), TB_THREADS, 0, st>>>(sa);
+  DL_CUDA(cudaMemsetAsync(T.tmp_begin, 0, sizeof(uint32_t) * (size_t)N, st));
+  k_subtree<<<(unsigned)ceil_div(N, TB_POINTS), TB_THREADS, 0, st>>>(sa);
   dl_count_launch();
   DL_CUDA(cudaGetLastError());
   // leaf numbering
@@ -371,16 +400,17 @@ int build_tree(const TreeBuildArgs &A, TreeTemp &T, cudaStream_t st) {
                           cudaMemcpyDeviceToDevice, st));
   k_scan_counts<<<1, 1024, 0, st>>>(T.leaf_base, Fmax, S + 0, S + 1);
   dl_count_launch();
+  k_tree_leaf_offsets<<<1, 32, 0, st>>>(T.node_begin, S + 0, T.leaf_base, S + 1, n, A.G, S + 4,
+                                        A.leaf_begin);
+  dl_count_launch();
   LeafWriteArgs lw;
-  lw.n = n; lw.L = A.L; lw.t = A.t;
+  lw.n = n; lw.L = A.L; lw.t0 = A.t0;
   lw.node_begin = T.node_begin; lw.leaf_base = T.leaf_base; lw.leaf_flag = T.tmp_begin;
+  lw.tree_leaf_off = S + 4;
   lw.perm = A.perm; lw.tmp_box = T.tmp_box;
   lw.leaf_begin = A.leaf_begin; lw.leaf_lo = A.leaf_lo; lw.leaf_hi = A.leaf_hi;
   lw.leaf_nb = A.leaf_nb; lw.leaf_of = A.leaf_of; lw.max_leaf = S + 3;
   k_leaf_write<<<(unsigned)ceil_div(Fmax * 32, 256), 256, 0, st>>>(lw, S + 0);
-  dl_count_launch();
-  DL_CUDA(cudaGetLastError());
-  k_set_at<<<1, 1, 0, st>>>(A.leaf_begin, S + 1, (uint32_t)n);
   dl_count_launch();
   DL_CUDA(cudaGetLastError());
   return DETLSH_OK;
