@@ -433,7 +433,7 @@ k_encode(const float *__restrict__ X, int64_t ldx, int64_t nrows, int d,
         const float dl2 = __fadd_ru(dlt, __fmul_ru(__fadd_ru(fabsf(y), dlt), 1.2e-7f));
         const float lo = __fsub_rd(y, dl2), hi = __fadd_ru(y, dl2);
         const float *Bc = Bs + bslot(c) * BSTRIDE;
-        const bool finite = isfinite(y) && isfinite(dl2);
+        const bool finite = isfinite(y);  // dl2 = +inf lists the output through lo = -inf
         const float below = reg == 0 ? -INFINITY : Bc[reg - 1];
         const float above = reg == (uint32_t)nint ? INFINITY : Bc[reg];
         bool list = !(finite && below < lo && above >= hi);
@@ -504,13 +504,15 @@ k_encode(const float *__restrict__ X, int64_t ldx, int64_t nrows, int d,
   cp_async_wait0();  // only empty groups can remain; drain them before exit
 }
 
-// Exact recomputation of the listed outputs, one warp per output.  Lanes
-// split the row (coalesced loads) and run the compensated recurrence on
-// their terms; lane 0 folds the 32 partial states (p_l, s_l, e_l) with the
-// same error-free TwoSum step, so the certificate of dot2_finish still
-// bounds the total error.  Uncertified outputs take the big-integer path.
-// The count is read on the device (no host synchronisation); if the list
-// overflowed, every output is recomputed.
+// Exact recomputation of the listed outputs, EX_GL lanes per output (eight
+// outputs per warp).  The lanes split the row and run the compensated
+// recurrence on their terms; the group folds its partial states
+// (p_l, s_l, e_l) with the same error-free TwoSum step, so the certificate
+// of dot2_finish still bounds the total error.  Uncertified outputs take the
+// big-integer path.  The count is read on the device (no host
+// synchronisation); if the list overflowed, every output is recomputed.
+constexpr int EX_GL = 4;
+
 template <int MODE>
 __global__ void __launch_bounds__(256)
 k_project_exact(const float *__restrict__ X, int64_t ldx, const uint32_t *__restrict__ rows,
@@ -521,30 +523,38 @@ k_project_exact(const float *__restrict__ X, int64_t ldx, const uint32_t *__rest
   if (blockIdx.x == 0 && threadIdx.x == 0 && o.fb_total)
     atomicAdd(o.fb_total, (unsigned long long)(all ? nrows * (int64_t)LK : (int64_t)cnt));
   const int64_t total = all ? nrows * (int64_t)LK : (int64_t)cnt;
-  const int lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31, gl = lane & (EX_GL - 1);
+  constexpr int PER_WARP = 32 / EX_GL;
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-  for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < total; i += warps) {
-    int64_t rr;
-    int oc;
+  // warp-uniform trip count: every lane takes part in the group shuffles
+  for (int64_t i0 = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * PER_WARP; i0 < total;
+       i0 += warps * PER_WARP) {
+    const int64_t i = i0 + lane / EX_GL;
+    const bool valid = i < total;
+    int64_t rr = 0;
+    int oc = 0;
     uint32_t hint = 0;
-    if (all) { rr = i / LK; oc = (int)(i % LK); }
-    else {
-      const uint2 f = o.fb_list[i];
-      rr = f.x;
-      oc = MODE == 2 ? (int)(f.y >> 8) : (int)f.y;
-      hint = MODE == 2 ? (f.y & 255u) : 0u;
+    if (valid) {
+      if (all) { rr = i / LK; oc = (int)(i % LK); }
+      else {
+        const uint2 f = o.fb_list[i];
+        rr = f.x;
+        oc = MODE == 2 ? (int)(f.y >> 8) : (int)f.y;
+        hint = MODE == 2 ? (f.y & 255u) : 0u;
+      }
     }
-    const int64_t src = rows ? (int64_t)rows[rr] : rr;
+    const int64_t src = valid ? (rows ? (int64_t)rows[rr] : rr) : 0;
     const float *ar = A + (int64_t)oc * d;
     const float *xr = X + src * ldx;
     float p = 0.0f, sc = 0.0f, ec = 0.0f;
-    for (int k2 = lane; k2 < d; k2 += 32) dot2_step(p, sc, ec, xr[k2], ar[k2]);
+    if (valid)
+      for (int k2 = gl; k2 < d; k2 += EX_GL) dot2_step(p, sc, ec, xr[k2], ar[k2]);
     // butterfly fold: (Pa,Sa,Ea) + (Pb,Sb,Eb) -> P = fl(Pa+Pb) with its exact
     // TwoSum error q, S = fl(fl(Sa+Sb) + q), E gathers both bounds and the
     // two new roundings; the true sum stays within u*E of P + S.
     float P = p, S = sc, E = ec;
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
+    for (int off = EX_GL / 2; off > 0; off >>= 1) {
       const float pb = __shfl_xor_sync(FULL, P, off), sb = __shfl_xor_sync(FULL, S, off);
       const float eb = __shfl_xor_sync(FULL, E, off);
       const float t = __fadd_rn(P, pb);
@@ -556,7 +566,7 @@ k_project_exact(const float *__restrict__ X, int64_t ldx, const uint32_t *__rest
       P = t;
       S = s2;
     }
-    if (lane != 0) continue;
+    if (gl != 0 || !valid) continue;
     float y;
     bool bad = false;
     if (!dot2_finish(P, S, E, d + 32, y)) y = exact_dot_rn(ar, xr, d, &bad);
