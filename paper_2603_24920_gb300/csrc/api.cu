@@ -298,10 +298,46 @@ __global__ void k_iota(uint32_t *p, int64_t n) {
 
 // BF16 copy of the data, one warp per row, with the FP32 squared norm of each
 // rounded row (the norm term of the tensor-core scores).
+// BF16 copy of the rows and ||bf16(x)||^2 per row, a warp per row; rows with
+// d a multiple of 4 go by 16-byte loads and 8-byte stores, two rows at a time.
 __global__ void k_rows_to_bf16(const float *s, __nv_bfloat16 *h, float *nrm, int64_t n, int d) {
   const int lane = threadIdx.x & 31;
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-  for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < n; r += warps) {
+  const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if ((d & 3) == 0) {
+    const int d4 = d >> 2;
+    for (int64_t r0 = 2 * w0; r0 < n; r0 += 2 * warps) {
+      float acc[2] = {0.0f, 0.0f};
+      for (int j = lane; j < d4; j += 32) {
+        float4 v[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u)
+          v[u] = r0 + u < n ? reinterpret_cast<const float4 *>(s + (r0 + u) * d)[j] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          if (r0 + u >= n) continue;
+          const __nv_bfloat162 a = __floats2bfloat162_rn(v[u].x, v[u].y);
+          const __nv_bfloat162 b = __floats2bfloat162_rn(v[u].z, v[u].w);
+          uint2 pk;
+          pk.x = *reinterpret_cast<const uint32_t *>(&a);
+          pk.y = *reinterpret_cast<const uint32_t *>(&b);
+          reinterpret_cast<uint2 *>(h + (r0 + u) * d)[j] = pk;
+          const float2 fa = __bfloat1622float2(a), fb = __bfloat1622float2(b);
+          acc[u] = __fmaf_rn(fa.x, fa.x, acc[u]);
+          acc[u] = __fmaf_rn(fa.y, fa.y, acc[u]);
+          acc[u] = __fmaf_rn(fb.x, fb.x, acc[u]);
+          acc[u] = __fmaf_rn(fb.y, fb.y, acc[u]);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        for (int o = 16; o > 0; o >>= 1) acc[u] = __fadd_rn(acc[u], __shfl_xor_sync(0xffffffffu, acc[u], o));
+        if (lane == 0 && r0 + u < n) nrm[r0 + u] = acc[u];
+      }
+    }
+    return;
+  }
+  for (int64_t r = w0; r < n; r += warps) {
     float acc = 0.0f;
     for (int j = lane; j < d; j += 32) {
       const __nv_bfloat16 v = __float2bfloat16_rn(s[r * d + j]);
@@ -514,12 +550,11 @@ int build_impl(detlsh_index *ix, const float *data, cudaStream_t st, const detls
   DL_TRY(tp.get(&tt.codesB, (size_t)N));
   DL_TRY(tp.get(&tt.idsB, (size_t)N));
   DL_TRY(tp.get(&tt.node_begin, (size_t)N + 1));
-  DL_TRY(tp.get(&tt.node_count, (size_t)N));
   DL_TRY(tp.get(&tt.block_counts, sample_blocks(N) + 4));
   DL_TRY(tp.get(&tt.tmp_begin, (size_t)N));
   DL_TRY(tp.get(&tt.tmp_box, (size_t)N * 48));
   DL_TRY(tp.get(&tt.lists, (size_t)N * 4));
-  DL_TRY(tp.get(&tt.leaf_base, (size_t)N));
+  DL_TRY(tp.get(&tt.leaf_start, (size_t)N));
   {
     const size_t cnt_cap = (size_t)G * 256 * sort_tiles(n);
     DL_TRY(tp.get(&tt.sort.counts, cnt_cap));
@@ -588,10 +623,13 @@ int build_impl(detlsh_index *ix, const float *data, cudaStream_t st, const detls
   for (int t = L + 1; t <= 16; ++t) ix->blk_off[t] = tb;
   DL_TRY(dalloc(ix, &ix->blk_lo, (size_t)tb * 16, st));
   DL_TRY(dalloc(ix, &ix->blk_hi, (size_t)tb * 16, st));
-  for (int t = 0; t < L; ++t)
-    DL_TRY(block_hulls(ix->leaf_lo + ix->leaf_off[t] * 16, ix->leaf_hi + ix->leaf_off[t] * 16,
-                       ix->nleaves[t], ix->blk_lo + ix->blk_off[t] * 16,
-                       ix->blk_hi + ix->blk_off[t] * 16, st));
+  {
+    HullSet h;
+    h.L = L;
+    for (int t = 0; t <= L; ++t) { h.in_off[t] = ix->leaf_off[t]; h.out_off[t] = ix->blk_off[t]; }
+    for (int t = 0; t < L; ++t) h.cnt[t] = ix->nleaves[t];
+    DL_TRY(block_hulls(ix->leaf_lo, ix->leaf_hi, h, ix->blk_lo, ix->blk_hi, st));
+  }
   // and hulls of runs of LEAF_BLOCK hulls (LEAF_BLOCK^2 leaves)
   int64_t ts = 0;
   for (int t = 0; t < L; ++t) {
@@ -601,10 +639,13 @@ int build_impl(detlsh_index *ix, const float *data, cudaStream_t st, const detls
   for (int t = L; t <= 16; ++t) ix->sblk_off[t] = ts;
   DL_TRY(dalloc(ix, &ix->sblk_lo, (size_t)ts * 16, st));
   DL_TRY(dalloc(ix, &ix->sblk_hi, (size_t)ts * 16, st));
-  for (int t = 0; t < L; ++t)
-    DL_TRY(block_hulls(ix->blk_lo + ix->blk_off[t] * 16, ix->blk_hi + ix->blk_off[t] * 16,
-                       ix->blk_off[t + 1] - ix->blk_off[t], ix->sblk_lo + ix->sblk_off[t] * 16,
-                       ix->sblk_hi + ix->sblk_off[t] * 16, st));
+  {
+    HullSet h;
+    h.L = L;
+    for (int t = 0; t <= L; ++t) { h.in_off[t] = ix->blk_off[t]; h.out_off[t] = ix->sblk_off[t]; }
+    for (int t = 0; t < L; ++t) h.cnt[t] = ix->blk_off[t + 1] - ix->blk_off[t];
+    DL_TRY(block_hulls(ix->blk_lo, ix->blk_hi, h, ix->sblk_lo, ix->sblk_hi, st));
+  }
   DL_CUDA(cudaEventRecord(ix->ev[4], st));
   DL_CUDA(cudaStreamSynchronize(st));
   ix->fb_total = (int64_t)fbt;

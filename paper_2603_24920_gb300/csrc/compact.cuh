@@ -50,7 +50,6 @@ __global__ void k_compact_count(int64_t n, Flag f, uint32_t *block_counts) {
   if (threadIdx.x == 0) block_counts[blockIdx.x] = tot;
 }
 
-// In-place exclusive scan of nb counts by one CTA; total to *total.
 // Exclusive scan of counts[0 .. nb) in place (nb read from *nb_dev when that
 // is given); *total (optional) receives the sum.
 __global__ void k_scan_counts(uint32_t *counts, int64_t nb, const uint32_t *nb_dev, uint32_t *total);

@@ -75,19 +75,26 @@ struct TreeTemp {
   uint32_t *keys = nullptr, *vals = nullptr;
   uint4 *codesA = nullptr, *codesB = nullptr;
   uint32_t *idsB = nullptr;
-  uint32_t *node_begin = nullptr, *node_count = nullptr, *block_counts = nullptr;
+  uint32_t *node_begin = nullptr, *block_counts = nullptr;
   uint32_t *tmp_begin = nullptr;  // [n] leaf start flags
   uint8_t *tmp_box = nullptr;  // [n][48]: lo, hi, nb of the leaf starting there
   uint4 *lists = nullptr;      // [2n][2]: the open nodes of two levels
-  uint32_t *leaf_base = nullptr;
+  uint32_t *leaf_start = nullptr;  // [G n] first position of every leaf
   SortTemp sort;
 };
 // Enqueues the build of G trees (no host synchronisation); the counts land in
 // a.scalars.  Temporaries hold G n entries; the leaf arrays G n (G n + G for
 // leaf_begin).
 int build_trees(const TreeBuildArgs &a, TreeTemp &tmp, cudaStream_t st);
-// Hull boxes of runs of LEAF_BLOCK leaves: [ceil(nleaves/LEAF_BLOCK)][16] each.
-int block_hulls(const uint8_t *lo, const uint8_t *hi, int64_t nleaves, uint8_t *hlo, uint8_t *hhi,
+// Hull boxes of runs of LEAF_BLOCK boxes, every tree in one launch: tree t's
+// ceil(cnt[t]/LEAF_BLOCK) hulls ([16] lo and hi bytes each) start at out_off[t].
+struct HullSet {
+  int L;
+  int64_t in_off[17];   // first input box of every tree; in_off[t] + cnt[t] ends it
+  int64_t cnt[16];      // input boxes per tree
+  int64_t out_off[17];  // first hull of every tree; out_off[L] = all hulls
+};
+int block_hulls(const uint8_t *lo, const uint8_t *hi, const HullSet &h, uint8_t *hlo, uint8_t *hhi,
                 cudaStream_t st);
 
 // ---- queries (query.cu) ----------------------------------------------------

@@ -67,30 +67,53 @@ __global__ void __launch_bounds__(256) k_radix_scan_totals(uint32_t *digit_total
   t[threadIdx.x] = ex;
 }
 
-// Stable scatter of one tile.  Elements are ranked in index order:
-// earlier rounds, then earlier warps of the round, then earlier lanes.
+// Stable scatter of one tile.  Elements are ranked in index order (earlier
+// rounds, then earlier warps of the round, then earlier lanes) into a
+// digit-sorted copy of the tile in shared memory; the copy is then written
+// out in order, so the elements of one digit leave as one contiguous run.
 __global__ void __launch_bounds__(SORT_THREADS)
 k_radix_scatter(const uint32_t *__restrict__ kin, const uint32_t *__restrict__ vin,
                 uint32_t *__restrict__ kout, uint32_t *__restrict__ vout, int64_t len, int shift,
                 const uint32_t *__restrict__ counts, const uint32_t *__restrict__ digit_base,
                 int tiles) {
   constexpr int NW = SORT_THREADS / 32;
-  __shared__ uint32_t running[256];
+  __shared__ uint32_t sk[SORT_TILE], sv[SORT_TILE];
+  __shared__ uint32_t running[256];   // next local position per digit
+  __shared__ uint32_t gshift[256];    // global position - local position, per digit
   __shared__ uint32_t wcnt[NW][256];
+  __shared__ uint32_t wt[32];
   const int seg = blockIdx.y, tile = blockIdx.x;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t soff = (int64_t)seg * len;
-  running[threadIdx.x] = digit_base[seg * 256 + threadIdx.x] +
-                         counts[((int64_t)seg * 256 + threadIdx.x) * tiles + tile];
+  const int64_t t0 = (int64_t)tile * SORT_TILE;
+  const int nvalid = (int)(len - t0 < SORT_TILE ? len - t0 : (int64_t)SORT_TILE);
   for (int w = 0; w < NW; ++w) wcnt[w][threadIdx.x] = 0;
+  running[threadIdx.x] = 0;
+  __syncthreads();
+  uint32_t key[SORT_ITEMS], val[SORT_ITEMS];
+#pragma unroll
+  for (int r = 0; r < SORT_ITEMS; ++r) {
+    const int i = r * SORT_THREADS + threadIdx.x;
+    key[r] = i < nvalid ? kin[soff + t0 + i] : 0u;
+    val[r] = (i < nvalid && vin) ? vin[soff + t0 + i] : 0u;
+    if (i < nvalid) atomicAdd(&running[(key[r] >> shift) & 255u], 1u);
+  }
+  __syncthreads();
+  {  // local digit starts; global shift = tile's global start of the digit - local start
+    const uint32_t cnt = running[threadIdx.x];
+    __syncthreads();
+    const uint32_t ls = block_exclusive_scan(cnt, wt, nullptr);
+    running[threadIdx.x] = ls;
+    gshift[threadIdx.x] = digit_base[seg * 256 + threadIdx.x] +
+                          counts[((int64_t)seg * 256 + threadIdx.x) * tiles + tile] - ls;
+  }
   __syncthreads();
   const unsigned lt = (1u << lane) - 1u;
+#pragma unroll
   for (int r = 0; r < SORT_ITEMS; ++r) {
-    const int64_t idx = (int64_t)tile * SORT_TILE + (int64_t)r * SORT_THREADS + threadIdx.x;
-    const bool valid = idx < len;
-    const uint32_t key = valid ? kin[soff + idx] : 0u;
-    const uint32_t val = (valid && vin) ? vin[soff + idx] : 0u;
-    const uint32_t digit = (key >> shift) & 255u;
+    const int i = r * SORT_THREADS + threadIdx.x;
+    const bool valid = i < nvalid;
+    const uint32_t digit = (key[r] >> shift) & 255u;
     const unsigned peers = __match_any_sync(FULL, valid ? digit : (0x10000u | (unsigned)lane));
     const int rank = __popc(peers & lt);
     if (valid && rank == 0) wcnt[warp][digit] = __popc(peers);
@@ -98,14 +121,20 @@ k_radix_scatter(const uint32_t *__restrict__ kin, const uint32_t *__restrict__ v
     if (valid) {
       uint32_t pre = running[digit] + rank;
       for (int w = 0; w < warp; ++w) pre += wcnt[w][digit];
-      kout[soff + pre] = key;
-      if (vin) vout[soff + pre] = val;
+      sk[pre] = key[r];
+      sv[pre] = val[r];
     }
     __syncthreads();
     uint32_t tot = 0;
     for (int w = 0; w < NW; ++w) { tot += wcnt[w][threadIdx.x]; wcnt[w][threadIdx.x] = 0; }
     running[threadIdx.x] += tot;
     __syncthreads();
+  }
+  for (int i = threadIdx.x; i < nvalid; i += SORT_THREADS) {
+    const uint32_t k = sk[i];
+    const uint32_t pos = gshift[(k >> shift) & 255u] + (uint32_t)i;
+    kout[soff + pos] = k;
+    if (vin) vout[soff + pos] = sv[i];
   }
 }
 

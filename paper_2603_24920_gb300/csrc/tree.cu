@@ -82,7 +82,6 @@ struct SubtreeArgs {
   uint4 *codesA, *codesB;
   uint32_t *idsA, *idsB;
   uint32_t *perm;
-  uint32_t *node_count;        // leaves per first-layer node (zeroed)
   uint32_t *leaf_flag;         // [n] 1 where a leaf starts (zeroed)
   uint8_t *tmp_box;            // [n][48] box of the leaf starting there
   NodeEntry *listA, *listB;    // [n] each: open nodes of a level
@@ -141,17 +140,45 @@ __global__ void __launch_bounds__(TB_THREADS) k_subtree(SubtreeArgs a) {
       bool eligible_any = false;
       for (int j = 0; j < K; ++j) eligible_any |= (int)code_byte(nbv, j) < bb;
       if (cnt > (uint32_t)a.M && eligible_any) {
+        // Per-dimension counts of the next prefix bit.  The bit of dimension j
+        // sits at bit bb-1-nb_j of code byte j: one mask per code word picks
+        // it out of four bytes at once, and per-byte counters (flushed before
+        // they can reach 256) accumulate four dimensions per add.  Loads run
+        // four rounds ahead.
+        uint32_t msk[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int nbj = (int)code_byte(nbv, j);
+          if (j < K && nbj < bb) msk[j >> 2] |= (1u << (bb - 1 - nbj)) << (8 * (j & 3));
+        }
         uint32_t c1[16];
 #pragma unroll
         for (int j = 0; j < 16; ++j) c1[j] = 0u;
-        for (uint32_t x = b + lane; x < e; x += 32) {
-          const uint4 c = src[x];
+        uint32_t pk[4] = {0u, 0u, 0u, 0u};
+        int rounds = 0;
+        auto flush = [&]() {
 #pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            const int nbj = (int)code_byte(nbv, j);
-            if (j < K && nbj < bb) c1[j] += (code_byte(c, j) >> (bb - 1 - nbj)) & 1u;
+          for (int j = 0; j < 16; ++j) c1[j] += (pk[j >> 2] >> (8 * (j & 3))) & 255u;
+#pragma unroll
+          for (int q = 0; q < 4; ++q) pk[q] = 0u;
+          rounds = 0;
+        };
+        for (uint32_t base = b; base < e; base += 128) {
+          uint4 cv[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const uint32_t x = base + u * 32 + lane;
+            cv[u] = x < e ? src[x] : make_uint4(0u, 0u, 0u, 0u);
           }
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const uint32_t wd[4] = {cv[u].x, cv[u].y, cv[u].z, cv[u].w};
+#pragma unroll
+            for (int q = 0; q < 4; ++q) pk[q] += __vcmpne4(wd[q] & msk[q], 0u) & 0x01010101u;
+          }
+          if ((rounds += 4) > 250) flush();
         }
+        flush();
         // most even split, ties to the smallest dimension
         int best = -1;
         int64_t bestd = 0;
@@ -183,21 +210,31 @@ __global__ void __launch_bounds__(TB_THREADS) k_subtree(SubtreeArgs a) {
         uint4 *dst = par ? a.codesA : a.codesB;
         uint32_t *dstid = par ? a.idsA : a.idsB;
         uint32_t zrun = 0, orun = 0;
-        for (uint32_t base = b; base < e; base += 32) {
-          const uint32_t x = base + lane;
-          const bool valid = x < e;
-          uint4 c = make_uint4(0, 0, 0, 0);
-          uint32_t id = 0, bit = 0;
-          if (valid) { c = src[x]; id = srcid[x]; bit = (code_byte(c, best) >> sh) & 1u; }
-          const unsigned ones = __ballot_sync(FULL, valid && bit);
-          const unsigned zeros = __ballot_sync(FULL, valid && !bit);
-          if (valid) {
-            const uint32_t pos = bit ? (b + n0 + orun + __popc(ones & lt)) : (b + zrun + __popc(zeros & lt));
-            dst[pos] = c;
-            dstid[pos] = id;
+        for (uint32_t base0 = b; base0 < e; base0 += 128) {
+          uint4 cv[4];
+          uint32_t idv[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {  // loads four rounds ahead of the stores
+            const uint32_t x = base0 + u * 32 + lane;
+            cv[u] = make_uint4(0u, 0u, 0u, 0u);
+            idv[u] = 0u;
+            if (x < e) { cv[u] = src[x]; idv[u] = srcid[x]; }
           }
-          zrun += __popc(zeros);
-          orun += __popc(ones);
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const uint32_t x = base0 + u * 32 + lane;
+            const bool valid = x < e;
+            const uint32_t bit = valid ? (code_byte(cv[u], best) >> sh) & 1u : 0u;
+            const unsigned ones = __ballot_sync(FULL, valid && bit);
+            const unsigned zeros = __ballot_sync(FULL, valid && !bit);
+            if (valid) {
+              const uint32_t pos = bit ? (b + n0 + orun + __popc(ones & lt)) : (b + zrun + __popc(zeros & lt));
+              dst[pos] = cv[u];
+              dstid[pos] = idv[u];
+            }
+            zrun += __popc(zeros);
+            orun += __popc(ones);
+          }
         }
         if (lane == 0) {
           const uint32_t q = atomicAdd(&nnext, 2u);
@@ -234,10 +271,7 @@ __global__ void __launch_bounds__(TB_THREADS) k_subtree(SubtreeArgs a) {
         a.tmp_box[(int64_t)b * 48 + 16 + lane] = bhi;
         a.tmp_box[(int64_t)b * 48 + 32 + lane] = lane < K ? (uint8_t)code_byte(nbv, lane) : 0;
       }
-      if (lane == 0) {
-        a.leaf_flag[b] = 1u;
-        atomicAdd(&a.node_count[ent.f], 1u);
-      }
+      if (lane == 0) a.leaf_flag[b] = 1u;
     }
     __syncthreads();  // this level's partitions and children are complete
     if (threadIdx.x == 0) ncur = nnext;
@@ -246,11 +280,23 @@ __global__ void __launch_bounds__(TB_THREADS) k_subtree(SubtreeArgs a) {
   }
 }
 
+// ---- leaf records --------------------------------------------------------
+// Leaves start at the flagged positions; in position order they are in
+// canonical (depth-first) order, so a leaf's number in the group is its rank
+// among the flags, and a tree's first leaf starts at the tree's first
+// position.
+struct LeafStart {
+  const uint32_t *flag;
+  __device__ bool operator()(int64_t i) const { return flag[i] != 0u; }
+};
+
 struct LeafWriteArgs {
-  int64_t n;
+  int64_t n, N;
   int L, t0;
-  const uint32_t *node_begin, *leaf_base, *leaf_flag, *perm;
+  const uint32_t *starts;         // [leaves] first position of every leaf
+  const uint32_t *total;          // number of leaves (device)
   const uint32_t *tree_leaf_off;  // [G+1] first leaf of every tree of the group
+  const uint32_t *perm, *leaf_flag, *block_offsets;
   const uint8_t *tmp_box;
   uint32_t *leaf_begin;
   uint8_t *leaf_lo, *leaf_hi, *leaf_nb;
@@ -258,100 +304,100 @@ struct LeafWriteArgs {
   uint32_t *max_leaf;
 };
 
-// One warp per first-layer node: its leaves in position order (= depth-first
-// order), numbered from the node's base; records copied, leaf_of written.
-// Leaf g of the group (tree t = its position / n) goes to record g and to
-// leaf_begin[g + t] (each tree's leaf_begin has one end entry more); leaf_of
-// gets the number within the tree, g - tree_leaf_off[t].
-__global__ void k_leaf_write(LeafWriteArgs a, const uint32_t *F) {
-  const int64_t f = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (f >= *F) return;
-  const uint32_t nb0 = a.node_begin[f], ne = a.node_begin[f + 1];
-  const uint32_t t = (uint32_t)(nb0 / a.n), pos0 = (uint32_t)(t * a.n);
-  const uint32_t g0 = a.tree_leaf_off[t];
-  uint32_t g = a.leaf_base[f];
-  auto emit = [&](uint32_t lb, uint32_t le) {
-    if (lane < 16) {
-      a.leaf_lo[(int64_t)g * 16 + lane] = a.tmp_box[(int64_t)lb * 48 + lane];
-      a.leaf_hi[(int64_t)g * 16 + lane] = a.tmp_box[(int64_t)lb * 48 + 16 + lane];
-      a.leaf_nb[(int64_t)g * 16 + lane] = a.tmp_box[(int64_t)lb * 48 + 32 + lane];
-    }
-    if (lane == 0) {
-      a.leaf_begin[g + t] = lb - pos0;
-      atomicMax(a.max_leaf, le - lb);
-    }
-    for (uint32_t i = lb + lane; i < le; i += 32) a.leaf_of[(int64_t)a.perm[i] * a.L + a.t0 + t] = g - g0;
-    ++g;
-  };
-  int64_t pend = -1;  // a leaf start whose end is the next start
-  for (uint32_t c0 = nb0; c0 < ne; c0 += 32) {
-    const uint32_t p = c0 + lane;
-    unsigned m = __ballot_sync(FULL, p < ne && a.leaf_flag[p] != 0u);
-    while (m) {
-      const uint32_t st = c0 + (uint32_t)(__ffs(m) - 1);
-      m &= m - 1u;
-      if (pend >= 0) emit((uint32_t)pend, st);
-      pend = st;
-    }
+// One thread per leaf g (tree t = its start / n): box record g, leaf_begin
+// entry g + t (each tree's leaf_begin has one end entry more), size.
+__global__ void k_leaf_records(LeafWriteArgs a) {
+  const uint32_t total = *a.total;
+  uint32_t big = 0;
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < (int64_t)total;
+       g += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t lb = a.starts[g];
+    const uint32_t t = (uint32_t)(lb / a.n);
+    const uint32_t tend = (uint32_t)((t + 1) * a.n);
+    const uint32_t le = g + 1 < total ? min(a.starts[g + 1], tend) : tend;
+    const uint4 *src = reinterpret_cast<const uint4 *>(a.tmp_box + (int64_t)lb * 48);
+    reinterpret_cast<uint4 *>(a.leaf_lo)[g] = src[0];
+    reinterpret_cast<uint4 *>(a.leaf_hi)[g] = src[1];
+    reinterpret_cast<uint4 *>(a.leaf_nb)[g] = src[2];
+    a.leaf_begin[g + t] = lb - (uint32_t)(t * a.n);
+    big = max(big, le - lb);
   }
-  if (pend >= 0) emit((uint32_t)pend, ne);
+  big = __reduce_max_sync(FULL, big);
+  if ((threadIdx.x & 31) == 0 && big) atomicMax(a.max_leaf, big);
+}
+
+// One thread per position: the leaf holding it is (flags up to it) - 1, from
+// the compaction's block offsets and an in-block scan; leaf_of gets the
+// number within the tree.
+__global__ void k_leaf_of(LeafWriteArgs a) {
+  __shared__ uint32_t wt[32];
+  const int64_t base = (int64_t)blockIdx.x * CP_TILE + (int64_t)threadIdx.x * CP_ITEMS;
+  uint32_t flags = 0, c = 0;
+  for (int i = 0; i < CP_ITEMS; ++i) {
+    const int64_t idx = base + i;
+    if (idx < a.N && a.leaf_flag[idx] != 0u) { flags |= 1u << i; ++c; }
+  }
+  uint32_t cur = a.block_offsets[blockIdx.x] + block_exclusive_scan(c, wt, nullptr);  // flags before base
+  for (int i = 0; i < CP_ITEMS; ++i) {
+    const int64_t idx = base + i;
+    if (idx >= a.N) break;
+    cur += (flags >> i) & 1u;
+    const uint32_t t = (uint32_t)(idx / a.n);
+    a.leaf_of[(int64_t)a.perm[idx] * a.L + a.t0 + t] = cur - 1u - a.tree_leaf_off[t];
+  }
 }
 
 __global__ void k_set_u32(uint32_t *p, uint32_t v) { *p = v; }
 // base[*idx] = v, the index read on the device
 __global__ void k_set_at(uint32_t *base, const uint32_t *idx, uint32_t v) { base[*idx] = v; }
 
-// First leaf of every tree of the group (its first first-layer node starts
-// at position t n), the total, and each tree's end entry of leaf_begin.
-__global__ void k_tree_leaf_offsets(const uint32_t *node_begin, const uint32_t *F,
-                                    const uint32_t *leaf_base, const uint32_t *total, int64_t n,
-                                    int G, uint32_t *off, uint32_t *leaf_begin) {
+// First leaf of every tree of the group (the leaf starting at position t n),
+// the total, and each tree's end entry of leaf_begin.
+__global__ void k_tree_leaf_offsets(const uint32_t *starts, const uint32_t *total, int64_t n, int G,
+                                    uint32_t *off, uint32_t *leaf_begin) {
   const int t = threadIdx.x;
   if (t > G) return;
-  uint32_t o = *total;
+  const uint32_t tot = *total;
+  uint32_t o = tot;
   if (t < G) {
-    uint32_t lo = 0, hi = *F;
+    uint32_t lo = 0, hi = tot;
     const uint32_t key = (uint32_t)(t * n);
-    while (lo < hi) { const uint32_t mid = (lo + hi) >> 1; if (node_begin[mid] < key) lo = mid + 1; else hi = mid; }
-    o = leaf_base[lo];
+    while (lo < hi) { const uint32_t mid = (lo + hi) >> 1; if (starts[mid] < key) lo = mid + 1; else hi = mid; }
+    o = lo;
   }
   off[t] = o;
   if (t > 0) leaf_begin[o + (uint32_t)t - 1] = (uint32_t)n;  // end of tree t - 1
 }
 
-// Hull boxes of consecutive runs of LEAF_BLOCK leaves (in canonical order):
-// per dimension the smallest lo and largest hi of the run.  A hull contains
-// every leaf box of its run, so its lower bound bounds theirs from below.
-__global__ void k_block_hulls(const uint8_t *__restrict__ lo, const uint8_t *__restrict__ hi,
-                              int64_t nleaves, int64_t nblocks, uint8_t *hlo, uint8_t *hhi) {
+// Hull boxes of consecutive runs of LEAF_BLOCK boxes (in canonical order),
+// for every tree in one launch: per dimension the smallest lo and largest hi
+// of the run (byte-wise SIMD min/max).  A hull contains every box of its run,
+// so its lower bound bounds theirs from below.
+__global__ void k_block_hulls(const uint4 *__restrict__ lo, const uint4 *__restrict__ hi, HullSet h,
+                              uint4 *hlo, uint4 *hhi) {
   const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= nblocks) return;
-  uint32_t mn[16], mx[16];
-  for (int j = 0; j < 16; ++j) { mn[j] = 255u; mx[j] = 0u; }
-  const int64_t l1 = nleaves < (b + 1) * LEAF_BLOCK ? nleaves : (b + 1) * LEAF_BLOCK;
-  for (int64_t l = b * LEAF_BLOCK; l < l1; ++l) {
-    const uint4 a = reinterpret_cast<const uint4 *>(lo)[l];
-    const uint4 c = reinterpret_cast<const uint4 *>(hi)[l];
-    for (int j = 0; j < 16; ++j) {
-      mn[j] = min(mn[j], code_byte(a, j));
-      mx[j] = max(mx[j], code_byte(c, j));
-    }
+  if (b >= h.out_off[h.L]) return;
+  int t = 0;
+  while (b >= h.out_off[t + 1]) ++t;
+  const int64_t l0 = h.in_off[t] + (b - h.out_off[t]) * LEAF_BLOCK;
+  const int64_t l1 = min(l0 + LEAF_BLOCK, h.in_off[t] + h.cnt[t]);
+  uint4 mn = make_uint4(~0u, ~0u, ~0u, ~0u), mx = make_uint4(0u, 0u, 0u, 0u);
+  for (int64_t l = l0; l < l1; ++l) {
+    const uint4 a = lo[l], c = hi[l];
+    mn.x = __vminu4(mn.x, a.x); mn.y = __vminu4(mn.y, a.y); mn.z = __vminu4(mn.z, a.z); mn.w = __vminu4(mn.w, a.w);
+    mx.x = __vmaxu4(mx.x, c.x); mx.y = __vmaxu4(mx.y, c.y); mx.z = __vmaxu4(mx.z, c.z); mx.w = __vmaxu4(mx.w, c.w);
   }
-  uint32_t w0[4] = {0, 0, 0, 0}, w1[4] = {0, 0, 0, 0};
-  for (int j = 0; j < 16; ++j) {
-    w0[j >> 2] |= mn[j] << (8 * (j & 3));
-    w1[j >> 2] |= mx[j] << (8 * (j & 3));
-  }
-  reinterpret_cast<uint4 *>(hlo)[b] = make_uint4(w0[0], w0[1], w0[2], w0[3]);
-  reinterpret_cast<uint4 *>(hhi)[b] = make_uint4(w1[0], w1[1], w1[2], w1[3]);
+  hlo[b] = mn;
+  hhi[b] = mx;
 }
 
-int block_hulls(const uint8_t *lo, const uint8_t *hi, int64_t nleaves, uint8_t *hlo, uint8_t *hhi,
+int block_hulls(const uint8_t *lo, const uint8_t *hi, const HullSet &h, uint8_t *hlo, uint8_t *hhi,
                 cudaStream_t st) {
-  const int64_t nb = ceil_div(nleaves, LEAF_BLOCK);
+  const int64_t nb = h.out_off[h.L];
   if (nb == 0) return DETLSH_OK;
-  k_block_hulls<<<(unsigned)ceil_div(nb, 128), 128, 0, st>>>(lo, hi, nleaves, nb, hlo, hhi);
+  k_block_hulls<<<(unsigned)ceil_div(nb, 128), 128, 0, st>>>(
+      reinterpret_cast<const uint4 *>(lo), reinterpret_cast<const uint4 *>(hi), h,
+      reinterpret_cast<uint4 *>(hlo), reinterpret_cast<uint4 *>(hhi));
   dl_count_launch();
   DL_CUDA(cudaGetLastError());
   return DETLSH_OK;
@@ -361,8 +407,7 @@ int build_trees(const TreeBuildArgs &A, TreeTemp &T, cudaStream_t st) {
   const int64_t n = A.n, N = (int64_t)A.G * n;
   const int gs = (int)std::min<int64_t>(ceil_div(N, 256), 4096);
   // no host round trip: counts stay on the device, launches are sized by
-  // their upper bounds (at most min(n, 2^K) first-layer nodes per tree)
-  const int64_t Fmax = A.G * std::min<int64_t>(n, (int64_t)1 << A.K);
+  // their upper bounds
   uint32_t *S = A.scalars;  // [0] F, [1] leaves, [2] error, [3] largest leaf, [4..] tree offsets
   DL_CUDA(cudaMemsetAsync(S, 0, 4 * sizeof(uint32_t), st));
   k_first_keys<<<gs, 256, 0, st>>>(A.codes, n, N, A.K, A.bbits, T.keys, T.vals);
@@ -384,33 +429,33 @@ int build_trees(const TreeBuildArgs &A, TreeTemp &T, cudaStream_t st) {
   sa.codesA = T.codesA; sa.codesB = T.codesB;
   sa.idsA = T.vals; sa.idsB = T.idsB;
   sa.perm = A.perm;
-  sa.node_count = T.node_count;
   sa.leaf_flag = T.tmp_begin;
   sa.tmp_box = T.tmp_box;
   sa.listA = reinterpret_cast<NodeEntry *>(T.lists);
   sa.listB = reinterpret_cast<NodeEntry *>(T.lists) + N;
   sa.err = reinterpret_cast<int *>(S + 2);
-  DL_CUDA(cudaMemsetAsync(T.node_count, 0, sizeof(uint32_t) * Fmax, st));
   DL_CUDA(cudaMemsetAsync(T.tmp_begin, 0, sizeof(uint32_t) * (size_t)N, st));
   k_subtree<<<(unsigned)ceil_div(N, TB_POINTS), TB_THREADS, 0, st>>>(sa);
   dl_count_launch();
   DL_CUDA(cudaGetLastError());
-  // leaf numbering
-  DL_CUDA(cudaMemcpyAsync(T.leaf_base, T.node_count, sizeof(uint32_t) * Fmax,
-                          cudaMemcpyDeviceToDevice, st));
-  k_scan_counts<<<1, 1024, 0, st>>>(T.leaf_base, Fmax, S + 0, S + 1);
-  dl_count_launch();
-  k_tree_leaf_offsets<<<1, 32, 0, st>>>(T.node_begin, S + 0, T.leaf_base, S + 1, n, A.G, S + 4,
-                                        A.leaf_begin);
+  // leaf numbering: compaction of the leaf start flags (position order)
+  uint32_t *starts = T.leaf_start;
+  DL_TRY(compact(N, LeafStart{T.tmp_begin}, T.block_counts, starts, S + 1, st));
+  k_tree_leaf_offsets<<<1, 32, 0, st>>>(starts, S + 1, n, A.G, S + 4, A.leaf_begin);
   dl_count_launch();
   LeafWriteArgs lw;
-  lw.n = n; lw.L = A.L; lw.t0 = A.t0;
-  lw.node_begin = T.node_begin; lw.leaf_base = T.leaf_base; lw.leaf_flag = T.tmp_begin;
-  lw.tree_leaf_off = S + 4;
-  lw.perm = A.perm; lw.tmp_box = T.tmp_box;
+  lw.n = n; lw.N = N; lw.L = A.L; lw.t0 = A.t0;
+  lw.starts = starts; lw.total = S + 1; lw.tree_leaf_off = S + 4;
+  lw.perm = A.perm; lw.leaf_flag = T.tmp_begin; lw.block_offsets = T.block_counts;
+  lw.tmp_box = T.tmp_box;
   lw.leaf_begin = A.leaf_begin; lw.leaf_lo = A.leaf_lo; lw.leaf_hi = A.leaf_hi;
   lw.leaf_nb = A.leaf_nb; lw.leaf_of = A.leaf_of; lw.max_leaf = S + 3;
-  k_leaf_write<<<(unsigned)ceil_div(Fmax * 32, 256), 256, 0, st>>>(lw, S + 0);
+  int dev = 0, sms = 0;
+  DL_CUDA(cudaGetDevice(&dev));
+  DL_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  k_leaf_records<<<(unsigned)std::min<int64_t>(ceil_div(N, 256), (int64_t)sms * 8), 256, 0, st>>>(lw);
+  dl_count_launch();
+  k_leaf_of<<<(unsigned)compact_blocks(N), CP_THREADS, 0, st>>>(lw);
   dl_count_launch();
   DL_CUDA(cudaGetLastError());
   return DETLSH_OK;
