@@ -67,69 +67,92 @@ __global__ void __launch_bounds__(256) k_radix_scan_totals(uint32_t *digit_total
   t[threadIdx.x] = ex;
 }
 
-// Stable scatter of one tile.  Elements are ranked in index order (earlier
-// rounds, then earlier warps of the round, then earlier lanes) into a
-// digit-sorted copy of the tile in shared memory; the copy is then written
-// out in order, so the elements of one digit leave as one contiguous run.
+// Stable scatter of one tile.  Warp w owns elements [512 w, 512 w + 512) of
+// the tile and ranks them in index order against its own digit counters
+// (lanes with equal digits found by one ballot per digit bit); one block
+// scan then turns the per-warp counts into positions in a digit-sorted copy
+// of the tile in shared memory, which is written out in order, so the
+// elements of one digit leave as one contiguous run.
+// FUSED: counts holds the raw per-tile histograms (few tiles per segment);
+// each tile sums the earlier tiles' counts and scans the segment's digit
+// totals itself.  Otherwise counts and digit_base come scanned.
+template <bool FUSED>
 __global__ void __launch_bounds__(SORT_THREADS)
 k_radix_scatter(const uint32_t *__restrict__ kin, const uint32_t *__restrict__ vin,
                 uint32_t *__restrict__ kout, uint32_t *__restrict__ vout, int64_t len, int shift,
                 const uint32_t *__restrict__ counts, const uint32_t *__restrict__ digit_base,
                 int tiles) {
   constexpr int NW = SORT_THREADS / 32;
+  constexpr int PER_WARP = SORT_TILE / NW;  // = 32 * SORT_ITEMS
   __shared__ uint32_t sk[SORT_TILE], sv[SORT_TILE];
-  __shared__ uint32_t running[256];   // next local position per digit
+  __shared__ uint32_t wh[NW][256];    // per-warp digit counters, then per-warp digit starts
   __shared__ uint32_t gshift[256];    // global position - local position, per digit
-  __shared__ uint32_t wcnt[NW][256];
   __shared__ uint32_t wt[32];
   const int seg = blockIdx.y, tile = blockIdx.x;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t soff = (int64_t)seg * len;
   const int64_t t0 = (int64_t)tile * SORT_TILE;
   const int nvalid = (int)(len - t0 < SORT_TILE ? len - t0 : (int64_t)SORT_TILE);
-  for (int w = 0; w < NW; ++w) wcnt[w][threadIdx.x] = 0;
-  running[threadIdx.x] = 0;
-  __syncthreads();
-  uint32_t key[SORT_ITEMS], val[SORT_ITEMS];
-#pragma unroll
-  for (int r = 0; r < SORT_ITEMS; ++r) {
-    const int i = r * SORT_THREADS + threadIdx.x;
-    key[r] = i < nvalid ? kin[soff + t0 + i] : 0u;
-    val[r] = (i < nvalid && vin) ? vin[soff + t0 + i] : 0u;
-    if (i < nvalid) atomicAdd(&running[(key[r] >> shift) & 255u], 1u);
-  }
-  __syncthreads();
-  {  // local digit starts; global shift = tile's global start of the digit - local start
-    const uint32_t cnt = running[threadIdx.x];
-    __syncthreads();
-    const uint32_t ls = block_exclusive_scan(cnt, wt, nullptr);
-    running[threadIdx.x] = ls;
-    gshift[threadIdx.x] = digit_base[seg * 256 + threadIdx.x] +
-                          counts[((int64_t)seg * 256 + threadIdx.x) * tiles + tile] - ls;
-  }
+  for (int w = 0; w < NW; ++w) wh[w][threadIdx.x] = 0;
   __syncthreads();
   const unsigned lt = (1u << lane) - 1u;
+  uint32_t key[SORT_ITEMS], val[SORT_ITEMS], rk[SORT_ITEMS];
 #pragma unroll
   for (int r = 0; r < SORT_ITEMS; ++r) {
-    const int i = r * SORT_THREADS + threadIdx.x;
+    const int i = warp * PER_WARP + r * 32 + lane;
     const bool valid = i < nvalid;
+    key[r] = valid ? kin[soff + t0 + i] : 0u;
+    val[r] = (valid && vin) ? vin[soff + t0 + i] : 0u;
     const uint32_t digit = (key[r] >> shift) & 255u;
-    const unsigned peers = __match_any_sync(FULL, valid ? digit : (0x10000u | (unsigned)lane));
-    const int rank = __popc(peers & lt);
-    if (valid && rank == 0) wcnt[warp][digit] = __popc(peers);
-    __syncthreads();
-    if (valid) {
-      uint32_t pre = running[digit] + rank;
-      for (int w = 0; w < warp; ++w) pre += wcnt[w][digit];
-      sk[pre] = key[r];
-      sv[pre] = val[r];
+    unsigned peers = __ballot_sync(FULL, valid);
+#pragma unroll
+    for (int bt = 0; bt < 8; ++bt) {
+      const bool set = (digit >> bt) & 1u;
+      const unsigned bb = __ballot_sync(FULL, set);
+      peers &= set ? bb : ~bb;
     }
-    __syncthreads();
-    uint32_t tot = 0;
-    for (int w = 0; w < NW; ++w) { tot += wcnt[w][threadIdx.x]; wcnt[w][threadIdx.x] = 0; }
-    running[threadIdx.x] += tot;
-    __syncthreads();
+    const int rank = __popc(peers & lt);
+    const uint32_t base = wh[warp][digit];
+    rk[r] = base + rank;
+    __syncwarp();
+    if (valid && rank == 0) wh[warp][digit] = base + __popc(peers);
+    __syncwarp();
   }
+  __syncthreads();
+  {  // digit d: local start, per-warp starts, global shift
+    const int d = threadIdx.x;
+    uint32_t cnt = 0;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) cnt += wh[w][d];
+    const uint32_t ls = block_exclusive_scan(cnt, wt, nullptr);
+    uint32_t acc = ls;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) { const uint32_t v = wh[w][d]; wh[w][d] = acc; acc += v; }
+    const uint32_t *cd = counts + ((int64_t)seg * 256 + d) * tiles;
+    if (FUSED) {
+      uint32_t pre = 0, tot = 0;
+      for (int t = 0; t < tiles; ++t) {
+        const uint32_t v = cd[t];
+        if (t < tile) pre += v;
+        tot += v;
+      }
+      const uint32_t db = block_exclusive_scan(tot, wt, nullptr);
+      gshift[d] = db + pre - ls;
+    } else {
+      gshift[d] = digit_base[seg * 256 + d] + cd[tile] - ls;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < SORT_ITEMS; ++r) {
+    const int i = warp * PER_WARP + r * 32 + lane;
+    if (i < nvalid) {
+      const uint32_t pos = wh[warp][(key[r] >> shift) & 255u] + rk[r];
+      sk[pos] = key[r];
+      sv[pos] = val[r];
+    }
+  }
+  __syncthreads();
   for (int i = threadIdx.x; i < nvalid; i += SORT_THREADS) {
     const uint32_t k = sk[i];
     const uint32_t pos = gshift[(k >> shift) & 255u] + (uint32_t)i;
@@ -149,13 +172,19 @@ int segmented_sort(uint32_t *keys, uint32_t *vals, int nseg, int64_t len, int nb
     dim3 g((unsigned)tiles, (unsigned)nseg);
     k_radix_hist<<<g, SORT_THREADS, 0, st>>>(kin, len, shift, tmp.counts, tiles);
     dl_count_launch();
-    k_radix_scan_digit<<<dim3(256, nseg), SORT_THREADS, 0, st>>>(tmp.counts, tiles, tmp.digit_base);
-    dl_count_launch();
-    k_radix_scan_totals<<<nseg, 256, 0, st>>>(tmp.digit_base);
-    dl_count_launch();
-    k_radix_scatter<<<g, SORT_THREADS, 0, st>>>(kin, vin, kout, vout, len, shift, tmp.counts,
-                                                tmp.digit_base, tiles);
-    dl_count_launch();
+    if (tiles <= 64) {  // few tiles per segment: the scatter scans the counts itself
+      k_radix_scatter<true><<<g, SORT_THREADS, 0, st>>>(kin, vin, kout, vout, len, shift,
+                                                        tmp.counts, tmp.digit_base, tiles);
+      dl_count_launch();
+    } else {
+      k_radix_scan_digit<<<dim3(256, nseg), SORT_THREADS, 0, st>>>(tmp.counts, tiles, tmp.digit_base);
+      dl_count_launch();
+      k_radix_scan_totals<<<nseg, 256, 0, st>>>(tmp.digit_base);
+      dl_count_launch();
+      k_radix_scatter<false><<<g, SORT_THREADS, 0, st>>>(kin, vin, kout, vout, len, shift,
+                                                         tmp.counts, tmp.digit_base, tiles);
+      dl_count_launch();
+    }
     DL_CUDA(cudaGetLastError());
     std::swap(kin, kout);
     std::swap(vin, vout);
