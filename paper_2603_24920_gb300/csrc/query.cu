@@ -296,7 +296,6 @@ __device__ __forceinline__ void expand_levels(QCtx &c) {
   const int K = ix.K, NR1 = ix.N_r + 1;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const float *qp = c.qa.Qp + c.qi * ix.LK;
-  const unsigned long long ep = sm.epoch;
   // The first tree starts from a guessed bound (this CTA's previous final
   // bound plus a margin) so that the second hull level can prune its scan as
   // well.  If the tree does not reach beta*n + k within the guess, it is
@@ -410,11 +409,10 @@ __device__ __forceinline__ void expand_levels(QCtx &c) {
         if (valid && more) lb = box_lb2_part<LUT_ROWS / 2, LUT_ROWS>(c.lut, blo, bhi, lb);
         if (valid && more) {
           // Leaves above Jnow are never needed again (every later test is
-          // against a bound <= Jnow), so only the others get their level,
-          // size and level-array entry; the rest read as level 255.
+          // against a bound <= Jnow), so only the others get their level and
+          // size and are listed; the rest read as level 255.
           if (lb <= thr) {
             lv = level_of(sm.T, lb, c.qa.lg_eps2, c.qa.inv_2lg_c);
-            c.s.lev[ix.leaf_off[t] + l] = (ep << 8) | lv;
             sz = leaf_begin_of(ix, t, l + 1) - leaf_begin_of(ix, t, l);
           }
         }
@@ -481,7 +479,11 @@ __device__ __forceinline__ void build_level_hash(QCtx &c) {
   __syncthreads();
   const uint32_t slots = 1u << bits;
   const bool use = bits >= 4 && sm.hash_count * 2u <= slots;
-  if (!use) {
+  if (!use) {  // the slot's epoch-tagged level array instead: every listed leaf
+    const unsigned long long ep = sm.epoch;
+    for (int t = 0; t < ix.L; ++t)
+      for (int64_t e = threadIdx.x; e < sm.nlist[t]; e += QT)
+        c.s.lev[ix.leaf_off[t] + c.s.lleaf[ix.leaf_off[t] + e]] = (ep << 8) | c.s.llev[ix.leaf_off[t] + e];
     if (threadIdx.x == 0) sm.use_hash = 0;
     __syncthreads();
     return;
@@ -593,7 +595,14 @@ __device__ __forceinline__ void visit_points(QCtx &c, int t, Pred pred, Fn fn, b
   }
 }
 
-// ---- step 2: owner-rule union counts and per-tree new-point counts -------
+// ---- step 2: union counts and per-tree new-point counts ------------------
+// A point of tree t's listed leaves at level lv_t is new in tree t for the
+// levels in [lv_t, f_t), f_t = its smallest level in trees u < t: D_t gets +1
+// at lv_t and -1 at f_t.  For every level j exactly one tree counts a point
+// whose smallest level is <= j (the first tree reaching j), so the union
+// increments are H[j] = sum_t D_t[j] and only the earlier trees' levels are
+// looked up.  The fixed-r_min loop needs per-tree owner counts instead
+// (owner = the tree of the point's smallest level): every tree's level.
 template <int LC>
 __device__ __forceinline__ void union_counts_t(QCtx &c) {
   const QueryIndexView &ix = c.ix;
@@ -603,31 +612,50 @@ __device__ __forceinline__ void union_counts_t(QCtx &c) {
   for (int t = 0; t < L; ++t) {
     const int64_t lo0 = ix.leaf_off[t];
     uint32_t *Dt = reinterpret_cast<uint32_t *>(c.D + t * 256);
-    visit_points(
-        c, t, [&](int64_t e) { return c.s.llev[lo0 + e] <= jhi; },
-        [&](bool valid, uint32_t p, uint32_t, uint32_t lvt) {
-          uint32_t m = 255u, f = 255u;
-          int owner = -1;
-          if (valid) {
-            const PointLeaves<LC> lf(ix, p);
+    if (fixed) {
+      visit_points(
+          c, t, [&](int64_t e) { return c.s.llev[lo0 + e] <= jhi; },
+          [&](bool valid, uint32_t p, uint32_t, uint32_t lvt) {
+            uint32_t m = 255u;
+            int owner = -1;
+            if (valid) {
+              const PointLeaves<LC> lf(ix, p);
 #pragma unroll
-            for (int u = 0; u < L; ++u) {
-              const uint32_t lv = (u == t) ? lvt : leaf_level_h(ix, c.s, c.sm, c.lut, u, lf[u]);
-              if (lv < m) { m = lv; owner = u; }
-              if (u < t) f = min(f, lv);
+              for (int u = 0; u < L; ++u) {
+                const uint32_t lv = (u == t) ? lvt : leaf_level_h(ix, c.s, c.sm, c.lut, u, lf[u]);
+                if (lv < m) { m = lv; owner = u; }
+              }
             }
-          }
-          warp_bin_count(c.sm.H, valid && owner == t, m, 1u);
-          if (fixed) {  // points owned by tree t, by smallest level
-            warp_bin_count(Dt, valid && owner == t, m, 1u);
-          } else {      // new in tree t for levels in [lvt, f)
+            warp_bin_count(c.sm.H, valid && owner == t, m, 1u);
+            warp_bin_count(Dt, valid && owner == t, m, 1u);  // owned by tree t, by smallest level
+          },
+          true);
+    } else {
+      visit_points(
+          c, t, [&](int64_t e) { return c.s.llev[lo0 + e] <= jhi; },
+          [&](bool valid, uint32_t p, uint32_t, uint32_t lvt) {
+            uint32_t f = 255u;
+            if (valid && t > 0) {
+              const PointLeaves<LC> lf(ix, p);
+#pragma unroll
+              for (int u = 0; u < L; ++u)
+                if (u < t) f = min(f, leaf_level_h(ix, c.s, c.sm, c.lut, u, lf[u]));
+            }
             warp_bin_count(Dt, valid && f > lvt, lvt, 1u);
             warp_bin_count(Dt, valid && f > lvt && f <= jhi, f, 0xffffffffu);  // -1 (two's complement)
-          }
-        },
-        true);
+          },
+          true);
+    }
   }
   __syncthreads();
+  if (!fixed) {
+    for (int j = threadIdx.x; j < 256; j += QT) {
+      int32_t h = 0;
+      for (int t = 0; t < L; ++t) h += c.D[t * 256 + j];
+      c.sm.H[j] = (uint32_t)h;
+    }
+    __syncthreads();
+  }
 }
 
 __device__ __forceinline__ void union_counts(QCtx &c) {
