@@ -12,14 +12,26 @@ namespace dl {
 constexpr int LUT_STRIDE = 257;
 constexpr int LUT_ROWS = 16;
 
-// Fills the table of tree t (whole block; the caller synchronises).
+// Fills the table of tree t (whole block; the caller synchronises).  The
+// entries are spread evenly over the threads, eight loads in flight each.
 __device__ __forceinline__ void build_lut(float *lut, const float *B, const float *qpt, int t,
                                           int K, int NR1) {
-  for (int j = 0; j < LUT_ROWS; ++j) {
-    const float qj = j < K ? qpt[j] : 0.0f;
-    const float *Bj = B + (int64_t)(t * K + (j < K ? j : 0)) * NR1;
-    for (int z = threadIdx.x; z < LUT_STRIDE; z += blockDim.x)
-      lut[j * LUT_STRIDE + z] = (j < K && z < NR1) ? __fsub_rn(Bj[z], qj) : 0.0f;
+  constexpr int TOTAL = LUT_ROWS * LUT_STRIDE;
+  for (int base = 0; base < TOTAL; base += 8 * (int)blockDim.x) {
+    float v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int idx = base + u * (int)blockDim.x + (int)threadIdx.x;
+      const int j = idx / LUT_STRIDE, z = idx - j * LUT_STRIDE;
+      v[u] = 0.0f;
+      if (idx < TOTAL && j < K && z < NR1)
+        v[u] = __fsub_rn(B[(int64_t)(t * K + j) * NR1 + z], qpt[j]);
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int idx = base + u * (int)blockDim.x + (int)threadIdx.x;
+      if (idx < TOTAL) lut[idx] = v[u];
+    }
   }
 }
 

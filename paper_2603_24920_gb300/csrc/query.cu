@@ -393,6 +393,17 @@ __device__ __forceinline__ void expand_levels(QCtx &c) {
     while (true) {
       const uint32_t Jnow = (uint32_t)sm.jhi;
       const uint32_t p0c = sm.cpos, p1c = min(nsel, p0c + (uint32_t)(2 * QW));
+      // the level of the first block after this chunk (thread 0 needs it
+      // after the chunk) and the second run of each warp are fetched early
+      int jnext = NLEV;
+      if (threadIdx.x == 0 && p1c < nsel) jnext = (int)blev[c.s.border[ix.blk_off[t] + p1c]];
+      if (p0c + warp + QW < p1c) {
+        const int64_t l2 = (int64_t)c.s.border[ix.blk_off[t] + p0c + warp + QW] * LEAF_BLOCK + lane;
+        if (l2 < nl) {
+          asm volatile("prefetch.global.L1 [%0];" ::"l"(llo + l2));
+          asm volatile("prefetch.global.L1 [%0];" ::"l"(lhi + l2));
+        }
+      }
       for (uint32_t i = p0c + warp; i < p1c; i += QW) {
         const uint32_t b = c.s.border[ix.blk_off[t] + i];
         const int64_t l = (int64_t)b * LEAF_BLOCK + lane;
@@ -433,7 +444,6 @@ __device__ __forceinline__ void expand_levels(QCtx &c) {
       }
       __syncthreads();
       if (threadIdx.x == 0) {
-        const int jnext = p1c < nsel ? (int)blev[c.s.border[ix.blk_off[t] + p1c]] : NLEV;
         int j = sm.jchk;
         for (; j < jnext && j <= sm.jhi; ++j) {
           sm.cum += hist_t[j];
