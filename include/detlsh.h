@@ -88,6 +88,9 @@ typedef struct {
     int32_t keep_bf16;      /* 1: also keep a BF16 copy of the data (default 1)    */
     int32_t keep_projections; /* 1: keep the n x L*K projections (default 0)      */
     int32_t encoding;       /* DETLSH_ENC_DYNAMIC (default) / DETLSH_ENC_STATIC    */
+    int32_t tree_group;     /* trees built per pass, 0..L; 0 (default) = as many as
+                               fit in half the free device memory.  The trees do
+                               not depend on it.                                   */
 } detlsh_build_params;
 
 typedef struct {

@@ -27,7 +27,7 @@ void dl_set_last_cuda_error(cudaError_t e, const char *what, const char *file, i
 struct detlsh_index {
   int device = 0;
   int64_t n = 0;
-  int d = 0, L = 0, K = 0, LK = 0, N_r = 0, bbits = 0, M = 0, box_mode = 0, encoding = 0;
+  int d = 0, L = 0, K = 0, LK = 0, N_r = 0, bbits = 0, M = 0, box_mode = 0, encoding = 0, tree_group = 0;
   uint64_t seed = 0;
   double frac = 0.1, eps2 = 0.0;
   int64_t m_sample = 0;
@@ -389,6 +389,7 @@ int validate_build(int64_t n, int32_t d, const detlsh_build_params *p) {
   if (!(p->sample_frac > 0.0 && p->sample_frac <= 1.0)) return DETLSH_ERR_INVALID_ARG;
   if (p->encoding != DETLSH_ENC_DYNAMIC && p->encoding != DETLSH_ENC_STATIC)
     return DETLSH_ERR_INVALID_ARG;
+  if (p->tree_group < 0 || p->tree_group > p->L) return DETLSH_ERR_INVALID_ARG;
   if (p->box_mode != DETLSH_BOX_PREFIX && p->box_mode != DETLSH_BOX_TIGHT)
     return DETLSH_ERR_INVALID_ARG;
   return DETLSH_OK;
@@ -404,6 +405,7 @@ int build_impl(detlsh_index *ix, const float *data, cudaStream_t st, const detls
   // data copy (the index keeps its own FP32 rows for verification)
   DL_TRY(dalloc(ix, &ix->X, (size_t)n * d, st));
   DL_TRY(copy_in(ix->X, data, sizeof(float) * (size_t)n * d, st));
+  const float *src = ix->X;
   // projection vectors (Eq. 1)
   std::vector<float> Ah((size_t)LK * d);
   projection_matrix(LK, d, ix->seed, Ah.data());
@@ -426,7 +428,6 @@ int build_impl(detlsh_index *ix, const float *data, cudaStream_t st, const detls
   pa.fb_total = fb_total; pa.err = err;
 
   const bool stat = ix->encoding == DETLSH_ENC_STATIC;
-  int e = 0;
   SortTemp srt;  // the sample-column sort
   if (stat) {
     // ---- static scheme: fixed N(0,1) breakpoints, no sample ----
@@ -458,9 +459,7 @@ int build_impl(detlsh_index *ix, const float *data, cudaStream_t st, const detls
     ProjArgs ps = pa;
     ps.P = Ps;
     ps.ldP = m;
-    DL_TRY(project_rows(ix->X, d, ix->sample, m, d, ix->A, LK, 1, ps, st));
-    e = check_err(err, st);
-    if (e) return e;
+    DL_TRY(project_rows(src, d, ix->sample, m, d, ix->A, LK, 1, ps, st));
     DL_CUDA(cudaEventRecord(ix->ev[1], st));
     DL_TRY(float_to_keys(Ps, (int64_t)LK * m, st));
     const size_t cnt_cap = (size_t)LK * 256 * sort_tiles(m);
@@ -503,9 +502,10 @@ int build_impl(detlsh_index *ix, const float *data, cudaStream_t st, const detls
   DL_TRY(tp.get(&fb_enc, fb_enc_cap));
   pe.fb_list = fb_enc;
   pe.fb_cap = fb_enc_cap;
-  DL_TRY(project_rows(ix->X, d, nullptr, n, d, ix->A, LK, 2, pe, st));
-  e = check_err(err, st);
-  if (e) return e;
+  // a non-finite input (flagged by the exact path) is reported after the
+  // trees' single host wait: the kernels in between stay in bounds on any
+  // values, and the index is not returned
+  DL_TRY(project_rows(src, d, nullptr, n, d, ix->A, LK, 2, pe, st));
   if (!stat) DL_TRY(finish_breakpoint_ends(minmax, LK, N_r, ix->B, st));
   DL_CUDA(cudaEventRecord(ix->ev[3], st));
   if (p->keep_projections) {
@@ -513,13 +513,13 @@ int build_impl(detlsh_index *ix, const float *data, cudaStream_t st, const detls
     ProjArgs pp = pa;
     pp.P = ix->P;
     pp.ldP = LK;
-    DL_TRY(project_rows(ix->X, d, nullptr, n, d, ix->A, LK, 0, pp, st));
+    DL_TRY(project_rows(src, d, nullptr, n, d, ix->A, LK, 0, pp, st));
   }
   if (p->keep_bf16) {
     DL_TRY(dalloc(ix, &ix->Xh, (size_t)n * d, st));
     DL_TRY(dalloc(ix, &ix->Xn, (size_t)n, st));
     k_rows_to_bf16<<<(unsigned)std::min<int64_t>(ceil_div(n, 8), 8192), 256, 0, st>>>(
-        ix->X, ix->Xh, ix->Xn, n, d);
+        src, ix->Xh, ix->Xn, n, d);
     dl_count_launch();
     DL_CUDA(cudaGetLastError());
   }
@@ -534,13 +534,14 @@ int build_impl(detlsh_index *ix, const float *data, cudaStream_t st, const detls
   // waits once.
   DL_TRY(dalloc(ix, &ix->perm, (size_t)L * n, st));
   DL_TRY(dalloc(ix, &ix->leaf_of, (size_t)L * n, st));
-  int G = L;
-  {
+  int G = ix->tree_group > 0 ? ix->tree_group : L;
+  if (ix->tree_group == 0) {
     size_t freeb = 0, totb = 0;
     DL_CUDA(cudaMemGetInfo(&freeb, &totb));
     const size_t per_tree = (size_t)n * 240;  // group temporaries per tree, bytes
-    while (G > 1 && ((size_t)G * per_tree > freeb / 2 || (int64_t)G * n + G > (int64_t)UINT32_MAX)) --G;
+    while (G > 1 && (size_t)G * per_tree > freeb / 2) --G;
   }
+  while (G > 1 && (int64_t)G * n + G > (int64_t)UINT32_MAX) --G;
   const int ngroups = (L + G - 1) / G;
   const int64_t N = (int64_t)G * n;
   TreeTemp tt;
@@ -586,7 +587,10 @@ int build_impl(detlsh_index *ix, const float *data, cudaStream_t st, const detls
   }
   std::vector<uint32_t> hs((size_t)SCAL * ngroups);
   DL_CUDA(cudaMemcpyAsync(hs.data(), scal, sizeof(uint32_t) * hs.size(), cudaMemcpyDeviceToHost, st));
+  int herr = 0;
+  DL_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st));
   DL_CUDA(cudaStreamSynchronize(st));
+  if (herr) return herr;
   for (int g = 0; g < ngroups; ++g) {
     const uint32_t *h = hs.data() + SCAL * g;
     if (h[2] != 0) return (int)h[2];
@@ -924,6 +928,7 @@ int detlsh_default_build_params(detlsh_build_params *p) {
   p->keep_bf16 = 1;
   p->keep_projections = 0;
   p->encoding = DETLSH_ENC_DYNAMIC;
+  p->tree_group = 0;
   return DETLSH_OK;
 }
 
@@ -969,7 +974,7 @@ int detlsh_build_ex(const float *data, int64_t n, int32_t d, const detlsh_build_
   if (!ix) return DETLSH_ERR_OOM;
   cudaGetDevice(&ix->device);
   ix->n = n; ix->d = d; ix->L = p->L; ix->K = p->K; ix->LK = p->L * p->K; ix->N_r = p->N_r;
-  ix->M = p->max_size; ix->box_mode = p->box_mode; ix->encoding = p->encoding; ix->seed = p->seed; ix->frac = p->sample_frac;
+  ix->M = p->max_size; ix->box_mode = p->box_mode; ix->encoding = p->encoding; ix->tree_group = p->tree_group; ix->seed = p->seed; ix->frac = p->sample_frac;
   while ((1 << ix->bbits) < ix->N_r) ++ix->bbits;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const int s = build_impl(ix, data, st, p);

@@ -31,7 +31,7 @@ class BuildParams(C.Structure):
     _fields_ = [("L", C.c_int32), ("K", C.c_int32), ("N_r", C.c_int32), ("max_size", C.c_int32),
                 ("seed", C.c_uint64), ("sample_frac", C.c_double), ("box_mode", C.c_int32),
                 ("keep_bf16", C.c_int32), ("keep_projections", C.c_int32),
-                ("encoding", C.c_int32)]
+                ("encoding", C.c_int32), ("tree_group", C.c_int32)]
 
 
 class QueryParams(C.Structure):

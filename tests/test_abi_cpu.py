@@ -43,6 +43,7 @@ def test_default_params(lib):
     p = D.detlsh_default_build_params()
     assert (p.L, p.K, p.N_r, p.max_size) == (4, 16, 256, 64)
     assert p.sample_frac == pytest.approx(0.1)
+    assert p.tree_group == 0
     q = D.detlsh_default_query_params()
     assert (q.beta, q.c, q.precision, q.rerank_mult) == (pytest.approx(0.1), 1.5, 0, 4)
 
@@ -50,7 +51,7 @@ def test_default_params(lib):
 @pytest.mark.parametrize("kw", [dict(L=0), dict(L=17), dict(K=0), dict(K=17), dict(N_r=3),
                                 dict(N_r=512), dict(N_r=1), dict(max_size=0),
                                 dict(sample_frac=0.0), dict(sample_frac=1.5), dict(box_mode=2),
-                                dict(L=16, K=17)])
+                                dict(L=16, K=17), dict(tree_group=-1), dict(L=2, tree_group=3)])
 def test_build_rejects_bad_parameters(lib, kw):
     X = np.zeros((10, 4), np.float32)
     with pytest.raises(D.DetlshError) as e:

@@ -274,3 +274,32 @@ def test_query_per_tree_check(pair, beta, k):
         assert np.array_equal(np.sort(S_g[i]), np.sort(r["S"])), i
         assert js[i] == r["jstar"] and ist[i] == r["istar"]
         _check_topk(ids[i], dists[i], r["S"], X, Q[i], k)
+
+
+@pytest.mark.parametrize("L,groups", [(4, (1, 2, 3)), (3, (2,)), (5, (4,))])
+def test_tree_group_independent(L, groups):
+    """Trees built G at a time (the group size only changes how many trees a
+    launch covers) equal the trees built all at once, array by array, and
+    give the same candidate sets, j* and i*."""
+    X = _gauss(6000, 24, seed=5)
+    Q = _queries(24, m=8)
+    h0 = D.detlsh_build(X, L=L, K=8, N_r=64, seed=3, max_size=16, tree_group=L)
+    try:
+        ref = [D.detlsh_get_tree(h0, t) for t in range(L)]
+        S0, j0, i0 = D.detlsh_query_candidates(h0, Q, 5, beta=0.05)
+        for g in groups:
+            h = D.detlsh_build(X, L=L, K=8, N_r=64, seed=3, max_size=16, tree_group=g)
+            try:
+                for t in range(L):
+                    got = D.detlsh_get_tree(h, t)
+                    for key, v in ref[t].items():
+                        np.testing.assert_array_equal(got[key], v, err_msg=f"group {g} tree {t} {key}")
+                S, js, ist = D.detlsh_query_candidates(h, Q, 5, beta=0.05)
+                np.testing.assert_array_equal(js, j0)
+                np.testing.assert_array_equal(ist, i0)
+                for a, b in zip(S, S0):
+                    np.testing.assert_array_equal(np.sort(a), np.sort(b))
+            finally:
+                D.detlsh_free(h)
+    finally:
+        D.detlsh_free(h0)
