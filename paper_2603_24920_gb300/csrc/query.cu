@@ -37,6 +37,7 @@ constexpr int QW = QT / 32;
 constexpr int KMAX = 1024;
 constexpr int RR_MAX = 4096;  // re-rank pool of the BF16 path
 constexpr int FLC = 512;      // listed leaves per chunk of a flattened visit
+constexpr int EXP_RUNS = 4;   // leaf runs per warp per chunk of the level-ordered expansion
 
 struct Slot {
   unsigned long long *lev;  // [total_leaves] (epoch << 8) | level of expanded leaves
@@ -392,16 +393,19 @@ __device__ __forceinline__ void expand_levels(QCtx &c) {
     const uint32_t nsel = sm.bstart[255];
     while (true) {
       const uint32_t Jnow = (uint32_t)sm.jhi;
-      const uint32_t p0c = sm.cpos, p1c = min(nsel, p0c + (uint32_t)(2 * QW));
+      const uint32_t p0c = sm.cpos, p1c = min(nsel, p0c + (uint32_t)(EXP_RUNS * QW));
       // the level of the first block after this chunk (thread 0 needs it
-      // after the chunk) and the second run of each warp are fetched early
+      // after the chunk) and each warp's later runs are fetched early
       int jnext = NLEV;
       if (threadIdx.x == 0 && p1c < nsel) jnext = (int)blev[c.s.border[ix.blk_off[t] + p1c]];
-      if (p0c + warp + QW < p1c) {
-        const int64_t l2 = (int64_t)c.s.border[ix.blk_off[t] + p0c + warp + QW] * LEAF_BLOCK + lane;
-        if (l2 < nl) {
-          asm volatile("prefetch.global.L1 [%0];" ::"l"(llo + l2));
-          asm volatile("prefetch.global.L1 [%0];" ::"l"(lhi + l2));
+#pragma unroll
+      for (int r = 1; r < EXP_RUNS; ++r) {
+        if (p0c + warp + r * QW < p1c) {
+          const int64_t l2 = (int64_t)c.s.border[ix.blk_off[t] + p0c + warp + r * QW] * LEAF_BLOCK + lane;
+          if (l2 < nl) {
+            asm volatile("prefetch.global.L1 [%0];" ::"l"(llo + l2));
+            asm volatile("prefetch.global.L1 [%0];" ::"l"(lhi + l2));
+          }
         }
       }
       for (uint32_t i = p0c + warp; i < p1c; i += QW) {
