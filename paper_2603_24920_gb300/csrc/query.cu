@@ -557,9 +557,15 @@ __device__ __forceinline__ void visit_points(QCtx &c, int t, Pred pred, Fn fn, b
         q[u] = 1;
       }
     }
-    uint32_t nq, np;
-    const uint32_t qs = block_exclusive_scan(q[0] + q[1], sm.wt, &nq);
-    const uint32_t ps = block_exclusive_scan(sz[0] + sz[1], sm.wt, &np);
+    uint32_t nq, np, qs, ps;
+    if (ix.max_leaf_size < 8192) {  // one scan of (count << 22 | points): 512 leaves of < 8192 points fit
+      uint32_t tot;
+      const uint32_t ex = block_exclusive_scan(((q[0] + q[1]) << 22) | (sz[0] + sz[1]), sm.wt, &tot);
+      qs = ex >> 22; ps = ex & 0x3fffffu; nq = tot >> 22; np = tot & 0x3fffffu;
+    } else {
+      qs = block_exclusive_scan(q[0] + q[1], sm.wt, &nq);
+      ps = block_exclusive_scan(sz[0] + sz[1], sm.wt, &np);
+    }
     {
       uint32_t slot = qs, pre = ps;
 #pragma unroll
