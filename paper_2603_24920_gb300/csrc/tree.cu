@@ -92,7 +92,8 @@ constexpr int TB_THREADS = 256;
 constexpr int TB_WARPS = TB_THREADS / 32;
 constexpr int TB_POINTS = 2048;  // first-layer nodes starting in a CTA's range of points
 
-__global__ void __launch_bounds__(TB_THREADS) k_subtree(SubtreeArgs a) {
+// four CTAs per SM (at most 64 registers): the levels are latency-bound
+__global__ void __launch_bounds__(TB_THREADS, 4) k_subtree(SubtreeArgs a) {
   __shared__ uint32_t ncur, nnext, f_lo, f_hi;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int K = a.K, bb = a.bbits;
