@@ -348,7 +348,6 @@ __global__ void k_leaf_of(LeafWriteArgs a) {
   }
 }
 
-__global__ void k_set_u32(uint32_t *p, uint32_t v) { *p = v; }
 // base[*idx] = v, the index read on the device
 __global__ void k_set_at(uint32_t *base, const uint32_t *idx, uint32_t v) { base[*idx] = v; }
 

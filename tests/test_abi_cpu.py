@@ -86,3 +86,34 @@ def test_no_device_is_reported(lib):
     with pytest.raises(D.DetlshError) as e:
         D.detlsh_build(np.random.rand(100, 8).astype(np.float32), L=2, K=4, N_r=16)
     assert e.value.status == -6
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """The binding's ctypes mirrors have the header's sizes and field offsets
+    (checked by compiling the header with the host C compiler)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no host C compiler")
+    pairs = [("detlsh_build_params", D.BuildParams), ("detlsh_query_params", D.QueryParams),
+             ("detlsh_info", D.Info), ("detlsh_timings", D.Timings)]
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "detlsh.h"', "int main(void) {"]
+    for cname, py in pairs:
+        lines.append('  printf("%%s size %%zu\\n", "%s", sizeof(%s));' % (cname, cname))
+        for f, _ in py._fields_:
+            lines.append('  printf("%%s %s %%zu\\n", "%s", offsetof(%s, %s));' % (f, cname, cname, f))
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True)
+    got = {}
+    for line in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.splitlines():
+        cname, key, val = line.split()
+        got[(cname, key)] = int(val)
+    for cname, py in pairs:
+        assert got[(cname, "size")] == C.sizeof(py), cname
+        for f, _ in py._fields_:
+            assert got[(cname, f)] == getattr(py, f).offset, (cname, f)
