@@ -19,7 +19,9 @@ Gaussian-mixture generators stand in for them with the same shapes:
                        1..4096, k uniform in {1,10,100}
 
 Rows are generated in fixed 65,536-row chunks, each from its own Philox stream,
-so any prefix or any chunk can be regenerated on its own.
+so any chunk can be regenerated on its own, and the first n rows of a longer
+draw are the n-row draw whenever n is a multiple of the chunk size (a partial
+last chunk is drawn for its own length).
 """
 import numpy as np
 
