@@ -16,8 +16,9 @@
 // open nodes one each, choosing the dimension that splits a node most evenly
 // and stably partitioning its range between two ping-pong buffers; a leaf is
 // recorded at the position where its points start; (3) leaves are numbered
-// by a scan over first-layer nodes and written out in position order, which
-// is depth-first order (child 0 holds the lower part of its parent's range).
+// by a compaction of those start flags: position order is depth-first order
+// (child 0 holds the lower part of its parent's range), so a leaf's rank
+// among the flags is its number and the records land in the final layout.
 //
 // Reading of Alg. 2 (insertion order and max_size are left open): a node is
 // split iff it holds more than max_size points and some dimension has prefix
