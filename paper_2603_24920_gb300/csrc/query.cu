@@ -13,8 +13,10 @@
 //     range query takes the whole leaf (optimisation (1) of Sec. VI-B2).
 //  2. Magic r_min (Sec. V-B1): N(j) = |union over trees of points in leaves
 //     of level <= j|; r_min = c^{j*}, j* = min{j : N(j) >= beta*n + k}.
-//     Union counts use an owner rule instead of per-query bitmaps: a point is
-//     counted once, by the first tree attaining its smallest level.
+//     Union counts need no per-query bitmaps: for every level j exactly one
+//     tree counts a point of the union (the first tree holding it within j),
+//     so N(j) is the sum over trees of per-tree difference arrays of new
+//     points, each point looking up only its levels in earlier trees.
 //  3. Alg. 5 at r_min: trees in order; a point is new in tree t if no earlier
 //     tree holds it within level j*; i* = first tree where the running count
 //     reaches beta*n + k; inside tree i* the leaves enter in ascending
