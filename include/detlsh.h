@@ -149,15 +149,17 @@ int detlsh_build_ex(const float *data, int64_t n, int32_t d, const detlsh_build_
  */
 int detlsh_query(const detlsh_index *ix, const float *queries, int64_t m, int32_t k, double c,
                  int64_t *ids, float *dists);
-/* As detlsh_query, with per-query k (nullable: k_max for all) and parameters;
+/* As detlsh_query (Alg. 5 from the r_min of Sec. V-B1, verification, top-k),
+ * with per-query k (nullable: k_max for all) and parameters (beta, c, precision,
+ * the r_min policy of Sec. V-B1 / Alg. 5, the priority order of Sec. VI-B2);
  * rows are k_max wide, padded with id -1 and dist +inf past the query's k. */
 int detlsh_query_ex(const detlsh_index *ix, const float *queries, int64_t m,
                     const int32_t *k_per_query, int32_t k_max, const detlsh_query_params *qp,
                     void *stream, int64_t *ids, float *dists);
 
 /*
- * detlsh_query_noalloc -- the queries of detlsh_query_ex (one k for every
- * query), for callers that cannot allocate device memory while serving: a
+ * detlsh_query_noalloc -- the queries of detlsh_query_ex (Alg. 5 at the
+ * magic r_min of Sec. V-B1; one k for every query), for callers that cannot allocate device memory while serving: a
  * process whose framework has already claimed nearly all device memory for
  * its own pool, a latency-critical path where cudaMalloc/cudaFree would stall
  * the device, or a deployment that forbids allocation after start-up.  The
@@ -208,13 +210,14 @@ typedef struct {
 int detlsh_get_info(const detlsh_index *ix, detlsh_info *info);
 /* Projection vectors A, (L*K) x d, row t = tree*K + dim (Eq. 1). */
 int detlsh_get_projection_matrix(const detlsh_index *ix, float *A);
-/* Sampled point ids, ascending (sample_size values). */
+/* Sampled point ids, ascending (sample_size values; the n_s = 0.1 n sample
+ * of Sec. III-A). */
 int detlsh_get_sample(const detlsh_index *ix, int64_t *ids);
 /* Breakpoints, (L*K) x (N_r+1) (Sec. III-A). */
 int detlsh_get_breakpoints(const detlsh_index *ix, float *B);
 /* Codes, n x (L*K) bytes, point-major (Alg. 1). */
 int detlsh_get_codes(const detlsh_index *ix, uint8_t *codes);
-/* Projections, n x (L*K); only if built with keep_projections. */
+/* Projections h(o) of Eq. 1, n x (L*K); only if built with keep_projections. */
 int detlsh_get_projections(const detlsh_index *ix, float *P);
 /* DE-Tree t (Alg. 2): leaves in canonical order (first-layer key ascending,
  * child 0 before child 1), perm = point ids leaf by leaf (ascending within a
@@ -222,7 +225,8 @@ int detlsh_get_projections(const detlsh_index *ix, float *P);
  * (num_leaves x K bytes each), leaf_of (n). */
 int detlsh_get_tree(const detlsh_index *ix, int32_t t, int64_t *perm, int64_t *leaf_begin,
                     uint8_t *box_lo, uint8_t *box_hi, uint8_t *nbits, int64_t *leaf_of);
-/* Squared-radius grid T(j) = fp32(eps^2 c^(2j)), j = -127..127, T(127) = inf. */
+/* Squared-radius grid of the magic r_min (Sec. V-B1; eps^2 from Eq. 2):
+ * T(j) = fp32(eps^2 c^(2j)), j = -127..127, T(127) = inf. */
 int detlsh_get_level_table(const detlsh_index *ix, double c, float *T);
 /* Device times (CUDA events on the caller's stream) of the last build and of
  * the last query call on this index, the number of kernels each launched,
@@ -246,8 +250,8 @@ typedef struct {
 } detlsh_timings;
 int detlsh_get_timings(const detlsh_index *ix, detlsh_timings *t);
 
-/* Exact FP32 projections of m rows with the index's A (m x L*K, host or
- * device in/out), the same kernels the build uses. */
+/* Exact FP32 projections (Eq. 1) of m rows with the index's A (m x L*K, host
+ * or device in/out), the same kernels the build uses. */
 int detlsh_project(const detlsh_index *ix, const float *rows, int64_t m, float *out,
                    void *stream);
 /* Candidate sets of Alg. 5 for m queries: S (host, m x cap, arrival order
@@ -260,7 +264,7 @@ int detlsh_query_candidates(const detlsh_index *ix, const float *queries, int64_
 
 /*
  * Queries that can be captured in a CUDA graph (batched serving: the paper has
- * no counterpart; same results as detlsh_query_ex).
+ * no counterpart; the same Alg. 5 queries and results as detlsh_query_ex).
  *
  * detlsh_query_reserve fixes the query parameters (beta, c, precision,
  * rerank_mult, r_min policy) and the largest batch (m_max queries, k <=
