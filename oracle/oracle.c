@@ -791,6 +791,20 @@ static float orc_ub2(const orc_index *ix, int t, const float *qp, const uint8_t 
     return acc;
 }
 
+/* Both node bounds of one box given directly by its breakpoints (K rows of
+ * N_r + 1), so that tests can check them on hand-worked boxes. */
+void orc_box_bounds(const float *B, int K, int N_r, const float *qp, const uint8_t *lo,
+                    const uint8_t *hi, float *lb2, float *ub2) {
+    orc_index one;
+    memset(&one, 0, sizeof one);
+    one.B = (float *)B;
+    one.K = K;
+    one.N_r = N_r;
+    one.L = 1;
+    *lb2 = orc_lb2(&one, 0, qp, lo, hi);
+    *ub2 = orc_ub2(&one, 0, qp, lo, hi);
+}
+
 /* Squared distance between a point's projection H_t(o) and q'_t in tree t's
  * projected space: FP32, dimensions in ascending order. */
 static float orc_proj_dist2(const orc_index *ix, int t, const float *qp, int64_t p) {

@@ -7,7 +7,7 @@
  *
  * Every function states the passage of the paper (DET-LSH / PDET-LSH,
  * arXiv 2603.24920) it follows.  Readings of passages the paper leaves open
- * are stated beside the function and listed in the design doc.
+ * are stated beside the function they shape.
  *
  * Precision: the projection is the correctly rounded FP32 value of the exact
  * real dot product (computed with exact big-integer arithmetic); breakpoints,
@@ -127,6 +127,10 @@ int64_t orc_index_range_exact(const orc_index *ix, int t, const float *q, double
                               int64_t *out);
 /* Upper bound of every leaf of tree t to query q (FP32, Sec. IV-C). */
 void orc_index_leaf_ub2(const orc_index *ix, int t, const float *q, float *ub2);
+/* Lower and upper bound (Sec. IV-C) of one box: B holds K rows of N_r + 1
+ * breakpoints, lo/hi the box's first and last region per dimension. */
+void orc_box_bounds(const float *B, int K, int N_r, const float *qp, const uint8_t *lo,
+                    const uint8_t *hi, float *lb2, float *ub2);
 /* Alg. 4, (r,c)-ANN: trees in order, S = union of the range queries (Alg. 3
  * as printed, or with optimised = 1 optimisation (1) of Sec. VI-B2: every
  * leaf whose lower bound is within r' whole);

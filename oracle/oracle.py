@@ -83,6 +83,8 @@ def lib():
         L.orc_index_query_batch.restype = C.c_int
         L.orc_index_leaf_lb2.argtypes = [C.c_void_p, C.c_int, _f32p, _f32p]
         L.orc_index_leaf_ub2.argtypes = [C.c_void_p, C.c_int, _f32p, _f32p]
+        L.orc_box_bounds.argtypes = [_f32p, C.c_int, C.c_int, _f32p, _u8p, _u8p,
+                                     C.POINTER(C.c_float), C.POINTER(C.c_float)]
         L.orc_index_range_exact.argtypes = [C.c_void_p, C.c_int, _f32p, C.c_double, _i64p]
         L.orc_index_range_exact.restype = C.c_int64
         L.orc_index_rc_ann.argtypes = [C.c_void_p, _f32p, C.c_double, C.c_double, C.c_double,
@@ -103,6 +105,16 @@ def philox4x32_10(ctr, key):
     out = np.zeros(4, np.uint32)
     lib().orc_philox4x32_10(np.asarray(ctr, np.uint32), np.asarray(key, np.uint32), out)
     return out
+
+
+def box_bounds(B, q, lo, hi):
+    """(LB^2, UB^2) of the box [B[j][lo_j], B[j][hi_j + 1]] to q (Sec. IV-C)."""
+    B = _f32(B)
+    K, R = B.shape
+    lb, ub = C.c_float(), C.c_float()
+    lib().orc_box_bounds(B, K, R - 1, _f32(q), np.ascontiguousarray(lo, np.uint8),
+                         np.ascontiguousarray(hi, np.uint8), C.byref(lb), C.byref(ub))
+    return lb.value, ub.value
 
 
 def projection_matrix(LK, d, seed):
