@@ -158,28 +158,34 @@ int detlsh_query_ex(const detlsh_index *ix, const float *queries, int64_t m,
                     void *stream, int64_t *ids, float *dists);
 
 /*
- * detlsh_query_noalloc -- the queries of detlsh_query_ex (Alg. 5 at the
- * magic r_min of Sec. V-B1; one k for every query), for callers that cannot allocate device memory while serving: a
- * process whose framework has already claimed nearly all device memory for
- * its own pool, a latency-critical path where cudaMalloc/cudaFree would stall
- * the device, or a deployment that forbids allocation after start-up.  The
- * paper has no counterpart; this entry point only changes where scratch
- * memory comes from.
+ * detlsh_query_noalloc -- the same queries and results as detlsh_query_ex
+ * (one k for every query, rmin_policy DETLSH_RMIN_MAGIC, per_tree 0 or 1),
+ * for callers that cannot allocate device memory while serving: a process
+ * whose framework has already claimed nearly all device memory for its own
+ * pool, a latency-critical path where cudaMalloc/cudaFree would stall the
+ * device, or a deployment that forbids allocation after start-up.  The paper
+ * has no counterpart; this entry point only changes where scratch memory
+ * comes from.
  *
  * All scratch lives in one fixed 32 MiB device array compiled into the
  * library (every GPU that loads the library holds it until the process
  * exits); the call allocates nothing.  queries (m x d FP32), ids (m x k
- * int64) and dists (m x k FP32) must be device memory owned by the caller.
+ * int64) and dists (m x k FP32) must be device memory owned by the caller,
+ * on the index's device, which must be the current device; queries must be
+ * 16-byte aligned when d is a multiple of 4 (4-byte aligned otherwise), ids
+ * 8-byte and dists 4-byte aligned.
  * Requests that do not fit (the query projections, BF16 query copy and one
  * per-CTA working slot, which grows with the index's leaf count and with
- * beta*n + k) fail with DETLSH_ERR_SCRATCH_LIMIT; smaller batches fit.
+ * beta*n + k, or with n when per_tree = 1) fail with
+ * DETLSH_ERR_SCRATCH_LIMIT; smaller batches fit.
  * The first call on a device looks up the array's device address with that
  * device current; make that first call before any stream capture.  Every
  * call reuses the same array and clears the part it uses at its start, so
  * calls that overlap on the GPU (other streams, other host threads) race:
  * serialise them.  Returns after the results are written.
- * Errors: as detlsh_query_ex, plus SCRATCH_LIMIT; INVALID_ARG for host
- * pointers and for rmin_policy other than DETLSH_RMIN_MAGIC.
+ * Errors: as detlsh_query_ex (NONFINITE_INPUT before the query kernel runs),
+ * plus SCRATCH_LIMIT; INVALID_ARG for host pointers, buffers on another
+ * device or misaligned, and for rmin_policy other than DETLSH_RMIN_MAGIC.
  */
 int detlsh_query_noalloc(const detlsh_index *ix, const float *queries, int64_t m, int32_t k,
                          const detlsh_query_params *qp, void *stream, int64_t *ids,

@@ -892,6 +892,9 @@ int index_query_view(const detlsh_index *ix, QueryIndexView *v, const float **A,
   return DETLSH_OK;
 }
 
+// Device that holds the index's memory (-1 for a null index).
+int index_device(const detlsh_index *ix) { return ix ? ix->device : -1; }
+
 // Argument checks shared with detlsh_query_ex, and the radius grid.
 int check_query_args(const detlsh_index *ix, int64_t m, int32_t k, const detlsh_query_params *qp) {
   return validate_query(ix, m, k, qp);

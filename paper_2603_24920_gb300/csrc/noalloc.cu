@@ -19,6 +19,7 @@
 
 namespace dl {
 int index_query_view(const detlsh_index *ix, QueryIndexView *v, const float **A, int *has_bf16);
+int index_device(const detlsh_index *ix);
 int check_query_args(const detlsh_index *ix, int64_t m, int32_t k, const detlsh_query_params *qp);
 void radius_grid(const detlsh_index *ix, double c, float T[256]);
 }  // namespace dl
@@ -53,13 +54,17 @@ int scratch_address(void **out) {
   return DETLSH_OK;
 }
 
-bool on_device(const void *p) {
+// True when p is device (or managed) memory of device `dev` and its address
+// is a multiple of `align` bytes.
+bool on_device(const void *p, int dev, uintptr_t align) {
   cudaPointerAttributes at;
   if (!p || cudaPointerGetAttributes(&at, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+  if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged) return false;
+  if (at.type == cudaMemoryTypeDevice && at.device != dev) return false;
+  return (reinterpret_cast<uintptr_t>(p) & (align - 1)) == 0;
 }
 
 int64_t up256(int64_t v) { return (v + 255) / 256 * 256; }
@@ -75,18 +80,30 @@ extern "C" int detlsh_query_noalloc(const detlsh_index *ix, const float *queries
   DL_TRY(check_query_args(ix, m, k, qp));
   if (qp->rmin_policy != DETLSH_RMIN_MAGIC) return DETLSH_ERR_INVALID_ARG;  // magic r_min only
   if (m == 0) return DETLSH_OK;
-  if (!on_device(queries) || !on_device(ids) || !on_device(dists)) return DETLSH_ERR_INVALID_ARG;
   QueryIndexView v;
   const float *A = nullptr;
   int has_bf16 = 0;
   DL_TRY(index_query_view(ix, &v, &A, &has_bf16));
+  // The caller's buffers go straight to the kernels (no staging copy), so
+  // they must live on the index's device, which must be the current one, and
+  // meet the kernels' vector-load alignment: 16 bytes for query rows read as
+  // float4 (d a multiple of 4), 8 for ids, 4 for dists.
+  int dev = -1;
+  DL_CUDA(cudaGetDevice(&dev));
+  if (index_device(ix) != dev) return DETLSH_ERR_INVALID_ARG;
+  const uintptr_t q_align = (v.d % 4 == 0) ? 16 : 4;
+  if (!on_device(queries, dev, q_align) || !on_device(ids, dev, 8) || !on_device(dists, dev, 4))
+    return DETLSH_ERR_INVALID_ARG;
   const bool bf16 = qp->precision == DETLSH_PREC_BF16_REFINE;
 
   // Carve the fixed scratch: status words, radius grid, projection fallback
   // list, query projections (and BF16 queries), then one slot per CTA.
   const double tb = std::ceil(qp->beta * (double)v.n);
   const int64_t tau_base = tb > (double)v.n ? v.n + 1 : (int64_t)tb;
-  const int64_t cap = (tau_base + k > v.n) ? v.n : std::min<int64_t>(v.n, tau_base + k + v.max_leaf_size);
+  // per_tree (Alg. 5 with whole trees joining S) can take up to every point
+  const int64_t cap = (tau_base + k > v.n || qp->per_tree)
+                          ? v.n
+                          : std::min<int64_t>(v.n, tau_base + k + v.max_leaf_size);
   const uint32_t fb_cap = 4096;
   const int64_t o_status = 0, o_T = 256, o_fb = o_T + 1024;
   const int64_t o_qp = up256(o_fb + 8 * (int64_t)fb_cap);
@@ -121,6 +138,11 @@ extern "C" int detlsh_query_noalloc(const detlsh_index *ix, const float *queries
   pa.fb_cap = fb_cap;
   pa.err = err;
   DL_TRY(project_rows(queries, v.d, nullptr, m, v.d, A, v.LK, 0, pa, st));
+  // a query holding NaN/Inf stops the call here, before the query kernel
+  int h = 0;
+  DL_CUDA(cudaMemcpyAsync(&h, err, sizeof h, cudaMemcpyDeviceToHost, st));
+  DL_CUDA(cudaStreamSynchronize(st));
+  if (h) return h;
   const __nv_bfloat16 *Qh = nullptr;
   if (bf16) {
     __nv_bfloat16 *qh = reinterpret_cast<__nv_bfloat16 *>(base + o_qh);
@@ -132,6 +154,7 @@ extern "C" int detlsh_query_noalloc(const detlsh_index *ix, const float *queries
   qa.lg_eps2 = (float)std::log2((double)Th[127]);  // T(0) = eps^2 seeds the level estimate
   qa.inv_2lg_c = (float)(1.0 / (2.0 * std::log2(qp->c)));
   qa.precision = qp->precision; qa.rerank_mult = qp->rerank_mult;
+  qa.per_tree = qp->per_tree;
   qa.ids = ids; qa.dists = dists;
   qa.cand_cap = cap;
   qa.slot_bytes = slot;
@@ -142,7 +165,6 @@ extern "C" int detlsh_query_noalloc(const detlsh_index *ix, const float *queries
   qa.stats = stats;
   qa.epoch_counter = reinterpret_cast<unsigned long long *>(base + o_status + 128);  // cleared above
   DL_TRY(run_queries(v, qa, st));
-  int h = 0;
   DL_CUDA(cudaMemcpyAsync(&h, err, sizeof h, cudaMemcpyDeviceToHost, st));
   DL_CUDA(cudaStreamSynchronize(st));
   return h;

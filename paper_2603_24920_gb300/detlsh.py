@@ -207,7 +207,7 @@ def detlsh_query_ex(h, queries, k, beta=0.1, c=1.5, precision=PREC_FP32, rerank_
 
 
 def detlsh_query_noalloc(h, queries, k, beta=0.1, c=1.5, precision=PREC_FP32, rerank_mult=4,
-                         stream=None, ids=None, dists=None):
+                         stream=None, ids=None, dists=None, per_tree=False):
     """Queries answered with the library's fixed scratch array: the call
     allocates no device memory (for callers that cannot allocate while
     serving).  queries, ids and dists must be CUDA tensors; ids/dists are
@@ -216,6 +216,7 @@ def detlsh_query_noalloc(h, queries, k, beta=0.1, c=1.5, precision=PREC_FP32, re
     m = queries.shape[0]
     qp = detlsh_default_query_params()
     qp.beta, qp.c, qp.precision, qp.rerank_mult = beta, c, precision, rerank_mult
+    qp.per_tree = int(per_tree)
     if ids is None:
         ids = torch.empty((m, k), dtype=torch.int64, device=queries.device)
         dists = torch.empty((m, k), dtype=torch.float32, device=queries.device)

@@ -29,12 +29,15 @@ def index():
     D.detlsh_free(h)
 
 
+@pytest.mark.parametrize("per_tree", [False, True])
 @pytest.mark.parametrize("precision", [D.PREC_FP32, D.PREC_BF16_REFINE])
-def test_noalloc_matches_query_ex_on_two_calls_in_a_row(index, precision):
+def test_noalloc_matches_query_ex_on_two_calls_in_a_row(index, precision, per_tree):
     h, Qd = index
-    ref_ids, ref_d = D.detlsh_query_ex(h, Qd, 10, beta=0.05, precision=precision)
+    ref_ids, ref_d = D.detlsh_query_ex(h, Qd, 10, beta=0.05, precision=precision,
+                                       per_tree=per_tree)
     for _ in range(2):
-        ids, dists = D.detlsh_query_noalloc(h, Qd, 10, beta=0.05, precision=precision)
+        ids, dists = D.detlsh_query_noalloc(h, Qd, 10, beta=0.05, precision=precision,
+                                            per_tree=per_tree)
         torch.cuda.synchronize()
         assert torch.equal(ids.cpu(), ref_ids.cpu())
         np.testing.assert_allclose(dists.cpu().numpy(), ref_d.cpu().numpy(), rtol=1e-5, atol=1e-6)
@@ -51,6 +54,40 @@ def test_noalloc_rejects_oversized_batches_and_host_buffers(index):
                                dists=np.zeros((Qd.shape[0], 10), np.float32))
     assert e.value.status == -1
     # a fitting call afterwards still matches
+    ref_ids, _ = D.detlsh_query_ex(h, Qd, 10, beta=0.05)
+    ids, _ = D.detlsh_query_noalloc(h, Qd, 10, beta=0.05)
+    assert torch.equal(ids.cpu(), ref_ids.cpu())
+
+
+def test_noalloc_rejects_misaligned_buffers_before_any_launch(index):
+    # The caller's buffers reach the kernels without a staging copy, so a
+    # query block that starts 4 bytes past a 16-byte boundary (d = 64, read
+    # as float4) and ids off an 8-byte boundary are refused on the host.
+    h, Qd = index
+    m, d = Qd.shape
+    buf = torch.zeros(m * d + 4, dtype=torch.float32, device="cuda")
+    shifted = buf[1:1 + m * d].view(m, d)
+    shifted.copy_(Qd)
+    assert shifted.data_ptr() % 16 == 4
+    with pytest.raises(D.DetlshError) as e:
+        D.detlsh_query_noalloc(h, shifted, 10, beta=0.05)
+    assert e.value.status == -1
+    raw = torch.zeros(m * 10 * 8 + 8, dtype=torch.uint8, device="cuda")
+    ids_bad = raw[4:4 + m * 10 * 8]
+    dists = torch.zeros((m, 10), dtype=torch.float32, device="cuda")
+    assert ids_bad.data_ptr() % 8 == 4
+    with pytest.raises(D.DetlshError) as e:
+        D.detlsh_query_noalloc(h, Qd, 10, beta=0.05, ids=ids_bad, dists=dists)
+    assert e.value.status == -1
+
+
+def test_noalloc_stops_on_a_nonfinite_query(index):
+    h, Qd = index
+    bad = Qd.clone()
+    bad[3, 5] = float("nan")
+    with pytest.raises(D.DetlshError) as e:
+        D.detlsh_query_noalloc(h, bad, 10, beta=0.05)
+    assert e.value.status == -2
     ref_ids, _ = D.detlsh_query_ex(h, Qd, 10, beta=0.05)
     ids, _ = D.detlsh_query_noalloc(h, Qd, 10, beta=0.05)
     assert torch.equal(ids.cpu(), ref_ids.cpu())
