@@ -142,23 +142,33 @@ def measured_peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-def profiled_traffic(kernel_src, summary):
-    """DRAM bytes per launch from a committed ncu summary, or None when the
-    kernel's source has changed since that capture (hash recorded in it)."""
+def profiled_counters(kernel_src, summary):
+    """Counters of one launch from a committed ncu summary (DRAM bytes, issue
+    utilisation, duration), or None when the kernel's source has changed since
+    that capture (its hash is recorded in the summary)."""
     import hashlib
     path = os.path.join(ROOT, "profiles", summary)
     if not os.path.exists(path):
         return None
-    sha = want = None
+    out = {}
     for line in open(path):
         if line.startswith("source sha256:"):
-            sha = line.split(":", 1)[1].split()[0]
+            out["sha"] = line.split(":", 1)[1].split()[0]
         elif line.startswith("dram bytes per launch:"):
-            want = float(line.split(":", 1)[1])
+            out["dram_bytes"] = float(line.split(":", 1)[1])
+        elif line.startswith("smsp__issue_active.avg.pct_of_peak_sustained_active"):
+            out["issue_pct"] = float(line.split("=", 1)[1].split()[0])
+        elif line.startswith("sm__pipe_tensor_cycles_active.avg.pct_of_peak_sustained_active"):
+            out["tensor_pct"] = float(line.split("=", 1)[1].split()[0])
+        elif line.startswith("gpu__time_duration.sum"):
+            v, unit = line.split("=", 1)[1].split()[:2]
+            out["ncu_ms"] = float(v) * {"ms": 1.0, "us": 1e-3, "s": 1e3}.get(unit, 1.0)
     src = os.path.join(ROOT, "paper_2603_24920_gb300", "csrc", kernel_src)
-    if sha is None or want is None or not os.path.exists(src):
+    if "sha" not in out or "dram_bytes" not in out or not os.path.exists(src):
         return None
-    return want if hashlib.sha256(open(src, "rb").read()).hexdigest() == sha else None
+    if hashlib.sha256(open(src, "rb").read()).hexdigest() != out["sha"]:
+        return None
+    return out
 
 
 def recall_at(ids, gt, k):
@@ -327,16 +337,43 @@ def run_gb300(args):
     build_mpts = world * n / (tmax[0] / 1e3) / 1e6
     launches = sum(r[1].build_launches + r[2].query_launches + r[3].query_launches for r in recs)
 
-    # dominant kernel: the persistent query kernel (BF16+refine call)
+    # dominant kernel: the persistent query kernel (BF16+refine call).
+    # Algorithmic bytes per query (HBM gathers of the verification step):
+    # |S| candidate rows in BF16 with their norms, |S| * (2d + 4), plus the
+    # FP32 re-rank pool, min(4k, |S|) * 4d.  The box data the range query
+    # scans (hulls and leaf boxes, ~7 MB) stays in L2 and is not counted.
     tb, tqb = recs[-1][1], recs[-1][2]
     kern_ms = mean([r[2].query_kernel_ms for r in recs])
     R = min(4 * k, 4096)
-    alg_bytes = (32.0 * (tqb.query_blocks + tqb.query_leaves)
-                 + tqb.query_points_visited * (4.0 + 4.0 * 4)
-                 + tqb.query_candidates * (2.0 * d + 4.0)
-                 + tqb.query_count * (R * 4.0 * d + 2.0 * d))
+    s_mean = tqb.query_candidates / max(tqb.query_count, 1)
+    alg_bytes = tqb.query_count * (s_mean * (2.0 * d + 4.0) + min(R, s_mean) * 4.0 * d)
     peaks, src = measured_peaks()
     achieved = alg_bytes / (kern_ms / 1e3) / 1e9
+    qprof = profiled_counters("query.cu", "k_query_sift1m.md")
+    roof_q = {"kernel": "k_query (BF16+refine)", "bound": "hbm", "achieved": achieved,
+              "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
+              "peak_source": src + " (HBM copy)",
+              "algorithmic_bytes_per_launch": alg_bytes,
+              "bytes_per_query": "|S|*(2d+4) + min(4k,|S|)*4d",
+              "mean_S": s_mean, "launch_ms": kern_ms,
+              "traffic": qprof["dram_bytes"] if qprof else None,
+              "traffic_source": "profiles/k_query_sift1m.md (ncu, same kernel source)"}
+    if qprof:
+        roof_q["dram_frac"] = qprof["dram_bytes"] / (kern_ms / 1e3) / 1e9 / peaks["hbm_gbs"]
+        roof_q["issue_frac"] = qprof["issue_pct"] / 100.0
+    # the build's dominant kernel: projection + region codes of all n points
+    enc_ms = mean([r[1].encode_ms for r in recs])
+    eprof = profiled_counters("project.cu", "k_encode_sift1m.md")
+    enc_bytes = n * (4.0 * d + 16.0 * 4)  # read each row once, write 16 B of codes per tree
+    roof_e = {"kernel": "encode stage (projection + codes)", "bound": "hbm",
+              "achieved": enc_bytes / (enc_ms / 1e3) / 1e9, "peak": peaks["hbm_gbs"],
+              "unit": "GB/s", "peak_source": src + " (HBM copy)",
+              "algorithmic_bytes_per_launch": enc_bytes, "bytes_per_point": "4d + 16L",
+              "launch_ms": enc_ms,
+              "traffic": eprof["dram_bytes"] if eprof else None,
+              "traffic_source": "profiles/k_encode_sift1m.md (ncu, same kernel source)",
+              "tensor_pipe_frac": (eprof.get("tensor_pct", 0.0) / 100.0) if eprof else None}
+    roof_e["frac"] = roof_e["achieved"] / peaks["hbm_gbs"]
     shares = {"query_kernel_ms": kern_ms,
               "query_kernel_fp32_ms": mean([r[3].query_kernel_ms for r in recs]),
               "build_ms": mean([r[1].build_ms for r in recs]),
@@ -378,13 +415,8 @@ def run_gb300(args):
         "quality": quality,
         "timings_ms": shares,
         "gpu_launches": int(launches),
-        "roofline": {"kernel": "k_query (BF16+refine)", "bound": "hbm", "achieved": achieved,
-                     "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
-                     "peak_source": src,
-                     "traffic": profiled_traffic("query.cu", "k_query_sift1m.md"),
-                     "traffic_source": "profiles/k_query_sift1m.md (ncu, same kernel source)",
-                     "algorithmic_bytes_per_launch": alg_bytes,
-                     "launch_ms": kern_ms},
+        "roofline": roof_q,
+        "roofline_build": roof_e,
         "e2e": {"value": m * world / e2e_max[0], "unit": "queries/s",
                 "h2d_bytes_per_step": int(m * d * 4), "d2h_bytes_per_step": int(m * k * 12),
                 "build_mpts_s": n * world / e2e_max[1] / 1e6,
