@@ -47,6 +47,11 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--beta", type=float, default=BETA)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-reps", type=int, default=0,
+                    help="profiler driver: build + BF16 and FP32 query calls this many times, "
+                         "nothing timed, no recall check, then exit")
+    ap.add_argument("--profile-config", default=CONFIG)
+    ap.add_argument("--profile-queries", type=int, default=0, help="first m queries (0 = all)")
     return ap.parse_args()
 
 
@@ -430,8 +435,40 @@ def run_gb300(args):
     print(json.dumps(line), flush=True)
 
 
+def run_profile(args):
+    """A plain driver for kernel profilers: the calls the bench times (build
+    from device-resident data, one BF16+refine and one FP32 query call per
+    repetition), so that a profiler sees few launches and little memory."""
+    import torch
+    from paper_2603_24920_gb300 import detlsh as D
+    cfg = workloads.CONFIGS[args.profile_config]
+    X = workloads.generate(cfg["kind"], cfg["n"], cfg["d"], cfg["seed"], 0)
+    Q = workloads.generate(cfg["kind"], cfg["m"], cfg["d"], cfg["seed"], 1)
+    if args.profile_queries:
+        Q = Q[:args.profile_queries]
+    k = cfg["k"] if isinstance(cfg["k"], int) else max(cfg["k"])
+    Xd = torch.from_numpy(X).cuda()
+    Qd = torch.from_numpy(Q).cuda()
+    st = torch.cuda.current_stream()
+    for _ in range(args.profile_reps):
+        h = D.detlsh_build(Xd, L=4, K=16, N_r=256, seed=0, max_size=64, stream=st)
+        D.detlsh_query_ex(h, Qd, k, beta=args.beta, c=C_RATIO, precision=D.PREC_BF16_REFINE,
+                          stream=st)
+        D.detlsh_query_ex(h, Qd, k, beta=args.beta, c=C_RATIO, precision=D.PREC_FP32, stream=st)
+        torch.cuda.synchronize()
+        t = D.detlsh_get_timings(h)
+        print("build %.3f ms (sample %.3f, breakpoints %.3f, encode %.3f, trees %.3f)  "
+              "query kernel %.3f ms  |S|/q %.0f" %
+              (t.build_ms, t.sample_ms, t.breakpoints_ms, t.encode_ms, t.trees_ms,
+               t.query_kernel_ms, t.query_candidates / max(1, t.query_count)), flush=True)
+        D.detlsh_free(h)
+
+
 def main():
     args = parse()
+    if args.profile_reps:
+        run_profile(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

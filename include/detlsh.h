@@ -41,8 +41,10 @@ typedef enum {
     DETLSH_ERR_CUDA = -4,            /* a CUDA runtime call failed             */
     DETLSH_ERR_CAPACITY = -5,        /* an internal work list overflowed       */
     DETLSH_ERR_NO_DEVICE = -6,       /* no usable CUDA device                  */
-    DETLSH_ERR_SCRATCH_LIMIT = -7    /* the request does not fit the fixed
+    DETLSH_ERR_SCRATCH_LIMIT = -7,   /* the request does not fit the fixed
                                         scratch of detlsh_query_noalloc        */
+    DETLSH_ERR_TIMEOUT = -8          /* a device-side pipeline wait ran past
+                                        its limit (the kernel stopped cleanly) */
 } detlsh_status;
 
 /* Node boxes used by the range query's lower bound (Sec. IV-C). */

@@ -12,7 +12,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libdetlsh.so")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["api.cu", "project.cu", "sort.cu", "tree.cu", "query.cu", "rcann.cu", "noalloc.cu"]
+SOURCES = ["api.cu", "project.cu", "sort.cu", "tree.cu", "query.cu", "rcann.cu", "noalloc.cu", "encode_tc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-diag-suppress", "128"]

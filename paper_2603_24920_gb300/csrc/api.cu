@@ -958,6 +958,7 @@ const char *detlsh_status_string(int s) {
     case DETLSH_ERR_NO_DEVICE: return "no CUDA device";
     case DETLSH_ERR_SCRATCH_LIMIT:
       return "request does not fit the fixed 32 MiB scratch of detlsh_query_noalloc";
+    case DETLSH_ERR_TIMEOUT: return "a device-side wait ran past its limit";
   }
   return "unknown status";
 }

@@ -28,6 +28,12 @@ struct ProjArgs {
   int *err = nullptr;                      // device status word
 };
 
+// Tensor-core encoder of all n points (encode_tc.cu), mode 2 of project_rows
+// for contiguous rows with d a multiple of 4 up to 128; *used = 0 when it
+// does not apply (the CUDA-core encoder then runs).
+int launch_encode_tc(const float *X, int64_t nrows, int d, const float *A, int LK, int W,
+                     ProjArgs o, cudaStream_t st, int *used);
+
 // rows == nullptr: rows 0..nrows-1 of X; else the listed row ids.
 int project_rows(const float *X, int64_t ldx, const uint32_t *rows, int64_t nrows, int d,
                  const float *A, int LK, int mode, ProjArgs o, cudaStream_t st);

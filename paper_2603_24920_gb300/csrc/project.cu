@@ -530,7 +530,7 @@ k_project_exact(const float *__restrict__ X, int64_t ldx, const uint32_t *__rest
   for (int64_t i0 = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * PER_WARP; i0 < total;
        i0 += warps * PER_WARP) {
     const int64_t i = i0 + lane / EX_GL;
-    const bool valid = i < total;
+    bool valid = i < total;
     int64_t rr = 0;
     int oc = 0;
     uint32_t hint = 0;
@@ -538,8 +538,9 @@ k_project_exact(const float *__restrict__ X, int64_t ldx, const uint32_t *__rest
       if (all) { rr = i / LK; oc = (int)(i % LK); }
       else {
         const uint2 f = o.fb_list[i];
-        rr = f.x;
-        oc = MODE == 2 ? (int)(f.y >> 8) : (int)f.y;
+        if (f.x == 0xffffffffu) valid = false;  // padding of a list reservation
+        rr = valid ? f.x : 0;
+        oc = valid ? (MODE == 2 ? (int)(f.y >> 8) : (int)f.y) : 0;
         hint = MODE == 2 ? (f.y & 255u) : 0u;
       }
     }
@@ -593,7 +594,13 @@ static int project_impl(const float *X, int64_t ldx, const uint32_t *rows, int64
   if (nrows <= 0) return DETLSH_OK;
   DL_CUDA(cudaMemsetAsync(o.fb_count, 0, sizeof(uint32_t), st));
   const int W = (MODE == 2) ? (EN_COLS / o.K) * o.K : PJ_COLS;
+  int tc = 0;
   if constexpr (MODE == 2) {
+    if (!rows && ldx == d) DL_TRY(launch_encode_tc(X, nrows, d, A, LK, W, o, st, &tc));
+  }
+  if (tc) {
+    // the tensor-core encoder ran
+  } else if constexpr (MODE == 2) {
     // gamma >= u / (1 - EN_CH u), u = 2^-24, rounded up
     o.gamma = std::nextafter((float)(0x1p-24 * (1.0 + 2.0 * EN_CH * 0x1p-24) * (1.0 + 1e-9)), INFINITY);
     const size_t dyn = encode_smem_bytes();
@@ -606,12 +613,14 @@ static int project_impl(const float *X, int64_t ldx, const uint32_t *rows, int64
     // persistent: one wave of CTAs, split over the column tiles
     const int64_t gx = std::min<int64_t>(tiles, std::max<int64_t>((int64_t)sms * std::max(per, 1) / ny, 1));
     k_encode<<<dim3((unsigned)gx, (unsigned)ny), EN_THREADS, dyn, st>>>(X, ldx, nrows, d, A, LK, W, o);
+    dl_count_launch();
+    DL_CUDA(cudaGetLastError());
   } else {
     dim3 grid((unsigned)ceil_div(nrows, PJ_ROWS), (unsigned)ceil_div(LK, W));
     k_project<MODE><<<grid, PJ_THREADS, 0, st>>>(X, ldx, rows, nrows, d, A, LK, W, o);
+    dl_count_launch();
+    DL_CUDA(cudaGetLastError());
   }
-  dl_count_launch();
-  DL_CUDA(cudaGetLastError());
   k_project_exact<MODE><<<2048, 256, 0, st>>>(X, ldx, rows, nrows, d, A, LK, o);
   dl_count_launch();
   DL_CUDA(cudaGetLastError());

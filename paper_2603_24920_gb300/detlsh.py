@@ -14,7 +14,8 @@ LIB_PATH = os.path.join(HERE, "libdetlsh.so")
 
 DETLSH_OK = 0
 STATUS = {0: "OK", -1: "INVALID_ARG", -2: "NONFINITE_INPUT", -3: "OOM", -4: "CUDA",
-          -5: "CAPACITY", -6: "NO_DEVICE", -7: "SCRATCH_LIMIT"}
+          -5: "CAPACITY", -6: "NO_DEVICE", -7: "SCRATCH_LIMIT",
+          -8: "TIMEOUT"}
 BOX_PREFIX, BOX_TIGHT = 0, 1
 PREC_FP32, PREC_BF16_REFINE = 0, 1
 RMIN_MAGIC, RMIN_FIXED, RMIN_CONTINUOUS = 0, 1, 2
