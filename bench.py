@@ -368,15 +368,15 @@ def run_gb300(args):
         roof_q["issue_frac"] = qprof["issue_pct"] / 100.0
     # the build's dominant kernel: projection + region codes of all n points
     enc_ms = mean([r[1].encode_ms for r in recs])
-    eprof = profiled_counters("project.cu", "k_encode_sift1m.md")
+    eprof = profiled_counters("encode_tc.cu", "k_encode_tc_sift1m.md")
     enc_bytes = n * (4.0 * d + 16.0 * 4)  # read each row once, write 16 B of codes per tree
-    roof_e = {"kernel": "encode stage (projection + codes)", "bound": "hbm",
+    roof_e = {"kernel": "encode stage (k_encode_tc: tensor-core projection + codes)", "bound": "hbm",
               "achieved": enc_bytes / (enc_ms / 1e3) / 1e9, "peak": peaks["hbm_gbs"],
               "unit": "GB/s", "peak_source": src + " (HBM copy)",
               "algorithmic_bytes_per_launch": enc_bytes, "bytes_per_point": "4d + 16L",
               "launch_ms": enc_ms,
               "traffic": eprof["dram_bytes"] if eprof else None,
-              "traffic_source": "profiles/k_encode_sift1m.md (ncu, same kernel source)",
+              "traffic_source": "profiles/k_encode_tc_sift1m.md (ncu, same kernel source)",
               "tensor_pipe_frac": (eprof.get("tensor_pct", 0.0) / 100.0) if eprof else None}
     roof_e["frac"] = roof_e["achieved"] / peaks["hbm_gbs"]
     shares = {"query_kernel_ms": kern_ms,
