@@ -380,6 +380,10 @@ def run_gb300(args):
               "tensor_pipe_frac": (eprof.get("tensor_pct", 0.0) / 100.0) if eprof else None}
     roof_e["frac"] = roof_e["achieved"] / peaks["hbm_gbs"]
     shares = {"query_kernel_ms": kern_ms,
+              "bf16_reranked_rows_per_query": tqb.query_reranked / max(tqb.query_count, 1),
+              "leaves_expanded_per_query": tqb.query_leaves / max(tqb.query_count, 1),
+              "hulls_tested_per_query": tqb.query_blocks / max(tqb.query_count, 1),
+              "points_visited_per_query": tqb.query_points_visited / max(tqb.query_count, 1),
               "query_kernel_fp32_ms": mean([r[3].query_kernel_ms for r in recs]),
               "build_ms": mean([r[1].build_ms for r in recs]),
               "build_stages_ms": {"sample": tb.sample_ms, "breakpoints": tb.breakpoints_ms,

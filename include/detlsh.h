@@ -43,8 +43,13 @@ typedef enum {
     DETLSH_ERR_NO_DEVICE = -6,       /* no usable CUDA device                  */
     DETLSH_ERR_SCRATCH_LIMIT = -7,   /* the request does not fit the fixed
                                         scratch of detlsh_query_noalloc        */
-    DETLSH_ERR_TIMEOUT = -8          /* a device-side pipeline wait ran past
+    DETLSH_ERR_TIMEOUT = -8,         /* a device-side pipeline wait ran past
                                         its limit (the kernel stopped cleanly) */
+    DETLSH_ERR_IO = -9,              /* an index file could not be opened,
+                                        read or written                        */
+    DETLSH_ERR_FORMAT = -10          /* not an index file of this format:
+                                        magic, version, byte order, sizes or
+                                        checksum                               */
 } detlsh_status;
 
 /* Node boxes used by the range query's lower bound (Sec. IV-C). */
@@ -59,8 +64,8 @@ enum { DETLSH_ENC_DYNAMIC = 0, /* sampled equal-frequency breakpoints (paper) */
 
 /* Precision of the exact-distance verification step (Alg. 5, top-k). */
 enum { DETLSH_PREC_FP32 = 0,        /* FP32 distances over every candidate  */
-       DETLSH_PREC_BF16_REFINE = 1  /* BF16 scores, FP32 re-rank of the top
-                                       rerank_mult * k                       */ };
+       DETLSH_PREC_BF16_REFINE = 1  /* BF16 tensor-core scores, then an FP32
+                                       re-rank (see rerank_mult)             */ };
 
 /* How Alg. 5 chooses its starting radius r_min (Sec. V-B1). */
 enum { DETLSH_RMIN_MAGIC = 0, /* the "magic" r_min: the smallest radius of the
@@ -100,8 +105,11 @@ typedef struct {
                                candidates (Alg. 5; default 0.1, Sec. VI-A)         */
     double c;               /* approximation ratio, 1.1 <= c <= 16 (default 1.5)   */
     int32_t precision;      /* DETLSH_PREC_FP32 (default) / DETLSH_PREC_BF16_REFINE */
-    int32_t rerank_mult;    /* BF16 path: FP32 re-rank of the top rerank_mult*k
-                               (default 4)                                         */
+    int32_t rerank_mult;    /* BF16 path: 0 (default) = re-rank in FP32 the
+                               certified pool (every candidate whose score interval
+                               can reach the k best), so the answer equals the
+                               FP32 path's exactly; r > 0 = re-rank the r*k best
+                               BF16 scores (an approximation)                      */
     int32_t rmin_policy;    /* DETLSH_RMIN_MAGIC (default) / DETLSH_RMIN_FIXED     */
     double r_min;           /* DETLSH_RMIN_FIXED: the starting radius (> 0); the
                                FP32 path only (precision must be FP32)             */
@@ -193,6 +201,39 @@ int detlsh_query_noalloc(const detlsh_index *ix, const float *queries, int64_t m
                          const detlsh_query_params *qp, void *stream, int64_t *ids,
                          float *dists);
 
+/*
+ * Index files (the index of Sec. III-B, Alg. 2, with the encoding of Sec.
+ * III-A, kept between processes).  The paper builds its index in memory and
+ * reports its size and build cost (Sec. VI, encoding and indexing); a file
+ * lets a serving process answer queries without rebuilding.
+ *
+ * detlsh_save writes everything the queries and accessors read: the build
+ * parameters, eps^2 (Eq. 2), the FP32 data, A (Eq. 1), the breakpoints, the
+ * sample ids, the codes, each tree's perm, leaf_begin, leaf boxes and prefix
+ * lengths, leaf_of, the leaf-run hulls, and the BF16 copy and projections when
+ * the index has them.  Layout: a fixed 672-byte header (magic "DETLSHIX",
+ * format version 1, byte-order mark, parameters, per-tree leaf counts and
+ * offsets), the arrays in a fixed order, each behind a 16-byte tag and byte
+ * count, then a 64-bit checksum of everything before it.  Arrays are in the
+ * host's byte order.  The file is written as path + ".tmp" and renamed, so a
+ * failed save leaves no partial file under path.  stream orders the
+ * device-to-host copies; the call returns when the file is closed.
+ * Errors: INVALID_ARG (null index or path), IO, CUDA, OOM (pinned staging).
+ *
+ * detlsh_load reads such a file into a new index on the current device (the
+ * caller frees it with detlsh_free); queries on it return what they return on
+ * the saved index.  The header is checked before any device call: a missing
+ * or unreadable file gives IO, a file that is not of this format (magic,
+ * version, byte order, parameters out of range, inconsistent leaf offsets)
+ * gives FORMAT; so do section sizes that disagree with the header, a short
+ * file, trailing bytes and a checksum mismatch.  The checksum detects
+ * accidental damage, not deliberate tampering: load only files you trust.
+ * On error *out is NULL and nothing stays allocated.
+ * Errors: INVALID_ARG (null path or out), IO, FORMAT, NO_DEVICE, OOM, CUDA.
+ */
+int detlsh_save(const detlsh_index *ix, const char *path, void *stream);
+int detlsh_load(const char *path, void *stream, detlsh_index **out);
+
 /* Release the index and its device memory.  NULL is accepted. */
 int detlsh_free(detlsh_index *ix);
 
@@ -255,6 +296,7 @@ typedef struct {
     int64_t query_leaves;      /* leaves whose bound was computed (expanded)    */
     int64_t query_blocks;      /* leaf-run hulls whose bound was computed       */
     int64_t query_points_visited; /* leaf points visited by the union counts   */
+    int64_t query_reranked;    /* rows the BF16 path re-ranked in FP32          */
 } detlsh_timings;
 int detlsh_get_timings(const detlsh_index *ix, detlsh_timings *t);
 

@@ -38,7 +38,7 @@ struct detlsh_index {
   // device arrays
   float *X = nullptr;
   __nv_bfloat16 *Xh = nullptr;
-  float *Xn = nullptr;  // squared norms of the BF16 rows (FP32)
+  float2 *Xn = nullptr;  // per row {||bf16(x)||^2, upper bound of ||x - bf16(x)||}
   float *A = nullptr, *B = nullptr, *P = nullptr;
   uint8_t *codes = nullptr;
   uint32_t *sample = nullptr;
@@ -67,7 +67,7 @@ struct detlsh_index {
     int32_t k_max = 0;
     int slots = 0;
     int64_t cap = 0, tau_base = 0;
-    int64_t off[13] = {0};
+    int64_t off[dl::SLOT_ARRAYS + 1] = {0};
   } plan;
   QBuf aQp, aQh, afb, aT, astat, ascratch;
 };
@@ -296,18 +296,27 @@ __global__ void k_iota(uint32_t *p, int64_t n) {
     p[i] = (uint32_t)i;
 }
 
-// BF16 copy of the data, one warp per row, with the FP32 squared norm of each
-// rounded row (the norm term of the tensor-core scores).
-// BF16 copy of the rows and ||bf16(x)||^2 per row, a warp per row; rows with
-// d a multiple of 4 go by 16-byte loads and 8-byte stores, two rows at a time.
-__global__ void k_rows_to_bf16(const float *s, __nv_bfloat16 *h, float *nrm, int64_t n, int d) {
+// BF16 copy of the rows, a warp per row, with two FP32 terms per row for the
+// certified BF16 scores: ||bf16(x)||^2 (round to nearest, the norm term of
+// the tensor-core scores) and an upper bound of ||x - bf16(x)|| (each
+// difference is exact, the squares and their sum round up, then a rounded-up
+// square root).  Rows with d a multiple of 4 go by 16-byte loads and 8-byte
+// stores, two rows at a time.
+__device__ __forceinline__ void bf16_row_terms(float x, __nv_bfloat16 b, float &nsq, float &res) {
+  const float f = __bfloat162float(b);
+  nsq = __fmaf_rn(f, f, nsq);
+  const float e = x - f;  // exact: bf16(x) is within a factor 2 of x
+  res = __fmaf_ru(e, e, res);
+}
+
+__global__ void k_rows_to_bf16(const float *s, __nv_bfloat16 *h, float2 *nrm, int64_t n, int d) {
   const int lane = threadIdx.x & 31;
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
   const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if ((d & 3) == 0) {
     const int d4 = d >> 2;
     for (int64_t r0 = 2 * w0; r0 < n; r0 += 2 * warps) {
-      float acc[2] = {0.0f, 0.0f};
+      float acc[2] = {0.0f, 0.0f}, res[2] = {0.0f, 0.0f};
       for (int j = lane; j < d4; j += 32) {
         float4 v[2];
 #pragma unroll
@@ -322,31 +331,36 @@ __global__ void k_rows_to_bf16(const float *s, __nv_bfloat16 *h, float *nrm, int
           pk.x = *reinterpret_cast<const uint32_t *>(&a);
           pk.y = *reinterpret_cast<const uint32_t *>(&b);
           reinterpret_cast<uint2 *>(h + (r0 + u) * d)[j] = pk;
-          const float2 fa = __bfloat1622float2(a), fb = __bfloat1622float2(b);
-          acc[u] = __fmaf_rn(fa.x, fa.x, acc[u]);
-          acc[u] = __fmaf_rn(fa.y, fa.y, acc[u]);
-          acc[u] = __fmaf_rn(fb.x, fb.x, acc[u]);
-          acc[u] = __fmaf_rn(fb.y, fb.y, acc[u]);
+          bf16_row_terms(v[u].x, a.x, acc[u], res[u]);
+          bf16_row_terms(v[u].y, a.y, acc[u], res[u]);
+          bf16_row_terms(v[u].z, b.x, acc[u], res[u]);
+          bf16_row_terms(v[u].w, b.y, acc[u], res[u]);
         }
       }
 #pragma unroll
       for (int u = 0; u < 2; ++u) {
-        for (int o = 16; o > 0; o >>= 1) acc[u] = __fadd_rn(acc[u], __shfl_xor_sync(0xffffffffu, acc[u], o));
-        if (lane == 0 && r0 + u < n) nrm[r0 + u] = acc[u];
+        for (int o = 16; o > 0; o >>= 1) {
+          acc[u] = __fadd_rn(acc[u], __shfl_xor_sync(0xffffffffu, acc[u], o));
+          res[u] = __fadd_ru(res[u], __shfl_xor_sync(0xffffffffu, res[u], o));
+        }
+        if (lane == 0 && r0 + u < n) nrm[r0 + u] = make_float2(acc[u], __fsqrt_ru(res[u]));
       }
     }
     return;
   }
   for (int64_t r = w0; r < n; r += warps) {
-    float acc = 0.0f;
+    float acc = 0.0f, res = 0.0f;
     for (int j = lane; j < d; j += 32) {
-      const __nv_bfloat16 v = __float2bfloat16_rn(s[r * d + j]);
+      const float x = s[r * d + j];
+      const __nv_bfloat16 v = __float2bfloat16_rn(x);
       h[r * d + j] = v;
-      const float f = __bfloat162float(v);
-      acc = __fmaf_rn(f, f, acc);
+      bf16_row_terms(x, v, acc, res);
     }
-    for (int o = 16; o > 0; o >>= 1) acc = __fadd_rn(acc, __shfl_xor_sync(0xffffffffu, acc, o));
-    if (lane == 0) nrm[r] = acc;
+    for (int o = 16; o > 0; o >>= 1) {
+      acc = __fadd_rn(acc, __shfl_xor_sync(0xffffffffu, acc, o));
+      res = __fadd_ru(res, __shfl_xor_sync(0xffffffffu, res, o));
+    }
+    if (lane == 0) nrm[r] = make_float2(acc, __fsqrt_ru(res));
   }
 }
 
@@ -712,7 +726,7 @@ int validate_query(const detlsh_index *ix, int64_t m, int32_t k_max, const detls
   if (qp->precision != DETLSH_PREC_FP32 && qp->precision != DETLSH_PREC_BF16_REFINE)
     return DETLSH_ERR_INVALID_ARG;
   if (qp->precision == DETLSH_PREC_BF16_REFINE &&
-      (!ix->Xh || (ix->d % 8) != 0 || qp->rerank_mult < 1))
+      (!ix->Xh || (ix->d % 8) != 0 || qp->rerank_mult < 0))
     return DETLSH_ERR_INVALID_ARG;
   if (qp->rmin_policy != DETLSH_RMIN_MAGIC && qp->rmin_policy != DETLSH_RMIN_FIXED &&
       qp->rmin_policy != DETLSH_RMIN_CONTINUOUS)
@@ -823,7 +837,7 @@ int query_impl(detlsh_index *ix, const float *queries, int64_t m, const int32_t 
   }
   qa.cand_cap = cap;
   query_slot_offsets(v, cap, qa.off);
-  qa.slot_bytes = qa.off[12];  // total bytes of one slot
+  qa.slot_bytes = qa.off[SLOT_ARRAYS];  // total bytes of one slot
   int slots = query_slots(v);
   slots = (int)std::min<int64_t>(slots, std::max<int64_t>(m, 1));
   // keep the scratch within a quarter of the free device memory
@@ -857,7 +871,7 @@ int query_impl(detlsh_index *ix, const float *queries, int64_t m, const int32_t 
   DL_CUDA(cudaEventRecord(ix->ev[7], st));
   e = check_err(err, st);
   if (e) return e;
-  unsigned long long hs[4];
+  unsigned long long hs[5];
   DL_CUDA(cudaMemcpy(hs, stats, sizeof hs, cudaMemcpyDeviceToHost));
   ix->timings.query_project_ms = ev_ms(ix->ev[5], ix->ev[6]);
   ix->timings.query_kernel_ms = ev_ms(ix->ev[6], ix->ev[7]);
@@ -868,6 +882,7 @@ int query_impl(detlsh_index *ix, const float *queries, int64_t m, const int32_t 
   ix->timings.query_leaves = (int64_t)hs[1];
   ix->timings.query_blocks = (int64_t)hs[2];
   ix->timings.query_points_visited = (int64_t)hs[3];
+  ix->timings.query_reranked = (int64_t)hs[4];
   if (ids) DL_TRY(copy_out(ids, qa.ids, sizeof(int64_t) * (size_t)m * k_max, st));
   if (dists) DL_TRY(copy_out(dists, qa.dists, sizeof(float) * (size_t)m * k_max, st));
   if (S) {
@@ -877,6 +892,287 @@ int query_impl(detlsh_index *ix, const float *queries, int64_t m, const int32_t 
     DL_CUDA(cudaMemcpyAsync(istar, qa.istar, sizeof(int32_t) * (size_t)m, cudaMemcpyDeviceToHost, st));
   }
   DL_CUDA(cudaStreamSynchronize(st));
+  return DETLSH_OK;
+}
+
+// ---- index files ------------------------------------------------------------
+// A file holds everything the queries and the accessors read, so a process can
+// serve an index without rebuilding it: a fixed header (magic, format version,
+// byte-order mark, build parameters, eps^2, per-tree leaf counts and offsets),
+// then the arrays in a fixed order, each behind its tag and byte count, then a
+// 64-bit checksum of all of it.  Arrays are written in the host's byte order;
+// the byte-order mark rejects a file from a machine of the other order.
+constexpr char kFileMagic[8] = {'D', 'E', 'T', 'L', 'S', 'H', 'I', 'X'};
+constexpr uint32_t kFileVersion = 1;
+constexpr uint32_t kByteOrderMark = 0x01020304u;
+constexpr size_t kFileChunk = (size_t)64 << 20;  // staging chunk (a multiple of 8)
+
+struct FileHeader {
+  char magic[8];
+  uint32_t version, bom, header_bytes, nsections;
+  int64_t n;
+  int32_t d, L, K, N_r, bbits, M, box_mode, encoding, tree_group, has_bf16, has_proj, reserved;
+  uint64_t seed;
+  double frac, eps2;
+  int64_t m_sample, max_leaf, max_leaves, fb_total;
+  int64_t nleaves[16], leaf_off[17], blk_off[17], sblk_off[17];
+};
+static_assert(sizeof(FileHeader) == 672, "the header size include/detlsh.h documents");
+
+struct SectionHead {
+  uint32_t tag, reserved;
+  uint64_t bytes;
+};
+
+// Order-dependent 64-bit checksum over 8-byte words (a multiply-rotate mix);
+// a block's last partial word is zero-padded.  Callers feed blocks whose
+// lengths are multiples of 8 except the last block of an array.
+struct Checksum {
+  uint64_t h = 0x9e3779b97f4a7c15ull;
+  void word(uint64_t w) {
+    h ^= w * 0xff51afd7ed558ccdull;
+    h = (h << 29) | (h >> 35);
+    h *= 0xc4ceb9fe1a85ec53ull;
+  }
+  void bytes(const void *p, size_t nb) {
+    const uint8_t *b = static_cast<const uint8_t *>(p);
+    size_t i = 0;
+    for (; i + 8 <= nb; i += 8) {
+      uint64_t w;
+      memcpy(&w, b + i, 8);
+      word(w);
+    }
+    if (i < nb) {
+      uint64_t w = 0;
+      memcpy(&w, b + i, nb - i);
+      word(w);
+    }
+  }
+};
+
+struct Section {
+  uint32_t tag;
+  void *dev;
+  uint64_t bytes;
+};
+
+// The arrays of an index file, in file order.  Sizes follow from the header
+// alone, so the loader knows every section's length before reading it.
+std::vector<Section> file_sections(const detlsh_index *ix) {
+  const int64_t n = ix->n, L = ix->L, LK = ix->LK, d = ix->d;
+  const int64_t tl = ix->leaf_off[ix->L], tb = ix->blk_off[ix->L], ts = ix->sblk_off[ix->L];
+  std::vector<Section> s = {
+      {1, ix->X, (uint64_t)(n * d * 4)},
+      {2, ix->A, (uint64_t)(LK * d * 4)},
+      {3, ix->B, (uint64_t)(LK * (ix->N_r + 1) * 4)},
+      {4, ix->sample, (uint64_t)(ix->m_sample * 4)},
+      {5, ix->codes, (uint64_t)(L * n * CODE_STRIDE)},
+      {6, ix->perm, (uint64_t)(L * n * 4)},
+      {7, ix->leaf_of, (uint64_t)(L * n * 4)},
+      {8, ix->leaf_begin, (uint64_t)((tl + L) * 4)},
+      {9, ix->leaf_lo, (uint64_t)(tl * 16)},
+      {10, ix->leaf_hi, (uint64_t)(tl * 16)},
+      {11, ix->leaf_nb, (uint64_t)(tl * 16)},
+      {12, ix->blk_lo, (uint64_t)(tb * 16)},
+      {13, ix->blk_hi, (uint64_t)(tb * 16)},
+      {14, ix->sblk_lo, (uint64_t)(ts * 16)},
+      {15, ix->sblk_hi, (uint64_t)(ts * 16)}};
+  if (ix->Xh) {
+    s.push_back({16, ix->Xh, (uint64_t)(n * d * 2)});
+    s.push_back({17, ix->Xn, (uint64_t)(n * 8)});
+  }
+  if (ix->P) s.push_back({18, ix->P, (uint64_t)(n * LK * 4)});
+  return s;
+}
+
+// Pinned staging buffer for the host side of the copies.
+struct Staging {
+  void *p = nullptr;
+  ~Staging() {
+    if (p) cudaFreeHost(p);
+  }
+};
+
+struct File {
+  FILE *f = nullptr;
+  ~File() {
+    if (f) fclose(f);
+  }
+};
+
+// Header checks that need no device: the format, and offsets consistent with
+// the leaf counts (the loader trusts nothing else it has not checked).
+int check_header(const FileHeader &h) {
+  if (memcmp(h.magic, kFileMagic, 8) != 0 || h.version != kFileVersion ||
+      h.bom != kByteOrderMark || h.header_bytes != sizeof(FileHeader))
+    return DETLSH_ERR_FORMAT;
+  detlsh_build_params p;
+  detlsh_default_build_params(&p);
+  p.L = h.L; p.K = h.K; p.N_r = h.N_r; p.max_size = h.M; p.sample_frac = h.frac;
+  p.box_mode = h.box_mode; p.encoding = h.encoding; p.tree_group = h.tree_group;
+  if (validate_build(h.n, h.d, &p) != DETLSH_OK) return DETLSH_ERR_FORMAT;
+  if ((1 << h.bbits) != h.N_r) return DETLSH_ERR_FORMAT;
+  if (h.has_bf16 != 0 && h.has_bf16 != 1) return DETLSH_ERR_FORMAT;
+  if (h.has_proj != 0 && h.has_proj != 1) return DETLSH_ERR_FORMAT;
+  if (h.m_sample < 0 || h.m_sample > h.n || (h.encoding == DETLSH_ENC_STATIC && h.m_sample != 0))
+    return DETLSH_ERR_FORMAT;
+  if (!(h.eps2 > 0.0) || !std::isfinite(h.eps2)) return DETLSH_ERR_FORMAT;
+  int64_t tl = 0, tb = 0, ts = 0, mx = 0;
+  for (int t = 0; t < 16; ++t) {
+    const int64_t nl = t < h.L ? h.nleaves[t] : 0;
+    if (nl < 0 || nl > h.n || (t < h.L && nl < 1)) return DETLSH_ERR_FORMAT;
+    if (h.leaf_off[t] != tl || h.blk_off[t] != tb || h.sblk_off[t] != ts) return DETLSH_ERR_FORMAT;
+    const int64_t nb = ceil_div(nl, LEAF_BLOCK);
+    tl += nl;
+    tb += nb;
+    ts += ceil_div(nb, LEAF_BLOCK);
+    mx = std::max(mx, nl);
+  }
+  if (h.leaf_off[16] != tl || h.blk_off[16] != tb || h.sblk_off[16] != ts) return DETLSH_ERR_FORMAT;
+  if (h.max_leaves != mx || h.max_leaf < 1 || h.max_leaf > h.n) return DETLSH_ERR_FORMAT;
+  return DETLSH_OK;
+}
+
+int save_impl(const detlsh_index *ix, const char *path, cudaStream_t st) {
+  FileHeader h;
+  memset(&h, 0, sizeof h);
+  memcpy(h.magic, kFileMagic, 8);
+  h.version = kFileVersion;
+  h.bom = kByteOrderMark;
+  h.header_bytes = sizeof(FileHeader);
+  const std::vector<Section> secs = file_sections(ix);
+  h.nsections = (uint32_t)secs.size();
+  h.n = ix->n; h.d = ix->d; h.L = ix->L; h.K = ix->K; h.N_r = ix->N_r; h.bbits = ix->bbits;
+  h.M = ix->M; h.box_mode = ix->box_mode; h.encoding = ix->encoding; h.tree_group = ix->tree_group;
+  h.has_bf16 = ix->Xh != nullptr; h.has_proj = ix->P != nullptr;
+  h.seed = ix->seed; h.frac = ix->frac; h.eps2 = ix->eps2;
+  h.m_sample = ix->m_sample; h.max_leaf = ix->max_leaf; h.max_leaves = ix->max_leaves;
+  h.fb_total = ix->fb_total;
+  for (int t = 0; t < 16; ++t) h.nleaves[t] = ix->nleaves[t];
+  for (int t = 0; t <= 16; ++t) {
+    h.leaf_off[t] = ix->leaf_off[std::min(t, ix->L)];
+    h.blk_off[t] = ix->blk_off[t];
+    h.sblk_off[t] = ix->sblk_off[t];
+  }
+  // written to path.tmp and renamed at the end, so a failed save leaves no
+  // partial file under the name
+  const std::string tmp = std::string(path) + ".tmp";
+  File f;
+  f.f = fopen(tmp.c_str(), "wb");
+  if (!f.f) return DETLSH_ERR_IO;
+  Checksum cs;
+  bool ok = fwrite(&h, sizeof h, 1, f.f) == 1;
+  cs.bytes(&h, sizeof h);
+  Staging buf;
+  DL_CUDA(cudaMallocHost(&buf.p, kFileChunk));
+  for (const Section &s : secs) {
+    if (!ok) break;
+    const SectionHead sh{s.tag, 0u, s.bytes};
+    ok = fwrite(&sh, sizeof sh, 1, f.f) == 1;
+    cs.bytes(&sh, sizeof sh);
+    for (uint64_t o = 0; ok && o < s.bytes; o += kFileChunk) {
+      const size_t nb = (size_t)std::min<uint64_t>(kFileChunk, s.bytes - o);
+      DL_CUDA(cudaMemcpyAsync(buf.p, static_cast<const char *>(s.dev) + o, nb,
+                              cudaMemcpyDeviceToHost, st));
+      DL_CUDA(cudaStreamSynchronize(st));
+      ok = fwrite(buf.p, 1, nb, f.f) == nb;
+      cs.bytes(buf.p, nb);
+    }
+  }
+  if (ok) ok = fwrite(&cs.h, sizeof cs.h, 1, f.f) == 1;
+  if (fclose(f.f) != 0) ok = false;
+  f.f = nullptr;
+  if (!ok || rename(tmp.c_str(), path) != 0) {
+    remove(tmp.c_str());
+    return DETLSH_ERR_IO;
+  }
+  return DETLSH_OK;
+}
+
+int load_impl(const char *path, cudaStream_t st, detlsh_index **out) {
+  File f;
+  f.f = fopen(path, "rb");
+  if (!f.f) return DETLSH_ERR_IO;
+  FileHeader h;
+  if (fread(&h, sizeof h, 1, f.f) != 1) return DETLSH_ERR_FORMAT;
+  DL_TRY(check_header(h));
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+    cudaGetLastError();
+    return DETLSH_ERR_NO_DEVICE;
+  }
+  detlsh_index *ix = new (std::nothrow) detlsh_index();
+  if (!ix) return DETLSH_ERR_OOM;
+  struct Guard {  // frees the index unless it is handed out
+    detlsh_index *ix;
+    cudaStream_t st;
+    ~Guard() {
+      if (ix) {
+        cudaStreamSynchronize(st);
+        free_index(ix);
+      }
+    }
+  } guard{ix, st};
+  cudaGetDevice(&ix->device);
+  ix->n = h.n; ix->d = h.d; ix->L = h.L; ix->K = h.K; ix->LK = h.L * h.K; ix->N_r = h.N_r;
+  ix->bbits = h.bbits; ix->M = h.M; ix->box_mode = h.box_mode; ix->encoding = h.encoding;
+  ix->tree_group = h.tree_group; ix->seed = h.seed; ix->frac = h.frac; ix->eps2 = h.eps2;
+  ix->m_sample = h.m_sample; ix->max_leaf = h.max_leaf; ix->max_leaves = h.max_leaves;
+  ix->fb_total = h.fb_total;
+  for (int t = 0; t < 16; ++t) ix->nleaves[t] = h.nleaves[t];
+  for (int t = 0; t <= 16; ++t) {
+    ix->leaf_off[t] = h.leaf_off[t];
+    ix->blk_off[t] = h.blk_off[t];
+    ix->sblk_off[t] = h.sblk_off[t];
+  }
+  const int64_t n = ix->n, d = ix->d, L = ix->L, LK = ix->LK;
+  const int64_t tl = ix->leaf_off[L], tb = ix->blk_off[L], ts = ix->sblk_off[L];
+  DL_TRY(dalloc(ix, &ix->X, (size_t)(n * d), st));
+  DL_TRY(dalloc(ix, &ix->A, (size_t)(LK * d), st));
+  DL_TRY(dalloc(ix, &ix->B, (size_t)(LK * (ix->N_r + 1)), st));
+  DL_TRY(dalloc(ix, &ix->sample, (size_t)std::max<int64_t>(ix->m_sample, 1), st));
+  DL_TRY(dalloc(ix, &ix->codes, (size_t)(L * n * CODE_STRIDE), st));
+  DL_TRY(dalloc(ix, &ix->perm, (size_t)(L * n), st));
+  DL_TRY(dalloc(ix, &ix->leaf_of, (size_t)(L * n), st));
+  DL_TRY(dalloc(ix, &ix->leaf_begin, (size_t)(tl + L), st));
+  DL_TRY(dalloc(ix, &ix->leaf_lo, (size_t)(tl * 16), st));
+  DL_TRY(dalloc(ix, &ix->leaf_hi, (size_t)(tl * 16), st));
+  DL_TRY(dalloc(ix, &ix->leaf_nb, (size_t)(tl * 16), st));
+  DL_TRY(dalloc(ix, &ix->blk_lo, (size_t)(tb * 16), st));
+  DL_TRY(dalloc(ix, &ix->blk_hi, (size_t)(tb * 16), st));
+  DL_TRY(dalloc(ix, &ix->sblk_lo, (size_t)(ts * 16), st));
+  DL_TRY(dalloc(ix, &ix->sblk_hi, (size_t)(ts * 16), st));
+  if (h.has_bf16) {
+    DL_TRY(dalloc(ix, &ix->Xh, (size_t)(n * d), st));
+    DL_TRY(dalloc(ix, &ix->Xn, (size_t)n, st));
+  }
+  if (h.has_proj) DL_TRY(dalloc(ix, &ix->P, (size_t)(n * LK), st));
+  const std::vector<Section> secs = file_sections(ix);
+  if (h.nsections != secs.size()) return DETLSH_ERR_FORMAT;
+  Checksum cs;
+  cs.bytes(&h, sizeof h);
+  Staging buf;
+  DL_CUDA(cudaMallocHost(&buf.p, kFileChunk));
+  for (const Section &s : secs) {
+    SectionHead sh;
+    if (fread(&sh, sizeof sh, 1, f.f) != 1) return DETLSH_ERR_FORMAT;
+    if (sh.tag != s.tag || sh.reserved != 0 || sh.bytes != s.bytes) return DETLSH_ERR_FORMAT;
+    cs.bytes(&sh, sizeof sh);
+    for (uint64_t o = 0; o < s.bytes; o += kFileChunk) {
+      const size_t nb = (size_t)std::min<uint64_t>(kFileChunk, s.bytes - o);
+      DL_CUDA(cudaStreamSynchronize(st));  // the previous chunk has left the buffer
+      if (fread(buf.p, 1, nb, f.f) != nb) return DETLSH_ERR_FORMAT;
+      cs.bytes(buf.p, nb);
+      DL_CUDA(cudaMemcpyAsync(static_cast<char *>(s.dev) + o, buf.p, nb, cudaMemcpyHostToDevice, st));
+    }
+  }
+  uint64_t want = 0;
+  if (fread(&want, sizeof want, 1, f.f) != 1 || want != cs.h) return DETLSH_ERR_FORMAT;
+  if (fgetc(f.f) != EOF) return DETLSH_ERR_FORMAT;  // trailing bytes
+  DL_CUDA(cudaStreamSynchronize(st));
+  DL_TRY(ensure_events(ix));
+  guard.ix = nullptr;
+  *out = ix;
   return DETLSH_OK;
 }
 
@@ -940,7 +1236,7 @@ int detlsh_default_query_params(detlsh_query_params *p) {
   p->beta = 0.1;
   p->c = 1.5;
   p->precision = DETLSH_PREC_FP32;
-  p->rerank_mult = 4;
+  p->rerank_mult = 0;
   p->rmin_policy = DETLSH_RMIN_MAGIC;
   p->r_min = 1.0;
   p->per_tree = 0;
@@ -959,6 +1255,8 @@ const char *detlsh_status_string(int s) {
     case DETLSH_ERR_SCRATCH_LIMIT:
       return "request does not fit the fixed 32 MiB scratch of detlsh_query_noalloc";
     case DETLSH_ERR_TIMEOUT: return "a device-side wait ran past its limit";
+    case DETLSH_ERR_IO: return "index file could not be opened, read or written";
+    case DETLSH_ERR_FORMAT: return "not a valid index file (format, version, size or checksum)";
   }
   return "unknown status";
 }
@@ -1081,9 +1379,9 @@ int detlsh_query_reserve(detlsh_index *ix, int64_t m_max, int32_t k_max,
   int slots = (int)std::min<int64_t>(query_slots(vw), m_max);
   size_t freeb = 0, totb = 0;
   DL_CUDA(cudaMemGetInfo(&freeb, &totb));
-  while (slots > 1 && (size_t)slots * P.off[12] > freeb / 4 + ix->ascratch.bytes) slots /= 2;
+  while (slots > 1 && (size_t)slots * P.off[SLOT_ARRAYS] > freeb / 4 + ix->ascratch.bytes) slots /= 2;
   bool fresh = false;
-  DL_TRY(grow(ix->ascratch, kScratchHeader + (size_t)slots * P.off[12], st, &fresh));
+  DL_TRY(grow(ix->ascratch, kScratchHeader + (size_t)slots * P.off[SLOT_ARRAYS], st, &fresh));
   if (fresh) DL_CUDA(cudaMemsetAsync(ix->ascratch.p, 0, ix->ascratch.bytes, st));
   DL_CUDA(cudaStreamSynchronize(st));
   P.qp = *qp;
@@ -1140,8 +1438,8 @@ int detlsh_query_async(const detlsh_index *cix, const float *queries, int64_t m,
     qa.per_tree = P.qp.per_tree;
     qa.ids = ids; qa.dists = dists;
     qa.cand_cap = P.cap;
-    for (int i = 0; i < 13; ++i) qa.off[i] = P.off[i];
-    qa.slot_bytes = P.off[12];
+    for (int i = 0; i <= SLOT_ARRAYS; ++i) qa.off[i] = P.off[i];
+    qa.slot_bytes = P.off[SLOT_ARRAYS];
     qa.epoch_counter = static_cast<unsigned long long *>(ix->ascratch.p);
     qa.scratch = static_cast<uint8_t *>(ix->ascratch.p) + kScratchHeader;
     qa.nslots = P.slots;
@@ -1374,6 +1672,17 @@ int detlsh_project(const detlsh_index *cix, const float *rows, int64_t m, float 
   DL_TRY(copy_out(out, ix->qQp.p, sizeof(float) * (size_t)m * ix->LK, st));
   DL_CUDA(cudaStreamSynchronize(st));
   return DETLSH_OK;
+}
+
+int detlsh_save(const detlsh_index *ix, const char *path, void *stream) {
+  if (!ix || !path) return DETLSH_ERR_INVALID_ARG;
+  return save_impl(ix, path, static_cast<cudaStream_t>(stream));
+}
+
+int detlsh_load(const char *path, void *stream, detlsh_index **out) {
+  if (!path || !out) return DETLSH_ERR_INVALID_ARG;
+  *out = nullptr;
+  return load_impl(path, static_cast<cudaStream_t>(stream), out);
 }
 
 }  // extern "C"

@@ -109,7 +109,7 @@ struct QueryIndexView {
   int d, L, K, LK, N_r;
   const float *X;
   const __nv_bfloat16 *Xh;
-  const float *Xn;           // [n] squared norms of the BF16 rows
+  const float2 *Xn;          // [n] {||bf16(x)||^2, upper bound of ||x - bf16(x)||}
   const float *P;            // [n][LK] exact projections (null unless kept at build)
   const float *B;            // [LK][N_r+1]
   const uint32_t *perm;      // [L][n]
@@ -124,6 +124,8 @@ struct QueryIndexView {
   int64_t max_leaves;        // max leaves of one tree
   int64_t max_leaf_size;
 };
+// Arrays of a query kernel's per-CTA scratch slot (query_slot_offsets).
+constexpr int SLOT_ARRAYS = 13;
 struct QueryArgs {
   const float *Q;            // [m][d]
   const __nv_bfloat16 *Qh;   // [m][d] (bf16 path)
@@ -148,7 +150,7 @@ struct QueryArgs {
   // scratch: one slot per CTA, offsets from query_slot_offsets
   uint8_t *scratch;
   int64_t slot_bytes;
-  int64_t off[13];
+  int64_t off[SLOT_ARRAYS + 1];
   int64_t cand_cap;
   unsigned long long *epoch_counter;  // leaf levels are tagged (epoch << 8 | level); each
                                       // query takes the next epoch from this device word
@@ -158,7 +160,7 @@ struct QueryArgs {
   unsigned long long *stats;  // [4]: candidates, leaves expanded, hull blocks, points visited
 };
 size_t query_slot_bytes(const QueryIndexView &ix, int64_t cand_cap, int rerank_cap);
-void query_slot_offsets(const QueryIndexView &ix, int64_t cand_cap, int64_t off[13]);
+void query_slot_offsets(const QueryIndexView &ix, int64_t cand_cap, int64_t off[SLOT_ARRAYS + 1]);
 int query_slots(const QueryIndexView &ix);
 int run_queries(const QueryIndexView &ix, const QueryArgs &qa, cudaStream_t st);
 

@@ -111,7 +111,7 @@ extern "C" int detlsh_query_noalloc(const detlsh_index *ix, const float *queries
   const int64_t o_slots = up256(o_qh + (bf16 ? 2 * m * v.d : 0));
   QueryArgs qa{};
   query_slot_offsets(v, cap, qa.off);
-  const int64_t slot = qa.off[12];
+  const int64_t slot = qa.off[SLOT_ARRAYS];
   if (o_slots + slot > (int64_t)kScratchBytes) return DETLSH_ERR_SCRATCH_LIMIT;
   int slots = query_slots(v);
   slots = (int)std::min<int64_t>({(int64_t)slots, m, ((int64_t)kScratchBytes - o_slots) / slot});

@@ -54,26 +54,27 @@ struct Slot {
   uint32_t *rid;    // [RR_MAX] re-rank ids
   uint32_t *rkey;   // [RR_MAX]
   uint8_t *cm;      // [cap] smallest level of each candidate (fixed r_min)
+  uint32_t *hkey;   // [cap] upper ends of the certified BF16 intervals
 };
 
 __host__ __device__ inline int64_t align_up(int64_t v, int64_t a) { return (v + a - 1) / a * a; }
 
-static void slot_layout(const QueryIndexView &ix, int64_t cap, int64_t off[13]) {
+static void slot_layout(const QueryIndexView &ix, int64_t cap, int64_t off[SLOT_ARRAYS + 1]) {
   const int64_t tl = ix.leaf_off[ix.L], tb = ix.blk_off[ix.L];
-  const int64_t sz[12] = {8 * tl, tb, 4 * tb, 4 * tl, 4 * tl, tl, 4 * ix.max_leaves,
-                          4 * cap, 4 * cap, 4 * RR_MAX, 4 * RR_MAX, cap};
+  const int64_t sz[SLOT_ARRAYS] = {8 * tl, tb, 4 * tb, 4 * tl, 4 * tl, tl, 4 * ix.max_leaves,
+                                   4 * cap, 4 * cap, 4 * RR_MAX, 4 * RR_MAX, cap, 4 * cap};
   int64_t o = 0;
-  for (int i = 0; i < 12; ++i) { off[i] = o; o = align_up(o + sz[i], 256); }
-  off[12] = o;
+  for (int i = 0; i < SLOT_ARRAYS; ++i) { off[i] = o; o = align_up(o + sz[i], 256); }
+  off[SLOT_ARRAYS] = o;
 }
 
 size_t query_slot_bytes(const QueryIndexView &ix, int64_t cand_cap, int) {
-  int64_t off[13];
+  int64_t off[SLOT_ARRAYS + 1];
   slot_layout(ix, cand_cap, off);
-  return (size_t)off[12];
+  return (size_t)off[SLOT_ARRAYS];
 }
 
-void query_slot_offsets(const QueryIndexView &ix, int64_t cand_cap, int64_t off[13]) {
+void query_slot_offsets(const QueryIndexView &ix, int64_t cand_cap, int64_t off[SLOT_ARRAYS + 1]) {
   slot_layout(ix, cand_cap, off);
 }
 
@@ -101,6 +102,7 @@ struct QShared {
   uint32_t cpos;
   int jchk;
   float qn;  // |q|^2 of the BF16 query
+  float qr;  // upper bound of ||q - bf16(q)||
   int jguess, crossed;  // bound guessed from this CTA's previous query; tree crossed tau
 };
 static_assert(KMAX >= 1024, "the flattened visit borrows the top-k arrays");
@@ -887,6 +889,37 @@ __device__ __forceinline__ void mma_bf16_16816(float (&c)[4], uint32_t a0, uint3
       : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
 }
 
+// Certified interval of the FP32 path's squared distance from a BF16 score.
+// s = fl(fl(qn + xn) - 2 acc) estimates D~ = ||q~ - x~||^2 (q~, x~ the BF16
+// rows): qn and xn are FMA sums of d non-negative terms (relative error at
+// most d u each, u = 2^-24), the products of acc are exact (8-bit
+// significands) and the tensor core's FP32 accumulation of the d products is
+// taken to err by at most 2 ulps of 24 bits per addition (4 d u in all,
+// relative to sum |q~_j x~_j| <= (|q~|^2 + |x~|^2) / 2), and the last two
+// roundings add u each on magnitudes below 2 (|q~|^2 + |x~|^2).  Together
+// |s - D~| <= (6d + 16) u (qn + xn) + d 2^-125 (the last term covers subnormal
+// products flushed to zero).  The triangle inequality moves from D~ to the
+// exact distance D of the FP32 rows: |sqrt(D) - sqrt(D~)| <= |q - q~| +
+// |x - x~| (both bounded from above at build / here).  The FP32 path computes
+// D with relative error at most (2d + 16) u plus d 2^-148 absolute.  Every
+// step rounds outwards, so lo <= FP32 key <= hi; any NaN or overflow gives
+// the empty information [0, inf].
+__device__ __forceinline__ float nonneg_bits(float v) {  // -0 -> +0 (keys compare as uint)
+  return __uint_as_float(__float_as_uint(v) & 0x7fffffffu);
+}
+__device__ __forceinline__ void bf16_interval(float s, float qn, float2 xn, float qr, int d,
+                                              float &lo, float &hi) {
+  const float fd = (float)d;  // the constants are recomputed here: no registers held across
+  const float e = __fmaf_ru(__fmaf_ru(6.0f, fd, 16.0f) * 0x1p-24f, __fadd_ru(qn, xn.x), fd * 0x1p-125f);
+  const float r = __fadd_ru(qr, xn.y);
+  const float g = __fmaf_ru(2.0f, fd, 16.0f) * 0x1p-24f;
+  const float dlo = fmaxf(__fsub_rd(__fsqrt_rd(fmaxf(__fsub_rd(s, e), 0.0f)), r), 0.0f);
+  const float dhi = __fadd_ru(__fsqrt_ru(__fadd_ru(s, e)), r);
+  lo = nonneg_bits(fmaxf(__fsub_rd(__fmul_rd(__fmul_rd(dlo, dlo), 1.0f - g), fd * 0x1p-148f), 0.0f));
+  hi = __fadd_ru(__fmul_ru(__fmul_ru(dhi, dhi), __fadd_ru(1.0f, g)), fd * 0x1p-148f);
+  if (!(lo <= hi)) { lo = 0.0f; hi = __int_as_float(0x7f800000); }
+}
+
 // BF16 scores on the tensor cores: score(x) = |q|^2 + |x|^2 - 2 q.x with the
 // dot products of 16 candidate rows per warp and k-block of 16 from one
 // m16n8k16 MMA (the query is column 0 of B; columns 1-7 are zero).  The dot
@@ -894,24 +927,32 @@ __device__ __forceinline__ void mma_bf16_16816(float (&c)[4], uint32_t a0, uint3
 // elements per row and k-block (8 bytes) and the same 4 query elements are
 // placed at the matching B positions: memory element 4t+{0,1,2,3} of a block
 // is MMA k-index {2t, 2t+1, 2t+8, 2t+9} for lane t = lane % 4.
-__device__ __forceinline__ void distances_bf16(QCtx &c, int64_t nc, bool allpts) {
+// cert: key[] and hkey[] get the certified interval of each candidate's FP32
+// key (bf16_interval); otherwise key[] gets the score.
+__device__ __forceinline__ void distances_bf16(QCtx &c, int64_t nc, bool allpts, bool cert) {
   const QueryIndexView &ix = c.ix;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int d = ix.d;  // d % 8 == 0 on this path
   const int g = lane >> 2, t = lane & 3;
   const __nv_bfloat16 *qh = c.qa.Qh + c.qi * d;
-  // |q|^2 of the BF16 query
+  // |q|^2 of the BF16 query and the bound of |q - bf16(q)|
   if (warp == 0) {
-    float a = 0.0f;
+    const float *qf = c.qa.Q + c.qi * d;
+    float a = 0.0f, r = 0.0f;
     for (int j = lane; j < d; j += 32) {
       const float f = __bfloat162float(qh[j]);
       a = __fmaf_rn(f, f, a);
+      const float e = qf[j] - f;  // exact
+      r = __fmaf_ru(e, e, r);
     }
-    for (int o = 16; o > 0; o >>= 1) a = __fadd_rn(a, __shfl_xor_sync(FULL, a, o));
-    if (lane == 0) c.sm.qn = a;
+    for (int o = 16; o > 0; o >>= 1) {
+      a = __fadd_rn(a, __shfl_xor_sync(FULL, a, o));
+      r = __fadd_ru(r, __shfl_xor_sync(FULL, r, o));
+    }
+    if (lane == 0) { c.sm.qn = a; c.sm.qr = __fsqrt_ru(r); }
   }
   __syncthreads();
-  const float qn = c.sm.qn;
+  const float qn = c.sm.qn, qr = c.sm.qr;
   const int nblk = (d + 15) >> 4;
   auto id_of = [&](int64_t r) -> uint32_t {
     return (lane < 16 && r + lane < nc) ? (allpts ? (uint32_t)(r + lane) : c.s.cand[r + lane]) : 0u;
@@ -920,11 +961,11 @@ __device__ __forceinline__ void distances_bf16(QCtx &c, int64_t nc, bool allpts)
   for (int64_t r0 = (int64_t)warp * 16; r0 < nc; r0 += QW * 16) {
     const uint32_t p0 = __shfl_sync(FULL, myid, g), p1 = __shfl_sync(FULL, myid, g + 8);
     const bool ok0 = r0 + g < nc, ok1 = r0 + g + 8 < nc;
-    // norms and the next rows' ids go out with this tile's row loads
+    // norm terms and the next rows' ids go out with this tile's row loads
     float xn0 = 0.0f, xn1 = 0.0f;
     if (t == 0) {
-      if (ok0) xn0 = ix.Xn[p0];
-      if (ok1) xn1 = ix.Xn[p1];
+      if (ok0) xn0 = ix.Xn[p0].x;
+      if (ok1) xn1 = ix.Xn[p1].x;
     }
     myid = id_of(r0 + QW * 16);
     const __nv_bfloat16 *x0 = ix.Xh + (int64_t)p0 * d + 4 * t;
@@ -955,17 +996,27 @@ __device__ __forceinline__ void distances_bf16(QCtx &c, int64_t nc, bool allpts)
       mma_bf16_16816(acc, xa.x, xb.x, xa.y, xb.y, qv.x, qv.y);
     }
     if (t == 0) {
-      if (ok0) {
-        const float s0 = __fadd_rn(__fadd_rn(qn, xn0), -2.0f * acc[0]);
-        c.s.key[r0 + g] = __float_as_uint(fmaxf(s0, 0.0f));
-      }
-      if (ok1) {
-        const float s1 = __fadd_rn(__fadd_rn(qn, xn1), -2.0f * acc[2]);
-        c.s.key[r0 + g + 8] = __float_as_uint(fmaxf(s1, 0.0f));
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        if (!(h ? ok1 : ok0)) continue;
+        const float sc = __fadd_rn(__fadd_rn(qn, h ? xn1 : xn0), -2.0f * acc[2 * h]);
+        const int64_t r = r0 + g + 8 * h;
+        if (cert) c.s.hkey[r] = __float_as_uint(sc);  // the interval follows below
+        else c.s.key[r] = __float_as_uint(nonneg_bits(fmaxf(sc, 0.0f)));
       }
     }
   }
   __syncthreads();
+  if (cert) {  // a second pass keeps the tile loop's registers free
+    for (int64_t i = threadIdx.x; i < nc; i += QT) {
+      const uint32_t p = allpts ? (uint32_t)i : c.s.cand[i];
+      float lo, hi;
+      bf16_interval(__uint_as_float(c.s.hkey[i]), qn, ix.Xn[p], qr, d, lo, hi);
+      c.s.key[i] = __float_as_uint(lo);
+      c.s.hkey[i] = __float_as_uint(hi);
+    }
+    __syncthreads();
+  }
 }
 
 // ---- step 5: top-k by (key, id) -------------------------------------------
@@ -1428,6 +1479,7 @@ __global__ void __launch_bounds__(QT, 5) k_query(QueryIndexView ix, QueryArgs qa
   s.rid = reinterpret_cast<uint32_t *>(base + qa.off[9]);
   s.rkey = reinterpret_cast<uint32_t *>(base + qa.off[10]);
   s.cm = base + qa.off[11];
+  s.hkey = reinterpret_cast<uint32_t *>(base + qa.off[12]);
   for (int i = threadIdx.x; i < 256; i += QT) sm.T[i] = i < NLEV ? qa.T[i] : __int_as_float(0x7f800000);
   if (threadIdx.x == 0) { sm.n_blocks = 0; sm.n_leaves = 0; sm.n_visit = 0; sm.jguess = NLEV - 1; }
   __syncthreads();
@@ -1527,16 +1579,48 @@ __global__ void __launch_bounds__(QT, 5) k_query(QueryIndexView ix, QueryArgs qa
     }
     if (!fixed_done) {
       // verification and top-k
-      if (qa.precision == DETLSH_PREC_BF16_REFINE) {
-        distances_bf16(c, nc, allpts);
+      auto get_s = [&](int64_t i, uint32_t &key, uint32_t &id) {
+        key = s.key[i];
+        id = allpts ? (uint32_t)i : s.cand[i];
+      };
+      auto get_r = [&](int64_t i, uint32_t &key, uint32_t &id) { key = s.rkey[i]; id = s.rid[i]; };
+      if (qa.precision == DETLSH_PREC_BF16_REFINE && qa.rerank_mult == 0) {
+        // certified pool: every candidate whose interval starts at or below
+        // the k-th smallest interval end T.  The k candidates with the
+        // smallest ends have FP32 keys <= T, so each of the FP32 path's top k
+        // has key <= T and lies in the pool: re-ranking the pool in FP32
+        // gives the FP32 path's answer exactly.
+        distances_bf16(c, nc, allpts, true);
+        auto gh = [&](int64_t i, uint32_t &kk2, uint32_t &w) { kk2 = s.hkey[i]; w = 1u; };
+        block_select(nc, gh, (uint32_t)k, sm);
+        const uint32_t T = sm.sel_v;
+        if (threadIdx.x == 0) sm.nres = 0;
+        __syncthreads();
+        for (int64_t i0 = 0; i0 < nc; i0 += QT) {  // uniform trip count: warp collectives inside
+          const int64_t i = i0 + threadIdx.x;
+          const bool in = i < nc && s.key[i] <= T;
+          const unsigned bm = __ballot_sync(FULL, in);
+          uint32_t pos0 = 0;
+          if ((threadIdx.x & 31) == 0 && bm) pos0 = atomicAdd(&sm.nres, (uint32_t)__popc(bm));
+          pos0 = __shfl_sync(FULL, pos0, 0) + __popc(bm & ((1u << (threadIdx.x & 31)) - 1u));
+          if (in && pos0 < RR_MAX) s.rid[pos0] = allpts ? (uint32_t)i : s.cand[i];
+        }
+        __syncthreads();
+        const int64_t np = sm.nres;
+        if (threadIdx.x == 0 && qa.stats) atomicAdd(&qa.stats[4], (unsigned long long)np);
+        if (np <= RR_MAX) {
+          dist_fp32(ix, qa.Q + qi * ix.d, np, [&](int64_t i) { return s.rid[i]; }, s.rkey);
+          topk_select(np, k, get_r, sm);
+        } else {  // a pool beyond the re-rank buffers: FP32 over every candidate
+          distances_fp32(c, nc, allpts);
+          topk_select(nc, k, get_s, sm);
+        }
+      } else if (qa.precision == DETLSH_PREC_BF16_REFINE) {
+        distances_bf16(c, nc, allpts, false);
         int R = qa.rerank_mult * k;
         if (R > RR_MAX) R = RR_MAX;
         if (R > nc) R = (int)nc;
         if (R < k) R = k;
-        auto get_s = [&](int64_t i, uint32_t &key, uint32_t &id) {
-          key = s.key[i];
-          id = allpts ? (uint32_t)i : s.cand[i];
-        };
         // pick the R best BF16 scores (unsorted is enough): threshold select
         auto gk = [&](int64_t i, uint32_t &kk2, uint32_t &w) { uint32_t id; get_s(i, kk2, id); w = 1u; };
         block_select(nc, gk, (uint32_t)R, sm);
@@ -1563,16 +1647,12 @@ __global__ void __launch_bounds__(QT, 5) k_query(QueryIndexView ix, QueryArgs qa
           }
         }
         __syncthreads();
+        if (threadIdx.x == 0 && qa.stats) atomicAdd(&qa.stats[4], (unsigned long long)R);
         // exact FP32 distances of the re-rank pool
         dist_fp32(ix, qa.Q + qi * ix.d, R, [&](int64_t i) { return s.rid[i]; }, s.rkey);
-        auto get_r = [&](int64_t i, uint32_t &key, uint32_t &id) { key = s.rkey[i]; id = s.rid[i]; };
         topk_select(R, k, get_r, sm);
       } else {
         distances_fp32(c, nc, allpts);
-        auto get_s = [&](int64_t i, uint32_t &key, uint32_t &id) {
-          key = s.key[i];
-          id = allpts ? (uint32_t)i : s.cand[i];
-        };
         topk_select(nc, k, get_s, sm);
       }
     }

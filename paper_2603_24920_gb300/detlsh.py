@@ -15,7 +15,7 @@ LIB_PATH = os.path.join(HERE, "libdetlsh.so")
 DETLSH_OK = 0
 STATUS = {0: "OK", -1: "INVALID_ARG", -2: "NONFINITE_INPUT", -3: "OOM", -4: "CUDA",
           -5: "CAPACITY", -6: "NO_DEVICE", -7: "SCRATCH_LIMIT",
-          -8: "TIMEOUT"}
+          -8: "TIMEOUT", -9: "IO", -10: "FORMAT"}
 BOX_PREFIX, BOX_TIGHT = 0, 1
 PREC_FP32, PREC_BF16_REFINE = 0, 1
 RMIN_MAGIC, RMIN_FIXED, RMIN_CONTINUOUS = 0, 1, 2
@@ -58,7 +58,7 @@ class Timings(C.Structure):
                 ("build_launches", C.c_int64), ("query_launches", C.c_int64),
                 ("query_count", C.c_int64), ("query_candidates", C.c_int64),
                 ("query_leaves", C.c_int64), ("query_blocks", C.c_int64),
-                ("query_points_visited", C.c_int64)]
+                ("query_points_visited", C.c_int64), ("query_reranked", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -76,6 +76,8 @@ SIGNATURES = [
     ("detlsh_query", C.c_int, [_P, _P, _I64, _I32, _F64, _P, _P]),
     ("detlsh_query_ex", C.c_int, [_P, _P, _I64, _P, _I32, C.POINTER(QueryParams), _P, _P, _P]),
     ("detlsh_query_noalloc", C.c_int, [_P, _P, _I64, _I32, C.POINTER(QueryParams), _P, _P, _P]),
+    ("detlsh_save", C.c_int, [_P, C.c_char_p, _P]),
+    ("detlsh_load", C.c_int, [C.c_char_p, _P, C.POINTER(_P)]),
     ("detlsh_free", C.c_int, [_P]),
     ("detlsh_status_string", C.c_char_p, [C.c_int]),
     ("detlsh_get_info", C.c_int, [_P, C.POINTER(Info)]),
@@ -172,12 +174,24 @@ def detlsh_build(data, L=4, K=16, N_r=256, seed=0, **kw):
     return h
 
 
+def detlsh_save(h, path, stream=None):
+    """Write the index to an index file at path (str or os.PathLike)."""
+    _check(lib().detlsh_save(h, os.fsencode(path), _stream_ptr(stream)), "detlsh_save")
+
+
+def detlsh_load(path, stream=None):
+    """Read an index file into a new index on the current device."""
+    h = C.c_void_p()
+    _check(lib().detlsh_load(os.fsencode(path), _stream_ptr(stream), C.byref(h)), "detlsh_load")
+    return h
+
+
 def detlsh_free(h):
     if h:
         lib().detlsh_free(h)
 
 
-def detlsh_query_ex(h, queries, k, beta=0.1, c=1.5, precision=PREC_FP32, rerank_mult=4,
+def detlsh_query_ex(h, queries, k, beta=0.1, c=1.5, precision=PREC_FP32, rerank_mult=0,
                     k_per_query=None, stream=None, ids=None, dists=None, r_min=None,
                     rmin_policy=None, per_tree=False):
     """Returns (ids int64 (m, k), dists float32 (m, k)); torch CUDA if queries are.
@@ -207,7 +221,7 @@ def detlsh_query_ex(h, queries, k, beta=0.1, c=1.5, precision=PREC_FP32, rerank_
     return ids, dists
 
 
-def detlsh_query_noalloc(h, queries, k, beta=0.1, c=1.5, precision=PREC_FP32, rerank_mult=4,
+def detlsh_query_noalloc(h, queries, k, beta=0.1, c=1.5, precision=PREC_FP32, rerank_mult=0,
                          stream=None, ids=None, dists=None, per_tree=False):
     """Queries answered with the library's fixed scratch array: the call
     allocates no device memory (for callers that cannot allocate while
@@ -336,7 +350,7 @@ def detlsh_query_candidates(h, queries, k, beta=0.1, c=1.5, cap=None, r_min=None
     return [S[r, :ssz[r]].copy() for r in range(m)], js, ist
 
 
-def detlsh_query_reserve(h, m_max, k_max, beta=0.1, c=1.5, precision=PREC_FP32, rerank_mult=4,
+def detlsh_query_reserve(h, m_max, k_max, beta=0.1, c=1.5, precision=PREC_FP32, rerank_mult=0,
                          r_min=None):
     """Fix the parameters and sizes of detlsh_query_async and allocate its buffers."""
     qp = detlsh_default_query_params()

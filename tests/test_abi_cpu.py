@@ -45,7 +45,7 @@ def test_default_params(lib):
     assert p.sample_frac == pytest.approx(0.1)
     assert p.tree_group == 0
     q = D.detlsh_default_query_params()
-    assert (q.beta, q.c, q.precision, q.rerank_mult) == (pytest.approx(0.1), 1.5, 0, 4)
+    assert (q.beta, q.c, q.precision, q.rerank_mult) == (pytest.approx(0.1), 1.5, 0, 0)
 
 
 @pytest.mark.parametrize("kw", [dict(L=0), dict(L=17), dict(K=0), dict(K=17), dict(N_r=3),

@@ -154,9 +154,12 @@ def test_bf16_refine_path(pair):
     Q = _queries(pair["d"])
     k = min(10, pair["n"])
     i32, d32 = D.detlsh_query_ex(h, Q, k, beta=0.1)
+    # certified pool (default): the FP32 path's answer, bit for bit
     ib, db = D.detlsh_query_ex(h, Q, k, beta=0.1, precision=D.PREC_BF16_REFINE)
+    assert np.array_equal(ib, i32) and np.array_equal(db.view(np.uint32), d32.view(np.uint32))
+    # fixed pool of the 4k best scores: exact FP32 distances of the returned ids
+    ib, db = D.detlsh_query_ex(h, Q, k, beta=0.1, precision=D.PREC_BF16_REFINE, rerank_mult=4)
     for i in range(Q.shape[0]):
-        # re-ranked distances are the exact FP32 distances of the returned ids
         dd = np.sqrt(((X[ib[i]].astype(np.float64) - Q[i]) ** 2).sum(1))
         np.testing.assert_allclose(db[i], dd, rtol=RTOL, atol=1e-6)
         assert len(set(ib[i].tolist()) & set(i32[i].tolist())) >= k - 1
