@@ -138,26 +138,67 @@ static float orc_acc_round(int64_t *acc) {
     return neg ? -v : v;
 }
 
+/* acc += a*b (or -= when negate), exactly; a and b finite. */
+static void orc_acc_add_product(int64_t *acc, float a, float b, int negate) {
+    int na, nx, ea, ex;
+    uint32_t ma, mx;
+    orc_fdecompose(a, &na, &ma, &ea);
+    orc_fdecompose(b, &nx, &mx, &ex);
+    if (ma == 0 || mx == 0) return;
+    uint64_t m = (uint64_t)ma * (uint64_t)mx; /* < 2^48, exact */
+    int off = ea + ex + ORC_BIAS;              /* >= 0 */
+    unsigned __int128 v = (unsigned __int128)m << (off & 31);
+    int c = off >> 5;
+    int64_t p0 = (int64_t)((uint64_t)v & 0xffffffffu);
+    int64_t p1 = (int64_t)((uint64_t)(v >> 32) & 0xffffffffu);
+    int64_t p2 = (int64_t)(uint64_t)(v >> 64);
+    if ((na ^ nx) ^ (negate != 0)) { acc[c] -= p0; acc[c + 1] -= p1; acc[c + 2] -= p2; }
+    else                           { acc[c] += p0; acc[c + 1] += p1; acc[c + 2] += p2; }
+}
+
 float orc_dot_rn32(const float *a, const float *x, int64_t d) {
     int64_t acc[ORC_NCHUNK];
     memset(acc, 0, sizeof acc);
-    for (int64_t i = 0; i < d; i++) {
-        int na, nx, ea, ex;
-        uint32_t ma, mx;
-        orc_fdecompose(a[i], &na, &ma, &ea);
-        orc_fdecompose(x[i], &nx, &mx, &ex);
-        if (ma == 0 || mx == 0) continue;
-        uint64_t m = (uint64_t)ma * (uint64_t)mx; /* < 2^48, exact */
-        int off = ea + ex + ORC_BIAS;              /* >= 0 */
-        unsigned __int128 v = (unsigned __int128)m << (off & 31);
-        int c = off >> 5;
-        int64_t p0 = (int64_t)((uint64_t)v & 0xffffffffu);
-        int64_t p1 = (int64_t)((uint64_t)(v >> 32) & 0xffffffffu);
-        int64_t p2 = (int64_t)(uint64_t)(v >> 64);
-        if (na ^ nx) { acc[c] -= p0; acc[c + 1] -= p1; acc[c + 2] -= p2; }
-        else         { acc[c] += p0; acc[c + 1] += p1; acc[c + 2] += p2; }
-    }
+    for (int64_t i = 0; i < d; i++) orc_acc_add_product(acc, a[i], x[i], 0);
     return orc_acc_round(acc);
+}
+
+/* Is ||q - x|| <= R, decided exactly (no rounding anywhere)?  The squared
+ * distance expands into products of two floats,
+ *     ||q - x||^2 = sum_j (q_j q_j + x_j x_j - q_j x_j - q_j x_j),
+ * and the double R is cut exactly into floats R = f_1 + ... + f_m, so R^2 is
+ * the sum of the products f_a f_b; both sums go into the exact fixed-point
+ * accumulator and the sign of the difference decides.  Returns 1 (within),
+ * 0 (beyond), or -1 when R cannot be cut into at most six floats (a radius
+ * outside the FP32 range).  R = +inf is within. */
+int orc_dist2_le(const float *q, const float *x, int64_t d, double R) {
+    if (isinf(R) && R > 0) return 1;
+    if (!(R >= 0.0) || R >= 0x1p127) return -1; /* the pieces must be finite floats */
+    float f[6];
+    int m = 0;
+    double rest = R;
+    while (rest != 0.0 && m < 6) {
+        f[m] = (float)rest;
+        rest -= (double)f[m]; /* exact: f[m] is rest rounded to 24 bits */
+        m++;
+    }
+    if (rest != 0.0) return -1;
+    int64_t acc[ORC_NCHUNK];
+    memset(acc, 0, sizeof acc);
+    for (int64_t j = 0; j < d; j++) {
+        orc_acc_add_product(acc, q[j], q[j], 0);
+        orc_acc_add_product(acc, x[j], x[j], 0);
+        orc_acc_add_product(acc, q[j], x[j], 1);
+        orc_acc_add_product(acc, q[j], x[j], 1);
+    }
+    for (int a = 0; a < m; a++)
+        for (int b = 0; b < m; b++) orc_acc_add_product(acc, f[a], f[b], 1);
+    /* acc = ||q - x||^2 - R^2: within when it is negative or zero */
+    orc_acc_normalise(acc);
+    if (acc[ORC_NCHUNK - 1] < 0) return 1;
+    for (int i = 0; i < ORC_NCHUNK; i++)
+        if (acc[i] != 0) return 0;
+    return 1;
 }
 
 void orc_project(const float *X, int64_t n, int64_t d, const float *A, int LK, float *P) {
@@ -754,8 +795,8 @@ static double orc_dist(const float *q, const float *x, int64_t d) {
     return sqrt(s);
 }
 
-/* |S| after the union over all L trees at radius index j (Alg. 5 lines 3-6
- * without the early return). */
+/* |S| after the union over all L trees at radius index j (the range queries
+ * of Alg. 5 at one radius, without its early return). */
 static int64_t orc_union_size(const orc_index *ix, const float *qproj, float T, uint8_t *mark,
                               orc_hits *hits) {
     memset(mark, 0, (size_t)ix->n);
@@ -922,7 +963,7 @@ int orc_index_query(const orc_index *ix, const float *q, int k, double beta, dou
 
 /* per_tree = 1: Alg. 5 without the priority queue of Sec. VI-B2: a tree's
  * range query joins S whole and the budget is checked after each tree
- * (lines 5-6 as printed). */
+ * (the check as Alg. 5 prints it). */
 int orc_index_query_ex(const orc_index *ix, const float *q, int k, double beta, double c,
                        int per_tree, int64_t *ids, double *dists, int64_t *S_out,
                        int64_t *S_size, int *jstar, int *istar) {
@@ -997,9 +1038,10 @@ int orc_index_query_ex(const orc_index *ix, const float *q, int k, double beta, 
 /* Alg. 5 run literally from a given r_min (no magic r_min): radii
  * r_i = r_min c^i, i = 0, 1, ...; at each radius the trees in order, leaves
  * of the range query entering S whole in ascending (LB^2, leaf id) order with
- * the check |S| >= beta*n + k after each leaf (condition 1, lines 6-7); after
- * the L trees, condition 2 (lines 8-9): at least k points of S within c*r
- * (FP64 distances).  S accumulates across radii.  jstop = i of the radius
+ * the check |S| >= beta*n + k after each leaf (condition 1); after the L
+ * trees, condition 2: at least k points of S within c*r, each distance
+ * compared with c*r exactly (orc_dist2_le; c*r is the FP64 value
+ * c * (r_min * c^i)).  S accumulates across radii.  jstop = i of the radius
  * that stopped, istop = the tree for condition 1, -1 for condition 2. */
 int orc_index_query_fixed(const orc_index *ix, const float *q, int k, double beta, double c,
                           double r_min, int64_t *ids, double *dists, int64_t *S_out,
@@ -1013,7 +1055,7 @@ int orc_index_query_fixed(const orc_index *ix, const float *q, int k, double bet
     orc_cand *cand = (orc_cand *)malloc(sizeof(orc_cand) * (size_t)n);
     orc_hits hits = {0};
     int64_t ns = 0;
-    int js = -1, is = -1;
+    int js = -1, is = -1, bad = 0;
     for (int i = 0; i < ORC_NLEV && js < 0; i++) {
         const float Ti = (i == ORC_NLEV - 1) ? INFINITY
                          : (float)(ix->eps2 * r_min * r_min * pow(c, 2.0 * (double)i));
@@ -1036,14 +1078,23 @@ int orc_index_query_fixed(const orc_index *ix, const float *q, int k, double bet
             }
         }
         if (js < 0) {
+            /* condition 2, decided exactly; the last radius is unbounded (its
+             * range query already takes every leaf) */
             const double cr = c * (r_min * pow(c, (double)i));
             int64_t within = 0;
-            for (int64_t e = 0; e < ns; e++) within += cand[e].dist <= cr;
+            for (int64_t e = 0; e < ns; e++) {
+                const int w = (i == ORC_NLEV - 1) ? 1
+                              : orc_dist2_le(q, ix->X + cand[e].id * ix->d, ix->d, cr);
+                if (w < 0) { bad = 1; break; }
+                within += w;
+            }
+            if (bad) break;
             if (within >= k) { js = i; is = -1; }
         }
     }
     free(hits.v);
     free(mark);
+    if (bad) { free(cand); return -2; }
     qsort(cand, (size_t)ns, sizeof(orc_cand), orc_cmp_cand);
     for (int i = 0; i < k; i++) {
         ids[i] = i < ns ? cand[i].id : -1;

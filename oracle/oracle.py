@@ -38,6 +38,8 @@ def lib():
         L.orc_projection_matrix.argtypes = [C.c_int, C.c_int64, C.c_uint64, _f32p]
         L.orc_dot_rn32.argtypes = [_f32p, _f32p, C.c_int64]
         L.orc_dot_rn32.restype = C.c_float
+        L.orc_dist2_le.argtypes = [_f32p, _f32p, C.c_int64, C.c_double]
+        L.orc_dist2_le.restype = C.c_int
         L.orc_project.argtypes = [_f32p, C.c_int64, C.c_int64, _f32p, C.c_int, _f32p]
         L.orc_sample.argtypes = [C.c_int64, C.c_uint64, C.c_double, C.c_int, _i64p]
         L.orc_sample.restype = C.c_int64
@@ -126,6 +128,12 @@ def projection_matrix(LK, d, seed):
 def dot_rn32(a, x):
     a, x = _f32(a), _f32(x)
     return np.float32(lib().orc_dot_rn32(a, x, a.size))
+
+
+def dist_le(q, x, R):
+    """Exact ||q - x|| <= R (condition 2 of Alg. 5): 1 within, 0 beyond, -1 out of range."""
+    q, x = _f32(q), _f32(x)
+    return int(lib().orc_dist2_le(q, x, q.size, float(R)))
 
 
 def project(X, A):

@@ -10,8 +10,9 @@
 // returned it, i.e. its projected distance in every earlier tree exceeds r'
 // (the bounds only accelerate that test: LB <= distance <= UB).  New points
 // are counted, written to S and folded into the running nearest point; once
-// |S| >= beta n + 1 the query stops (Alg. 4, lines 6-7); after all L trees
-// the nearest point of S is returned only if it lies within c r (lines 8-10).
+// |S| >= beta n + 1 the query stops (Alg. 4, first condition); after all L
+// trees the nearest point of S is returned only if it lies within c r (its
+// second condition).
 #include "common.cuh"
 #include "compact.cuh"
 #include "kernels.h"

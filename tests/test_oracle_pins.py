@@ -550,6 +550,61 @@ def _fixed_grid(ix, r_min, c, i):
     return np.float32(oracle.eps2(ix.K, ix.L) * r_min * r_min * c ** (2.0 * i))
 
 
+def _exact_within(q, x, R):
+    """||q - x|| <= R in exact rational arithmetic."""
+    d2 = sum((Fraction(float(a)) - Fraction(float(b))) ** 2 for a, b in zip(q, x))
+    return d2 <= Fraction(R) ** 2
+
+
+def _within_count(X, q, ids, dist, R):
+    """Points of ids within R of q, exactly: FP64 decides where it is clear
+    by a wide margin, exact rationals decide the rest."""
+    n = 0
+    for p in ids:
+        if abs(dist[p] - R) > 1e-9 * R:
+            n += int(dist[p] < R)
+        else:
+            n += int(_exact_within(q, X[p], R))
+    return n
+
+
+@pytest.mark.parametrize("d", [1, 3, 16, 128])
+def test_dist2_le_equals_exact_rational(d):
+    g = np.random.default_rng(d)
+    for trial in range(60):
+        scale = 2.0 ** g.integers(-30, 30)
+        q = (g.normal(size=d) * scale).astype(np.float32)
+        x = (q + g.normal(size=d) * scale * 10.0 ** g.integers(-7, 1)).astype(np.float32)
+        d2 = sum((Fraction(float(a)) - Fraction(float(b))) ** 2 for a, b in zip(q, x))
+        r = float(np.sqrt(float(d2)))
+        for R in (r, np.nextafter(r, 0.0), np.nextafter(r, np.inf), r * (1 + 1e-12), 0.0):
+            if 0.0 < R < 1e-30:
+                continue  # below what FP32 pieces can hold (the function says -1)
+            assert oracle.dist_le(q, x, R) == int(_exact_within(q, x, R)), (d, trial, R)
+
+
+def test_dist2_le_special_cases():
+    q, x = np.zeros(2, np.float32), np.array([3.0, 4.0], np.float32)
+    assert oracle.dist_le(q, x, 5.0) == 1                      # on the sphere: within
+    assert oracle.dist_le(q, x, np.nextafter(5.0, 0.0)) == 0   # one ulp inside: beyond
+    assert oracle.dist_le(q, q, 0.0) == 1                      # zero distance, zero radius
+    assert oracle.dist_le(q, x, float("inf")) == 1
+    assert oracle.dist_le(q, x, -1.0) == -1
+    assert oracle.dist_le(q, x, 1e300) == -1                   # beyond the FP32 pieces
+    # a radius whose square needs the low pieces: 1 + 2^-40 against a point at 1
+    one = np.array([1.0], np.float32)
+    assert oracle.dist_le(np.zeros(1, np.float32), one, 1.0 + 2.0 ** -40) == 1
+    assert oracle.dist_le(np.zeros(1, np.float32), one, 1.0 - 2.0 ** -40) == 0
+    # subnormal coordinates against FP32 radii (a single piece each)
+    tiny = np.array([1e-45, 3e-45], np.float32)
+    d2 = sum(Fraction(float(v)) ** 2 for v in tiny)
+    r = np.float32(np.sqrt(float(d2)))
+    for R in (r, np.nextafter(r, np.float32(0)), np.nextafter(r, np.float32(1))):
+        assert oracle.dist_le(np.zeros(2, np.float32), tiny, float(R)) == int(d2 <= Fraction(float(R)) ** 2)
+    # a double radius with bits below FP32's subnormal spacing cannot be cut
+    assert oracle.dist_le(np.zeros(2, np.float32), tiny, 3.133398622996355e-45) == -1
+
+
 def test_query_fixed_rmin_follows_alg5():
     # Alg. 5 literally, from a given r_min: the loop recomputed from the
     # exported leaves (their lower bounds and members) with numpy, and the
@@ -582,7 +637,7 @@ def test_query_fixed_rmin_follows_alg5():
                             break
                     if js is not None:
                         break
-                    if (dist[inS] <= c * r_min * c ** i).sum() >= k:
+                    if _within_count(X, q, np.nonzero(inS)[0], dist, c * (r_min * c ** i)) >= k:
                         js, ist = i, -1
                         break
                 assert (got["jstop"], got["istop"]) == (js, ist)
@@ -591,7 +646,7 @@ def test_query_fixed_rmin_follows_alg5():
                 order = np.lexsort((S, dist[S]))[:k]
                 assert np.array_equal(got["ids"], S[order])
                 if ist == -1:  # condition 2 holds here and neither held one radius before
-                    assert (dist[S] <= c * r_min * c ** js).sum() >= k
+                    assert _within_count(X, q, S, dist, c * (r_min * c ** js)) >= k
                     assert S.size < tau
                 seen.add(ist == -1)
     assert seen == {True, False}
