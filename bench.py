@@ -262,7 +262,8 @@ def config_dict(beta):
     return {"workload": "SIFT-like clustered n=1e6 d=128 (ints 0-255 as fp32), 10k queries, k=50",
             "n": c["n"], "d": c["d"], "queries": c["m"], "k": c["k"], "L": 4, "K": 16,
             "N_r": 256, "max_size": 64, "beta": beta, "c": C_RATIO,
-            "l2": "inputs larger than L2 (fp32 data 512 MB, bf16 copy 256 MB)"}
+            "l2": "inputs larger than L2 (fp32 data 512 MB, bf16 copy 256 MB); L2 flushed "
+                  "by a 256 MB write before each query call, outside the timed parts"}
 
 
 def run_gb300(args):
@@ -284,24 +285,33 @@ def run_gb300(args):
     st = torch.cuda.current_stream()
     kw = dict(L=4, K=16, N_r=256, seed=0, max_size=64, stream=st)
 
+    # Both query paths start from the same cache state: a 256 MB write (twice
+    # the L2) before each query call, outside the timed parts, so neither
+    # inherits the index structures the other (or the build) left in L2.
+    flush = torch.empty(64 * 2 ** 20, dtype=torch.float32, device="cuda")
+
     def step():
-        e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
         e[0].record(st)
         h = D.detlsh_build(Xd, **kw)
         e[1].record(st)
         tb = D.detlsh_get_timings(h)
+        flush.zero_()
+        e[2].record(st)
         ib, db = D.detlsh_query_ex(h, Qd, k, beta=args.beta, c=C_RATIO,
                                    precision=D.PREC_BF16_REFINE, stream=st)
-        e[2].record(st)
+        e[3].record(st)
         tq_b = D.detlsh_get_timings(h)
+        flush.zero_()
+        e[4].record(st)
         i32, d32 = D.detlsh_query_ex(h, Qd, k, beta=args.beta, c=C_RATIO,
                                      precision=D.PREC_FP32, stream=st)
-        e[3].record(st)
+        e[5].record(st)
         tq_f = D.detlsh_get_timings(h)
         torch.cuda.synchronize()
         info = D.detlsh_get_info(h)
         D.detlsh_free(h)
-        ms = [e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2]), e[2].elapsed_time(e[3])]
+        ms = [e[0].elapsed_time(e[1]), e[2].elapsed_time(e[3]), e[4].elapsed_time(e[5])]
         return ms, tb, tq_b, tq_f, info, (ib, db, i32, d32)
 
     # quality at the operating point (untimed): exact FP64 ground truth

@@ -169,11 +169,12 @@ float orc_dot_rn32(const float *a, const float *x, int64_t d) {
  * and the double R is cut exactly into floats R = f_1 + ... + f_m, so R^2 is
  * the sum of the products f_a f_b; both sums go into the exact fixed-point
  * accumulator and the sign of the difference decides.  Returns 1 (within),
- * 0 (beyond), or -1 when R cannot be cut into at most six floats (a radius
- * outside the FP32 range).  R = +inf is within. */
+ * 0 (beyond), or -1 when R is negative, NaN or too small to be cut into at
+ * most six floats.  A radius of 2^127 or more (beyond FP32, +inf included)
+ * counts every point as within: the reading shared with the CUDA path. */
 int orc_dist2_le(const float *q, const float *x, int64_t d, double R) {
-    if (isinf(R) && R > 0) return 1;
-    if (!(R >= 0.0) || R >= 0x1p127) return -1; /* the pieces must be finite floats */
+    if (R >= 0x1p127) return 1; /* beyond FP32: every point counts as within */
+    if (!(R >= 0.0)) return -1;
     float f[6];
     int m = 0;
     double rest = R;

@@ -96,7 +96,8 @@ int orc_index_query(const orc_index *ix, const float *q, int k, double beta, dou
  * with c*r exactly) checked after each radius.  jstop = the stopping radius index, istop = the tree for
  * condition 1 or -1 for condition 2.  S_out (capacity n, nullable). */
 /* Exact ||q - x|| <= R for FP32 rows and a double R (1 within, 0 beyond, -1 if
- * R cannot be cut into FP32 pieces).  Condition 2 of Alg. 5. */
+ * R cannot be cut into FP32 pieces; R >= 2^127 is within).  Condition 2 of
+ * Alg. 5. */
 int orc_dist2_le(const float *q, const float *x, int64_t d, double R);
 int orc_index_query_fixed(const orc_index *ix, const float *q, int k, double beta, double c,
                           double r_min, int64_t *ids, double *dists, int64_t *S_out,

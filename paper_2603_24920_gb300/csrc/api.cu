@@ -733,13 +733,58 @@ int validate_query(const detlsh_index *ix, int64_t m, int32_t k_max, const detls
     return DETLSH_ERR_INVALID_ARG;
   if (qp->per_tree != 0 && qp->per_tree != 1) return DETLSH_ERR_INVALID_ARG;
   if (qp->per_tree && qp->rmin_policy != DETLSH_RMIN_MAGIC) return DETLSH_ERR_INVALID_ARG;
+  // a fixed r_min: c r_min >= 2^-60 keeps the radii of condition 2 exactly
+  // representable as three FP32 pieces
   if (qp->rmin_policy == DETLSH_RMIN_FIXED &&
-      (!(qp->r_min > 0.0) || !std::isfinite(qp->r_min) || qp->precision != DETLSH_PREC_FP32))
+      (!(qp->r_min > 0.0) || !std::isfinite(qp->r_min) || qp->precision != DETLSH_PREC_FP32 ||
+       !(qp->c * qp->r_min >= 0x1p-60)))
     return DETLSH_ERR_INVALID_ARG;
   return DETLSH_OK;
 }
 
 // Shared body of detlsh_query_ex and detlsh_query_candidates (qmu held).
+// Float round-down / round-up of a double.
+float f32_down(double x) {
+  float f = (float)x;
+  if ((double)f > x) f = std::nextafter(f, -INFINITY);
+  return f;
+}
+float f32_up(double x) {
+  float f = (float)x;
+  if ((double)f < x) f = std::nextafter(f, INFINITY);
+  return f;
+}
+
+// Query tables (TABLE_FLOATS floats, layout in kernels.h): the squared-radius
+// grid of the range queries and, for a fixed r_min, the radii c r_i of
+// condition 2 of Alg. 5 (c r_i = c (r_min c^i) in FP64): a rounded-down and
+// a rounded-up FP32 copy of (c r_i)^2 for the certified FP32 test, and c r_i
+// cut exactly into three FP32 pieces for the exact test near the sphere.  A
+// radius of 2^127 or more (beyond FP32) takes every point.
+void query_tables(const detlsh_index *ix, const detlsh_query_params *qp, float *Th) {
+  float *T = Th, *Tcl = Th + 256, *Tch = Th + 512, *Rp = Th + 768;
+  for (int i = 0; i < TABLE_FLOATS; ++i) Th[i] = INFINITY;
+  if (qp->rmin_policy == DETLSH_RMIN_FIXED) {
+    const double r0 = qp->r_min, c = qp->c;
+    for (int i = 0; i < NLEV - 1; ++i) {
+      T[i] = (float)(ix->eps2 * r0 * r0 * std::pow(c, 2.0 * (double)i));
+      const double cr = c * (r0 * std::pow(c, (double)i));
+      if (cr >= 0x1p127) continue;  // every point within: the tables stay +inf
+      const double r2 = cr * cr;    // relative error <= 2^-53
+      Tcl[i] = f32_down(r2 * (1.0 - 0x1p-52));
+      Tch[i] = f32_up(r2 * (1.0 + 0x1p-52));
+      double rest = cr;  // cr >= 2^-60 (checked): three pieces are exact
+      for (int p = 0; p < 3; ++p) {
+        Rp[3 * i + p] = (float)rest;
+        rest -= (double)Rp[3 * i + p];
+      }
+    }
+  } else {
+    level_table(ix->eps2, qp->c, T);
+  }
+  T[255] = INFINITY;
+}
+
 int query_impl(detlsh_index *ix, const float *queries, int64_t m, const int32_t *kq,
                int32_t k_max, const detlsh_query_params *qp, cudaStream_t st, int64_t *ids,
                float *dists, int64_t S_cap, int64_t *S, int64_t *S_size, int32_t *jstar,
@@ -759,7 +804,7 @@ int query_impl(detlsh_index *ix, const float *queries, int64_t m, const int32_t 
   DL_TRY(grow(ix->qQp, sizeof(float) * (size_t)m * LK, st));
   DL_TRY(grow(ix->qids, sizeof(int64_t) * (size_t)m * k_max, st));
   DL_TRY(grow(ix->qdists, sizeof(float) * (size_t)m * k_max, st));
-  DL_TRY(grow(ix->qT, sizeof(float) * 512, st));
+  DL_TRY(grow(ix->qT, sizeof(float) * TABLE_FLOATS, st));
   DL_TRY(grow(ix->qstat, 256, st));
   float *Q = static_cast<float *>(ix->qQ.p);
   float *Qp = static_cast<float *>(ix->qQp.p);
@@ -783,23 +828,10 @@ int query_impl(detlsh_index *ix, const float *queries, int64_t m, const int32_t 
     DL_TRY(dl::f32_to_bf16(Q, static_cast<__nv_bfloat16 *>(ix->qQh.p), m * (int64_t)d, st));
     Qh = static_cast<const __nv_bfloat16 *>(ix->qQh.p);
   }
-  // radius grid (and for a fixed r_min the condition-2 radii (c r_i)^2)
+  // radius grid (and for a fixed r_min the condition-2 radii)
   const bool fixed = qp->rmin_policy == DETLSH_RMIN_FIXED;
-  float Th[512];
-  if (fixed) {
-    const double r0 = qp->r_min, c = qp->c;
-    for (int i = 0; i < NLEV - 1; ++i) {
-      Th[i] = (float)(ix->eps2 * r0 * r0 * std::pow(c, 2.0 * (double)i));
-      const double cr = c * (r0 * std::pow(c, (double)i));
-      Th[256 + i] = (float)(cr * cr);
-    }
-    Th[NLEV - 1] = Th[255] = INFINITY;
-    Th[256 + NLEV - 1] = Th[511] = INFINITY;
-  } else {
-    level_table(ix->eps2, qp->c, Th);
-    Th[255] = INFINITY;
-    for (int i = 256; i < 512; ++i) Th[i] = INFINITY;
-  }
+  float Th[TABLE_FLOATS];
+  query_tables(ix, qp, Th);
   DL_CUDA(cudaMemcpyAsync(ix->qT.p, Th, sizeof Th, cudaMemcpyHostToDevice, st));
   int32_t *kd = nullptr;
   if (kq) {
@@ -1326,25 +1358,6 @@ int detlsh_query(const detlsh_index *ix, const float *queries, int64_t m, int32_
   return detlsh_query_ex(ix, queries, m, nullptr, k, &qp, nullptr, ids, dists);
 }
 
-namespace {
-// Radius grid (and for a fixed r_min the condition-2 radii) for qp, 512 floats.
-void query_tables(const detlsh_index *ix, const detlsh_query_params *qp, float Th[512]) {
-  if (qp->rmin_policy == DETLSH_RMIN_FIXED) {
-    const double r0 = qp->r_min, c = qp->c;
-    for (int i = 0; i < NLEV - 1; ++i) {
-      Th[i] = (float)(ix->eps2 * r0 * r0 * std::pow(c, 2.0 * (double)i));
-      const double cr = c * (r0 * std::pow(c, (double)i));
-      Th[256 + i] = (float)(cr * cr);
-    }
-    Th[NLEV - 1] = Th[255] = INFINITY;
-    Th[256 + NLEV - 1] = Th[511] = INFINITY;
-  } else {
-    level_table(ix->eps2, qp->c, Th);
-    Th[255] = INFINITY;
-    for (int i = 256; i < 512; ++i) Th[i] = INFINITY;
-  }
-}
-}  // namespace
 
 int detlsh_query_reserve(detlsh_index *ix, int64_t m_max, int32_t k_max,
                          const detlsh_query_params *qp) {
@@ -1364,9 +1377,9 @@ int detlsh_query_reserve(detlsh_index *ix, int64_t m_max, int32_t k_max,
     DL_TRY(grow(ix->aQh, sizeof(__nv_bfloat16) * (size_t)m_max * d, st));
   const uint32_t fb_cap = (uint32_t)std::max<int64_t>(1024, m_max * LK / 64);
   DL_TRY(grow(ix->afb, sizeof(uint2) * fb_cap, st));
-  DL_TRY(grow(ix->aT, sizeof(float) * 512, st));
+  DL_TRY(grow(ix->aT, sizeof(float) * TABLE_FLOATS, st));
   DL_TRY(grow(ix->astat, 256, st));
-  float Th[512];
+  float Th[TABLE_FLOATS];
   query_tables(ix, qp, Th);
   DL_CUDA(cudaMemcpyAsync(ix->aT.p, Th, sizeof Th, cudaMemcpyHostToDevice, st));
   const double tb = std::ceil(qp->beta * (double)ix->n);

@@ -124,6 +124,10 @@ struct QueryIndexView {
   int64_t max_leaves;        // max leaves of one tree
   int64_t max_leaf_size;
 };
+// Query tables: T[256] squared-radius grid; for a fixed r_min also
+// (c r_i)^2 rounded down [256] and up [256] and c r_i as three FP32 pieces
+// [256][3] (the exact test of condition 2 near the sphere).
+constexpr int TABLE_FLOATS = 256 * 6;
 // Arrays of a query kernel's per-CTA scratch slot (query_slot_offsets).
 constexpr int SLOT_ARRAYS = 13;
 struct QueryArgs {
@@ -135,7 +139,8 @@ struct QueryArgs {
   int k_max;
   int64_t tau_base;          // ceil(beta * n)
   const float *T;            // [255] radius grid
-  const float *Tc;           // [255] fp32((c r_i)^2) (fixed r_min, condition 2)
+  const float *Tc;           // fixed r_min, condition 2: the query tables from offset 256
+                             // (rounded-down (c r_i)^2 [256], rounded-up [256], pieces [3][256])
   int policy;                // DETLSH_RMIN_MAGIC / DETLSH_RMIN_FIXED / _CONTINUOUS
   int per_tree;              // 1: whole trees join S (no priority queue)
   float lg_eps2, inv_2lg_c;  // log2(eps^2), 1/(2 log2 c): level estimate before the exact fix-up

@@ -1078,6 +1078,71 @@ __device__ __forceinline__ void topk_select(int64_t n, int kk, Get get, QShared 
   }
 }
 
+// ---- exact test of condition 2 near the sphere ---------------------------
+// ||q - x||^2 <= R^2 decided without rounding: the square expands into
+// products of two floats, sum_j (q_j q_j + x_j x_j - 2 q_j x_j), and
+// R = R0 + R1 + R2 (three FP32 pieces, exact) gives R^2 as nine products;
+// every product is added exactly to a 640-bit fixed-point accumulator
+// (digit i weighs 2^(32 i - 298)) and the sign of the sum decides.  Only
+// candidates whose certified FP32 interval straddles a tested radius come
+// here, one thread each.
+struct Fixed640 {
+  long long dig[20];
+  __device__ void add(float a, float b, bool neg) {
+    const uint32_t ab = __float_as_uint(a), bb = __float_as_uint(b);
+    const uint32_t ae = (ab >> 23) & 0xffu, be = (bb >> 23) & 0xffu;
+    const uint64_t am = (ab & 0x7fffffu) | (ae ? 0x800000u : 0u);
+    const uint64_t bm = (bb & 0x7fffffu) | (be ? 0x800000u : 0u);
+    if (am == 0 || bm == 0) return;
+    const int pos = (int)(ae ? ae : 1u) + (int)(be ? be : 1u) - 2;  // weight of the product's bit 0: 2^(pos - 298)
+    const uint64_t prod = am * bm;                                   // < 2^48, exact
+    const int ci = pos >> 5, sh = pos & 31;
+    const uint64_t lo = prod << sh;
+    const uint64_t hi = sh ? (prod >> (64 - sh)) : 0ull;
+    const long long p0 = (long long)(lo & 0xffffffffull), p1 = (long long)(lo >> 32), p2 = (long long)hi;
+    if (neg != (((ab ^ bb) >> 31) != 0)) { dig[ci] -= p0; dig[ci + 1] -= p1; dig[ci + 2] -= p2; }
+    else { dig[ci] += p0; dig[ci + 1] += p1; dig[ci + 2] += p2; }
+  }
+  // -1, 0 or +1: the sign of the accumulated value
+  __device__ int sign() {
+    for (int i = 0; i < 19; ++i) {
+      const long long carry = dig[i] >> 32;  // floor division: digits end in [0, 2^32)
+      dig[i] -= carry * 4294967296ll;
+      dig[i + 1] += carry;
+    }
+    if (dig[19] < 0) return -1;
+    for (int i = 0; i < 20; ++i)
+      if (dig[i]) return 1;
+    return 0;
+  }
+};
+
+__device__ __noinline__ bool exact_within(const float *__restrict__ q, const float *__restrict__ x,
+                                          int d, const float *__restrict__ Rp) {
+  Fixed640 acc;
+  for (int i = 0; i < 20; ++i) acc.dig[i] = 0;
+  for (int j = 0; j < d; ++j) {
+    const float a = q[j], b = x[j];
+    acc.add(a, a, false);
+    acc.add(b, b, false);
+    acc.add(a, b, true);
+    acc.add(a, b, true);
+  }
+  for (int u = 0; u < 3; ++u)
+    for (int v = 0; v < 3; ++v) acc.add(Rp[u], Rp[v], true);
+  return acc.sign() <= 0;
+}
+
+// First index i of a nondecreasing table with x <= tab[i] (tab[254] = +inf).
+__device__ __forceinline__ int first_at_or_above(const float *tab, float x) {
+  int lo = 0, hi = NLEV - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (x <= tab[mid]) hi = mid; else lo = mid + 1;
+  }
+  return lo;
+}
+
 // ---- Alg. 5 from a fixed r_min, with condition 2 -------------------------
 // Radius index i stands for r_min c^i.  j1 = the first radius whose union
 // holds beta*n + k points (condition 1), if any.  Every radius before j1 is
@@ -1206,8 +1271,12 @@ __device__ __forceinline__ int64_t fixed_rmin_query(QCtx &c, int k) {
   QShared &sm = c.sm;
   const int64_t tau = c.tau;
   const uint32_t j1 = (sm.sel_g <= sm.jhi) ? (uint32_t)sm.sel_g : (uint32_t)NLEV;
-  float *Tc = reinterpret_cast<float *>(sm.bstart);  // free after the expansion
-  for (int i = threadIdx.x; i < 256; i += QT) Tc[i] = c.qa.Tc[i];
+  // rounded-down and rounded-up (c r_i)^2 in shared memory (both arrays are
+  // free after the expansion and the union counts)
+  float *Tcl = reinterpret_cast<float *>(sm.bstart);
+  float *Tch = reinterpret_cast<float *>(sm.H);
+  for (int i = threadIdx.x; i < 256; i += QT) { Tcl[i] = c.qa.Tc[i]; Tch[i] = c.qa.Tc[256 + i]; }
+  const float *Rp = c.qa.Tc + 512;
   const float *q = c.qa.Q + c.qi * ix.d;
   const uint32_t *cand = c.s.cand;
   int64_t ncA = 0;
@@ -1218,14 +1287,27 @@ __device__ __forceinline__ int64_t fixed_rmin_query(QCtx &c, int k) {
     // condition 2: first j < j1 with k points of max(level, covering radius) <= j
     sm.rh[threadIdx.x] = 0;
     __syncthreads();
+    // The covering radius of a candidate (first i with ||q - x|| <= c r_i):
+    // the FP32 key is within (2d + 16) u relative plus d 2^-148 of the exact
+    // squared distance, so from i1 (its upper end below the rounded-down
+    // (c r_i)^2) it is certainly within and before i0 (its lower end above
+    // the rounded-up one) certainly not; the radii in between are decided
+    // exactly.  Only max(covering radius, smallest level) < j1 matters.
+    const float fd = (float)ix.d;
+    const float g = __fmaf_ru(2.0f, fd, 16.0f) * 0x1p-24f;
     for (int64_t i = threadIdx.x; i < ncA; i += QT) {
       const float d2 = __uint_as_float(c.s.key[i]);
-      int lo = 0, hi = NLEV - 1;  // first radius index with d2 <= Tc (Tc[254] = inf)
-      while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (d2 <= Tc[mid]) hi = mid; else lo = mid + 1;
+      const float lo2 = fmaxf(__fsub_rd(__fmul_rd(d2, 1.0f - g), fd * 0x1p-148f), 0.0f);
+      const float hi2 = __fadd_ru(__fmul_ru(d2, __fadd_ru(1.0f, g)), fd * 0x1p-148f);
+      const int i1 = first_at_or_above(Tcl, hi2), i0 = first_at_or_above(Tch, lo2);
+      const uint32_t cmv = c.s.cm[i];
+      int cov = i1;
+      if (i0 < i1 && (uint32_t)i0 < j1 && cmv < (uint32_t)i1) {
+        const float *xp = ix.X + (int64_t)cand[i] * ix.d;
+        for (int r = i0; r < i1; ++r)
+          if (exact_within(q, xp, ix.d, Rp + 3 * r)) { cov = r; break; }
       }
-      const uint32_t b = max((uint32_t)lo, (uint32_t)c.s.cm[i]);
+      const uint32_t b = max((uint32_t)cov, cmv);
       if (b < j1) atomicAdd(&sm.rh[b], 1u);
     }
     __syncthreads();

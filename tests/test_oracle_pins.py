@@ -590,7 +590,7 @@ def test_dist2_le_special_cases():
     assert oracle.dist_le(q, q, 0.0) == 1                      # zero distance, zero radius
     assert oracle.dist_le(q, x, float("inf")) == 1
     assert oracle.dist_le(q, x, -1.0) == -1
-    assert oracle.dist_le(q, x, 1e300) == -1                   # beyond the FP32 pieces
+    assert oracle.dist_le(q, x, 1e300) == 1                    # beyond FP32: within
     # a radius whose square needs the low pieces: 1 + 2^-40 against a point at 1
     one = np.array([1.0], np.float32)
     assert oracle.dist_le(np.zeros(1, np.float32), one, 1.0 + 2.0 ** -40) == 1
