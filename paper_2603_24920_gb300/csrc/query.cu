@@ -399,31 +399,40 @@ __device__ __forceinline__ void expand_levels(QCtx &c) {
       const uint32_t Jnow = (uint32_t)sm.jhi;
       const uint32_t p0c = sm.cpos, p1c = min(nsel, p0c + (uint32_t)(EXP_RUNS * QW));
       // the level of the first block after this chunk (thread 0 needs it
-      // after the chunk) and each warp's later runs are fetched early
+      // after the chunk)
       int jnext = NLEV;
       if (threadIdx.x == 0 && p1c < nsel) jnext = (int)blev[c.s.border[ix.blk_off[t] + p1c]];
-#pragma unroll
-      for (int r = 1; r < EXP_RUNS; ++r) {
-        if (p0c + warp + r * QW < p1c) {
-          const int64_t l2 = (int64_t)c.s.border[ix.blk_off[t] + p0c + warp + r * QW] * LEAF_BLOCK + lane;
-          if (l2 < nl) {
-            asm volatile("prefetch.global.L1 [%0];" ::"l"(llo + l2));
-            asm volatile("prefetch.global.L1 [%0];" ::"l"(lhi + l2));
-          }
+      // This warp's runs of the chunk are p0c + warp + r QW, r < nr: their
+      // block ids in one load, then each run's boxes and leaf offsets are
+      // fetched one run ahead of the run being tested.
+      const int nr = p1c > p0c + (uint32_t)warp ? (int)((p1c - p0c - warp + QW - 1) / QW) : 0;
+      uint32_t myb = 0;
+      if (lane < nr) myb = c.s.border[ix.blk_off[t] + p0c + warp + lane * QW];
+      const float thr = sm.T[Jnow];
+      const uint32_t *lbeg = ix.leaf_begin + ix.leaf_off[t] + t;
+      uint4 nlo = make_uint4(0, 0, 0, 0), nhi = make_uint4(0, 0, 0, 0);
+      uint32_t nb0 = 0, nb1 = 0, nl_id = 0;
+      auto fetch = [&](int r) {  // run r into the "next" registers
+        nl_id = __shfl_sync(FULL, myb, r) * LEAF_BLOCK + lane;
+        if (nl_id < (uint32_t)nl) {
+          nlo = llo[nl_id];
+          nhi = lhi[nl_id];
+          nb0 = lbeg[nl_id];
+          nb1 = lbeg[nl_id + 1];
         }
-      }
-      for (uint32_t i = p0c + warp; i < p1c; i += QW) {
-        const uint32_t b = c.s.border[ix.blk_off[t] + i];
-        const int64_t l = (int64_t)b * LEAF_BLOCK + lane;
-        const bool valid = l < nl;
+      };
+      if (nr > 0) fetch(0);
+      for (int r = 0; r < nr; ++r) {
+        const uint4 blo = nlo, bhi = nhi;
+        const uint32_t l = nl_id, sz_all = nb1 - nb0;
+        if (r + 1 < nr) fetch(r + 1);
+        const bool valid = l < (uint32_t)nl;
         uint32_t lv = 255u;
         float lb = 0.0f;
         uint32_t sz = 0;
         // Half the dimensions first: when every leaf of the run is already
         // above T[Jnow] the rest is skipped (partial sums only grow).
-        const float thr = sm.T[Jnow];
-        uint4 blo = make_uint4(0, 0, 0, 0), bhi = make_uint4(0, 0, 0, 0);
-        if (valid) { blo = llo[l]; bhi = lhi[l]; lb = box_lb2_part<0, LUT_ROWS / 2>(c.lut, blo, bhi, 0.0f); }
+        if (valid) lb = box_lb2_part<0, LUT_ROWS / 2>(c.lut, blo, bhi, 0.0f);
         const bool more = __any_sync(FULL, valid && lb <= thr);
         if (valid && more) lb = box_lb2_part<LUT_ROWS / 2, LUT_ROWS>(c.lut, blo, bhi, lb);
         if (valid && more) {
@@ -432,7 +441,7 @@ __device__ __forceinline__ void expand_levels(QCtx &c) {
           // size and are listed; the rest read as level 255.
           if (lb <= thr) {
             lv = level_of(sm.T, lb, c.qa.lg_eps2, c.qa.inv_2lg_c);
-            sz = leaf_begin_of(ix, t, l + 1) - leaf_begin_of(ix, t, l);
+            sz = sz_all;
           }
         }
         const bool keep = valid && lv <= Jnow;
@@ -445,7 +454,7 @@ __device__ __forceinline__ void expand_levels(QCtx &c) {
         p0 = __shfl_sync(FULL, p0, 0);
         if (keep) {
           const uint32_t pos = (uint32_t)ix.leaf_off[t] + p0 + __popc(km & ((1u << lane) - 1u));
-          c.s.lleaf[pos] = (uint32_t)l;
+          c.s.lleaf[pos] = l;
           c.s.llb2[pos] = lb;
           c.s.llev[pos] = (uint8_t)lv;
         }
@@ -603,17 +612,26 @@ __device__ __forceinline__ void visit_points(QCtx &c, int t, Pred pred, Fn fn, b
         if (fl_pre[mid] <= i0) cur = mid; else hi = mid;
       }
     }
+    // Software pipeline: the point of step r + 1 is read from perm while
+    // step r runs, and its leaf ids (leaf_of, read by every caller) are
+    // prefetched into L1 after step r.
+    auto locate = [&](uint32_t i, uint32_t &p, uint32_t &ent, uint32_t &lev) {
+      while (fl_pre[cur + 1] <= i) ++cur;
+      p = permt[fl_beg[cur] + (i - fl_pre[cur])];
+      ent = fl_ent[cur];
+      lev = fl_lev[cur];
+    };
+    uint32_t pn = 0, entn = 0, levn = 255u;
+    bool validn = P > 0 && i0 < np;
+    if (validn) locate(i0, pn, entn, levn);
     for (uint32_t r = 0; r < P; ++r) {
-      const uint32_t i = i0 + r * 32u;
-      const bool valid = i < np;
-      uint32_t p = 0, ent = 0, lev = 255u;
-      if (valid) {
-        while (fl_pre[cur + 1] <= i) ++cur;
-        p = permt[fl_beg[cur] + (i - fl_pre[cur])];
-        ent = fl_ent[cur];
-        lev = fl_lev[cur];
-      }
+      const bool valid = validn;
+      const uint32_t p = pn, ent = entn, lev = levn;
+      const uint32_t inext = i0 + (r + 1) * 32u;
+      validn = r + 1 < P && inext < np;
+      if (validn) locate(inext, pn, entn, levn);
       fn(valid, p, ent, lev);
+      if (validn) asm volatile("prefetch.global.L1 [%0];" ::"l"(ix.leaf_of + (int64_t)pn * ix.L));
     }
     __syncthreads();
   }
