@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--beta", type=float, default=BETA)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the query kernel's default knobs")
     ap.add_argument("--profile-reps", type=int, default=0,
                     help="profiler driver: build + BF16 and FP32 query calls this many times, "
                          "nothing timed, no recall check, then exit")
@@ -161,13 +163,14 @@ def profiled_counters(kernel_src, summary):
             out["sha"] = line.split(":", 1)[1].split()[0]
         elif line.startswith("dram bytes per launch:"):
             out["dram_bytes"] = float(line.split(":", 1)[1])
+        # the first captured launch (the summary lists it first)
         elif line.startswith("smsp__issue_active.avg.pct_of_peak_sustained_active"):
-            out["issue_pct"] = float(line.split("=", 1)[1].split()[0])
+            out.setdefault("issue_pct", float(line.split("=", 1)[1].split()[0]))
         elif line.startswith("sm__pipe_tensor_cycles_active.avg.pct_of_peak_sustained_active"):
-            out["tensor_pct"] = float(line.split("=", 1)[1].split()[0])
+            out.setdefault("tensor_pct", float(line.split("=", 1)[1].split()[0]))
         elif line.startswith("gpu__time_duration.sum"):
             v, unit = line.split("=", 1)[1].split()[:2]
-            out["ncu_ms"] = float(v) * {"ms": 1.0, "us": 1e-3, "s": 1e3}.get(unit, 1.0)
+            out.setdefault("ncu_ms", float(v) * {"ms": 1.0, "us": 1e-3, "s": 1e3}.get(unit, 1.0))
     src = os.path.join(ROOT, "paper_2603_24920_gb300", "csrc", kernel_src)
     if "sha" not in out or "dram_bytes" not in out or not os.path.exists(src):
         return None
@@ -290,11 +293,15 @@ def run_gb300(args):
     # inherits the index structures the other (or the build) left in L2.
     flush = torch.empty(64 * 2 ** 20, dtype=torch.float32, device="cuda")
 
+    tuning = {}
+
     def step():
         e = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
         e[0].record(st)
         h = D.detlsh_build(Xd, **kw)
         e[1].record(st)
+        if tuning:
+            D.detlsh_set_tuning(h, **tuning)
         tb = D.detlsh_get_timings(h)
         flush.zero_()
         e[2].record(st)
@@ -326,6 +333,20 @@ def run_gb300(args):
                "overall_ratio_bf16": overall_ratio(db, gt_d, k),
                "overall_ratio_fp32": overall_ratio(d32, gt_d, k),
                "recall_queries": RECALL_QUERIES}
+
+    # the query kernel's knobs, chosen once on 2,048 of the queries (untimed;
+    # a cache file keyed by device and shape skips the search next time)
+    if not args.no_autotune:
+        h = D.detlsh_build(Xd, **kw)
+        t, cached = D.detlsh_autotune(h, Qd[:2048], k, beta=args.beta, c=C_RATIO,
+                                      precision=D.PREC_BF16_REFINE,
+                                      cache_path=os.path.join(tempfile.gettempdir(),
+                                                              "detlsh_tuning.txt"), stream=st)
+        D.detlsh_free(h)
+        tuning.update(t.as_dict())
+        tuning_info = dict(t.as_dict(), from_cache=cached, sample_queries=2048)
+    else:
+        tuning_info = dict(D.Tuning(0, 4, 512).as_dict(), from_cache=False, sample_queries=0)
 
     for _ in range(args.warmup):
         step()
@@ -409,6 +430,8 @@ def run_gb300(args):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         h = D.detlsh_build(Xh, L=4, K=16, N_r=256, seed=0, max_size=64)
+        if tuning:
+            D.detlsh_set_tuning(h, **tuning)
         t1 = time.perf_counter()
         D.detlsh_query_ex(h, Qh, k, beta=args.beta, c=C_RATIO, precision=D.PREC_BF16_REFINE,
                           ids=ids_h, dists=d_h)
@@ -434,6 +457,7 @@ def run_gb300(args):
         "quality": quality,
         "timings_ms": shares,
         "gpu_launches": int(launches),
+        "tuning": tuning_info,
         "roofline": roof_q,
         "roofline_build": roof_e,
         "e2e": {"value": m * world / e2e_max[0], "unit": "queries/s",
@@ -464,8 +488,17 @@ def run_profile(args):
     Xd = torch.from_numpy(X).cuda()
     Qd = torch.from_numpy(Q).cuda()
     st = torch.cuda.current_stream()
+    # the bench's tuning, from the same cache file (searched here only when
+    # the cache has no line for this device and shape)
+    h = D.detlsh_build(Xd, L=4, K=16, N_r=256, seed=0, max_size=64, stream=st)
+    tun, _ = D.detlsh_autotune(h, Qd[:2048], k, beta=args.beta, c=C_RATIO,
+                               precision=D.PREC_BF16_REFINE,
+                               cache_path=os.path.join(tempfile.gettempdir(), "detlsh_tuning.txt"),
+                               stream=st)
+    D.detlsh_free(h)
     for _ in range(args.profile_reps):
         h = D.detlsh_build(Xd, L=4, K=16, N_r=256, seed=0, max_size=64, stream=st)
+        D.detlsh_set_tuning(h, **tun.as_dict())
         D.detlsh_query_ex(h, Qd, k, beta=args.beta, c=C_RATIO, precision=D.PREC_BF16_REFINE,
                           stream=st)
         D.detlsh_query_ex(h, Qd, k, beta=args.beta, c=C_RATIO, precision=D.PREC_FP32, stream=st)

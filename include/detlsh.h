@@ -342,6 +342,45 @@ int detlsh_query_async(const detlsh_index *ix, const float *queries, int64_t m,
                        const int32_t *k_per_query, int32_t k_max, void *stream, int64_t *ids,
                        float *dists, int32_t *status);
 
+/*
+ * Tuning of the query kernel (batched serving; the paper has no counterpart:
+ * these knobs change how the work of Alg. 3 and Alg. 5 is scheduled on the
+ * GPU, never the candidate sets or the answers).
+ *   query_ctas_per_sm  persistent query CTAs per SM, 1..5; 0 = as many as fit
+ *                      (default 0, i.e. 5 on sm_103a)
+ *   expand_runs        runs of 32 leaves each warp tests per chunk of the
+ *                      level-ordered range-query expansion, 1..8 (default 4)
+ *   visit_chunk        listed leaves laid out per chunk of a flattened point
+ *                      visit, 64..512, a multiple of 64 (default 512)
+ * detlsh_set_tuning / detlsh_get_tuning set and read an index's knobs (used
+ * by detlsh_query, detlsh_query_ex, detlsh_query_candidates and batches
+ * enqueued by detlsh_query_async after the change; detlsh_query_noalloc
+ * keeps the defaults).  Errors: INVALID_ARG.
+ *
+ * detlsh_autotune chooses the knobs for this index on a sample of queries
+ * (m x d FP32, host or device; m >= 1) with the query parameters qp and k:
+ * starting from the defaults, each knob in turn takes the value with the
+ * smallest query-kernel time (CUDA events on stream, best of two runs after
+ * a warm-up run), the others held fixed.  The choice is stored in the index
+ * and returned in *out (nullable).  With cache_path non-NULL, a text file
+ * of one line per key "<key> <ctas_per_sm> <expand_runs> <visit_chunk> <ms>"
+ * is read first: the key names the device and the shape (d, L, K, N_r, n
+ * and beta*n + k to the nearest power of two, k, precision, r_min policy);
+ * a match is taken without measuring (*from_cache = 1), otherwise the
+ * search runs and appends its line.  Blocks until done.
+ * Errors: as detlsh_query_ex, and IO when the cache file cannot be written.
+ */
+typedef struct {
+    int32_t query_ctas_per_sm;
+    int32_t expand_runs;
+    int32_t visit_chunk;
+} detlsh_tuning;
+int detlsh_get_tuning(const detlsh_index *ix, detlsh_tuning *t);
+int detlsh_set_tuning(detlsh_index *ix, const detlsh_tuning *t);
+int detlsh_autotune(detlsh_index *ix, const float *queries, int64_t m, int32_t k,
+                    const detlsh_query_params *qp, const char *cache_path, void *stream,
+                    detlsh_tuning *out, int32_t *from_cache);
+
 /* (r,c)-ANN query, Alg. 4 of the paper (Sec. V-B), over the range query of
  * Alg. 3 as printed (Sec. IV-C): for each tree in order, nodes whose lower
  * bound exceeds r' = eps*r are pruned, a leaf whose upper bound is within r'

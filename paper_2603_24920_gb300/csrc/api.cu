@@ -39,6 +39,7 @@ struct detlsh_index {
   float *X = nullptr;
   __nv_bfloat16 *Xh = nullptr;
   float2 *Xn = nullptr;  // per row {||bf16(x)||^2, upper bound of ||x - bf16(x)||}
+  int bf16_exact = 0;    // every row equals its BF16 copy
   float *A = nullptr, *B = nullptr, *P = nullptr;
   uint8_t *codes = nullptr;
   uint32_t *sample = nullptr;
@@ -50,6 +51,7 @@ struct detlsh_index {
   int64_t sblk_off[17] = {0};
   cudaEvent_t ev[8] = {nullptr};
   detlsh_timings timings{};
+  detlsh_tuning tuning{0, 4, 512};  // query kernel knobs (detlsh_set_tuning / detlsh_autotune)
   std::vector<void *> owned;
   // per-index query buffers, reused across calls (guarded by qmu)
   std::mutex qmu;
@@ -309,7 +311,8 @@ __device__ __forceinline__ void bf16_row_terms(float x, __nv_bfloat16 b, float &
   res = __fmaf_ru(e, e, res);
 }
 
-__global__ void k_rows_to_bf16(const float *s, __nv_bfloat16 *h, float2 *nrm, int64_t n, int d) {
+__global__ void k_rows_to_bf16(const float *s, __nv_bfloat16 *h, float2 *nrm, int64_t n, int d,
+                               uint32_t *inexact) {
   const int lane = threadIdx.x & 31;
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
   const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -343,7 +346,10 @@ __global__ void k_rows_to_bf16(const float *s, __nv_bfloat16 *h, float2 *nrm, in
           acc[u] = __fadd_rn(acc[u], __shfl_xor_sync(0xffffffffu, acc[u], o));
           res[u] = __fadd_ru(res[u], __shfl_xor_sync(0xffffffffu, res[u], o));
         }
-        if (lane == 0 && r0 + u < n) nrm[r0 + u] = make_float2(acc[u], __fsqrt_ru(res[u]));
+        if (lane == 0 && r0 + u < n) {
+          nrm[r0 + u] = make_float2(acc[u], __fsqrt_ru(res[u]));
+          if (res[u] != 0.0f) atomicOr(inexact, 1u);
+        }
       }
     }
     return;
@@ -360,7 +366,10 @@ __global__ void k_rows_to_bf16(const float *s, __nv_bfloat16 *h, float2 *nrm, in
       acc = __fadd_rn(acc, __shfl_xor_sync(0xffffffffu, acc, o));
       res = __fadd_ru(res, __shfl_xor_sync(0xffffffffu, res, o));
     }
-    if (lane == 0) nrm[r] = make_float2(acc, __fsqrt_ru(res));
+    if (lane == 0) {
+      nrm[r] = make_float2(acc, __fsqrt_ru(res));
+      if (res != 0.0f) atomicOr(inexact, 1u);
+    }
   }
 }
 
@@ -529,16 +538,21 @@ int build_impl(detlsh_index *ix, const float *data, cudaStream_t st, const detls
     pp.ldP = LK;
     DL_TRY(project_rows(src, d, nullptr, n, d, ix->A, LK, 0, pp, st));
   }
+  uint32_t *inexact = nullptr;  // set when some row differs from its BF16 copy
+  DL_TRY(tp.get(&inexact, 1));
+  DL_CUDA(cudaMemsetAsync(inexact, 0, sizeof(uint32_t), st));
   if (p->keep_bf16) {
     DL_TRY(dalloc(ix, &ix->Xh, (size_t)n * d, st));
     DL_TRY(dalloc(ix, &ix->Xn, (size_t)n, st));
     k_rows_to_bf16<<<(unsigned)std::min<int64_t>(ceil_div(n, 8), 8192), 256, 0, st>>>(
-        src, ix->Xh, ix->Xn, n, d);
+        src, ix->Xh, ix->Xn, n, d, inexact);
     dl_count_launch();
     DL_CUDA(cudaGetLastError());
   }
   unsigned long long fbt = 0;
   DL_CUDA(cudaMemcpyAsync(&fbt, fb_total, sizeof fbt, cudaMemcpyDeviceToHost, st));
+  uint32_t hinexact = 1;
+  DL_CUDA(cudaMemcpyAsync(&hinexact, inexact, sizeof hinexact, cudaMemcpyDeviceToHost, st));
 
   // ---- DE-Trees (Alg. 2) ----
   // Trees are built G at a time (every kernel runs over G * n positions);
@@ -667,6 +681,7 @@ int build_impl(detlsh_index *ix, const float *data, cudaStream_t st, const detls
   DL_CUDA(cudaEventRecord(ix->ev[4], st));
   DL_CUDA(cudaStreamSynchronize(st));
   ix->fb_total = (int64_t)fbt;
+  ix->bf16_exact = (ix->Xh != nullptr && hinexact == 0) ? 1 : 0;
   ix->eps2 = eps2_of(K, L);
   ix->timings.build_ms = ev_ms(ix->ev[0], ix->ev[4]);
   ix->timings.sample_ms = ev_ms(ix->ev[0], ix->ev[1]);
@@ -715,6 +730,7 @@ QueryIndexView view_of(const detlsh_index *ix) {
   for (int t = 0; t <= 16; ++t) v.leaf_off[t] = t <= ix->L ? ix->leaf_off[t] : ix->leaf_off[ix->L];
   v.max_leaves = ix->max_leaves;
   v.max_leaf_size = ix->max_leaf;
+  v.bf16_exact = ix->bf16_exact;
   return v;
 }
 
@@ -856,6 +872,9 @@ int query_impl(detlsh_index *ix, const float *queries, int64_t m, const int32_t 
                      : (float)std::log2(ix->eps2);
   qa.inv_2lg_c = (float)(1.0 / (2.0 * std::log2(qp->c)));
   qa.precision = qp->precision; qa.rerank_mult = qp->rerank_mult;
+  qa.ctas_per_sm = ix->tuning.query_ctas_per_sm;
+  qa.expand_runs = ix->tuning.expand_runs;
+  qa.visit_chunk = ix->tuning.visit_chunk;
   qa.per_tree = qp->per_tree;
   qa.ids = static_cast<int64_t *>(ix->qids.p);
   qa.dists = static_cast<float *>(ix->qdists.p);
@@ -943,7 +962,7 @@ struct FileHeader {
   char magic[8];
   uint32_t version, bom, header_bytes, nsections;
   int64_t n;
-  int32_t d, L, K, N_r, bbits, M, box_mode, encoding, tree_group, has_bf16, has_proj, reserved;
+  int32_t d, L, K, N_r, bbits, M, box_mode, encoding, tree_group, has_bf16, has_proj, bf16_exact;
   uint64_t seed;
   double frac, eps2;
   int64_t m_sample, max_leaf, max_leaves, fb_total;
@@ -1046,6 +1065,7 @@ int check_header(const FileHeader &h) {
   if ((1 << h.bbits) != h.N_r) return DETLSH_ERR_FORMAT;
   if (h.has_bf16 != 0 && h.has_bf16 != 1) return DETLSH_ERR_FORMAT;
   if (h.has_proj != 0 && h.has_proj != 1) return DETLSH_ERR_FORMAT;
+  if (h.bf16_exact != 0 && h.bf16_exact != h.has_bf16) return DETLSH_ERR_FORMAT;
   if (h.m_sample < 0 || h.m_sample > h.n || (h.encoding == DETLSH_ENC_STATIC && h.m_sample != 0))
     return DETLSH_ERR_FORMAT;
   if (!(h.eps2 > 0.0) || !std::isfinite(h.eps2)) return DETLSH_ERR_FORMAT;
@@ -1076,7 +1096,7 @@ int save_impl(const detlsh_index *ix, const char *path, cudaStream_t st) {
   h.nsections = (uint32_t)secs.size();
   h.n = ix->n; h.d = ix->d; h.L = ix->L; h.K = ix->K; h.N_r = ix->N_r; h.bbits = ix->bbits;
   h.M = ix->M; h.box_mode = ix->box_mode; h.encoding = ix->encoding; h.tree_group = ix->tree_group;
-  h.has_bf16 = ix->Xh != nullptr; h.has_proj = ix->P != nullptr;
+  h.has_bf16 = ix->Xh != nullptr; h.has_proj = ix->P != nullptr; h.bf16_exact = ix->bf16_exact;
   h.seed = ix->seed; h.frac = ix->frac; h.eps2 = ix->eps2;
   h.m_sample = ix->m_sample; h.max_leaf = ix->max_leaf; h.max_leaves = ix->max_leaves;
   h.fb_total = ix->fb_total;
@@ -1151,6 +1171,7 @@ int load_impl(const char *path, cudaStream_t st, detlsh_index **out) {
   ix->tree_group = h.tree_group; ix->seed = h.seed; ix->frac = h.frac; ix->eps2 = h.eps2;
   ix->m_sample = h.m_sample; ix->max_leaf = h.max_leaf; ix->max_leaves = h.max_leaves;
   ix->fb_total = h.fb_total;
+  ix->bf16_exact = h.bf16_exact;
   for (int t = 0; t < 16; ++t) ix->nleaves[t] = h.nleaves[t];
   for (int t = 0; t <= 16; ++t) {
     ix->leaf_off[t] = h.leaf_off[t];
@@ -1205,6 +1226,113 @@ int load_impl(const char *path, cudaStream_t st, detlsh_index **out) {
   DL_TRY(ensure_events(ix));
   guard.ix = nullptr;
   *out = ix;
+  return DETLSH_OK;
+}
+
+// ---- tuning -----------------------------------------------------------------
+int check_tuning(const detlsh_tuning *t) {
+  if (!t) return DETLSH_ERR_INVALID_ARG;
+  if (t->query_ctas_per_sm < 0 || t->query_ctas_per_sm > 5) return DETLSH_ERR_INVALID_ARG;
+  if (t->expand_runs < 1 || t->expand_runs > 8) return DETLSH_ERR_INVALID_ARG;
+  if (t->visit_chunk < 64 || t->visit_chunk > 512 || (t->visit_chunk & 63)) return DETLSH_ERR_INVALID_ARG;
+  return DETLSH_OK;
+}
+
+// The cache key of a tuning: the device's name and the index and query shape
+// it was measured on (d, L, K, N_r, n and beta*n + k to the nearest power of
+// two, k, precision, r_min policy).
+std::string tuning_key(const detlsh_index *ix, int32_t k, const detlsh_query_params *qp) {
+  cudaDeviceProp prop;
+  std::string name = "device";
+  if (cudaGetDeviceProperties(&prop, ix->device) == cudaSuccess) name = prop.name;
+  else cudaGetLastError();
+  for (char &ch : name)
+    if (ch == ' ' || ch == '\t' || ch == '|') ch = '_';
+  const double tau = std::ceil(qp->beta * (double)ix->n) + k;
+  char buf[512];
+  snprintf(buf, sizeof buf, "%s|d%d|L%d|K%d|Nr%d|n2^%d|tau2^%d|k%d|p%d|r%d", name.c_str(), ix->d, ix->L,
+           ix->K, ix->N_r, (int)std::lround(std::log2((double)ix->n)),
+           (int)std::lround(std::log2(std::max(tau, 1.0))), k, qp->precision, qp->rmin_policy);
+  return buf;
+}
+
+// One text line per key: "<key> <ctas_per_sm> <expand_runs> <visit_chunk> <ms>".
+bool tuning_lookup(const char *path, const std::string &key, detlsh_tuning *t) {
+  FILE *f = fopen(path, "r");
+  if (!f) return false;
+  char line[1024];
+  bool found = false;
+  while (fgets(line, sizeof line, f)) {
+    char k[600];
+    detlsh_tuning c{};
+    double ms = 0.0;
+    if (sscanf(line, "%599s %d %d %d %lf", k, &c.query_ctas_per_sm, &c.expand_runs, &c.visit_chunk,
+               &ms) == 5 &&
+        key == k && check_tuning(&c) == DETLSH_OK) {
+      *t = c;  // the last matching line wins
+      found = true;
+    }
+  }
+  fclose(f);
+  return found;
+}
+
+int autotune_impl(detlsh_index *ix, const float *queries, int64_t m, int32_t k,
+                  const detlsh_query_params *qp, const char *cache_path, cudaStream_t st,
+                  detlsh_tuning *out, int32_t *from_cache) {
+  DL_TRY(validate_query(ix, m, k, qp));
+  if (m < 1) return DETLSH_ERR_INVALID_ARG;
+  const std::string key = tuning_key(ix, k, qp);
+  detlsh_tuning best = ix->tuning;
+  if (from_cache) *from_cache = 0;
+  if (cache_path && tuning_lookup(cache_path, key, &best)) {
+    ix->tuning = best;
+    if (out) *out = best;
+    if (from_cache) *from_cache = 1;
+    return DETLSH_OK;
+  }
+  // Coordinate descent from the hand-picked defaults: each knob in turn
+  // takes the value with the smallest query-kernel time (CUDA events, the
+  // better of two runs after a warm-up run) on the sample, the others fixed.
+  auto measure = [&](const detlsh_tuning &t, float *ms) -> int {
+    ix->tuning = t;
+    float b = INFINITY;
+    for (int rep = 0; rep < 3; ++rep) {
+      DL_TRY(query_impl(ix, queries, m, nullptr, k, qp, st, nullptr, nullptr, 0, nullptr, nullptr,
+                        nullptr, nullptr));
+      if (rep > 0) b = std::min(b, ix->timings.query_kernel_ms);
+    }
+    *ms = b;
+    return DETLSH_OK;
+  };
+  detlsh_tuning cur{0, 4, 512};
+  float cur_ms = 0.0f;
+  DL_TRY(measure(cur, &cur_ms));
+  const int ctas[] = {3, 4, 0};
+  const int runs[] = {2, 3, 4, 6, 8};
+  const int chunks[] = {128, 256, 512};
+  for (int knob = 0; knob < 3; ++knob) {
+    const int *vals = knob == 0 ? ctas : knob == 1 ? runs : chunks;
+    const int nv = knob == 0 ? 3 : knob == 1 ? 5 : 3;
+    for (int i = 0; i < nv; ++i) {
+      detlsh_tuning t = cur;
+      int &slot = knob == 0 ? t.query_ctas_per_sm : knob == 1 ? t.expand_runs : t.visit_chunk;
+      if (slot == vals[i]) continue;
+      slot = vals[i];
+      float ms = 0.0f;
+      DL_TRY(measure(t, &ms));
+      if (ms < cur_ms) { cur = t; cur_ms = ms; }
+    }
+  }
+  ix->tuning = cur;
+  if (out) *out = cur;
+  if (cache_path) {
+    FILE *f = fopen(cache_path, "a");
+    if (!f) return DETLSH_ERR_IO;
+    fprintf(f, "%s %d %d %d %.4f\n", key.c_str(), cur.query_ctas_per_sm, cur.expand_runs,
+            cur.visit_chunk, cur_ms);
+    if (fclose(f) != 0) return DETLSH_ERR_IO;
+  }
   return DETLSH_OK;
 }
 
@@ -1448,6 +1576,9 @@ int detlsh_query_async(const detlsh_index *cix, const float *queries, int64_t m,
                        : (float)std::log2(ix->eps2);
     qa.inv_2lg_c = (float)(1.0 / (2.0 * std::log2(P.qp.c)));
     qa.precision = P.qp.precision; qa.rerank_mult = P.qp.rerank_mult;
+    qa.ctas_per_sm = ix->tuning.query_ctas_per_sm;
+    qa.expand_runs = ix->tuning.expand_runs;
+    qa.visit_chunk = ix->tuning.visit_chunk;
     qa.per_tree = P.qp.per_tree;
     qa.ids = ids; qa.dists = dists;
     qa.cand_cap = P.cap;
@@ -1696,6 +1827,32 @@ int detlsh_load(const char *path, void *stream, detlsh_index **out) {
   if (!path || !out) return DETLSH_ERR_INVALID_ARG;
   *out = nullptr;
   return load_impl(path, static_cast<cudaStream_t>(stream), out);
+}
+
+int detlsh_get_tuning(const detlsh_index *ix, detlsh_tuning *t) {
+  if (!ix || !t) return DETLSH_ERR_INVALID_ARG;
+  *t = ix->tuning;
+  return DETLSH_OK;
+}
+
+int detlsh_set_tuning(detlsh_index *ix, const detlsh_tuning *t) {
+  if (!ix) return DETLSH_ERR_INVALID_ARG;
+  DL_TRY(check_tuning(t));
+  std::lock_guard<std::mutex> g(ix->qmu);
+  ix->tuning = *t;
+  return DETLSH_OK;
+}
+
+int detlsh_autotune(detlsh_index *ix, const float *queries, int64_t m, int32_t k,
+                    const detlsh_query_params *qp, const char *cache_path, void *stream,
+                    detlsh_tuning *out, int32_t *from_cache) {
+  if (!ix || !queries) return DETLSH_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> g(ix->qmu);
+  const detlsh_tuning keep = ix->tuning;
+  const int s = autotune_impl(ix, queries, m, k, qp, cache_path, static_cast<cudaStream_t>(stream),
+                              out, from_cache);
+  if (s != DETLSH_OK) ix->tuning = keep;
+  return s;
 }
 
 }  // extern "C"

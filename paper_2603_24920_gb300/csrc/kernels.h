@@ -123,6 +123,7 @@ struct QueryIndexView {
   int64_t sblk_off[17];      // super-block index offset of each tree (prefix)
   int64_t max_leaves;        // max leaves of one tree
   int64_t max_leaf_size;
+  int bf16_exact;            // 1: every row equals its BF16 copy (no residuals)
 };
 // Query tables: T[256] squared-radius grid; for a fixed r_min also
 // (c r_i)^2 rounded down [256] and up [256] and c r_i as three FP32 pieces
@@ -162,7 +163,12 @@ struct QueryArgs {
   int nslots;
   uint32_t *work_counter;
   int *err;
-  unsigned long long *stats;  // [4]: candidates, leaves expanded, hull blocks, points visited
+  unsigned long long *stats;  // [5]: candidates, leaves expanded, hull blocks, points visited,
+                              // rows re-ranked
+  // tuning knobs (detlsh_tuning; the defaults are the hand-picked values)
+  int ctas_per_sm = 0;        // persistent CTAs per SM (0: as many as fit)
+  int expand_runs = 4;        // leaf runs per warp per chunk of the level-ordered expansion, 1..8
+  int visit_chunk = 512;      // listed leaves per chunk of a flattened visit, 64..512
 };
 size_t query_slot_bytes(const QueryIndexView &ix, int64_t cand_cap, int rerank_cap);
 void query_slot_offsets(const QueryIndexView &ix, int64_t cand_cap, int64_t off[SLOT_ARRAYS + 1]);

@@ -38,8 +38,9 @@ constexpr int QT = 256;
 constexpr int QW = QT / 32;
 constexpr int KMAX = 1024;
 constexpr int RR_MAX = 4096;  // re-rank pool of the BF16 path
-constexpr int FLC = 512;      // listed leaves per chunk of a flattened visit
-constexpr int EXP_RUNS = 4;   // leaf runs per warp per chunk of the level-ordered expansion
+constexpr int FLC = 512;      // largest chunk of listed leaves of a flattened visit
+// (the chunk itself and the leaf runs per warp per expansion chunk are the
+// tuning knobs qa.visit_chunk and qa.expand_runs)
 
 struct Slot {
   unsigned long long *lev;  // [total_leaves] (epoch << 8) | level of expanded leaves
@@ -397,7 +398,7 @@ __device__ __forceinline__ void expand_levels(QCtx &c) {
     const uint32_t nsel = sm.bstart[255];
     while (true) {
       const uint32_t Jnow = (uint32_t)sm.jhi;
-      const uint32_t p0c = sm.cpos, p1c = min(nsel, p0c + (uint32_t)(EXP_RUNS * QW));
+      const uint32_t p0c = sm.cpos, p1c = min(nsel, p0c + (uint32_t)(c.qa.expand_runs * QW));
       // the level of the first block after this chunk (thread 0 needs it
       // after the chunk)
       int jnext = NLEV;
@@ -557,13 +558,14 @@ __device__ __forceinline__ void visit_points(QCtx &c, int t, Pred pred, Fn fn, b
   uint8_t *fl_lev = reinterpret_cast<uint8_t *>(sm.topk_key + 520);
   uint32_t *fl_beg = sm.topk_id;
   uint32_t *fl_ent = sm.topk_id + FLC;
-  for (int64_t e0 = 0; e0 < nlist; e0 += FLC) {
+  const int fc = c.qa.visit_chunk;  // <= FLC
+  for (int64_t e0 = 0; e0 < nlist; e0 += fc) {
     uint32_t q[2], sz[2], bg[2];
 #pragma unroll
     for (int u = 0; u < 2; ++u) {
       const int64_t e = e0 + threadIdx.x * 2 + u;
       q[u] = 0; sz[u] = 0; bg[u] = 0;
-      if (e < nlist && pred(e)) {
+      if ((int)threadIdx.x * 2 + u < fc && e < nlist && pred(e)) {
         const uint32_t leaf = c.s.lleaf[lo0 + e];
         bg[u] = leaf_begin_of(ix, t, leaf);
         sz[u] = leaf_begin_of(ix, t, leaf + 1) - bg[u];
@@ -873,9 +875,11 @@ __device__ __forceinline__ void dist_fp32_rows(const QueryIndexView &ix, const f
   }
 }
 
-template <class GetId>
+// Rows ids[0..nrows) (ids == nullptr: rows 0..nrows) -- one instantiation
+// for every caller keeps the kernel's code small.
 __device__ __forceinline__ void dist_fp32(const QueryIndexView &ix, const float *q, int64_t nrows,
-                                          GetId get_id, uint32_t *out) {
+                                          const uint32_t *ids, uint32_t *out) {
+  auto get_id = [ids](int64_t i) { return ids ? ids[i] : (uint32_t)i; };
   const int d = ix.d;
   if ((d & 3) == 0) {
     const int nch = d >> 2;
@@ -890,11 +894,22 @@ __device__ __forceinline__ void dist_fp32(const QueryIndexView &ix, const float 
   __syncthreads();
 }
 
-__device__ __forceinline__ void distances_fp32(QCtx &c, int64_t nc, bool allpts) {
-  const uint32_t *cand = c.s.cand;
-  dist_fp32(c.ix, c.qa.Q + c.qi * c.ix.d, nc,
-            [&](int64_t i) { return allpts ? (uint32_t)i : cand[i]; }, c.s.key);
-}
+// (key, id) of item i from two arrays (ids == nullptr: id = i).
+struct ArrGet {
+  const uint32_t *keys, *ids;
+  __device__ void operator()(int64_t i, uint32_t &key, uint32_t &id) const {
+    key = keys[i];
+    id = ids ? ids[i] : (uint32_t)i;
+  }
+};
+// key of item i from an array, weight 1.
+struct ArrKey {
+  const uint32_t *keys;
+  __device__ void operator()(int64_t i, uint32_t &key, uint32_t &w) const {
+    key = keys[i];
+    w = 1u;
+  }
+};
 
 // One m16n8k16 BF16 tensor-core product with FP32 accumulation (c += a b).
 __device__ __forceinline__ void mma_bf16_16816(float (&c)[4], uint32_t a0, uint32_t a1,
@@ -971,6 +986,13 @@ __device__ __forceinline__ void distances_bf16(QCtx &c, int64_t nc, bool allpts,
   }
   __syncthreads();
   const float qn = c.sm.qn, qr = c.sm.qr;
+  // exact BF16 rows and query: the interval needs no square roots and is
+  // formed in the tile loop (constants as in bf16_interval)
+  const bool fast = ix.bf16_exact && qr == 0.0f;
+  const float fdd = (float)d;
+  const float ecs = __fmaf_ru(6.0f, fdd, 16.0f) * 0x1p-24f, eabs = fdd * 0x1p-125f;
+  const float gg = __fmaf_ru(2.0f, fdd, 16.0f) * 0x1p-24f;
+  const float glo = 1.0f - gg, ghi = __fadd_ru(1.0f, gg), dabs = fdd * 0x1p-148f;
   const int nblk = (d + 15) >> 4;
   auto id_of = [&](int64_t r) -> uint32_t {
     return (lane < 16 && r + lane < nc) ? (allpts ? (uint32_t)(r + lane) : c.s.cand[r + lane]) : 0u;
@@ -1019,13 +1041,25 @@ __device__ __forceinline__ void distances_bf16(QCtx &c, int64_t nc, bool allpts,
         if (!(h ? ok1 : ok0)) continue;
         const float sc = __fadd_rn(__fadd_rn(qn, h ? xn1 : xn0), -2.0f * acc[2 * h]);
         const int64_t r = r0 + g + 8 * h;
-        if (cert) c.s.hkey[r] = __float_as_uint(sc);  // the interval follows below
-        else c.s.key[r] = __float_as_uint(nonneg_bits(fmaxf(sc, 0.0f)));
+        if (cert && fast) {
+          // rows and query exact in BF16 (no residuals): the interval of
+          // bf16_interval without its square roots
+          const float e = __fmaf_ru(ecs, __fadd_ru(qn, h ? xn1 : xn0), eabs);
+          const float lo = fmaxf(__fsub_rd(__fmul_rd(fmaxf(__fsub_rd(sc, e), 0.0f), glo), dabs), 0.0f);
+          const float hi = __fadd_ru(__fmul_ru(__fadd_ru(sc, e), ghi), dabs);
+          const bool okv = lo <= hi;  // false on NaN
+          c.s.key[r] = okv ? __float_as_uint(nonneg_bits(lo)) : 0u;
+          c.s.hkey[r] = okv ? __float_as_uint(hi) : 0x7f800000u;
+        } else if (cert) {
+          c.s.hkey[r] = __float_as_uint(sc);  // the interval follows below
+        } else {
+          c.s.key[r] = __float_as_uint(nonneg_bits(fmaxf(sc, 0.0f)));
+        }
       }
     }
   }
   __syncthreads();
-  if (cert) {  // a second pass keeps the tile loop's registers free
+  if (cert && !fast) {  // a second pass keeps the tile loop's registers free
     for (int64_t i = threadIdx.x; i < nc; i += QT) {
       const uint32_t p = allpts ? (uint32_t)i : c.s.cand[i];
       float lo, hi;
@@ -1301,7 +1335,7 @@ __device__ __forceinline__ int64_t fixed_rmin_query(QCtx &c, int k) {
   if (j1 > 0) {
     collect_below<LC>(c, j1 - 1);
     ncA = min((int64_t)sm.ncand, c.qa.cand_cap);
-    dist_fp32(ix, q, ncA, [&](int64_t i) { return cand[i]; }, c.s.key);
+    dist_fp32(ix, q, ncA, cand, c.s.key);
     // condition 2: first j < j1 with k points of max(level, covering radius) <= j
     sm.rh[threadIdx.x] = 0;
     __syncthreads();
@@ -1372,7 +1406,7 @@ __device__ __forceinline__ int64_t fixed_rmin_query(QCtx &c, int k) {
   cut_and_collect_fixed<LC>(c, j1);
   const int64_t nc = min((int64_t)sm.ncand, c.qa.cand_cap);
   if (sm.ncand > c.qa.cand_cap && threadIdx.x == 0) atomicExch(c.qa.err, (int)DETLSH_ERR_CAPACITY);
-  dist_fp32(ix, q, nc - ncA, [&](int64_t i) { return cand[ncA + i]; }, c.s.key + ncA);
+  dist_fp32(ix, q, nc - ncA, cand + ncA, c.s.key + ncA);
   auto get_s = [&](int64_t i, uint32_t &key, uint32_t &id) { key = c.s.key[i]; id = cand[i]; };
   topk_select(nc, k, get_s, sm);
   return nc;
@@ -1679,82 +1713,66 @@ __global__ void __launch_bounds__(QT, 5) k_query(QueryIndexView ix, QueryArgs qa
     }
     if (!fixed_done) {
       // verification and top-k
-      auto get_s = [&](int64_t i, uint32_t &key, uint32_t &id) {
-        key = s.key[i];
-        id = allpts ? (uint32_t)i : s.cand[i];
-      };
-      auto get_r = [&](int64_t i, uint32_t &key, uint32_t &id) { key = s.rkey[i]; id = s.rid[i]; };
-      if (qa.precision == DETLSH_PREC_BF16_REFINE && qa.rerank_mult == 0) {
-        // certified pool: every candidate whose interval starts at or below
-        // the k-th smallest interval end T.  The k candidates with the
-        // smallest ends have FP32 keys <= T, so each of the FP32 path's top k
-        // has key <= T and lies in the pool: re-ranking the pool in FP32
-        // gives the FP32 path's answer exactly.
-        distances_bf16(c, nc, allpts, true);
-        auto gh = [&](int64_t i, uint32_t &kk2, uint32_t &w) { kk2 = s.hkey[i]; w = 1u; };
-        block_select(nc, gh, (uint32_t)k, sm);
+      // Every branch ends in one FP32 distance pass over (rows, ids) and one
+      // top-k over its keys: single call sites keep the kernel's code small.
+      const uint32_t *cid = allpts ? nullptr : s.cand;
+      int64_t rows = nc;
+      const uint32_t *rids = cid;
+      uint32_t *rkeys = s.key;
+      if (qa.precision == DETLSH_PREC_BF16_REFINE) {
+        distances_bf16(c, nc, allpts, qa.rerank_mult == 0);
+        uint32_t need;
+        const uint32_t *selk;
+        if (qa.rerank_mult == 0) {
+          // certified pool: every candidate whose interval starts at or
+          // below the k-th smallest interval end T.  The k candidates with
+          // the smallest ends have FP32 keys <= T, so each of the FP32
+          // path's top k has key <= T and lies in the pool: re-ranking the
+          // pool in FP32 gives the FP32 path's answer exactly.
+          need = (uint32_t)k;
+          selk = s.hkey;
+        } else {  // the rerank_mult * k best scores
+          int64_t R = min((int64_t)qa.rerank_mult * k, (int64_t)RR_MAX);
+          need = (uint32_t)max(min(R, nc), (int64_t)k);
+          selk = s.key;
+        }
+        block_select(nc, ArrKey{selk}, need, sm);
         const uint32_t T = sm.sel_v;
-        if (threadIdx.x == 0) sm.nres = 0;
-        __syncthreads();
-        for (int64_t i0 = 0; i0 < nc; i0 += QT) {  // uniform trip count: warp collectives inside
-          const int64_t i = i0 + threadIdx.x;
-          const bool in = i < nc && s.key[i] <= T;
-          const unsigned bm = __ballot_sync(FULL, in);
-          uint32_t pos0 = 0;
-          if ((threadIdx.x & 31) == 0 && bm) pos0 = atomicAdd(&sm.nres, (uint32_t)__popc(bm));
-          pos0 = __shfl_sync(FULL, pos0, 0) + __popc(bm & ((1u << (threadIdx.x & 31)) - 1u));
-          if (in && pos0 < RR_MAX) s.rid[pos0] = allpts ? (uint32_t)i : s.cand[i];
-        }
-        __syncthreads();
-        const int64_t np = sm.nres;
-        if (threadIdx.x == 0 && qa.stats) atomicAdd(&qa.stats[4], (unsigned long long)np);
-        if (np <= RR_MAX) {
-          dist_fp32(ix, qa.Q + qi * ix.d, np, [&](int64_t i) { return s.rid[i]; }, s.rkey);
-          topk_select(np, k, get_r, sm);
-        } else {  // a pool beyond the re-rank buffers: FP32 over every candidate
-          distances_fp32(c, nc, allpts);
-          topk_select(nc, k, get_s, sm);
-        }
-      } else if (qa.precision == DETLSH_PREC_BF16_REFINE) {
-        distances_bf16(c, nc, allpts, false);
-        int R = qa.rerank_mult * k;
-        if (R > RR_MAX) R = RR_MAX;
-        if (R > nc) R = (int)nc;
-        if (R < k) R = k;
-        // pick the R best BF16 scores (unsorted is enough): threshold select
-        auto gk = [&](int64_t i, uint32_t &kk2, uint32_t &w) { uint32_t id; get_s(i, kk2, id); w = 1u; };
-        block_select(nc, gk, (uint32_t)R, sm);
-        const uint32_t vk = sm.sel_v, below = sm.sel_below;
+        // fixed pool: ties at T by smaller id
         uint32_t idcut = 0xffffffffu;
-        if ((uint32_t)R - below < sm.sel_at) {
+        if (qa.rerank_mult != 0 && need - sm.sel_below < sm.sel_at) {
           auto gi = [&](int64_t i, uint32_t &kk2, uint32_t &w) {
-            uint32_t key, id;
-            get_s(i, key, id);
-            kk2 = id;
-            w = key == vk ? 1u : 0u;
+            kk2 = cid ? cid[i] : (uint32_t)i;
+            w = s.key[i] == T ? 1u : 0u;
           };
-          block_select(nc, gi, (uint32_t)R - below, sm);
+          block_select(nc, gi, need - sm.sel_below, sm);
           idcut = sm.sel_v;
         }
         if (threadIdx.x == 0) sm.nres = 0;
         __syncthreads();
-        for (int64_t i = threadIdx.x; i < nc; i += QT) {
-          uint32_t key, id;
-          get_s(i, key, id);
-          if (key < vk || (key == vk && id <= idcut)) {
-            const uint32_t pos = atomicAdd(&sm.nres, 1u);
-            if (pos < RR_MAX) s.rid[pos] = id;
+        for (int64_t i0 = 0; i0 < nc; i0 += QT) {  // uniform trip count: warp collectives inside
+          const int64_t i = i0 + threadIdx.x;
+          bool in = false;
+          uint32_t id = 0;
+          if (i < nc) {
+            const uint32_t kv = s.key[i];
+            id = cid ? cid[i] : (uint32_t)i;
+            in = kv < T || (kv == T && id <= idcut);
           }
+          const unsigned bm = __ballot_sync(FULL, in);
+          uint32_t pos0 = 0;
+          if ((threadIdx.x & 31) == 0 && bm) pos0 = atomicAdd(&sm.nres, (uint32_t)__popc(bm));
+          pos0 = __shfl_sync(FULL, pos0, 0) + __popc(bm & ((1u << (threadIdx.x & 31)) - 1u));
+          if (in && pos0 < RR_MAX) s.rid[pos0] = id;
         }
         __syncthreads();
-        if (threadIdx.x == 0 && qa.stats) atomicAdd(&qa.stats[4], (unsigned long long)R);
-        // exact FP32 distances of the re-rank pool
-        dist_fp32(ix, qa.Q + qi * ix.d, R, [&](int64_t i) { return s.rid[i]; }, s.rkey);
-        topk_select(R, k, get_r, sm);
-      } else {
-        distances_fp32(c, nc, allpts);
-        topk_select(nc, k, get_s, sm);
+        const int64_t np = sm.nres;
+        if (threadIdx.x == 0 && qa.stats) atomicAdd(&qa.stats[4], (unsigned long long)min(np, nc));
+        if (np <= RR_MAX) { rows = np; rids = s.rid; rkeys = s.rkey; }
+        // else a pool beyond the re-rank buffers: FP32 over every candidate
       }
+      dist_fp32(ix, qa.Q + qi * ix.d, rows, rids, rkeys);
+      topk_select(rows, k, ArrGet{rkeys, rids}, sm);
     }
     if (threadIdx.x == 0 && qa.stats) atomicAdd(&qa.stats[0], (unsigned long long)nc);
     for (int r = threadIdx.x; r < qa.k_max; r += QT) {
@@ -1800,7 +1818,13 @@ int run_queries(const QueryIndexView &ix, const QueryArgs &qa, cudaStream_t st) 
                                                     : k_query<DETLSH_RMIN_MAGIC>;
   DL_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   DL_CUDA(cudaMemsetAsync(qa.work_counter, 0, sizeof(uint32_t), st));
-  const int grid = (int)std::min<int64_t>(qa.nslots, qa.m);
+  int grid = (int)std::min<int64_t>(qa.nslots, qa.m);
+  if (qa.ctas_per_sm > 0) {  // tuned: at most this many CTAs per SM
+    int dev = 0, sms = 0;
+    DL_CUDA(cudaGetDevice(&dev));
+    DL_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    grid = std::max(1, std::min(grid, sms * qa.ctas_per_sm));
+  }
   kern<<<grid, QT, smem, st>>>(ix, qa);
   dl_count_launch();
   DL_CUDA(cudaGetLastError());

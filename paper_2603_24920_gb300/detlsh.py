@@ -50,6 +50,14 @@ class Info(C.Structure):
                 ("projection_fallbacks", C.c_int64), ("encoding", C.c_int32)]
 
 
+class Tuning(C.Structure):
+    _fields_ = [("query_ctas_per_sm", C.c_int32), ("expand_runs", C.c_int32),
+                ("visit_chunk", C.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class Timings(C.Structure):
     _fields_ = [("build_ms", C.c_float), ("sample_ms", C.c_float),
                 ("breakpoints_ms", C.c_float), ("encode_ms", C.c_float),
@@ -79,6 +87,10 @@ SIGNATURES = [
     ("detlsh_save", C.c_int, [_P, C.c_char_p, _P]),
     ("detlsh_load", C.c_int, [C.c_char_p, _P, C.POINTER(_P)]),
     ("detlsh_free", C.c_int, [_P]),
+    ("detlsh_get_tuning", C.c_int, [_P, C.POINTER(Tuning)]),
+    ("detlsh_set_tuning", C.c_int, [_P, C.POINTER(Tuning)]),
+    ("detlsh_autotune", C.c_int, [_P, _P, _I64, _I32, C.POINTER(QueryParams), C.c_char_p, _P,
+                                  C.POINTER(Tuning), C.POINTER(C.c_int32)]),
     ("detlsh_status_string", C.c_char_p, [C.c_int]),
     ("detlsh_get_info", C.c_int, [_P, C.POINTER(Info)]),
     ("detlsh_get_projection_matrix", C.c_int, [_P, _P]),
@@ -184,6 +196,30 @@ def detlsh_load(path, stream=None):
     h = C.c_void_p()
     _check(lib().detlsh_load(os.fsencode(path), _stream_ptr(stream), C.byref(h)), "detlsh_load")
     return h
+
+
+def detlsh_get_tuning(h):
+    t = Tuning()
+    _check(lib().detlsh_get_tuning(h, C.byref(t)), "detlsh_get_tuning")
+    return t
+
+
+def detlsh_set_tuning(h, query_ctas_per_sm=0, expand_runs=4, visit_chunk=512):
+    t = Tuning(query_ctas_per_sm, expand_runs, visit_chunk)
+    _check(lib().detlsh_set_tuning(h, C.byref(t)), "detlsh_set_tuning")
+
+
+def detlsh_autotune(h, queries, k, beta=0.1, c=1.5, precision=PREC_FP32, rerank_mult=0,
+                    cache_path=None, stream=None):
+    """Choose the query kernel's knobs on a sample of queries; returns
+    (Tuning, from_cache)."""
+    qp = detlsh_default_query_params()
+    qp.beta, qp.c, qp.precision, qp.rerank_mult = beta, c, precision, rerank_mult
+    t, fc = Tuning(), C.c_int32(0)
+    path = os.fsencode(cache_path) if cache_path is not None else None
+    _check(lib().detlsh_autotune(h, _ptr(queries), queries.shape[0], k, C.byref(qp), path,
+                                 _stream_ptr(stream), C.byref(t), C.byref(fc)), "detlsh_autotune")
+    return t, bool(fc.value)
 
 
 def detlsh_free(h):

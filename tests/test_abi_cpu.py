@@ -77,6 +77,10 @@ def test_query_and_accessors_reject_null_index(lib):
     assert lib.detlsh_get_info(None, None) == -1
     assert lib.detlsh_get_tree(None, 0, None, None, None, None, None, None) == -1
     assert lib.detlsh_free(None) == 0
+    t = D.Tuning(0, 4, 512)
+    assert lib.detlsh_get_tuning(None, C.byref(t)) == -1
+    assert lib.detlsh_set_tuning(None, C.byref(t)) == -1
+    assert lib.detlsh_autotune(None, D._ptr(Q), 2, 3, None, None, None, None, None) == -1
 
 
 def test_no_device_is_reported(lib):
@@ -97,7 +101,7 @@ def test_struct_layouts_match_the_header(tmp_path):
     if cc is None:
         pytest.skip("no host C compiler")
     pairs = [("detlsh_build_params", D.BuildParams), ("detlsh_query_params", D.QueryParams),
-             ("detlsh_info", D.Info), ("detlsh_timings", D.Timings)]
+             ("detlsh_info", D.Info), ("detlsh_timings", D.Timings), ("detlsh_tuning", D.Tuning)]
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "detlsh.h"', "int main(void) {"]
     for cname, py in pairs:
         lines.append('  printf("%%s size %%zu\\n", "%s", sizeof(%s));' % (cname, cname))

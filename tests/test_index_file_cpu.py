@@ -16,7 +16,7 @@ class Header(C.Structure):
                  ("header_bytes", C.c_uint32), ("nsections", C.c_uint32), ("n", C.c_int64)]
                 + [(f, C.c_int32) for f in ("d", "L", "K", "N_r", "bbits", "M", "box_mode",
                                             "encoding", "tree_group", "has_bf16", "has_proj",
-                                            "reserved")]
+                                            "bf16_exact")]
                 + [("seed", C.c_uint64), ("frac", C.c_double), ("eps2", C.c_double)]
                 + [(f, C.c_int64) for f in ("m_sample", "max_leaf", "max_leaves", "fb_total")]
                 + [("nleaves", C.c_int64 * 16), ("leaf_off", C.c_int64 * 17),
@@ -69,7 +69,7 @@ def test_missing_and_foreign_files(lib, tmp_path):
 
 @pytest.mark.parametrize("field,value", [("version", 2), ("bom", 0x04030201), ("N_r", 24),
                                          ("bbits", 5), ("L", 0), ("m_sample", 1001),
-                                         ("max_leaves", 69), ("eps2", -1.0)])
+                                         ("max_leaves", 69), ("eps2", -1.0), ("bf16_exact", 2)])
 def test_bad_header_fields(lib, tmp_path, field, value):
     h = _valid_header()
     setattr(h, field, value)
