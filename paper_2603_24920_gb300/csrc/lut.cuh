@@ -12,25 +12,22 @@ namespace dl {
 constexpr int LUT_STRIDE = 257;
 constexpr int LUT_ROWS = 16;
 
-// Fills the table of tree t (whole block; the caller synchronises).  The
-// entries are spread evenly over the threads, eight loads in flight each.
+// Fills the table of tree t (whole block; the caller synchronises).  A
+// thread takes table columns z (one region boundary, all rows): coalesced
+// reads of B along z, no index division, eight loads in flight.
 __device__ __forceinline__ void build_lut(float *lut, const float *B, const float *qpt, int t,
                                           int K, int NR1) {
-  constexpr int TOTAL = LUT_ROWS * LUT_STRIDE;
-  for (int base = 0; base < TOTAL; base += 8 * (int)blockDim.x) {
-    float v[8];
+  for (int z = threadIdx.x; z < LUT_STRIDE; z += blockDim.x) {
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int idx = base + u * (int)blockDim.x + (int)threadIdx.x;
-      const int j = idx / LUT_STRIDE, z = idx - j * LUT_STRIDE;
-      v[u] = 0.0f;
-      if (idx < TOTAL && j < K && z < NR1)
-        v[u] = __fsub_rn(B[(int64_t)(t * K + j) * NR1 + z], qpt[j]);
-    }
+    for (int j0 = 0; j0 < LUT_ROWS; j0 += 8) {
+      float v[8];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int idx = base + u * (int)blockDim.x + (int)threadIdx.x;
-      if (idx < TOTAL) lut[idx] = v[u];
+      for (int u = 0; u < 8; ++u) {
+        const int j = j0 + u;
+        v[u] = (j < K && z < NR1) ? __fsub_rn(B[(int64_t)(t * K + j) * NR1 + z], qpt[j]) : 0.0f;
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) lut[(j0 + u) * LUT_STRIDE + z] = v[u];
     }
   }
 }

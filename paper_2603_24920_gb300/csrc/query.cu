@@ -194,11 +194,13 @@ __device__ __forceinline__ void warp_first_crossing(const uint32_t *bins, uint64
 // Block-wide weighted radix select over 32-bit keys: finds the smallest key
 // v with W(key <= v) >= need, where item i has (key_i, weight_i) from get(i)
 // (weight 0 = absent).  Returns v in sm.sel_v, W(key < v) in sm.sel_below and
-// W(key == v) in sm.sel_at.
+// W(key == v) in sm.sel_at.  With last_shift = 8 s > 0 it stops after the top
+// 32 - 8 s bits: sel_v is then that prefix of v with the low bits zero.
 template <class Get>
-__device__ __forceinline__ void block_select(int64_t N, Get get, uint32_t need, QShared &sm) {
+__device__ __forceinline__ void block_select(int64_t N, Get get, uint32_t need, QShared &sm,
+                                             int last_shift = 0) {
   uint32_t prefix = 0, below = 0;
-  for (int shift = 24; shift >= 0; shift -= 8) {
+  for (int shift = 24; shift >= last_shift; shift -= 8) {
     sm.rh[threadIdx.x] = 0;
     __syncthreads();
     const uint32_t hmask = (shift == 24) ? 0u : (0xffffffffu << (shift + 8));
@@ -207,8 +209,7 @@ __device__ __forceinline__ void block_select(int64_t N, Get get, uint32_t need, 
       get(i, k, w);
       if (w && (k & hmask) == (prefix & hmask)) atomicAdd(&sm.rh[(k >> shift) & 255u], w);
     }
-    __syncthreads();
-    warp_first_crossing(sm.rh, below, need, &sm.sel_g, &sm.sel_bf);
+    __syncthreads();    warp_first_crossing(sm.rh, below, need, &sm.sel_g, &sm.sel_bf);
     __syncthreads();
     prefix |= (uint32_t)sm.sel_g << shift;
     below = (uint32_t)sm.sel_bf;
@@ -348,10 +349,17 @@ __device__ __forceinline__ void expand_levels(QCtx &c) {
       const int64_t i = b0 + threadIdx.x;
       const int64_t b = i < nscan ? blk(i) : nb;
       uint32_t lv = 255u;
+      // level <= J0 exactly when LB^2 <= T[J0]; only those need their level.
+      // Half the dimensions first: a warp whose hulls are all beyond T[J0]
+      // by then skips the rest (partial sums only grow).
+      const float thr0 = sm.T[J0];
+      uint4 hl = make_uint4(0, 0, 0, 0), hh = make_uint4(0, 0, 0, 0);
+      float lb = 0.0f;
+      if (b < nb) { hl = hlo[b]; hh = hhi[b]; lb = box_lb2_part<0, LUT_ROWS / 2>(c.lut, hl, hh, 0.0f); }
+      if (__any_sync(FULL, b < nb && lb <= thr0) && b < nb)
+        lb = box_lb2_part<LUT_ROWS / 2, LUT_ROWS>(c.lut, hl, hh, lb);
       if (b < nb) {
-        // level <= J0 exactly when LB^2 <= T[J0]; only those need their level
-        const float lb = box_lb2(c.lut, hlo[b], hhi[b]);
-        if (lb <= sm.T[J0]) lv = level_of(sm.T, lb, c.qa.lg_eps2, c.qa.inv_2lg_c);
+        if (lb <= thr0) lv = level_of(sm.T, lb, c.qa.lg_eps2, c.qa.inv_2lg_c);
         blev[b] = (uint8_t)lv;
         if (lv <= J0) atomicMin(&sm.jcur, (int)lv);
       }
@@ -984,6 +992,13 @@ __device__ __forceinline__ void distances_bf16(QCtx &c, int64_t nc, bool allpts,
     }
     if (lane == 0) { c.sm.qn = a; c.sm.qr = __fsqrt_ru(r); }
   }
+  // the query's B fragments come from shared memory (the top-k arrays are
+  // free until the top-k step) when the row fits
+  if (2 * d <= 4 * KMAX) {
+    for (int i = threadIdx.x; i < d / 2; i += QT)
+      c.sm.topk_key[i] = reinterpret_cast<const uint32_t *>(qh)[i];
+    qh = reinterpret_cast<const __nv_bfloat16 *>(c.sm.topk_key);
+  }
   __syncthreads();
   const float qn = c.sm.qn, qr = c.sm.qr;
   // exact BF16 rows and query: the interval needs no square roots and is
@@ -1013,17 +1028,27 @@ __device__ __forceinline__ void distances_bf16(QCtx &c, int64_t nc, bool allpts,
     const __nv_bfloat16 *qt = qh + 4 * t;
     float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
     int b = 0;
-    for (; b + 4 <= nblk && (b + 4) * 16 <= d; b += 4) {  // four k-blocks: loads first
-      uint2 xa[4], xb[4], qv[4];
+    // Pairs of k-blocks by 16-byte loads: in a 32-element chunk lane t holds
+    // elements 8t..8t+7, the first four in the first block's positions
+    // {2t, 2t+1, 2t+8, 2t+9}, the next four in the second block's (the same
+    // bijection for the rows and the query), two chunks per step.
+    const __nv_bfloat16 *x0w = ix.Xh + (int64_t)p0 * d + 8 * t;
+    const __nv_bfloat16 *x1w = ix.Xh + (int64_t)p1 * d + 8 * t;
+    const __nv_bfloat16 *qw = qh + 8 * t;
+    for (; (b + 4) * 16 <= d; b += 4) {
+      uint4 xa[2], xb[2], qv[2];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int e = (b + u) * 16;
-        xa[u] = ok0 ? *reinterpret_cast<const uint2 *>(x0 + e) : make_uint2(0u, 0u);
-        xb[u] = ok1 ? *reinterpret_cast<const uint2 *>(x1 + e) : make_uint2(0u, 0u);
-        qv[u] = g == 0 ? *reinterpret_cast<const uint2 *>(qt + e) : make_uint2(0u, 0u);
+      for (int u = 0; u < 2; ++u) {
+        const int e = (b + 2 * u) * 16;
+        xa[u] = ok0 ? *reinterpret_cast<const uint4 *>(x0w + e) : make_uint4(0u, 0u, 0u, 0u);
+        xb[u] = ok1 ? *reinterpret_cast<const uint4 *>(x1w + e) : make_uint4(0u, 0u, 0u, 0u);
+        qv[u] = g == 0 ? *reinterpret_cast<const uint4 *>(qw + e) : make_uint4(0u, 0u, 0u, 0u);
       }
 #pragma unroll
-      for (int u = 0; u < 4; ++u) mma_bf16_16816(acc, xa[u].x, xb[u].x, xa[u].y, xb[u].y, qv[u].x, qv[u].y);
+      for (int u = 0; u < 2; ++u) {
+        mma_bf16_16816(acc, xa[u].x, xb[u].x, xa[u].y, xb[u].y, qv[u].x, qv[u].y);
+        mma_bf16_16816(acc, xa[u].z, xb[u].z, xa[u].w, xb[u].w, qv[u].z, qv[u].w);
+      }
     }
     for (; b < nblk; ++b) {
       const int e = b * 16;
@@ -1725,10 +1750,10 @@ __global__ void __launch_bounds__(QT, 5) k_query(QueryIndexView ix, QueryArgs qa
         const uint32_t *selk;
         if (qa.rerank_mult == 0) {
           // certified pool: every candidate whose interval starts at or
-          // below the k-th smallest interval end T.  The k candidates with
-          // the smallest ends have FP32 keys <= T, so each of the FP32
-          // path's top k has key <= T and lies in the pool: re-ranking the
-          // pool in FP32 gives the FP32 path's answer exactly.
+          // below T, some bound at or above the k-th smallest interval end.
+          // The k candidates with the smallest ends have FP32 keys <= T, so
+          // each of the FP32 path's top k has key <= T and lies in the pool:
+          // re-ranking the pool in FP32 gives the FP32 path's answer exactly.
           need = (uint32_t)k;
           selk = s.hkey;
         } else {  // the rerank_mult * k best scores
@@ -1736,8 +1761,11 @@ __global__ void __launch_bounds__(QT, 5) k_query(QueryIndexView ix, QueryArgs qa
           need = (uint32_t)max(min(R, nc), (int64_t)k);
           selk = s.key;
         }
-        block_select(nc, ArrKey{selk}, need, sm);
-        const uint32_t T = sm.sel_v;
+        // the certified pool only needs some T >= the k-th end: its top 24
+        // bits (three radix passes) with the low byte all ones
+        const bool cert = qa.rerank_mult == 0;
+        block_select(nc, ArrKey{selk}, need, sm, cert ? 8 : 0);
+        const uint32_t T = cert ? (sm.sel_v | 0xffu) : sm.sel_v;
         // fixed pool: ties at T by smaller id
         uint32_t idcut = 0xffffffffu;
         if (qa.rerank_mult != 0 && need - sm.sel_below < sm.sel_at) {
