@@ -915,15 +915,19 @@ int query_impl(detlsh_index *ix, const float *queries, int64_t m, const int32_t 
   qa.work_counter = counter;
   qa.err = err;
   qa.stats = stats;
-  int e = check_err(err, st);  // projection status (non-finite queries)
-  if (e) return e;
+  // No host wait between the projections and the query kernel: a status set
+  // by the projections (NaN/Inf in a query) makes the kernel return at once,
+  // and one read of the status block after it reports either.
   DL_CUDA(cudaEventRecord(ix->ev[6], st));
   DL_TRY(run_queries(v, qa, st));
   DL_CUDA(cudaEventRecord(ix->ev[7], st));
-  e = check_err(err, st);
+  unsigned long long hblk[32];  // the 256-byte status block: err at 0, stats from byte 64
+  DL_CUDA(cudaMemcpyAsync(hblk, ix->qstat.p, sizeof hblk, cudaMemcpyDeviceToHost, st));
+  DL_CUDA(cudaStreamSynchronize(st));
+  int e = 0;
+  memcpy(&e, hblk, sizeof e);
   if (e) return e;
-  unsigned long long hs[5];
-  DL_CUDA(cudaMemcpy(hs, stats, sizeof hs, cudaMemcpyDeviceToHost));
+  const unsigned long long *hs = hblk + 8;
   ix->timings.query_project_ms = ev_ms(ix->ev[5], ix->ev[6]);
   ix->timings.query_kernel_ms = ev_ms(ix->ev[6], ix->ev[7]);
   ix->timings.query_ms = ev_ms(ix->ev[5], ix->ev[7]);

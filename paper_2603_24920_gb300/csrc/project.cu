@@ -154,58 +154,63 @@ __device__ __forceinline__ uint32_t region_smem(const float *Bs, float y) {
   return pos;
 }
 
-template <int MODE>
+// RI = rows per thread (16 RI rows per tile): RI = 1 gives small batches
+// (queries) four times as many CTAs.
+template <int MODE, int RI>
 __global__ void __launch_bounds__(PJ_THREADS)
 k_project(const float *__restrict__ X, int64_t ldx, const uint32_t *__restrict__ rows,
           int64_t nrows, int d, const float *__restrict__ A, int LK, int W, ProjArgs o) {
   // W = columns per tile, a multiple of K so that a tile never splits a tree
-  __shared__ float Xs[PJ_ROWS][PJ_KC + 1];
+  constexpr int ROWS = 16 * RI;
+  __shared__ float Xs[ROWS][PJ_KC + 1];
   __shared__ float As[PJ_COLS][PJ_KC + 1];
 
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
-  const int64_t row0 = (int64_t)blockIdx.x * PJ_ROWS;
+  const int64_t row0 = (int64_t)blockIdx.x * ROWS;
   const int col0 = blockIdx.y * W;
   const int LKt = min(LK, col0 + W);  // end of this tile's columns
 
-  float p[4][4], s[4][4], e[4][4];
+  float p[RI][4], s[RI][4], e[RI][4];
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < RI; ++i)
 #pragma unroll
     for (int j = 0; j < 4; ++j) p[i][j] = s[i][j] = e[i][j] = 0.0f;
 
   for (int kc = 0; kc < d; kc += PJ_KC) {
     const int kmax = min(PJ_KC, d - kc);
     __syncthreads();
-    for (int idx = tid; idx < PJ_ROWS * PJ_KC; idx += PJ_THREADS) {
+    for (int idx = tid; idx < PJ_COLS * PJ_KC; idx += PJ_THREADS) {
       const int r = idx / PJ_KC, c = idx % PJ_KC;
-      const int64_t rr = row0 + r;
-      float v = 0.0f;
-      if (rr < nrows && c < kmax) {
-        const int64_t src = rows ? (int64_t)rows[rr] : rr;
-        v = X[src * ldx + kc + c];
+      if (r < ROWS) {
+        const int64_t rr = row0 + r;
+        float v = 0.0f;
+        if (rr < nrows && c < kmax) {
+          const int64_t src = rows ? (int64_t)rows[rr] : rr;
+          v = X[src * ldx + kc + c];
+        }
+        Xs[r][c] = v;
       }
-      Xs[r][c] = v;
       const int oc = col0 + r;
       As[r][c] = (oc < LKt && c < kmax) ? A[(int64_t)oc * d + kc + c] : 0.0f;
     }
     __syncthreads();
 #pragma unroll 2
     for (int kk = 0; kk < kmax; ++kk) {
-      float xv[4], av[4];
+      float xv[RI], av[4];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) xv[i] = Xs[ty + 16 * i][kk];
+      for (int i = 0; i < RI; ++i) xv[i] = Xs[ty + 16 * i][kk];
 #pragma unroll
       for (int j = 0; j < 4; ++j) av[j] = As[tx + 16 * j][kk];
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+      for (int i = 0; i < RI; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) dot2_step(p[i][j], s[i][j], e[i][j], xv[i], av[j]);
     }
   }
 
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
+  for (int i = 0; i < RI; ++i) {
     const int64_t rr = row0 + ty + 16 * i;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
@@ -616,8 +621,18 @@ static int project_impl(const float *X, int64_t ldx, const uint32_t *rows, int64
     dl_count_launch();
     DL_CUDA(cudaGetLastError());
   } else {
-    dim3 grid((unsigned)ceil_div(nrows, PJ_ROWS), (unsigned)ceil_div(LK, W));
-    k_project<MODE><<<grid, PJ_THREADS, 0, st>>>(X, ldx, rows, nrows, d, A, LK, W, o);
+    // batches below two waves of 64-row tiles take 16-row tiles
+    int dev = 0, sms = 0;
+    DL_CUDA(cudaGetDevice(&dev));
+    DL_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int64_t ny = ceil_div(LK, W);
+    if (ceil_div(nrows, PJ_ROWS) * ny < 2 * (int64_t)sms) {
+      dim3 grid((unsigned)ceil_div(nrows, 16), (unsigned)ny);
+      k_project<MODE, 1><<<grid, PJ_THREADS, 0, st>>>(X, ldx, rows, nrows, d, A, LK, W, o);
+    } else {
+      dim3 grid((unsigned)ceil_div(nrows, PJ_ROWS), (unsigned)ny);
+      k_project<MODE, PJ_ROWS / 16><<<grid, PJ_THREADS, 0, st>>>(X, ldx, rows, nrows, d, A, LK, W, o);
+    }
     dl_count_launch();
     DL_CUDA(cudaGetLastError());
   }

@@ -1640,8 +1640,14 @@ __global__ void __launch_bounds__(QT, 5) k_query(QueryIndexView ix, QueryArgs qa
   s.cm = base + qa.off[11];
   s.hkey = reinterpret_cast<uint32_t *>(base + qa.off[12]);
   for (int i = threadIdx.x; i < 256; i += QT) sm.T[i] = i < NLEV ? qa.T[i] : __int_as_float(0x7f800000);
-  if (threadIdx.x == 0) { sm.n_blocks = 0; sm.n_leaves = 0; sm.n_visit = 0; sm.jguess = NLEV - 1; }
+  if (threadIdx.x == 0) {
+    sm.n_blocks = 0; sm.n_leaves = 0; sm.n_visit = 0; sm.jguess = NLEV - 1;
+    // a status already set (a query projection found NaN/Inf) stops the
+    // launch before any query: the caller reports it
+    sm.stop = *(volatile int *)qa.err;
+  }
   __syncthreads();
+  if (sm.stop) return;
 
   while (true) {
     if (threadIdx.x == 0) sm.qi = atomicAdd(qa.work_counter, 1u);
