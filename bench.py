@@ -213,12 +213,18 @@ def cpu_baseline(X, Q, k, beta, nq=64):
     t0 = time.perf_counter()
     ix.query_batch(Q[:nq], k, beta=beta, c=C_RATIO)
     tq = time.perf_counter() - t0
+    # the literal single-thread oracle on a smaller sample
+    n1 = max(nq // 8, 1)
+    t0 = time.perf_counter()
+    ix.query_batch(Q[:n1], k, beta=beta, c=C_RATIO, nthreads=1)
+    t1 = time.perf_counter() - t0
     cores = os.cpu_count()
     return {"value": nq / tq, "unit": "queries/s", "cores": cores, "kind": "oracle",
+            "single_thread_value": n1 / t1,
             "build_mpts_s": X.shape[0] / tb / 1e6,
             "sample": "oracle index built on all %d points (%.1f s), then %d of the %d queries "
-                      "(OpenMP over queries, %d threads, %.1f s)"
-                      % (X.shape[0], tb, nq, Q.shape[0], cores, tq)}
+                      "(OpenMP over queries, %d threads, %.1f s) and %d queries on one thread "
+                      "(%.1f s)" % (X.shape[0], tb, nq, Q.shape[0], cores, tq, n1, t1)}
 
 
 def run_reference(args):
