@@ -49,6 +49,8 @@ struct detlsh_index {
   int64_t blk_off[17] = {0};
   uint8_t *sblk_lo = nullptr, *sblk_hi = nullptr;  // hulls of LEAF_BLOCK-hull runs
   int64_t sblk_off[17] = {0};
+  uint8_t *tblk_lo = nullptr, *tblk_hi = nullptr;  // hulls of LEAF_BLOCK super-hull runs
+  int64_t tblk_off[17] = {0};
   cudaEvent_t ev[8] = {nullptr};
   detlsh_timings timings{};
   detlsh_tuning tuning{0, 4, 512};  // query kernel knobs (detlsh_set_tuning / detlsh_autotune)
@@ -418,6 +420,26 @@ int validate_build(int64_t n, int32_t d, const detlsh_build_params *p) {
   return DETLSH_OK;
 }
 
+// Third hull level: hulls of runs of LEAF_BLOCK super-hulls (LEAF_BLOCK^3
+// leaves each), so that the range query's pruned scan starts from n/32768
+// boxes per tree.  Derived from the super-hulls, so a loaded index rebuilds it.
+int build_top_hulls(detlsh_index *ix, cudaStream_t st) {
+  const int L = ix->L;
+  int64_t tt = 0;
+  for (int t = 0; t < L; ++t) {
+    ix->tblk_off[t] = tt;
+    tt += ceil_div(ix->sblk_off[t + 1] - ix->sblk_off[t], LEAF_BLOCK);
+  }
+  for (int t = L; t <= 16; ++t) ix->tblk_off[t] = tt;
+  DL_TRY(dalloc(ix, &ix->tblk_lo, (size_t)tt * 16, st));
+  DL_TRY(dalloc(ix, &ix->tblk_hi, (size_t)tt * 16, st));
+  HullSet h;
+  h.L = L;
+  for (int t = 0; t <= L; ++t) { h.in_off[t] = ix->sblk_off[t]; h.out_off[t] = ix->tblk_off[t]; }
+  for (int t = 0; t < L; ++t) h.cnt[t] = ix->sblk_off[t + 1] - ix->sblk_off[t];
+  return block_hulls(ix->sblk_lo, ix->sblk_hi, h, ix->tblk_lo, ix->tblk_hi, st);
+}
+
 int build_impl(detlsh_index *ix, const float *data, cudaStream_t st, const detlsh_build_params *p) {
   const int64_t n = ix->n;
   const int d = ix->d, L = ix->L, K = ix->K, LK = ix->LK, N_r = ix->N_r;
@@ -678,6 +700,7 @@ int build_impl(detlsh_index *ix, const float *data, cudaStream_t st, const detls
     for (int t = 0; t < L; ++t) h.cnt[t] = ix->blk_off[t + 1] - ix->blk_off[t];
     DL_TRY(block_hulls(ix->blk_lo, ix->blk_hi, h, ix->sblk_lo, ix->sblk_hi, st));
   }
+  DL_TRY(build_top_hulls(ix, st));
   DL_CUDA(cudaEventRecord(ix->ev[4], st));
   DL_CUDA(cudaStreamSynchronize(st));
   ix->fb_total = (int64_t)fbt;
@@ -727,6 +750,8 @@ QueryIndexView view_of(const detlsh_index *ix) {
   for (int t = 0; t <= 16; ++t) v.blk_off[t] = ix->blk_off[t];
   v.sblk_lo = ix->sblk_lo; v.sblk_hi = ix->sblk_hi;
   for (int t = 0; t <= 16; ++t) v.sblk_off[t] = ix->sblk_off[t];
+  v.tblk_lo = ix->tblk_lo; v.tblk_hi = ix->tblk_hi;
+  for (int t = 0; t <= 16; ++t) v.tblk_off[t] = ix->tblk_off[t];
   for (int t = 0; t <= 16; ++t) v.leaf_off[t] = t <= ix->L ? ix->leaf_off[t] : ix->leaf_off[ix->L];
   v.max_leaves = ix->max_leaves;
   v.max_leaf_size = ix->max_leaf;
@@ -1226,6 +1251,7 @@ int load_impl(const char *path, cudaStream_t st, detlsh_index **out) {
   uint64_t want = 0;
   if (fread(&want, sizeof want, 1, f.f) != 1 || want != cs.h) return DETLSH_ERR_FORMAT;
   if (fgetc(f.f) != EOF) return DETLSH_ERR_FORMAT;  // trailing bytes
+  DL_TRY(build_top_hulls(ix, st));
   DL_CUDA(cudaStreamSynchronize(st));
   DL_TRY(ensure_events(ix));
   guard.ix = nullptr;

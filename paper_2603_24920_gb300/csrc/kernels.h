@@ -121,6 +121,8 @@ struct QueryIndexView {
   int64_t blk_off[17];       // block index offset of each tree (prefix)
   const uint8_t *sblk_lo, *sblk_hi;  // [total_sblocks][16] hulls of LEAF_BLOCK blocks
   int64_t sblk_off[17];      // super-block index offset of each tree (prefix)
+  const uint8_t *tblk_lo, *tblk_hi;  // [total_tblocks][16] hulls of LEAF_BLOCK super-blocks
+  int64_t tblk_off[17];      // top-block index offset of each tree (prefix)
   int64_t max_leaves;        // max leaves of one tree
   int64_t max_leaf_size;
   int bf16_exact;            // 1: every row equals its BF16 copy (no residuals)
@@ -130,7 +132,7 @@ struct QueryIndexView {
 // [256][3] (the exact test of condition 2 near the sphere).
 constexpr int TABLE_FLOATS = 256 * 6;
 // Arrays of a query kernel's per-CTA scratch slot (query_slot_offsets).
-constexpr int SLOT_ARRAYS = 13;
+constexpr int SLOT_ARRAYS = 14;
 struct QueryArgs {
   const float *Q;            // [m][d]
   const __nv_bfloat16 *Qh;   // [m][d] (bf16 path)

@@ -56,6 +56,7 @@ struct Slot {
   uint32_t *rkey;   // [RR_MAX]
   uint8_t *cm;      // [cap] smallest level of each candidate (fixed r_min)
   uint32_t *hkey;   // [cap] upper ends of the certified BF16 intervals
+  uint32_t *guess;  // [1] this slot's last final bound + 1 (0: none), kept across launches
 };
 
 __host__ __device__ inline int64_t align_up(int64_t v, int64_t a) { return (v + a - 1) / a * a; }
@@ -63,7 +64,7 @@ __host__ __device__ inline int64_t align_up(int64_t v, int64_t a) { return (v + 
 static void slot_layout(const QueryIndexView &ix, int64_t cap, int64_t off[SLOT_ARRAYS + 1]) {
   const int64_t tl = ix.leaf_off[ix.L], tb = ix.blk_off[ix.L];
   const int64_t sz[SLOT_ARRAYS] = {8 * tl, tb, 4 * tb, 4 * tl, 4 * tl, tl, 4 * ix.max_leaves,
-                                   4 * cap, 4 * cap, 4 * RR_MAX, 4 * RR_MAX, cap, 4 * cap};
+                                   4 * cap, 4 * cap, 4 * RR_MAX, 4 * RR_MAX, cap, 4 * cap, 4};
   int64_t o = 0;
   for (int i = 0; i < SLOT_ARRAYS; ++i) { off[i] = o; o = align_up(o + sz[i], 256); }
   off[SLOT_ARRAYS] = o;
@@ -335,10 +336,33 @@ __device__ __forceinline__ void expand_levels(QCtx &c) {
       const int64_t ns = ix.sblk_off[t + 1] - ix.sblk_off[t];
       const uint4 *slo = reinterpret_cast<const uint4 *>(ix.sblk_lo) + ix.sblk_off[t];
       const uint4 *shi = reinterpret_cast<const uint4 *>(ix.sblk_hi) + ix.sblk_off[t];
-      if (threadIdx.x == 0) { sm.cpos = 0; sm.n_blocks += (unsigned long long)ns; }
+      // With more than TOP_MIN super-hulls (about a million leaves per tree)
+      // the top hulls (runs of LEAF_BLOCK super-hulls) are tested first and
+      // only the super-hulls of the listed ones follow; their list goes after
+      // the top list (both fit: nt + ns <= 2 ns <= the tree's leaves).
+      constexpr int64_t TOP_MIN = (int64_t)LEAF_BLOCK * LEAF_BLOCK;
+      const bool two = ns > TOP_MIN;
+      int64_t nsc = ns;
+      uint32_t *tlist = c.s.cval;
+      if (two) {
+        const int64_t nt = ix.tblk_off[t + 1] - ix.tblk_off[t];
+        const uint4 *tlo = reinterpret_cast<const uint4 *>(ix.tblk_lo) + ix.tblk_off[t];
+        const uint4 *thi = reinterpret_cast<const uint4 *>(ix.tblk_hi) + ix.tblk_off[t];
+        if (threadIdx.x == 0) { sm.cpos = 0; sm.n_blocks += (unsigned long long)nt; }
+        __syncthreads();
+        for (int64_t u = threadIdx.x; u < nt; u += QT)
+          if (box_lb2(c.lut, tlo[u], thi[u]) <= sm.T[J0]) tlist[atomicAdd(&sm.cpos, 1u)] = (uint32_t)u;
+        __syncthreads();
+        nsc = (int64_t)sm.cpos * LEAF_BLOCK;
+        slist = c.s.cval + nt;
+        __syncthreads();  // every thread has read cpos
+      }
+      if (threadIdx.x == 0) { sm.cpos = 0; sm.n_blocks += (unsigned long long)nsc; }
       __syncthreads();
-      for (int64_t u = threadIdx.x; u < ns; u += QT)
-        if (box_lb2(c.lut, slo[u], shi[u]) <= sm.T[J0]) slist[atomicAdd(&sm.cpos, 1u)] = (uint32_t)u;
+      for (int64_t i = threadIdx.x; i < nsc; i += QT) {
+        const int64_t u = two ? (int64_t)tlist[i / LEAF_BLOCK] * LEAF_BLOCK + (i % LEAF_BLOCK) : i;
+        if (u < ns && box_lb2(c.lut, slo[u], shi[u]) <= sm.T[J0]) slist[atomicAdd(&sm.cpos, 1u)] = (uint32_t)u;
+      }
       __syncthreads();
       nscan = (int64_t)sm.cpos * LEAF_BLOCK;
     }
@@ -1639,9 +1663,14 @@ __global__ void __launch_bounds__(QT, 5) k_query(QueryIndexView ix, QueryArgs qa
   s.rkey = reinterpret_cast<uint32_t *>(base + qa.off[10]);
   s.cm = base + qa.off[11];
   s.hkey = reinterpret_cast<uint32_t *>(base + qa.off[12]);
+  s.guess = reinterpret_cast<uint32_t *>(base + qa.off[13]);
   for (int i = threadIdx.x; i < 256; i += QT) sm.T[i] = i < NLEV ? qa.T[i] : __int_as_float(0x7f800000);
   if (threadIdx.x == 0) {
-    sm.n_blocks = 0; sm.n_leaves = 0; sm.n_visit = 0; sm.jguess = NLEV - 1;
+    // the bound guess survives launches in the slot (queries of later
+    // batches start from it; any value gives the same results)
+    const uint32_t g = *s.guess;
+    sm.n_blocks = 0; sm.n_leaves = 0; sm.n_visit = 0;
+    sm.jguess = (g >= 1u && g <= (uint32_t)NLEV) ? (int)g - 1 : NLEV - 1;
     // a status already set (a query projection found NaN/Inf) stops the
     // launch before any query: the caller reports it
     sm.stop = *(volatile int *)qa.err;
@@ -1820,6 +1849,7 @@ __global__ void __launch_bounds__(QT, 5) k_query(QueryIndexView ix, QueryArgs qa
     }
     __syncthreads();
   }
+  if (threadIdx.x == 0) *s.guess = (uint32_t)sm.jguess + 1u;
   if (threadIdx.x == 0 && qa.stats) {
     atomicAdd(&qa.stats[1], sm.n_leaves);
     atomicAdd(&qa.stats[2], sm.n_blocks);
