@@ -350,7 +350,8 @@ __global__ void k_rows_to_bf16(const float *s, __nv_bfloat16 *h, float2 *nrm, in
         }
         if (lane == 0 && r0 + u < n) {
           nrm[r0 + u] = make_float2(acc[u], __fsqrt_ru(res[u]));
-          if (res[u] != 0.0f) atomicOr(inexact, 1u);
+          // one atomic per row would serialise on the flag: set it once
+          if (res[u] != 0.0f && *(volatile uint32_t *)inexact == 0u) atomicOr(inexact, 1u);
         }
       }
     }
@@ -370,7 +371,7 @@ __global__ void k_rows_to_bf16(const float *s, __nv_bfloat16 *h, float2 *nrm, in
     }
     if (lane == 0) {
       nrm[r] = make_float2(acc, __fsqrt_ru(res));
-      if (res != 0.0f) atomicOr(inexact, 1u);
+      if (res != 0.0f && *(volatile uint32_t *)inexact == 0u) atomicOr(inexact, 1u);
     }
   }
 }
