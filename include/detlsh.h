@@ -352,6 +352,10 @@ int detlsh_query_async(const detlsh_index *ix, const float *queries, int64_t m,
  *                      level-ordered range-query expansion, 1..8 (default 4)
  *   visit_chunk        listed leaves laid out per chunk of a flattened point
  *                      visit, 64..512, a multiple of 64 (default 512)
+ *   top_hull_min       super-hulls (runs of 32 x 32 leaves) a tree needs before
+ *                      its pruned range query starts from the hulls of runs
+ *                      of 32 super-hulls, >= 1 (default 1024: trees of about
+ *                      a million leaves); not searched by detlsh_autotune
  * detlsh_set_tuning / detlsh_get_tuning set and read an index's knobs (used
  * by detlsh_query, detlsh_query_ex, detlsh_query_candidates and batches
  * enqueued by detlsh_query_async after the change; detlsh_query_noalloc
@@ -374,6 +378,7 @@ typedef struct {
     int32_t query_ctas_per_sm;
     int32_t expand_runs;
     int32_t visit_chunk;
+    int32_t top_hull_min;
 } detlsh_tuning;
 int detlsh_get_tuning(const detlsh_index *ix, detlsh_tuning *t);
 int detlsh_set_tuning(detlsh_index *ix, const detlsh_tuning *t);

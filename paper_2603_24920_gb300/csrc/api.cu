@@ -53,7 +53,7 @@ struct detlsh_index {
   int64_t tblk_off[17] = {0};
   cudaEvent_t ev[8] = {nullptr};
   detlsh_timings timings{};
-  detlsh_tuning tuning{0, 4, 512};  // query kernel knobs (detlsh_set_tuning / detlsh_autotune)
+  detlsh_tuning tuning{0, 4, 512, 1024};  // query kernel knobs (detlsh_set_tuning / detlsh_autotune)
   std::vector<void *> owned;
   // per-index query buffers, reused across calls (guarded by qmu)
   std::mutex qmu;
@@ -901,6 +901,7 @@ int query_impl(detlsh_index *ix, const float *queries, int64_t m, const int32_t 
   qa.ctas_per_sm = ix->tuning.query_ctas_per_sm;
   qa.expand_runs = ix->tuning.expand_runs;
   qa.visit_chunk = ix->tuning.visit_chunk;
+  qa.top_min = ix->tuning.top_hull_min;
   qa.per_tree = qp->per_tree;
   qa.ids = static_cast<int64_t *>(ix->qids.p);
   qa.dists = static_cast<float *>(ix->qdists.p);
@@ -1266,6 +1267,7 @@ int check_tuning(const detlsh_tuning *t) {
   if (t->query_ctas_per_sm < 0 || t->query_ctas_per_sm > 5) return DETLSH_ERR_INVALID_ARG;
   if (t->expand_runs < 1 || t->expand_runs > 8) return DETLSH_ERR_INVALID_ARG;
   if (t->visit_chunk < 64 || t->visit_chunk > 512 || (t->visit_chunk & 63)) return DETLSH_ERR_INVALID_ARG;
+  if (t->top_hull_min < 1) return DETLSH_ERR_INVALID_ARG;
   return DETLSH_OK;
 }
 
@@ -1289,13 +1291,14 @@ std::string tuning_key(const detlsh_index *ix, int32_t k, const detlsh_query_par
 
 // One text line per key: "<key> <ctas_per_sm> <expand_runs> <visit_chunk> <ms>".
 bool tuning_lookup(const char *path, const std::string &key, detlsh_tuning *t) {
+  const int32_t ix_top_min = t->top_hull_min;  // not part of a cache line
   FILE *f = fopen(path, "r");
   if (!f) return false;
   char line[1024];
   bool found = false;
   while (fgets(line, sizeof line, f)) {
     char k[600];
-    detlsh_tuning c{};
+    detlsh_tuning c{0, 4, 512, ix_top_min};
     double ms = 0.0;
     if (sscanf(line, "%599s %d %d %d %lf", k, &c.query_ctas_per_sm, &c.expand_runs, &c.visit_chunk,
                &ms) == 5 &&
@@ -1336,7 +1339,7 @@ int autotune_impl(detlsh_index *ix, const float *queries, int64_t m, int32_t k,
     *ms = b;
     return DETLSH_OK;
   };
-  detlsh_tuning cur{0, 4, 512};
+  detlsh_tuning cur{0, 4, 512, ix->tuning.top_hull_min};
   float cur_ms = 0.0f;
   DL_TRY(measure(cur, &cur_ms));
   const int ctas[] = {3, 4, 0};
@@ -1610,6 +1613,7 @@ int detlsh_query_async(const detlsh_index *cix, const float *queries, int64_t m,
     qa.ctas_per_sm = ix->tuning.query_ctas_per_sm;
     qa.expand_runs = ix->tuning.expand_runs;
     qa.visit_chunk = ix->tuning.visit_chunk;
+    qa.top_min = ix->tuning.top_hull_min;
     qa.per_tree = P.qp.per_tree;
     qa.ids = ids; qa.dists = dists;
     qa.cand_cap = P.cap;

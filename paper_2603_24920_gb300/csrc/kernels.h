@@ -171,6 +171,7 @@ struct QueryArgs {
   int ctas_per_sm = 0;        // persistent CTAs per SM (0: as many as fit)
   int expand_runs = 4;        // leaf runs per warp per chunk of the level-ordered expansion, 1..8
   int visit_chunk = 512;      // listed leaves per chunk of a flattened visit, 64..512
+  int top_min = 1024;         // super-hulls per tree above which pruning starts from top hulls
 };
 size_t query_slot_bytes(const QueryIndexView &ix, int64_t cand_cap, int rerank_cap);
 void query_slot_offsets(const QueryIndexView &ix, int64_t cand_cap, int64_t off[SLOT_ARRAYS + 1]);

@@ -336,12 +336,12 @@ __device__ __forceinline__ void expand_levels(QCtx &c) {
       const int64_t ns = ix.sblk_off[t + 1] - ix.sblk_off[t];
       const uint4 *slo = reinterpret_cast<const uint4 *>(ix.sblk_lo) + ix.sblk_off[t];
       const uint4 *shi = reinterpret_cast<const uint4 *>(ix.sblk_hi) + ix.sblk_off[t];
-      // With more than TOP_MIN super-hulls (about a million leaves per tree)
-      // the top hulls (runs of LEAF_BLOCK super-hulls) are tested first and
-      // only the super-hulls of the listed ones follow; their list goes after
-      // the top list (both fit: nt + ns <= 2 ns <= the tree's leaves).
-      constexpr int64_t TOP_MIN = (int64_t)LEAF_BLOCK * LEAF_BLOCK;
-      const bool two = ns > TOP_MIN;
+      // With more than qa.top_min super-hulls (by default 1,024: about a
+      // million leaves per tree) the top hulls (runs of LEAF_BLOCK
+      // super-hulls) are tested first and only the super-hulls of the listed
+      // ones follow; their list goes after the top list (both fit: nt + ns <=
+      // 2 ns <= the tree's leaves once ns > 1; smaller trees skip this level).
+      const bool two = ns > max((int64_t)c.qa.top_min, (int64_t)1);
       int64_t nsc = ns;
       uint32_t *tlist = c.s.cval;
       if (two) {

@@ -1,5 +1,6 @@
 """Tuning knobs and the autotuner: every tuning gives the same answers (the
-knobs only schedule the work of Alg. 3 and Alg. 5), out-of-range knobs are
+knobs only schedule the work of Alg. 3 and Alg. 5, including the top-hull
+level of the pruned scan that large trees use), out-of-range knobs are
 refused, and the autotuner picks a valid tuning, stores it in the index and
 in its cache file, and takes it from the file the second time."""
 import numpy as np
@@ -21,7 +22,10 @@ def ix():
     D.detlsh_free(h)
 
 
-TUNINGS = [(0, 4, 512), (1, 1, 64), (3, 8, 128), (5, 2, 256), (2, 6, 448)]
+# the last two force the top-hull level of the pruned scan (normally used only
+# for trees of over a million leaves) on this small index
+TUNINGS = [(0, 4, 512, 1024), (1, 1, 64, 1024), (3, 8, 128, 1024), (5, 2, 256, 1024),
+           (2, 6, 448, 1024), (0, 4, 512, 1), (4, 3, 192, 2)]
 
 
 @pytest.mark.parametrize("prec", [D.PREC_FP32, D.PREC_BF16_REFINE])
@@ -43,13 +47,14 @@ def test_every_tuning_gives_the_same_answers(ix, prec):
     D.detlsh_set_tuning(h)
 
 
-@pytest.mark.parametrize("bad", [(-1, 4, 512), (6, 4, 512), (0, 0, 512), (0, 9, 512),
-                                 (0, 4, 32), (0, 4, 1024), (0, 4, 100)])
+@pytest.mark.parametrize("bad", [(-1, 4, 512, 1024), (6, 4, 512, 1024), (0, 0, 512, 1024),
+                                 (0, 9, 512, 1024), (0, 4, 32, 1024), (0, 4, 1024, 1024),
+                                 (0, 4, 100, 1024), (0, 4, 512, 0)])
 def test_bad_tunings_are_refused(ix, bad):
     with pytest.raises(D.DetlshError):
         D.detlsh_set_tuning(ix["h"], *bad)
     t = D.detlsh_get_tuning(ix["h"])
-    assert (t.query_ctas_per_sm, t.expand_runs, t.visit_chunk) == (0, 4, 512)
+    assert (t.query_ctas_per_sm, t.expand_runs, t.visit_chunk, t.top_hull_min) == (0, 4, 512, 1024)
 
 
 def test_autotune_and_its_cache(ix, tmp_path):
@@ -72,3 +77,20 @@ def test_autotune_and_its_cache(ix, tmp_path):
     _, cached3 = D.detlsh_autotune(h, Q, 5, beta=0.003, cache_path=path)
     assert not cached3 and len(path.read_text().splitlines()) == 2
     D.detlsh_set_tuning(h)
+
+
+def test_bound_guess_carried_across_launches(ix):
+    # each CTA starts its first tree from the bound its slot kept from the
+    # previous launch; a guess from another radius grid (c) or another
+    # budget (beta) must not change any answer
+    h, Q = ix["h"], ix["Q"]
+    ref = D.detlsh_query_ex(h, Q, 10, beta=0.003, c=1.5)
+    S_ref = D.detlsh_query_candidates(h, Q[:40], 10, beta=0.003, c=1.5)
+    for beta, c in ((0.2, 3.0), (0.0005, 1.1), (0.003, 16.0), (0.05, 1.5)):
+        D.detlsh_query_ex(h, Q, 10, beta=beta, c=c)  # leaves its bounds in the slots
+        got = D.detlsh_query_ex(h, Q, 10, beta=0.003, c=1.5)
+        assert np.array_equal(got[0], ref[0]) and np.array_equal(got[1].view(np.uint32), ref[1].view(np.uint32))
+        S = D.detlsh_query_candidates(h, Q[:40], 10, beta=0.003, c=1.5)
+        assert np.array_equal(S[1], S_ref[1]) and np.array_equal(S[2], S_ref[2])
+        for i in range(40):
+            assert np.array_equal(np.sort(S[0][i]), np.sort(S_ref[0][i]))
