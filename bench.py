@@ -352,7 +352,7 @@ def run_gb300(args):
         tuning.update(t.as_dict())
         tuning_info = dict(t.as_dict(), from_cache=cached, sample_queries=2048)
     else:
-        tuning_info = dict(D.Tuning(0, 4, 512, 1024).as_dict(), from_cache=False, sample_queries=0)
+        tuning_info = dict(D.Tuning(0, 4, 512, 1024, 0, 0).as_dict(), from_cache=False, sample_queries=0)
 
     for _ in range(args.warmup):
         step()

@@ -356,6 +356,22 @@ int detlsh_query_async(const detlsh_index *ix, const float *queries, int64_t m,
  *                      its pruned range query starts from the hulls of runs
  *                      of 32 super-hulls, >= 1 (default 1024: trees of about
  *                      a million leaves); not searched by detlsh_autotune
+ *   hash_kb            shared memory (KiB) per query CTA for the hash of the
+ *                      levels of listed leaves that the union counts, the
+ *                      cut and the collection read; 0..160, 0 = the 16 KiB
+ *                      projection-LUT region (up to 1,024 leaves; default).
+ *                      When more leaves are listed the levels are read from
+ *                      the CTA's device scratch instead.  A larger region
+ *                      holds 2^b slots of 5 bytes (at most half of them
+ *                      used) and leaves fewer CTAs resident per SM; the
+ *                      launch takes no more CTAs than fit.
+ *   query_scratch_mb   device memory (MiB) for the query CTAs' scratch slots
+ *                      (one per concurrent query; a slot holds per-leaf
+ *                      arrays of every tree, about 17 bytes per leaf);
+ *                      0 = a quarter of the free device memory (default).
+ *                      Fewer slots than CTAs limit the queries in flight;
+ *                      never more than 90% of the free memory is taken.
+ *                      Not searched by detlsh_autotune.
  * detlsh_set_tuning / detlsh_get_tuning set and read an index's knobs (used
  * by detlsh_query, detlsh_query_ex, detlsh_query_candidates and batches
  * enqueued by detlsh_query_async after the change; detlsh_query_noalloc
@@ -367,7 +383,8 @@ int detlsh_query_async(const detlsh_index *ix, const float *queries, int64_t m,
  * smallest query-kernel time (CUDA events on stream, best of two runs after
  * a warm-up run), the others held fixed.  The choice is stored in the index
  * and returned in *out (nullable).  With cache_path non-NULL, a text file
- * of one line per key "<key> <ctas_per_sm> <expand_runs> <visit_chunk> <ms>"
+ * of one line per key "<key> <ctas_per_sm> <expand_runs> <visit_chunk>
+ * <hash_kb> <ms>"
  * is read first: the key names the device and the shape (d, L, K, N_r, n
  * and beta*n + k to the nearest power of two, k, precision, r_min policy);
  * a match is taken without measuring (*from_cache = 1), otherwise the
@@ -379,6 +396,8 @@ typedef struct {
     int32_t expand_runs;
     int32_t visit_chunk;
     int32_t top_hull_min;
+    int32_t hash_kb;
+    int32_t query_scratch_mb;
 } detlsh_tuning;
 int detlsh_get_tuning(const detlsh_index *ix, detlsh_tuning *t);
 int detlsh_set_tuning(detlsh_index *ix, const detlsh_tuning *t);

@@ -53,7 +53,7 @@ struct detlsh_index {
   int64_t tblk_off[17] = {0};
   cudaEvent_t ev[8] = {nullptr};
   detlsh_timings timings{};
-  detlsh_tuning tuning{0, 4, 512, 1024};  // query kernel knobs (detlsh_set_tuning / detlsh_autotune)
+  detlsh_tuning tuning{0, 4, 512, 1024, 0, 0};  // query kernel knobs (detlsh_set_tuning / detlsh_autotune)
   std::vector<void *> owned;
   // per-index query buffers, reused across calls (guarded by qmu)
   std::mutex qmu;
@@ -166,6 +166,23 @@ int grow(detlsh_index::QBuf &b, size_t bytes, cudaStream_t st, bool *fresh = nul
   DL_TRY(pool_alloc(&b.p, bytes, st));
   b.bytes = bytes;
   if (fresh) *fresh = true;
+  return DETLSH_OK;
+}
+
+// Scratch slots for the query kernel: `want`, or as many as fit in the budget
+// (tuning.query_scratch_mb MiB; 0 = a quarter of the free device memory), both
+// counting the scratch `held` that the index already owns and would give up;
+// never more than 90% of that free memory, and at least one slot.
+int slots_within_budget(const detlsh_index *ix, int want, size_t slot_bytes, size_t held,
+                        int *out) {
+  size_t freeb = 0, totb = 0;
+  DL_CUDA(cudaMemGetInfo(&freeb, &totb));
+  const size_t avail = freeb + held;
+  size_t budget = ix->tuning.query_scratch_mb > 0 ? (size_t)ix->tuning.query_scratch_mb << 20
+                                                  : freeb / 4 + held;
+  budget = std::min(budget, avail / 10 * 9);
+  const int64_t fit = slot_bytes ? (int64_t)(budget / slot_bytes) : (int64_t)want;
+  *out = (int)std::max<int64_t>(1, std::min<int64_t>(want, fit));
   return DETLSH_OK;
 }
 
@@ -902,6 +919,7 @@ int query_impl(detlsh_index *ix, const float *queries, int64_t m, const int32_t 
   qa.expand_runs = ix->tuning.expand_runs;
   qa.visit_chunk = ix->tuning.visit_chunk;
   qa.top_min = ix->tuning.top_hull_min;
+  qa.hash_kb = ix->tuning.hash_kb;
   qa.per_tree = qp->per_tree;
   qa.ids = static_cast<int64_t *>(ix->qids.p);
   qa.dists = static_cast<float *>(ix->qdists.p);
@@ -918,10 +936,8 @@ int query_impl(detlsh_index *ix, const float *queries, int64_t m, const int32_t 
   qa.slot_bytes = qa.off[SLOT_ARRAYS];  // total bytes of one slot
   int slots = query_slots(v);
   slots = (int)std::min<int64_t>(slots, std::max<int64_t>(m, 1));
-  // keep the scratch within a quarter of the free device memory
-  size_t freeb = 0, totb = 0;
-  DL_CUDA(cudaMemGetInfo(&freeb, &totb));
-  while (slots > 1 && (size_t)slots * qa.slot_bytes > freeb / 4 + ix->qscratch.bytes) slots /= 2;
+  // keep the scratch within its budget (a quarter of the free memory by default)
+  DL_TRY(slots_within_budget(ix, slots, (size_t)qa.slot_bytes, ix->qscratch.bytes, &slots));
   const size_t need_bytes = kScratchHeader + (size_t)slots * qa.slot_bytes;
   if (!ix->qscratch.p && ix->device >= 0 && ix->device < kPoolDevices) {
     std::lock_guard<std::mutex> g(g_scratch_mu);
@@ -1268,6 +1284,8 @@ int check_tuning(const detlsh_tuning *t) {
   if (t->expand_runs < 1 || t->expand_runs > 8) return DETLSH_ERR_INVALID_ARG;
   if (t->visit_chunk < 64 || t->visit_chunk > 512 || (t->visit_chunk & 63)) return DETLSH_ERR_INVALID_ARG;
   if (t->top_hull_min < 1) return DETLSH_ERR_INVALID_ARG;
+  if (t->hash_kb < 0 || t->hash_kb > 160) return DETLSH_ERR_INVALID_ARG;
+  if (t->query_scratch_mb < 0) return DETLSH_ERR_INVALID_ARG;
   return DETLSH_OK;
 }
 
@@ -1283,25 +1301,27 @@ std::string tuning_key(const detlsh_index *ix, int32_t k, const detlsh_query_par
     if (ch == ' ' || ch == '\t' || ch == '|') ch = '_';
   const double tau = std::ceil(qp->beta * (double)ix->n) + k;
   char buf[512];
-  snprintf(buf, sizeof buf, "%s|d%d|L%d|K%d|Nr%d|n2^%d|tau2^%d|k%d|p%d|r%d", name.c_str(), ix->d, ix->L,
+  snprintf(buf, sizeof buf, "%s|d%d|L%d|K%d|Nr%d|n2^%d|tau2^%d|k%d|p%d|r%d|v2", name.c_str(), ix->d, ix->L,
            ix->K, ix->N_r, (int)std::lround(std::log2((double)ix->n)),
            (int)std::lround(std::log2(std::max(tau, 1.0))), k, qp->precision, qp->rmin_policy);
   return buf;
 }
 
-// One text line per key: "<key> <ctas_per_sm> <expand_runs> <visit_chunk> <ms>".
+// One text line per key: "<key> <ctas_per_sm> <expand_runs> <visit_chunk> <hash_kb> <ms>"
+// (the key ends in "|v2", so lines of the older four-number format never match).
 bool tuning_lookup(const char *path, const std::string &key, detlsh_tuning *t) {
   const int32_t ix_top_min = t->top_hull_min;  // not part of a cache line
+  const int32_t ix_scratch = t->query_scratch_mb;  // nor is this
   FILE *f = fopen(path, "r");
   if (!f) return false;
   char line[1024];
   bool found = false;
   while (fgets(line, sizeof line, f)) {
     char k[600];
-    detlsh_tuning c{0, 4, 512, ix_top_min};
+    detlsh_tuning c{0, 4, 512, ix_top_min, 0, ix_scratch};
     double ms = 0.0;
-    if (sscanf(line, "%599s %d %d %d %lf", k, &c.query_ctas_per_sm, &c.expand_runs, &c.visit_chunk,
-               &ms) == 5 &&
+    if (sscanf(line, "%599s %d %d %d %d %lf", k, &c.query_ctas_per_sm, &c.expand_runs,
+               &c.visit_chunk, &c.hash_kb, &ms) == 6 &&
         key == k && check_tuning(&c) == DETLSH_OK) {
       *t = c;  // the last matching line wins
       found = true;
@@ -1339,18 +1359,22 @@ int autotune_impl(detlsh_index *ix, const float *queries, int64_t m, int32_t k,
     *ms = b;
     return DETLSH_OK;
   };
-  detlsh_tuning cur{0, 4, 512, ix->tuning.top_hull_min};
+  detlsh_tuning cur{0, 4, 512, ix->tuning.top_hull_min, 0, ix->tuning.query_scratch_mb};
   float cur_ms = 0.0f;
   DL_TRY(measure(cur, &cur_ms));
   const int ctas[] = {3, 4, 0};
   const int runs[] = {2, 3, 4, 6, 8};
   const int chunks[] = {128, 256, 512};
-  for (int knob = 0; knob < 3; ++knob) {
-    const int *vals = knob == 0 ? ctas : knob == 1 ? runs : chunks;
-    const int nv = knob == 0 ? 3 : knob == 1 ? 5 : 3;
+  const int hashes[] = {0, 20, 40, 80};  // hash regions for 5 / 4 / 3 / 2 CTAs per SM
+  for (int knob = 0; knob < 4; ++knob) {
+    const int *vals = knob == 0 ? ctas : knob == 1 ? runs : knob == 2 ? chunks : hashes;
+    const int nv = knob == 0 ? 3 : knob == 1 ? 5 : knob == 2 ? 3 : 4;
     for (int i = 0; i < nv; ++i) {
       detlsh_tuning t = cur;
-      int &slot = knob == 0 ? t.query_ctas_per_sm : knob == 1 ? t.expand_runs : t.visit_chunk;
+      int &slot = knob == 0   ? t.query_ctas_per_sm
+                  : knob == 1 ? t.expand_runs
+                  : knob == 2 ? t.visit_chunk
+                              : t.hash_kb;
       if (slot == vals[i]) continue;
       slot = vals[i];
       float ms = 0.0f;
@@ -1363,8 +1387,8 @@ int autotune_impl(detlsh_index *ix, const float *queries, int64_t m, int32_t k,
   if (cache_path) {
     FILE *f = fopen(cache_path, "a");
     if (!f) return DETLSH_ERR_IO;
-    fprintf(f, "%s %d %d %d %.4f\n", key.c_str(), cur.query_ctas_per_sm, cur.expand_runs,
-            cur.visit_chunk, cur_ms);
+    fprintf(f, "%s %d %d %d %d %.4f\n", key.c_str(), cur.query_ctas_per_sm, cur.expand_runs,
+            cur.visit_chunk, cur.hash_kb, cur_ms);
     if (fclose(f) != 0) return DETLSH_ERR_IO;
   }
   return DETLSH_OK;
@@ -1552,9 +1576,7 @@ int detlsh_query_reserve(detlsh_index *ix, int64_t m_max, int32_t k_max,
   QueryIndexView vw = view_of(ix);
   query_slot_offsets(vw, P.cap, P.off);
   int slots = (int)std::min<int64_t>(query_slots(vw), m_max);
-  size_t freeb = 0, totb = 0;
-  DL_CUDA(cudaMemGetInfo(&freeb, &totb));
-  while (slots > 1 && (size_t)slots * P.off[SLOT_ARRAYS] > freeb / 4 + ix->ascratch.bytes) slots /= 2;
+  DL_TRY(slots_within_budget(ix, slots, (size_t)P.off[SLOT_ARRAYS], ix->ascratch.bytes, &slots));
   bool fresh = false;
   DL_TRY(grow(ix->ascratch, kScratchHeader + (size_t)slots * P.off[SLOT_ARRAYS], st, &fresh));
   if (fresh) DL_CUDA(cudaMemsetAsync(ix->ascratch.p, 0, ix->ascratch.bytes, st));
@@ -1614,6 +1636,7 @@ int detlsh_query_async(const detlsh_index *cix, const float *queries, int64_t m,
     qa.expand_runs = ix->tuning.expand_runs;
     qa.visit_chunk = ix->tuning.visit_chunk;
     qa.top_min = ix->tuning.top_hull_min;
+    qa.hash_kb = ix->tuning.hash_kb;
     qa.per_tree = P.qp.per_tree;
     qa.ids = ids; qa.dists = dists;
     qa.cand_cap = P.cap;

@@ -172,6 +172,7 @@ struct QueryArgs {
   int expand_runs = 4;        // leaf runs per warp per chunk of the level-ordered expansion, 1..8
   int visit_chunk = 512;      // listed leaves per chunk of a flattened visit, 64..512
   int top_min = 1024;         // super-hulls per tree above which pruning starts from top hulls
+  int hash_kb = 0;  // shared memory (KiB) for the leaf-level hash; 0 = the LUT region
 };
 size_t query_slot_bytes(const QueryIndexView &ix, int64_t cand_cap, int rerank_cap);
 void query_slot_offsets(const QueryIndexView &ix, int64_t cand_cap, int64_t off[SLOT_ARRAYS + 1]);

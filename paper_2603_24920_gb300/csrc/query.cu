@@ -522,13 +522,21 @@ __device__ __forceinline__ void expand_levels(QCtx &c) {
 // ---- step 1b: shared-memory table of the levels at or below the bound ----
 // Reuses the lookup table's space (no longer needed): keys (global leaf
 // index + 1, 0 = empty) then one level byte per slot, linear probing.
+// Floats of the shared region that holds the projection LUT during the
+// expansion and the leaf-level hash after it: the LUT's size, or hash_kb KiB
+// when that is larger (a larger hash keeps the levels of more listed leaves
+// on chip, at the cost of fewer resident CTAs per SM).
+__host__ __device__ __forceinline__ int lut_region_floats(int hash_kb) {
+  return LUT_ROWS * LUT_STRIDE > hash_kb * 256 ? LUT_ROWS * LUT_STRIDE : hash_kb * 256;
+}
+
 __device__ __forceinline__ void build_level_hash(QCtx &c) {
   const QueryIndexView &ix = c.ix;
   QShared &sm = c.sm;
   const uint32_t jhi = (uint32_t)sm.jhi;
-  const uint32_t bytes = (uint32_t)(LUT_ROWS * LUT_STRIDE * sizeof(float));
+  const uint32_t bytes = (uint32_t)(lut_region_floats(c.qa.hash_kb) * sizeof(float));
   uint32_t bits = 0;
-  while ((1u << (bits + 1)) * 5u <= bytes && bits + 1 <= 12) ++bits;
+  while ((1u << (bits + 1)) * 5u <= bytes && bits + 1 <= 16) ++bits;
   if (threadIdx.x == 0) { sm.hash_count = 0; sm.hash_bits = bits; }
   __syncthreads();
   uint32_t cnt = 0;
@@ -1645,7 +1653,7 @@ __global__ void __launch_bounds__(QT, 5) k_query(QueryIndexView ix, QueryArgs qa
   extern __shared__ __align__(16) uint8_t dsm[];
   QShared &sm = *reinterpret_cast<QShared *>(dsm);
   float *lut = reinterpret_cast<float *>(dsm + align_up(sizeof(QShared), 16));
-  uint32_t *hist = reinterpret_cast<uint32_t *>(lut + LUT_ROWS * LUT_STRIDE);
+  uint32_t *hist = reinterpret_cast<uint32_t *>(lut + lut_region_floats(qa.hash_kb));
   int32_t *D = reinterpret_cast<int32_t *>(hist + 256 * ix.L);
 
   uint8_t *base = qa.scratch + (int64_t)blockIdx.x * qa.slot_bytes;
@@ -1857,8 +1865,8 @@ __global__ void __launch_bounds__(QT, 5) k_query(QueryIndexView ix, QueryArgs qa
   }
 }
 
-static size_t query_smem(const QueryIndexView &ix) {
-  return (size_t)align_up(sizeof(QShared), 16) + sizeof(float) * LUT_ROWS * LUT_STRIDE +
+static size_t query_smem(const QueryIndexView &ix, int hash_kb) {
+  return (size_t)align_up(sizeof(QShared), 16) + sizeof(float) * lut_region_floats(hash_kb) +
          sizeof(uint32_t) * 256 * ix.L * 2;
 }
 
@@ -1866,7 +1874,7 @@ int query_slots(const QueryIndexView &ix) {
   int dev = 0, sms = 0, per = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const size_t smem = query_smem(ix);
+  const size_t smem = query_smem(ix, 0);
   cudaFuncSetAttribute(k_query<DETLSH_RMIN_MAGIC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)smem);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_query<DETLSH_RMIN_MAGIC>, QT, smem);
@@ -1876,7 +1884,7 @@ int query_slots(const QueryIndexView &ix) {
 
 int run_queries(const QueryIndexView &ix, const QueryArgs &qa, cudaStream_t st) {
   if (qa.m <= 0) return DETLSH_OK;
-  const size_t smem = query_smem(ix);
+  const size_t smem = query_smem(ix, qa.hash_kb);
   auto kern = qa.policy == DETLSH_RMIN_FIXED        ? k_query<DETLSH_RMIN_FIXED>
               : qa.policy == DETLSH_RMIN_CONTINUOUS ? k_query<DETLSH_RMIN_CONTINUOUS>
                                                     : k_query<DETLSH_RMIN_MAGIC>;
@@ -1888,6 +1896,14 @@ int run_queries(const QueryIndexView &ix, const QueryArgs &qa, cudaStream_t st) 
     DL_CUDA(cudaGetDevice(&dev));
     DL_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     grid = std::max(1, std::min(grid, sms * qa.ctas_per_sm));
+  }
+  if (qa.hash_kb > 0) {  // a larger shared region: no more CTAs than fit at once
+    int dev = 0, sms = 0, per = 0;
+    DL_CUDA(cudaGetDevice(&dev));
+    DL_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    DL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, QT, smem));
+    if (per < 1) return DETLSH_ERR_INVALID_ARG;
+    grid = std::max(1, std::min(grid, sms * per));
   }
   kern<<<grid, QT, smem, st>>>(ix, qa);
   dl_count_launch();

@@ -52,7 +52,8 @@ class Info(C.Structure):
 
 class Tuning(C.Structure):
     _fields_ = [("query_ctas_per_sm", C.c_int32), ("expand_runs", C.c_int32),
-                ("visit_chunk", C.c_int32), ("top_hull_min", C.c_int32)]
+                ("visit_chunk", C.c_int32), ("top_hull_min", C.c_int32),
+                ("hash_kb", C.c_int32), ("query_scratch_mb", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -204,8 +205,9 @@ def detlsh_get_tuning(h):
     return t
 
 
-def detlsh_set_tuning(h, query_ctas_per_sm=0, expand_runs=4, visit_chunk=512, top_hull_min=1024):
-    t = Tuning(query_ctas_per_sm, expand_runs, visit_chunk, top_hull_min)
+def detlsh_set_tuning(h, query_ctas_per_sm=0, expand_runs=4, visit_chunk=512, top_hull_min=1024,
+                      hash_kb=0, query_scratch_mb=0):
+    t = Tuning(query_ctas_per_sm, expand_runs, visit_chunk, top_hull_min, hash_kb, query_scratch_mb)
     _check(lib().detlsh_set_tuning(h, C.byref(t)), "detlsh_set_tuning")
 
 

@@ -77,7 +77,7 @@ def test_query_and_accessors_reject_null_index(lib):
     assert lib.detlsh_get_info(None, None) == -1
     assert lib.detlsh_get_tree(None, 0, None, None, None, None, None, None) == -1
     assert lib.detlsh_free(None) == 0
-    t = D.Tuning(0, 4, 512, 1024)
+    t = D.Tuning(0, 4, 512, 1024, 0, 0)
     assert lib.detlsh_get_tuning(None, C.byref(t)) == -1
     assert lib.detlsh_set_tuning(None, C.byref(t)) == -1
     assert lib.detlsh_autotune(None, D._ptr(Q), 2, 3, None, None, None, None, None) == -1

@@ -22,10 +22,14 @@ def ix():
     D.detlsh_free(h)
 
 
-# the last two force the top-hull level of the pruned scan (normally used only
-# for trees of over a million leaves) on this small index
-TUNINGS = [(0, 4, 512, 1024), (1, 1, 64, 1024), (3, 8, 128, 1024), (5, 2, 256, 1024),
-           (2, 6, 448, 1024), (0, 4, 512, 1), (4, 3, 192, 2)]
+# (0, 4, 512, 1) and (4, 3, 192, 2) force the top-hull level of the pruned
+# scan (normally used only for trees of over a million leaves) on this small
+# index; hash_kb > 0 gives the leaf-level hash a larger shared region (and
+# fewer resident CTAs), so more queries keep their levels on chip
+TUNINGS = [(0, 4, 512, 1024, 0), (1, 1, 64, 1024, 0), (3, 8, 128, 1024, 0), (5, 2, 256, 1024, 0),
+           (2, 6, 448, 1024, 0), (0, 4, 512, 1, 0), (4, 3, 192, 2, 0), (0, 4, 512, 1024, 40),
+           (0, 2, 256, 1024, 160), (5, 4, 512, 2, 80), (0, 4, 512, 1024, 1), (0, 4, 512, 1024, 0, 1),
+           (0, 4, 512, 1024, 40, 3)]
 
 
 @pytest.mark.parametrize("prec", [D.PREC_FP32, D.PREC_BF16_REFINE])
@@ -49,12 +53,14 @@ def test_every_tuning_gives_the_same_answers(ix, prec):
 
 @pytest.mark.parametrize("bad", [(-1, 4, 512, 1024), (6, 4, 512, 1024), (0, 0, 512, 1024),
                                  (0, 9, 512, 1024), (0, 4, 32, 1024), (0, 4, 1024, 1024),
-                                 (0, 4, 100, 1024), (0, 4, 512, 0)])
+                                 (0, 4, 100, 1024), (0, 4, 512, 0), (0, 4, 512, 1024, -1),
+                                 (0, 4, 512, 1024, 161), (0, 4, 512, 1024, 0, -1)])
 def test_bad_tunings_are_refused(ix, bad):
     with pytest.raises(D.DetlshError):
         D.detlsh_set_tuning(ix["h"], *bad)
     t = D.detlsh_get_tuning(ix["h"])
-    assert (t.query_ctas_per_sm, t.expand_runs, t.visit_chunk, t.top_hull_min) == (0, 4, 512, 1024)
+    assert (t.query_ctas_per_sm, t.expand_runs, t.visit_chunk, t.top_hull_min, t.hash_kb,
+            t.query_scratch_mb) == (0, 4, 512, 1024, 0, 0)
 
 
 def test_autotune_and_its_cache(ix, tmp_path):
@@ -65,9 +71,11 @@ def test_autotune_and_its_cache(ix, tmp_path):
     assert not cached
     assert 0 <= t.query_ctas_per_sm <= 5 and 1 <= t.expand_runs <= 8
     assert t.visit_chunk in (128, 256, 512)
+    assert t.hash_kb in (0, 20, 40, 80)
     assert D.detlsh_get_tuning(h).as_dict() == t.as_dict()
     lines = path.read_text().splitlines()
     assert len(lines) == 1 and "|d128|L4|K16|Nr256|" in lines[0]
+    assert len(lines[0].split()) == 6 and lines[0].split()[0].endswith("|v2")
     D.detlsh_set_tuning(h)
     t2, cached2 = D.detlsh_autotune(h, Q, 20, beta=0.003, precision=D.PREC_BF16_REFINE,
                                     cache_path=path)
