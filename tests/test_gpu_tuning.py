@@ -102,3 +102,77 @@ def test_bound_guess_carried_across_launches(ix):
         assert np.array_equal(S[1], S_ref[1]) and np.array_equal(S[2], S_ref[2])
         for i in range(40):
             assert np.array_equal(np.sort(S[0][i]), np.sort(S_ref[0][i]))
+
+
+def _kept_leaves_bounds(h, Q, js, tau, c=1.5):
+    """Per query, bounds on the number of leaves whose levels the query keeps
+    (the leaves at or below its final expansion bound J, with j* <= J <= the
+    first level at which one tree alone holds tau points), from the exported
+    boxes: each leaf's lower bound (Sec. IV-C: the gap to the box per
+    projected dimension, squared and summed), here in float64 with a small
+    margin either way.  Returns (lower, upper)."""
+    info = D.detlsh_get_info(h)
+    B = D.detlsh_get_breakpoints(h).astype(np.float64)
+    P = D.detlsh_project(h, np.ascontiguousarray(Q)).astype(np.float64)
+    T = D.detlsh_get_level_table(h, c).astype(np.float64)  # j = -127..127 at j + 127
+    K = info.K
+    lb2, size = [], []
+    for t in range(info.L):
+        tr = D.detlsh_get_tree(h, t)
+        cols = np.arange(t * K, (t + 1) * K)[None, :]
+        blo = B[cols, tr["lo"].astype(np.int64)]
+        bhi = B[cols, tr["hi"].astype(np.int64) + 1]
+        per = []
+        for i in range(len(Q)):
+            q = P[i, t * K:(t + 1) * K]
+            gap = np.maximum(0.0, np.maximum(blo - q, q - bhi))
+            per.append((gap * gap).sum(1))
+        lb2.append(np.array(per))
+        size.append(np.diff(tr["begin"]))
+    lower = np.zeros(len(Q), np.int64)
+    upper = np.zeros(len(Q), np.int64)
+    for i in range(len(Q)):
+        lower[i] = sum(np.count_nonzero(lb2[t][i] <= T[js[i] + 127] * (1.0 - 1e-6))
+                       for t in range(info.L))
+        jt = []
+        for t in range(info.L):
+            o = np.argsort(lb2[t][i], kind="stable")
+            cum = np.cumsum(size[t][o])
+            p = int(np.searchsorted(cum, tau))  # first leaf prefix holding tau points
+            jt.append(int(np.searchsorted(T, lb2[t][i][o[p]] * (1.0 + 1e-6))))
+        upper[i] = sum(np.count_nonzero(lb2[t][i] <= T[min(jt)] * (1.0 + 1e-6))
+                       for t in range(info.L))
+    return lower, upper
+
+
+@pytest.mark.parametrize("prec", [D.PREC_FP32, D.PREC_BF16_REFINE])
+def test_level_hash_and_slot_levels_agree(ix, prec):
+    # Queries that keep the levels of more leaves (at or below their final
+    # expansion bound, bounded from both sides below from the exported
+    # boxes) than the default shared hash holds (1,024 at load 1/2) read them
+    # in the union counts, the cut and the collection from the slot's
+    # epoch-tagged array in device memory; a 160 KiB region (16,384) keeps
+    # them on chip.  The answers and S must not depend on where the levels
+    # come from.
+    h, Q = ix["h"], ix["Q"]
+    beta, k = 0.05, 20
+    S0 = D.detlsh_query_candidates(h, Q[:64], k, beta=beta)
+    tau = int(np.ceil(beta * D.detlsh_get_info(h).n)) + k
+    lower, upper = _kept_leaves_bounds(h, Q[:64], S0[1], tau)
+    pick = np.flatnonzero((lower > 1024) & (upper <= 16384))
+    assert len(pick) >= 8, (lower, upper)
+    Qs = np.ascontiguousarray(Q[:64][pick])
+    want = None
+    for hk in (0, 160, 20):
+        D.detlsh_set_tuning(h, hash_kb=hk)
+        got = D.detlsh_query_ex(h, Qs, k, beta=beta, precision=prec)
+        S = D.detlsh_query_candidates(h, Qs, k, beta=beta)
+        if want is None:
+            want = (got, S)
+            continue
+        assert np.array_equal(got[0], want[0][0]), hk
+        assert np.array_equal(got[1].view(np.uint32), want[0][1].view(np.uint32)), hk
+        for i in range(len(pick)):
+            assert np.array_equal(np.sort(S[0][i]), np.sort(want[1][0][i])), (hk, i)
+        assert np.array_equal(S[1], want[1][1]) and np.array_equal(S[2], want[1][2])
+    D.detlsh_set_tuning(h)
