@@ -369,9 +369,14 @@ int detlsh_query_async(const detlsh_index *ix, const float *queries, int64_t m,
  *                      (one per concurrent query; a slot holds per-leaf
  *                      arrays of every tree, about 17 bytes per leaf);
  *                      0 = a quarter of the free device memory (default).
- *                      Fewer slots than CTAs limit the queries in flight;
- *                      never more than 90% of the free memory is taken.
- *                      Not searched by detlsh_autotune.
+ *                      A set budget caps the slots in use.  Fewer slots
+ *                      than CTAs limit the queries in flight.  The scratch
+ *                      is kept between calls and never shrinks; it is
+ *                      replaced by a larger one only for over a quarter
+ *                      more slots, within 90% of the free memory plus what
+ *                      it holds, and if that allocation fails the call
+ *                      runs with the slots held before (or half of them)
+ *                      instead of failing.  Not searched by detlsh_autotune.
  * detlsh_set_tuning / detlsh_get_tuning set and read an index's knobs (used
  * by detlsh_query, detlsh_query_ex, detlsh_query_candidates and batches
  * enqueued by detlsh_query_async after the change; detlsh_query_noalloc

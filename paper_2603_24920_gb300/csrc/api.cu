@@ -169,21 +169,55 @@ int grow(detlsh_index::QBuf &b, size_t bytes, cudaStream_t st, bool *fresh = nul
   return DETLSH_OK;
 }
 
-// Scratch slots for the query kernel: `want`, or as many as fit in the budget
-// (tuning.query_scratch_mb MiB; 0 = a quarter of the free device memory), both
-// counting the scratch `held` that the index already owns and would give up;
-// never more than 90% of that free memory, and at least one slot.
+// Scratch slots for the query kernel.  `want` is capped by a set budget
+// (tuning.query_scratch_mb MiB) and served from the scratch already `held`
+// when it fits there (no driver call).  Otherwise the budget is the set one,
+// or by default a quarter of the free device memory plus the held scratch,
+// never above 90% of the two together; a larger scratch replaces the held
+// block only for a clear gain (over a quarter more slots), since the new
+// block is a separate allocation.  At least one slot.
 int slots_within_budget(const detlsh_index *ix, int want, size_t slot_bytes, size_t held,
                         int *out) {
+  const int64_t mb = ix->tuning.query_scratch_mb;
+  const int64_t have =
+      (slot_bytes && held > kScratchHeader) ? (int64_t)((held - kScratchHeader) / slot_bytes) : 0;
+  int64_t cap = want;
+  if (mb > 0 && slot_bytes) cap = std::min<int64_t>(cap, (int64_t)(((size_t)mb << 20) / slot_bytes));
+  cap = std::max<int64_t>(cap, 1);
+  if (cap <= have) {
+    *out = (int)cap;
+    return DETLSH_OK;
+  }
   size_t freeb = 0, totb = 0;
   DL_CUDA(cudaMemGetInfo(&freeb, &totb));
-  const size_t avail = freeb + held;
-  size_t budget = ix->tuning.query_scratch_mb > 0 ? (size_t)ix->tuning.query_scratch_mb << 20
-                                                  : freeb / 4 + held;
-  budget = std::min(budget, avail / 10 * 9);
-  const int64_t fit = slot_bytes ? (int64_t)(budget / slot_bytes) : (int64_t)want;
-  *out = (int)std::max<int64_t>(1, std::min<int64_t>(want, fit));
+  size_t budget = mb > 0 ? (size_t)mb << 20 : freeb / 4 + held;
+  budget = std::min(budget, (freeb + held) / 10 * 9);
+  int64_t s = slot_bytes ? std::min<int64_t>(cap, (int64_t)(budget / slot_bytes)) : cap;
+  if (have > 0 && s <= have + have / 4) s = std::min<int64_t>(cap, have);
+  *out = (int)std::max<int64_t>(1, s);
   return DETLSH_OK;
+}
+
+// Grows a query scratch to hold *slots slots.  The larger block is a new
+// allocation that the pool may be unable to assemble from the block it
+// replaces: when it fails, the scratch falls back to the slots it held
+// before, then to halves of that (the failed allocation's error is cleared),
+// so the call runs with fewer queries in flight instead of failing.
+int grow_scratch(detlsh_index::QBuf &b, int *slots, size_t slot_bytes, cudaStream_t st,
+                 bool *fresh) {
+  int64_t held = (slot_bytes && b.bytes > kScratchHeader) ? (int64_t)((b.bytes - kScratchHeader) / slot_bytes) : 0;
+  int64_t s = *slots;
+  while (true) {
+    const int rc = grow(b, kScratchHeader + (size_t)s * slot_bytes, st, fresh);
+    if (rc == DETLSH_OK) {
+      *slots = (int)s;
+      return DETLSH_OK;
+    }
+    if (rc != DETLSH_ERR_OOM || s <= 1) return rc;
+    cudaGetLastError();
+    s = (held > 0 && held < s) ? held : s / 2;
+    held = 0;
+  }
 }
 
 bool is_device_ptr(const void *p) {
@@ -949,7 +983,7 @@ int query_impl(detlsh_index *ix, const float *queries, int64_t m, const int32_t 
     }
   }
   bool fresh = false;
-  DL_TRY(grow(ix->qscratch, need_bytes, st, &fresh));
+  DL_TRY(grow_scratch(ix->qscratch, &slots, (size_t)qa.slot_bytes, st, &fresh));
   // new scratch: zero tags and epoch counter (epochs then start at 1)
   if (fresh) DL_CUDA(cudaMemsetAsync(ix->qscratch.p, 0, ix->qscratch.bytes, st));
   qa.epoch_counter = static_cast<unsigned long long *>(ix->qscratch.p);
@@ -1578,7 +1612,7 @@ int detlsh_query_reserve(detlsh_index *ix, int64_t m_max, int32_t k_max,
   int slots = (int)std::min<int64_t>(query_slots(vw), m_max);
   DL_TRY(slots_within_budget(ix, slots, (size_t)P.off[SLOT_ARRAYS], ix->ascratch.bytes, &slots));
   bool fresh = false;
-  DL_TRY(grow(ix->ascratch, kScratchHeader + (size_t)slots * P.off[SLOT_ARRAYS], st, &fresh));
+  DL_TRY(grow_scratch(ix->ascratch, &slots, (size_t)P.off[SLOT_ARRAYS], st, &fresh));
   if (fresh) DL_CUDA(cudaMemsetAsync(ix->ascratch.p, 0, ix->ascratch.bytes, st));
   DL_CUDA(cudaStreamSynchronize(st));
   P.qp = *qp;
