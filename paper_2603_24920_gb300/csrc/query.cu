@@ -309,7 +309,7 @@ __device__ __forceinline__ void expand_levels(QCtx &c) {
   // well.  If the tree does not reach beta*n + k within the guess, it is
   // expanded again without one; either way every leaf at or below its
   // crossing level is listed and counted, so the results do not depend on it.
-  if (threadIdx.x == 0) sm.jhi = min(NLEV - 1, sm.jguess + 3);
+  if (threadIdx.x == 0) sm.jhi = min(NLEV - 1, sm.jguess + 2);
   __syncthreads();
   for (int t = 0; t < ix.L; ++t) {
     build_lut(c.lut, ix.B, qp + t * K, t, K, NR1);
